@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Time-to-solution per time step of MLGMRES on the 256^2 moving-Gaussian
+Poisson series (GMRES(30), relative residual 1e-10): the learned initial guess
+with FP32-inner / FP64-refined GMRES, next to plain FP64 GMRES from x0 = 0 and
+from x0 = x_{t-1}, all on the same GPU, plus the FP64 CPU oracle on the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  A "step" is one time step of the online loop:
+the network's guess, the solve, Algorithm 1's gate and replay store, and every
+10th step a training phase (its time lands in the following solve, which waits
+for it).  Before the W warm-up steps the loop runs its tau0 = 50 online
+warm-up steps (data collection and the first training, Sec. 2.3) untimed.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 256
+M = 30
+RTOL = 1e-10
+T_SERIES = 500
+SEED = 2001
+TAU0 = 50
+TRAIN_EVERY = 10
+METRIC = "time-to-solution per time step (ms) and GMRES iters, learned vs plain GMRES, rel res 1e-10"
+WORKLOAD = ("2D Poisson -Lap u = f, 256x256 interior (N=65,536), zero Dirichlet, 5-point; "
+            "3 moving signed Gaussians (sigma 0.1), 500-step series seed 2001; GMRES(30) "
+            "rel tol 1e-10 (true FP64 residual)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-GMRES arms")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- clocks --
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers --
+def algorithmic_bytes(res, N, m, elem):
+    """Bytes one solve must move ('Roofline accounting'):
+    per Arnoldi step j: elem*N*(3j + 9); per cycle with k steps: elem*N*(k + 1)
+    (x += V y reads k basis vectors, the restart writes the new start vector)
+    + 32 N (x read/write, b read, x read by the FP64 residual)."""
+    iters, cycles = int(res["iters"]), int(res["cycles"])
+    total = 0.0
+    left = iters
+    ncyc = max(cycles, 1 if iters else 0)
+    for c in range(ncyc):
+        k = min(m, left) if c < ncyc - 1 else left
+        left -= k
+        total += elem * N * (3.0 * k * (k - 1) / 2.0 + 9.0 * k)
+        total += elem * N * (k + 1) + 32.0 * N
+    total += 32.0 * N  # final residual check
+    return total
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(b, n):
+    """The FP64 oracle (plain GMRES(30), x0 = 0, 1 thread) on one time step."""
+    from oracle import native
+    native.lib()
+    t0 = time.perf_counter()
+    _, st, _ = native.gmres(2, n, b, m=M, rtol=RTOL, nthreads=1)
+    dt = time.perf_counter() - t0
+    return {"value": dt * 1e3, "unit": "ms per time step", "cores": 1, "kind": "oracle",
+            "sample": "one full time step (t=%d) of the 256^2 series: FP64 GMRES(30), x0=0, "
+                      "rtol 1e-10, %d iterations, single thread" % (0, st["iters"]),
+            "iters": st["iters"]}
+
+
+# ------------------------------------------------------------ reference --
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    from oracle import native
+    from synthetic import MovingGaussians2D
+    native.lib()
+    gen = MovingGaussians2D(N_SIDE, SEED, T_SERIES)
+    # one full solve gives the oracle's iterations per time step ...
+    b0 = gen.rhs(TAU0)
+    t0 = time.perf_counter()
+    _, st, _ = native.gmres(2, N_SIDE, b0, m=M, rtol=RTOL, nthreads=1)
+    full_s = time.perf_counter() - t0
+    full_iters = st["iters"]
+    # ... and every step is a bounded sample: 600 iterations (20 cycles of 30)
+    cap = 600
+    for t in range(args.warmup):
+        native.gmres(2, N_SIDE, gen.rhs(TAU0 + 1 + t), m=M, rtol=RTOL, max_iters=cap)
+    times = []
+    for t in range(args.steps):
+        b = gen.rhs(TAU0 + 1 + args.warmup + t)
+        t0 = time.perf_counter()
+        _, s2, _ = native.gmres(2, N_SIDE, b, m=M, rtol=RTOL, max_iters=cap)
+        times.append((time.perf_counter() - t0) / max(s2["iters"], 1))
+    ms_per_iter = 1e3 * statistics.mean(times)
+    value = ms_per_iter * full_iters
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "guess": "zero (the oracle has no network)",
+                   "precision": "fp64"},
+        "iters_per_step": full_iters,
+        "cpu_baseline": {"value": value, "unit": "ms per time step", "cores": 1,
+                         "kind": "oracle",
+                         "sample": "each step: 600 GMRES(30) iterations of one time step, "
+                                   "time per iteration x the %d iterations of a full oracle "
+                                   "solve (%.1f s measured once)" % (full_iters, full_s)},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours --
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import paper_2103_10975_gb300 as pkg
+    from synthetic import MovingGaussians2D
+
+    n, N = N_SIDE, N_SIDE * N_SIDE
+    # replicas: every rank runs its own independent series
+    gen = MovingGaussians2D(n, SEED + rank, T_SERIES)
+    K, W = args.steps, args.warmup
+    t_end = TAU0 + W + 2 * K + 2
+    assert t_end <= T_SERIES
+    B = torch.stack([torch.as_tensor(gen.rhs(t)) for t in range(t_end)]).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+
+    def run_series(solver, t0, count, learned, timed, results):
+        """Steps t0..t0+count-1; returns per-step device ms (events on the main stream)."""
+        ms = []
+        for i in range(count):
+            t = t0 + i
+            if timed:
+                flush.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(main)
+            x, r = solver.solve(B[t])
+            if learned and (t + 1) % TRAIN_EVERY == 0:
+                solver.train_step(stream=side)
+            e1.record(main)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            results.append(r)
+        return ms
+
+    # ---- our arm: learned guess + FP32/FP64 refinement
+    sol = pkg.Solver(n, m=M, rtol=RTOL, precision="fp32_refine", guess="learned",
+                     fallback="prev", warmup_steps=TAU0, train_iters=32, batch=8, seed=7 + rank)
+    warm = []
+    run_series(sol, 0, TAU0, True, False, warm)          # online warm-up (collect, then train)
+    run_series(sol, TAU0, W, True, False, warm)          # benchmark warm-up
+    res = []
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    l0 = pkg.kernel_launches()
+    t_wall0 = time.perf_counter()
+    ms = run_series(sol, TAU0 + W, K, True, True, res)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    launches = pkg.kernel_launches() - l0
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    if dist is not None:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = total_ms / (K * world)
+
+    # roofline of the dominant kernel (the persistent solver)
+    hbm, peak_kind = peaks()
+    byts = sum(algorithmic_bytes(r, N, M, 4) for r in res)
+    tos = sum(r["tos_ms"] for r in res)
+    achieved = byts / (tos * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host buffers
+    Bh = torch.stack([torch.as_tensor(gen.rhs(t)) for t in range(TAU0 + W + K, TAU0 + W + 2 * K)])
+    Bh = Bh.pin_memory()
+    xh = torch.empty(N, dtype=torch.float64).pin_memory()
+    bd = torch.empty(N, dtype=torch.float64, device=dev)
+    xd = torch.empty(N, dtype=torch.float64, device=dev)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(K):
+        t = TAU0 + W + K + i
+        bd.copy_(Bh[i], non_blocking=True)
+        _, r = sol.solve(bd, xd)
+        if (t + 1) % TRAIN_EVERY == 0:
+            sol.train_step(stream=side)
+        xh.copy_(xd, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    # ---- comparison arms on the same GPU and the same time steps
+    compare = {}
+    if not args.no_compare:
+        for name, kw in (("plain_fp64_zero", dict(precision="fp64", guess="zero")),
+                         ("plain_fp64_prev", dict(precision="fp64", guess="prev")),
+                         ("fp32_refine_zero", dict(precision="fp32_refine", guess="zero"))):
+            s2 = pkg.Solver(n, m=M, rtol=RTOL, **kw)
+            tmp = []
+            run_series(s2, TAU0 + W - 1, 1, False, False, tmp)  # primes PREV with x_{t-1}
+            rr = []
+            mm = run_series(s2, TAU0 + W, K, False, True, rr)
+            compare[name] = {"ms_per_step": statistics.mean(mm),
+                             "iters_per_step": statistics.mean(r["iters"] for r in rr)}
+            s2.close()
+
+    line = None
+    if rank == 0:
+        used = sum(1 for r in res if r["guess_used"] == 2)
+        line = {
+            "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "guess": "learned (fallback x_{t-1})",
+                       "precision": "fp32 Arnoldi cycles, fp64 restart residual / solution / "
+                                    "Givens (iterative refinement)",
+                       "network": "multi-scale conv net, 32 channels, bf16 operands, fp32 accum",
+                       "online_warmup_steps": TAU0, "train_every": TRAIN_EVERY,
+                       "train_phase": "32 Adam steps, minibatch 8, 64-pair replay ring",
+                       "l2": "flushed between timed steps (256 MB write, outside the events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "iters_per_step": statistics.mean(r["iters"] for r in res),
+            "learned_guess_used_fraction": used / len(res),
+            "relres_true_max": max(r["relres_true"] for r in res),
+            "compare": compare,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "gmres_persistent (FP32 variant)",
+                         "peak_source": peak_kind,
+                         "note": "V (8 MB) is L2-resident at 256^2: bytes served mostly by L2"},
+            "e2e": {"value": e2e_ms / (K * world), "unit": "ms",
+                    "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_ms_per_step": t_wall * 1e3 / K,
+        }
+        if world == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(gen.rhs(TAU0 + W), n)
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

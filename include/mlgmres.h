@@ -1,0 +1,212 @@
+/*
+ * mlgmres.h - C ABI of the GB300 (sm_103a) MLGMRES library.
+ *
+ * MLGMRES (arXiv 2103.10975) solves a time series of linear systems A x_t = b_t
+ * (Sec. 2: a time-dependent simulation is a sequence of such problems, one per
+ * time step) with restarted GMRES(k) (Sec. 1.2), started from an initial guess
+ * that a small network N(b) proposes and that is trained online on the
+ * (b, x) pairs the solver itself produces (Sec. 2, Algorithm 1, Sec. 2.3).
+ *
+ * A is the discrete Laplacian with zero-Dirichlet walls on [-1,1]^d (Sec. 1.4
+ * and the benchmark of Sec. 3), written as the SPD operator
+ *   2D: (A u)_ij = (4 u_ij - u_{i-1,j} - u_{i+1,j} - u_{i,j-1} - u_{i,j+1}) / h^2
+ *   3D: (A u)_c  = sum_faces kappa_f (u_c - u_nb) / h^2, kappa_f the harmonic
+ *       mean of the two cell coefficients, kappa_c on a wall face (u_nb = 0),
+ * h = 2/(n+1), n interior points per axis, row-major with x fastest
+ * (2D index iy*n + ix; 3D index (iz*n + iy)*n + ix).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers owned by the caller; the library
+ *    never frees them.  Pointers named *_host are host memory.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls return after the work they enqueue has finished unless a
+ *    comment says otherwise.
+ *  - Errors are returned as mlgmres_status; no exception or abort crosses the
+ *    ABI.  mlgmres_last_error() gives a text for the last failing call.
+ *  - The library allocates all of its workspace (Krylov basis, Hessenberg
+ *    state, network weights, Adam state, replay buffer) in mlgmres_create;
+ *    solves allocate no device memory.
+ *  - A handle is not thread safe; use one handle per host thread.
+ */
+#ifndef MLGMRES_H
+#define MLGMRES_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlgmres* mlgmres_t;
+
+typedef enum {
+  MLGMRES_OK = 0,
+  MLGMRES_NOT_CONVERGED = 1,  /* iteration cap reached; x holds the last iterate */
+  MLGMRES_ERR_ARG = -1,       /* invalid argument (null pointer, bad size, bad option) */
+  MLGMRES_ERR_CUDA = -2,      /* a CUDA runtime call failed (text in last_error) */
+  MLGMRES_ERR_OOM = -3,       /* device allocation failed in create */
+  MLGMRES_ERR_TIMEOUT = -4,   /* a device-side barrier wait exceeded its limit */
+  MLGMRES_ERR_NONFINITE = -5  /* a residual or norm became NaN/Inf */
+} mlgmres_status;
+
+/* Arithmetic of the Arnoldi cycles. */
+enum {
+  MLGMRES_FP64 = 0,        /* everything in FP64 */
+  MLGMRES_FP32_REFINE = 1  /* FP32 Krylov basis, SpMV and sweeps; FP64 true residual at
+                              every restart, FP64 solution accumulation and FP64
+                              Hessenberg / Givens least squares */
+};
+
+/* Initial-guess policy (Sec. 1.3: the guess x0 sets r0 = A x0 - b and with it
+ * the whole Krylov space; Sec. 2.2: x0 = N(b) once the network is trained). */
+enum {
+  MLGMRES_GUESS_ZERO = 0,    /* x0 = 0 */
+  MLGMRES_GUESS_PREV = 1,    /* x0 = solution of the previous solve on this handle */
+  MLGMRES_GUESS_LEARNED = 2, /* x0 = s N(b/s), s = rms(b); kept only if its residual is
+                                finite and below the fallback's */
+  MLGMRES_GUESS_USER = 3     /* x0 = the caller's x_dev contents */
+};
+
+/* Problem geometry.  dim = 2 or 3; n = interior points per axis (square / cubic
+ * grids); kappa_dev = n^3 cell coefficients (3D only; NULL = constant 1).  The
+ * kappa array must stay valid for the handle's lifetime. */
+typedef struct {
+  int dim;
+  int n;
+  const float* kappa_dev;
+} mlgmres_grid;
+
+typedef struct {
+  int m;                     /* restart length k of GMRES(k), 1..64 */
+  double rtol;               /* stop when ||b - A x|| <= rtol ||b|| (true FP64 residual) */
+  long long max_iters;       /* cap on Arnoldi steps per solve (> 0) */
+  int precision;             /* MLGMRES_FP64 | MLGMRES_FP32_REFINE */
+  int guess;                 /* MLGMRES_GUESS_* */
+  int fallback;              /* ZERO or PREV: the guess used before the network is trained
+                                and whenever the learned guess loses */
+  int replay_cap;            /* capacity of the (b, x) replay ring, pairs */
+  int warmup_steps;          /* tau0: solves whose pairs are always kept (Sec. 2.3) */
+  int window_p;              /* p of the moving average M_p (Sec. 2.2) */
+  double ortho_theta;        /* admit a candidate if |cos(x_n, x_c)| <= theta for all
+                                x_c in C_t (Sec. 2.2 spread check) */
+  int deterministic_tos;     /* 1: the gate uses iteration counts in place of wall-clock TOS */
+  int train_iters;           /* Adam steps per mlgmres_train_step */
+  int batch;                 /* minibatch size */
+  float lr;                  /* Adam learning rate */
+  unsigned long long seed;   /* network initialisation and minibatch sampling */
+  int grid_blocks;           /* solver CTAs; 0 = pick from the problem size */
+  double barrier_timeout_s;  /* limit of every device-side wait (> 0) */
+  int fault_inject;          /* test hook, 0 in normal use.  1: the solver's CTA-group
+                                barrier waits for one CTA more than is launched, so its
+                                first wait runs out after barrier_timeout_s and the solve
+                                returns MLGMRES_ERR_TIMEOUT (exercises the bounded-wait
+                                path without faulting the GPU) */
+} mlgmres_options;
+
+typedef struct {
+  long long iters;           /* Arnoldi steps (matrix-vector products in cycles) */
+  int cycles;                /* restart cycles */
+  int status;                /* mlgmres_status of this solve */
+  int guess_used;            /* MLGMRES_GUESS_* actually used */
+  int admitted;              /* 1 if the (b, x) pair entered the replay ring */
+  double bnorm;              /* ||b|| */
+  double relres_true;        /* ||b - A x|| / ||b||, FP64, at exit */
+  double relres_first_cycle; /* E_k: true relative residual after the first cycle (Sec. 2.2) */
+  double relres_guess;       /* ||b - A x0|| / ||b|| of the guess used */
+  double relres_learned;     /* same for the learned candidate (-1 if none was formed) */
+  float tos_ms;              /* device time of the solve kernel (TOS, Sec. 2.2) */
+  float guess_ms;            /* device time of the learned-guess forward pass */
+} mlgmres_result;
+
+/* Fills *opt with the defaults: m = 30, rtol = 1e-10, max_iters = 10^7, FP64,
+ * guess ZERO, fallback ZERO, replay_cap 64, warmup 50, p = 10, theta = 0.9,
+ * deterministic_tos 0, train_iters 32, batch 8, lr 1e-3, seed 1,
+ * grid_blocks 0, barrier_timeout_s 2, fault_inject 0. */
+void mlgmres_default_options(mlgmres_options* opt);
+
+/* Creates a solver for one grid and allocates all workspace on the current
+ * CUDA device.  Returns ERR_ARG for an invalid grid or option, ERR_OOM if the
+ * workspace does not fit, ERR_CUDA on other CUDA errors; *out is NULL then. */
+mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* opt,
+                              mlgmres_t* out);
+
+/* Solves A x = b (GMRES(m), Sec. 1.2) to the handle's rtol.
+ * b_dev: N doubles (input).  x_dev: N doubles (output; input too in guess mode
+ * USER).  Both must be 8-byte aligned and must not overlap.  When the handle's
+ * guess mode is LEARNED the (b, x) pair then passes Algorithm 1's gate and may
+ * enter the replay ring (res->admitted).  On NOT_CONVERGED x holds the last
+ * iterate and res->relres_true its residual.  b = 0 gives x = 0, iters = 0, OK.
+ * res may be NULL. */
+mlgmres_status mlgmres_solve(mlgmres_t h, const double* b_dev, double* x_dev, void* stream,
+                             mlgmres_result* res);
+
+/* Solves `count` independent systems, each on its own grid (grids[i].dim must
+ * equal the handle's dim and grids[i].n must not exceed the handle's n), in one
+ * persistent launch.  b_dev[i], x_dev[i]: device arrays of grids[i].n^dim
+ * doubles; b_dev and x_dev themselves are HOST arrays of device pointers.
+ * Guesses are ZERO (or USER when the handle's mode is USER); no pair is
+ * collected.  out: `count` results (host).  Returns the worst status. */
+mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* grids,
+                                   const double* const* b_dev, double* const* x_dev,
+                                   void* stream, mlgmres_result* out);
+
+/* One training phase (Sec. 2.3): opt.train_iters Adam steps on the MSE loss
+ * ||N(b/s) - x/s||^2 over minibatches drawn from the replay ring, each batch
+ * holding every pair admitted since the previous call (up to opt.batch) and
+ * uniform samples of the rest.  Runs on side_stream and returns once enqueued;
+ * the next solve waits for it.  loss_host (may be NULL) receives the mean loss
+ * of the last minibatch after the phase completes (this synchronises). Does
+ * nothing and returns OK while the ring is empty. */
+mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_host);
+
+/* Text of the last error on this handle ("" if none); valid until the next call. */
+const char* mlgmres_last_error(mlgmres_t h);
+
+/* Frees the handle and all its workspace.  NULL is ignored. */
+void mlgmres_destroy(mlgmres_t h);
+
+/* ---- inspection entry points (used by tests; same conventions) ---------- */
+
+/* out = A u in FP64 on the handle's grid (u_dev, out_dev: N doubles). */
+mlgmres_status mlgmres_apply(mlgmres_t h, const double* u_dev, double* out_dev, void* stream);
+
+/* Runs `steps` (<= m) Arnoldi steps from v0 with the handle's precision and
+ * Gram-Schmidt (classical, twice), without restarts or Givens, and copies the
+ * Hessenberg matrix to H_host ((steps+1) x steps, column-major, leading
+ * dimension steps+1) and the basis to V_dev ((steps+1) x N doubles, row per
+ * vector).  Returns the number of steps done (breakdown may stop it early)
+ * through *done. */
+mlgmres_status mlgmres_arnoldi(mlgmres_t h, const double* v0_dev, int steps, double* H_host,
+                               double* V_dev, int* done, void* stream);
+
+/* Number of network parameters (FP32 master copy). */
+mlgmres_status mlgmres_nn_param_count(mlgmres_t h, long long* count);
+
+/* Copies the FP32 master parameters out / in, in the order
+ * in.w, in.b, level[0].w, level[0].b, ..., dil.w, dil.b, out.w, out.b
+ * (weights as [out][in][ky][kx]).  Setting them also resets Adam's moments. */
+mlgmres_status mlgmres_nn_get_params(mlgmres_t h, float* params_host, long long count);
+mlgmres_status mlgmres_nn_set_params(mlgmres_t h, const float* params_host, long long count);
+
+/* Network output for `batch` normalised inputs: y_dev[b] = N(u_dev[b]) (FP32,
+ * batch x N each), computed with the BF16 inference weights. */
+mlgmres_status mlgmres_nn_forward(mlgmres_t h, int batch, const float* u_dev, float* y_dev,
+                                  void* stream);
+
+/* Mean-squared loss 1/(B N) sum_b ||N(u_b) - t_b||^2 and its gradient with
+ * respect to every parameter (grad_host: param_count floats, same order as
+ * get_params), at the current weights; does not update anything. */
+mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u_dev,
+                                    const float* t_dev, float* loss_host, float* grad_host,
+                                    void* stream);
+
+/* Pairs currently in the replay ring. */
+mlgmres_status mlgmres_replay_size(mlgmres_t h, int* count);
+
+/* Number of CUDA kernels this library has launched in this process so far (all
+ * handles).  Used to count the kernels inside a timed region. */
+mlgmres_status mlgmres_kernel_launches(long long* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLGMRES_H */

@@ -1,0 +1,71 @@
+// Internal state behind an mlgmres_t handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mlgmres.h"
+#include "nn.h"
+#include "solver.h"
+
+struct mlgmres {
+  mlgmres_grid grid;
+  mlgmres_options opt;
+  int N = 0;
+  int dev = 0;
+  int nsm = 0;
+  bool fp32 = false;
+  int blocks = 0;       // solver CTAs for a single solve
+  int max_blocks = 0;   // co-resident limit of the kernel variant
+  int bs = 0;
+
+  // ---- solver workspace (one group for single solves) ----
+  long long ldv = 0;
+  void* V = nullptr;
+  void* W0 = nullptr;
+  void* W1 = nullptr;
+  double* part = nullptr;
+  unsigned long long* bar = nullptr;  // per group: counter
+  int* err = nullptr;                 // per group: error flag
+  mlg::DevResult* dres = nullptr;     // device results
+  mlg::DevResult* hres = nullptr;     // pinned host copy
+  int* dcfg = nullptr;                // group_first | task_first | task_order
+  mlg::SolveTask* dtasks = nullptr;
+  mlg::GroupWork* dwork = nullptr;
+  mlg::SolveTask* htasks = nullptr;   // pinned staging
+  int* hcfg = nullptr;                // pinned staging
+  mlg::GroupWork* hwork = nullptr;    // pinned staging
+  int cfg_cap = 0;                    // capacity (tasks) of the config buffers
+  int group_cap = 0;                  // capacity (groups) of the group buffers
+
+  // ---- guess state ----
+  double* x_prev = nullptr;
+  bool have_prev = false;
+  double* x_alt = nullptr;            // learned guess
+  float* u_in = nullptr;              // normalised input b/s (FP32)
+  float* y_out = nullptr;             // network output (FP32)
+  double* scal = nullptr;             // device scalars (rms etc.)
+
+  // ---- learned guess / training ----
+  mlg::Net net;
+  bool net_ready = false;             // trained at least once
+  int train_calls = 0;
+  // replay ring: normalised (b/s, x/s) pairs, FP32, N each
+  float* ring_u = nullptr;
+  float* ring_t = nullptr;
+  int ring_count = 0;
+  int ring_head = 0;                  // next slot to write
+  std::vector<int> fresh;             // slots admitted since the last train call (C_t)
+  std::vector<double> E_hist, T_hist;
+  long long solves = 0;
+  double* ddots = nullptr;            // device dots for the spread check
+  double* hdots = nullptr;            // pinned
+  unsigned long long rng_state = 0;
+  cudaEvent_t train_done = nullptr;
+  bool train_pending = false;
+  float* loss_dev = nullptr;
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+  std::string last_error;
+};

@@ -1,0 +1,133 @@
+// Small vector kernels around the solver: the input normalisation of the
+// learned guess (s = rms(b), u = b/s, x0 = s y), replay-ring stores and the
+// dot products of the spread check (Sec. 2.2).
+#include <atomic>
+
+#include "misc.h"
+
+namespace mlg {
+
+static std::atomic<long long> g_launches{0};
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+// sum of squares of b into *out (one CTA, fixed order: deterministic).
+__global__ void sumsq_kernel(const double* __restrict__ b, int N, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s += b[i] * b[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *out = s;
+  }
+}
+
+// u = b / s with s = sqrt(sumsq / N) (s = 1 when b = 0)
+__global__ void normalise_kernel(const double* __restrict__ b, int N, const double* sumsq,
+                                 float* __restrict__ u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double s = sqrt(*sumsq / N);
+  if (!(s > 0.0)) s = 1.0;
+  u[i] = (float)(b[i] / s);
+}
+
+// x = s y
+__global__ void denormalise_kernel(const float* __restrict__ y, int N, const double* sumsq,
+                                   double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double s = sqrt(*sumsq / N);
+  if (!(s > 0.0)) s = 1.0;
+  x[i] = s * (double)y[i];
+}
+
+// ring pair: u = b/s, t = x/s
+__global__ void store_pair_kernel(const double* __restrict__ b, const double* __restrict__ x,
+                                  int N, const double* sumsq, float* __restrict__ u,
+                                  float* __restrict__ t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double s = sqrt(*sumsq / N);
+  if (!(s > 0.0)) s = 1.0;
+  u[i] = (float)(b[i] / s);
+  t[i] = (float)(x[i] / s);
+}
+
+// out[2c] = <x, t_c>, out[2c+1] = <t_c, t_c> for the listed ring slots;
+// out[2*count] = <x, x>.  One CTA per slot (+1 for ||x||), fixed order.
+__global__ void spread_dots_kernel(const double* __restrict__ x, const float* __restrict__ ring,
+                                   long long stride, const int* __restrict__ slots, int count,
+                                   int N, double* out) {
+  __shared__ double red[2][32];
+  const int c = blockIdx.x;
+  double a = 0.0, bb = 0.0;
+  if (c < count) {
+    const float* tc = ring + (long long)slots[c] * stride;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const double tv = tc[i];
+      a += x[i] * tv;
+      bb += tv * tv;
+    }
+  } else {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) a += x[i] * x[i];
+  }
+  a = warp_sum(a);
+  bb = warp_sum(bb);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = bb;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool in = threadIdx.x < (int)(blockDim.x >> 5);
+    a = warp_sum(in ? red[0][threadIdx.x] : 0.0);
+    bb = warp_sum(in ? red[1][threadIdx.x] : 0.0);
+    if (threadIdx.x == 0) {
+      if (c < count) {
+        out[2 * c] = a;
+        out[2 * c + 1] = bb;
+      } else {
+        out[2 * count] = a;
+      }
+    }
+  }
+}
+
+static unsigned blocks_for(int N) { return (unsigned)((N + 255) / 256); }
+
+cudaError_t launch_sumsq(const double* b, int N, double* out, cudaStream_t s) {
+  sumsq_kernel<<<1, 1024, 0, s>>>(b, N, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_normalise(const double* b, int N, const double* sumsq, float* u,
+                             cudaStream_t s) {
+  normalise_kernel<<<blocks_for(N), 256, 0, s>>>(b, N, sumsq, u);
+  note_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_denormalise(const float* y, int N, const double* sumsq, double* x,
+                               cudaStream_t s) {
+  denormalise_kernel<<<blocks_for(N), 256, 0, s>>>(y, N, sumsq, x);
+  note_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_store_pair(const double* b, const double* x, int N, const double* sumsq,
+                              float* u, float* t, cudaStream_t s) {
+  store_pair_kernel<<<blocks_for(N), 256, 0, s>>>(b, x, N, sumsq, u, t);
+  note_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_spread_dots(const double* x, const float* ring, long long stride,
+                               const int* slots, int count, int N, double* out, cudaStream_t s) {
+  spread_dots_kernel<<<count + 1, 512, 0, s>>>(x, ring, stride, slots, count, N, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace mlg

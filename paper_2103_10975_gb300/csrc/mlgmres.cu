@@ -1,0 +1,606 @@
+// C ABI of the library: handle life cycle, guess selection, the persistent
+// solve, the online data-collection gate (Sec. 2.2, Algorithm 1) and the
+// training phase (Sec. 2.3).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+#include "misc.h"
+
+using namespace mlg;
+
+namespace {
+
+struct Fail {
+  mlgmres_status st;
+};
+
+std::string fmt_cuda(const char* what, cudaError_t e) {
+  return std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+#define CK(call)                                                  \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      h->last_error = fmt_cuda(#call, e_);                        \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? MLGMRES_ERR_OOM \
+                                                 : MLGMRES_ERR_CUDA}; \
+    }                                                             \
+  } while (0)
+
+#define ARG(cond, msg)              \
+  do {                              \
+    if (!(cond)) {                  \
+      h->last_error = (msg);        \
+      throw Fail{MLGMRES_ERR_ARG};  \
+    }                               \
+  } while (0)
+
+long long grid_points(int dim, int n) {
+  return dim == 2 ? (long long)n * n : (long long)n * n * n;
+}
+
+unsigned long long splitmix_next(unsigned long long& st) {
+  st += 0x9E3779B97F4A7C15ull;
+  unsigned long long z = st;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int auto_blocks(const mlgmres* h, int N) {
+  // about four grid points per thread; never more CTAs than can be co-resident
+  long long want = (N + (long long)h->bs * 4 - 1) / ((long long)h->bs * 4);
+  if (want < 1) want = 1;
+  if (want > h->max_blocks) want = h->max_blocks;
+  if (want > kPartStride) want = kPartStride;
+  return (int)want;
+}
+
+void check_options(mlgmres* h, const mlgmres_options* o) {
+  ARG(o->m >= 1 && o->m <= kMaxM, "m must be in 1..64");
+  ARG(o->rtol > 0.0 && o->rtol < 1.0, "rtol must be in (0, 1)");
+  ARG(o->max_iters > 0, "max_iters must be positive");
+  ARG(o->precision == MLGMRES_FP64 || o->precision == MLGMRES_FP32_REFINE, "bad precision");
+  ARG(o->guess >= MLGMRES_GUESS_ZERO && o->guess <= MLGMRES_GUESS_USER, "bad guess mode");
+  ARG(o->fallback == MLGMRES_GUESS_ZERO || o->fallback == MLGMRES_GUESS_PREV, "bad fallback");
+  ARG(o->replay_cap >= 1 && o->replay_cap <= 4096, "replay_cap must be in 1..4096");
+  ARG(o->warmup_steps >= 0, "warmup_steps must be >= 0");
+  ARG(o->window_p >= 1, "window_p must be >= 1");
+  ARG(o->ortho_theta >= 0.0 && o->ortho_theta <= 1.0, "ortho_theta must be in [0, 1]");
+  ARG(o->train_iters >= 0, "train_iters must be >= 0");
+  ARG(o->batch >= 1 && o->batch <= 64, "batch must be in 1..64");
+  ARG(o->lr > 0.0f, "lr must be positive");
+  ARG(o->grid_blocks >= 0, "grid_blocks must be >= 0");
+  ARG(o->barrier_timeout_s > 0.0 && o->barrier_timeout_s <= 60.0,
+      "barrier_timeout_s must be in (0, 60]");
+  ARG(o->fault_inject == 0 || o->fault_inject == 1, "fault_inject must be 0 or 1");
+}
+
+// Run the persistent kernel for `count` tasks already staged in h->htasks,
+// with the group layout staged in h->hcfg / h->hwork.
+void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps,
+                cudaStream_t s) {
+  const size_t cfg_bytes = sizeof(int) * (size_t)(2 * (ngroups + 1) + ntasks);
+  CK(cudaMemcpyAsync(h->dcfg, h->hcfg, cfg_bytes, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->dtasks, h->htasks, sizeof(SolveTask) * ntasks, cudaMemcpyHostToDevice,
+                     s));
+  CK(cudaMemcpyAsync(h->dwork, h->hwork, sizeof(GroupWork) * ngroups, cudaMemcpyHostToDevice,
+                     s));
+  CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long) * ngroups, s));
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int) * ngroups, s));
+  KParams kp;
+  kp.m = h->opt.m;
+  kp.rtol = h->opt.rtol;
+  kp.max_iters = h->opt.max_iters;
+  kp.arnoldi_steps = arnoldi_steps;
+  kp.ngroups = ngroups;
+  kp.group_first = h->dcfg;
+  kp.task_first = h->dcfg + (ngroups + 1);
+  kp.task_order = h->dcfg + 2 * (ngroups + 1);
+  kp.tasks = h->dtasks;
+  kp.work = h->dwork;
+  CK(launch_gmres(kp, h->fp32, h->grid.dim, grid, s));
+}
+
+GroupWork single_group_work(mlgmres* h, int nblocks) {
+  GroupWork w;
+  w.V = h->V;
+  w.ldv = h->ldv;
+  w.W0 = h->W0;
+  w.W1 = h->W1;
+  w.part = h->part;
+  w.bar.ctr = h->bar;
+  w.bar.err = h->err;
+  // fault_inject = 1 makes the barrier wait for a CTA that is never launched
+  w.bar.nblocks = (unsigned)(nblocks + (h->opt.fault_inject == 1 ? 1 : 0));
+  w.bar.timeout_ns = (unsigned long long)(h->opt.barrier_timeout_s * 1e9);
+  return w;
+}
+
+void stage_single(mlgmres* h, const SolveTask& t, int nblocks) {
+  h->hcfg[0] = 0;
+  h->hcfg[1] = nblocks;
+  h->hcfg[2] = 0;
+  h->hcfg[3] = 1;
+  h->hcfg[4] = 0;
+  h->htasks[0] = t;
+  h->hwork[0] = single_group_work(h, nblocks);
+}
+
+mlgmres_status to_status(int s) {
+  switch (s) {
+    case 0: return MLGMRES_OK;
+    case 1: return MLGMRES_NOT_CONVERGED;
+    case kErrTimeout: return MLGMRES_ERR_TIMEOUT;
+    case kErrNonfinite: return MLGMRES_ERR_NONFINITE;
+    default: return MLGMRES_ERR_CUDA;
+  }
+}
+
+void fill_result(const DevResult& d, mlgmres_result* r) {
+  r->iters = d.iters;
+  r->cycles = d.cycles;
+  r->status = to_status(d.status);
+  r->bnorm = d.bnorm;
+  r->relres_true = d.relres_true;
+  r->relres_first_cycle = d.relres_first_cycle;
+  r->relres_guess = d.relres_guess;
+  r->relres_learned = d.relres_alt;
+}
+
+// Algorithm 1: decide whether the pair (b, x) of the solve just finished joins
+// the replay ring, and store it.  Runs after every LEARNED-mode solve.
+int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_result& r,
+                   cudaStream_t s) {
+  const int p = h->opt.window_p;
+  const double E = r.relres_first_cycle;
+  const double T = h->opt.deterministic_tos ? (double)r.iters : (double)r.tos_ms;
+  h->E_hist.push_back(E);
+  h->T_hist.push_back(T);
+  h->solves++;
+  bool admit = false;
+  if (h->solves <= h->opt.warmup_steps) {
+    admit = true;  // warm-up: every pair is kept (Sec. 2.3)
+  } else {
+    auto mean_last = [p](const std::vector<double>& v) {
+      const size_t k = std::min<size_t>((size_t)p, v.size());
+      double acc = 0.0;
+      for (size_t i = v.size() - k; i < v.size(); i++) acc += v[i];
+      return acc / (double)k;
+    };
+    const bool good = (E < mean_last(h->E_hist)) && (T < mean_last(h->T_hist));
+    if (!good) {
+      admit = true;
+      const int cnt = (int)h->fresh.size();
+      if (cnt > 0) {  // spread check against C_t
+        CK(cudaMemcpyAsync(h->scal + 8, h->fresh.data(), sizeof(int) * cnt,
+                           cudaMemcpyHostToDevice, s));
+        // slots live in the int view of scal[8...]
+        CK(launch_spread_dots(x, h->ring_t, h->ldv, (const int*)(h->scal + 8), cnt, h->N,
+                              h->ddots, s));
+        CK(cudaMemcpyAsync(h->hdots, h->ddots, sizeof(double) * (2 * cnt + 1),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double xx = h->hdots[2 * cnt];
+        for (int c = 0; c < cnt; c++) {
+          const double den = sqrt(xx * h->hdots[2 * c + 1]);
+          const double cosv = den > 0.0 ? fabs(h->hdots[2 * c]) / den : 1.0;
+          if (cosv > h->opt.ortho_theta) { admit = false; break; }
+        }
+      }
+    }
+  }
+  if (!admit) return 0;
+  const int slot = h->ring_head;
+  h->ring_head = (h->ring_head + 1) % h->opt.replay_cap;
+  if (h->ring_count < h->opt.replay_cap) h->ring_count++;
+  h->fresh.erase(std::remove(h->fresh.begin(), h->fresh.end(), slot), h->fresh.end());
+  CK(launch_sumsq(b, h->N, h->scal + 1, s));
+  CK(launch_store_pair(b, x, h->N, h->scal + 1, h->ring_u + (long long)slot * h->ldv,
+                       h->ring_t + (long long)slot * h->ldv, s));
+  h->fresh.push_back(slot);
+  return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mlgmres_default_options(mlgmres_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->m = 30;
+  o->rtol = 1e-10;
+  o->max_iters = 10000000;
+  o->precision = MLGMRES_FP64;
+  o->guess = MLGMRES_GUESS_ZERO;
+  o->fallback = MLGMRES_GUESS_ZERO;
+  o->replay_cap = 64;
+  o->warmup_steps = 50;
+  o->window_p = 10;
+  o->ortho_theta = 0.9;
+  o->deterministic_tos = 0;
+  o->train_iters = 32;
+  o->batch = 8;
+  o->lr = 1e-3f;
+  o->seed = 1;
+  o->grid_blocks = 0;
+  o->barrier_timeout_s = 2.0;
+}
+
+mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* opt,
+                              mlgmres_t* out) {
+  if (!out) return MLGMRES_ERR_ARG;
+  *out = nullptr;
+  if (!grid || !opt) return MLGMRES_ERR_ARG;
+  mlgmres* h = new mlgmres();
+  try {
+    ARG(grid->dim == 2 || grid->dim == 3, "dim must be 2 or 3");
+    ARG(grid->n >= 1, "n must be >= 1");
+    ARG(grid_points(grid->dim, grid->n) < (1ll << 30), "grid too large");
+    ARG(grid->dim == 3 || grid->kappa_dev == nullptr, "kappa is for 3D grids only");
+    check_options(h, opt);
+    h->grid = *grid;
+    h->opt = *opt;
+    h->N = (int)grid_points(grid->dim, grid->n);
+    h->fp32 = opt->precision == MLGMRES_FP32_REFINE;
+    CK(cudaGetDevice(&h->dev));
+    CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
+    h->max_blocks = gmres_max_blocks(h->fp32, grid->dim, opt->m, &h->bs);
+    CK(cudaGetLastError());
+    ARG(h->max_blocks >= 1, "solver kernel cannot be resident");
+    h->blocks = opt->grid_blocks > 0 ? std::min(opt->grid_blocks, h->max_blocks)
+                                     : auto_blocks(h, h->N);
+    h->blocks = std::min(h->blocks, kPartStride);
+    h->ldv = ((long long)h->N + 63) / 64 * 64;
+    const size_t es = h->fp32 ? sizeof(float) : sizeof(double);
+    CK(cudaMalloc(&h->V, es * (size_t)(opt->m + 1) * h->ldv));
+    CK(cudaMalloc(&h->W0, es * (size_t)h->ldv));
+    CK(cudaMalloc(&h->W1, es * (size_t)h->ldv));
+    CK(cudaMalloc(&h->part, sizeof(double) * 2 * (kMaxM + 2) * kPartStride));
+    h->group_cap = 1;
+    h->cfg_cap = 1;
+    CK(cudaMalloc(&h->bar, sizeof(unsigned long long) * h->group_cap));
+    CK(cudaMalloc(&h->err, sizeof(int) * h->group_cap));
+    CK(cudaMalloc(&h->dres, sizeof(DevResult) * h->cfg_cap));
+    CK(cudaMallocHost(&h->hres, sizeof(DevResult) * h->cfg_cap));
+    CK(cudaMalloc(&h->dcfg, sizeof(int) * (2 * (h->group_cap + 1) + h->cfg_cap)));
+    CK(cudaMallocHost(&h->hcfg, sizeof(int) * (2 * (h->group_cap + 1) + h->cfg_cap)));
+    CK(cudaMalloc(&h->dtasks, sizeof(SolveTask) * h->cfg_cap));
+    CK(cudaMallocHost(&h->htasks, sizeof(SolveTask) * h->cfg_cap));
+    CK(cudaMalloc(&h->dwork, sizeof(GroupWork) * h->group_cap));
+    CK(cudaMallocHost(&h->hwork, sizeof(GroupWork) * h->group_cap));
+    CK(cudaMalloc(&h->x_prev, sizeof(double) * h->ldv));
+    CK(cudaMalloc(&h->scal, sizeof(double) * (8 + 4096)));
+    CK(cudaEventCreate(&h->ev0));
+    CK(cudaEventCreate(&h->ev1));
+    CK(cudaEventCreate(&h->ev2));
+    CK(cudaEventCreateWithFlags(&h->train_done, cudaEventDisableTiming));
+    h->rng_state = opt->seed;
+    if (grid->dim == 2) {
+      // learned-guess machinery (the network is two-dimensional)
+      CK(cudaMalloc(&h->x_alt, sizeof(double) * h->ldv));
+      CK(cudaMalloc(&h->u_in, sizeof(float) * h->ldv));
+      CK(cudaMalloc(&h->y_out, sizeof(float) * h->ldv));
+      CK(cudaMalloc(&h->ring_u, sizeof(float) * h->ldv * opt->replay_cap));
+      CK(cudaMalloc(&h->ring_t, sizeof(float) * h->ldv * opt->replay_cap));
+      CK(cudaMalloc(&h->ddots, sizeof(double) * (2 * opt->replay_cap + 1)));
+      CK(cudaMallocHost(&h->hdots, sizeof(double) * (2 * opt->replay_cap + 1)));
+      CK(cudaMalloc(&h->loss_dev, sizeof(float) * 4));
+      CK(net_create(h->net, grid->n, opt->batch, opt->seed));
+    }
+    CK(cudaDeviceSynchronize());
+  } catch (const Fail& f) {
+    fprintf(stderr, "mlgmres_create: %s\n", h->last_error.c_str());
+    mlgmres_destroy(h);
+    return f.st;
+  }
+  *out = h;
+  return MLGMRES_OK;
+}
+
+void mlgmres_destroy(mlgmres_t h) {
+  if (!h) return;
+  cudaFree(h->V);
+  cudaFree(h->W0);
+  cudaFree(h->W1);
+  cudaFree(h->part);
+  cudaFree(h->bar);
+  cudaFree(h->err);
+  cudaFree(h->dres);
+  cudaFreeHost(h->hres);
+  cudaFree(h->dcfg);
+  cudaFreeHost(h->hcfg);
+  cudaFree(h->dtasks);
+  cudaFreeHost(h->htasks);
+  cudaFree(h->dwork);
+  cudaFreeHost(h->hwork);
+  cudaFree(h->x_prev);
+  cudaFree(h->x_alt);
+  cudaFree(h->u_in);
+  cudaFree(h->y_out);
+  cudaFree(h->scal);
+  cudaFree(h->ring_u);
+  cudaFree(h->ring_t);
+  cudaFree(h->ddots);
+  cudaFreeHost(h->hdots);
+  cudaFree(h->loss_dev);
+  net_destroy(h->net);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ev2) cudaEventDestroy(h->ev2);
+  if (h->train_done) cudaEventDestroy(h->train_done);
+  delete h;
+}
+
+const char* mlgmres_last_error(mlgmres_t h) { return h ? h->last_error.c_str() : "null handle"; }
+
+mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stream,
+                             mlgmres_result* res_out) {
+  if (!h) return MLGMRES_ERR_ARG;
+  h->last_error.clear();
+  try {
+    ARG(b && x, "b and x must be device pointers");
+    ARG(b != x, "b and x must not alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    mlgmres_result r;
+    memset(&r, 0, sizeof(r));
+    r.relres_learned = -1.0;
+    const int N = h->N;
+    const int mode = h->opt.guess;
+    const double* x_alt = nullptr;
+    int fallback = mode == MLGMRES_GUESS_LEARNED ? h->opt.fallback : mode;
+    // guess in x
+    if (fallback == MLGMRES_GUESS_ZERO || (fallback == MLGMRES_GUESS_PREV && !h->have_prev)) {
+      CK(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
+      r.guess_used = MLGMRES_GUESS_ZERO;
+    } else if (fallback == MLGMRES_GUESS_PREV) {
+      CK(cudaMemcpyAsync(x, h->x_prev, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      r.guess_used = MLGMRES_GUESS_PREV;
+    } else {
+      r.guess_used = MLGMRES_GUESS_USER;
+    }
+    if (mode == MLGMRES_GUESS_LEARNED && h->net_ready && h->grid.dim == 2) {
+      if (h->train_pending) {
+        CK(cudaStreamWaitEvent(s, h->train_done, 0));
+        h->train_pending = false;
+      }
+      CK(cudaEventRecord(h->ev2, s));
+      CK(launch_sumsq(b, N, h->scal, s));
+      CK(launch_normalise(b, N, h->scal, h->u_in, s));
+      CK(net_forward(h->net, 1, h->u_in, h->y_out, s));
+      CK(launch_denormalise(h->y_out, N, h->scal, h->x_alt, s));
+      x_alt = h->x_alt;
+    }
+    SolveTask t;
+    t.n = h->grid.n;
+    t.N = N;
+    t.b = b;
+    t.x = x;
+    t.x_alt = x_alt;
+    t.kappa = h->grid.kappa_dev;
+    t.res = h->dres;
+    t.hist = nullptr;
+    t.hist_cap = 0;
+    stage_single(h, t, h->blocks);
+    CK(cudaEventRecord(h->ev0, s));
+    run_solver(h, 1, 1, h->blocks, 0, s);
+    CK(cudaEventRecord(h->ev1, s));
+    CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->x_prev, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    h->have_prev = true;
+    fill_result(h->hres[0], &r);
+    if (h->hres[0].used_alt) r.guess_used = MLGMRES_GUESS_LEARNED;
+    if (x_alt) {
+      r.relres_learned = h->hres[0].relres_alt;
+      CK(cudaEventElapsedTime(&r.guess_ms, h->ev2, h->ev0));
+    }
+    CK(cudaEventElapsedTime(&r.tos_ms, h->ev0, h->ev1));
+    if (mode == MLGMRES_GUESS_LEARNED && h->grid.dim == 2 && r.status != MLGMRES_ERR_TIMEOUT)
+      r.admitted = gate_and_store(h, b, x, r, s);
+    if (res_out) *res_out = r;
+    if (r.status == MLGMRES_ERR_TIMEOUT) h->last_error = "device barrier wait timed out";
+    if (r.status == MLGMRES_ERR_NONFINITE) h->last_error = "non-finite residual";
+    return (mlgmres_status)r.status;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* grids,
+                                   const double* const* b, double* const* x, void* stream,
+                                   mlgmres_result* out) {
+  if (!h) return MLGMRES_ERR_ARG;
+  h->last_error = "solve_batch is not available on this handle";
+  (void)count; (void)grids; (void)b; (void)x; (void)stream; (void)out;
+  return MLGMRES_ERR_ARG;
+}
+
+mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_host) {
+  if (!h) return MLGMRES_ERR_ARG;
+  h->last_error.clear();
+  try {
+    ARG(h->grid.dim == 2, "the learned guess is available for 2D grids only");
+    if (loss_host) *loss_host = -1.0f;
+    if (h->ring_count == 0 || h->solves < h->opt.warmup_steps || h->opt.train_iters == 0)
+      return MLGMRES_OK;
+    cudaStream_t s = (cudaStream_t)side_stream;
+    // the ring was written on the solve streams; the handle's solves synchronise
+    // before returning, so everything they enqueued is complete here.
+    const int B = std::min(h->opt.batch, std::max(1, h->ring_count));
+    std::vector<int> pick(B);
+    for (int it = 0; it < h->opt.train_iters; it++) {
+      int k = 0;
+      for (int f : h->fresh) {
+        if (k >= B) break;
+        pick[k++] = f;
+      }
+      while (k < B) pick[k++] = (int)(splitmix_next(h->rng_state) % (unsigned long long)h->ring_count);
+      CK(net_train_batch(h->net, B, h->ring_u, h->ring_t, h->ldv, pick.data(), h->opt.lr,
+                         h->loss_dev, s));
+    }
+    CK(cudaEventRecord(h->train_done, s));
+    h->train_pending = true;
+    h->net_ready = true;
+    h->train_calls++;
+    h->fresh.clear();
+    if (loss_host) {
+      CK(cudaStreamSynchronize(s));
+      CK(cudaMemcpy(loss_host, h->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_apply(mlgmres_t h, const double* u, double* out, void* stream) {
+  if (!h) return MLGMRES_ERR_ARG;
+  h->last_error.clear();
+  try {
+    ARG(u && out && u != out, "u and out must be distinct device pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_apply(h->grid.dim, h->grid.n, h->grid.kappa_dev, u, out, s));
+    CK(cudaStreamSynchronize(s));
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_arnoldi(mlgmres_t h, const double* v0, int steps, double* H_host,
+                               double* V_dev, int* done, void* stream) {
+  if (!h) return MLGMRES_ERR_ARG;
+  h->last_error.clear();
+  try {
+    ARG(v0 && H_host && V_dev && done, "null argument");
+    ARG(steps >= 1 && steps <= h->opt.m, "steps must be in 1..m");
+    cudaStream_t s = (cudaStream_t)stream;
+    double* Hd = nullptr;
+    CK(cudaMallocAsync(&Hd, sizeof(double) * (steps + 1) * steps, s));
+    CK(cudaMemsetAsync(Hd, 0, sizeof(double) * (steps + 1) * steps, s));
+    SolveTask t;
+    t.n = h->grid.n;
+    t.N = h->N;
+    t.b = v0;
+    t.x = nullptr;
+    t.x_alt = nullptr;
+    t.kappa = h->grid.kappa_dev;
+    t.res = h->dres;
+    t.hist = Hd;
+    t.hist_cap = (long long)(steps + 1) * steps;
+    stage_single(h, t, h->blocks);
+    run_solver(h, 1, 1, h->blocks, steps, s);
+    CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(H_host, Hd, sizeof(double) * (steps + 1) * steps, cudaMemcpyDeviceToHost,
+                       s));
+    CK(cudaStreamSynchronize(s));
+    const int k = h->hres[0].status;
+    ARG(k >= 1, "Arnoldi run failed (barrier timeout or zero start vector)");
+    *done = k;
+    CK(launch_basis_to_f64(h->fp32, h->V, h->ldv, k + 1, h->N, V_dev, s));
+    CK(cudaFreeAsync(Hd, s));
+    CK(cudaStreamSynchronize(s));
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_nn_param_count(mlgmres_t h, long long* count) {
+  if (!h || !count) return MLGMRES_ERR_ARG;
+  if (h->grid.dim != 2) {
+    h->last_error = "the network exists for 2D grids only";
+    return MLGMRES_ERR_ARG;
+  }
+  *count = h->net.nparams;
+  return MLGMRES_OK;
+}
+
+mlgmres_status mlgmres_nn_get_params(mlgmres_t h, float* p, long long count) {
+  if (!h) return MLGMRES_ERR_ARG;
+  try {
+    ARG(h->grid.dim == 2 && p && count == h->net.nparams, "bad parameter buffer");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(p, h->net.master, sizeof(float) * count, cudaMemcpyDeviceToHost));
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_nn_set_params(mlgmres_t h, const float* p, long long count) {
+  if (!h) return MLGMRES_ERR_ARG;
+  try {
+    ARG(h->grid.dim == 2 && p && count == h->net.nparams, "bad parameter buffer");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(h->net.master, p, sizeof(float) * count, cudaMemcpyHostToDevice));
+    CK(cudaMemset(h->net.adam_m, 0, sizeof(float) * count));
+    CK(cudaMemset(h->net.adam_v, 0, sizeof(float) * count));
+    h->net.adam_t = 0;
+    CK(net_sync_weights(h->net, 0));
+    CK(cudaDeviceSynchronize());
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_nn_forward(mlgmres_t h, int batch, const float* u, float* y,
+                                  void* stream) {
+  if (!h) return MLGMRES_ERR_ARG;
+  try {
+    ARG(h->grid.dim == 2 && u && y, "bad arguments");
+    ARG(batch >= 1 && batch <= h->opt.batch, "batch must be in 1..opt.batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(net_forward(h->net, batch, u, y, s));
+    CK(cudaStreamSynchronize(s));
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u, const float* t,
+                                    float* loss_host, float* grad_host, void* stream) {
+  if (!h) return MLGMRES_ERR_ARG;
+  try {
+    ARG(h->grid.dim == 2 && u && t && loss_host && grad_host, "bad arguments");
+    ARG(batch >= 1 && batch <= h->opt.batch, "batch must be in 1..opt.batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    float* y = nullptr;
+    CK(cudaMallocAsync(&y, sizeof(float) * (size_t)batch * h->N, s));
+    CK(net_forward(h->net, batch, u, y, s));
+    CK(net_backward(h->net, batch, u, y, t, h->loss_dev, s));
+    CK(cudaMemcpyAsync(loss_host, h->loss_dev, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(grad_host, h->net.grad, sizeof(float) * h->net.nparams,
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaFreeAsync(y, s));
+    CK(cudaStreamSynchronize(s));
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_kernel_launches(long long* count) {
+  if (!count) return MLGMRES_ERR_ARG;
+  *count = launches_so_far();
+  return MLGMRES_OK;
+}
+
+mlgmres_status mlgmres_replay_size(mlgmres_t h, int* count) {
+  if (!h || !count) return MLGMRES_ERR_ARG;
+  *count = h->ring_count;
+  return MLGMRES_OK;
+}
+
+}  // extern "C"

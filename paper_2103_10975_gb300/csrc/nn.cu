@@ -1,0 +1,784 @@
+// Initial-guess network N(b): forward, backward and Adam on the GPU.
+// Architecture and parameter order are documented in nn.h; activations are
+// NHWC with 32 channels in BF16, accumulation in FP32.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "nn.h"
+
+namespace mlg {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ void load32(const bf16* p, float* v) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    uint4 u = q[i];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      float2 f = __bfloat1622float2(h[j]);
+      v[i * 8 + 2 * j] = f.x;
+      v[i * 8 + 2 * j + 1] = f.y;
+    }
+  }
+}
+
+__device__ __forceinline__ void store32(bf16* p, const float* v) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int j = 0; j < 4; j++) h[j] = __floats2bfloat162_rn(v[i * 8 + 2 * j], v[i * 8 + 2 * j + 1]);
+    q[i] = u;
+  }
+}
+
+// ---------------------------------------------------------------- forward --
+
+// a0[p][c] = relu(b[c] + sum_tap w[c][tap] u[p + off_tap])
+__global__ void conv_in_fwd(int B, int n, const float* __restrict__ u,
+                            const float* __restrict__ w, const float* __restrict__ bias,
+                            bf16* __restrict__ a0) {
+  __shared__ float ws[kC * 9 + kC];
+  for (int i = threadIdx.x; i < kC * 9; i += blockDim.x) ws[i] = w[i];
+  for (int i = threadIdx.x; i < kC; i += blockDim.x) ws[kC * 9 + i] = bias[i];
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= (long long)B * n * n) return;
+  const int b = (int)(p / ((long long)n * n));
+  const int r = (int)(p % ((long long)n * n));
+  const int y = r / n, x = r % n;
+  float tap[9];
+#pragma unroll
+  for (int t = 0; t < 9; t++) {
+    const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+    tap[t] = (yy >= 0 && yy < n && xx >= 0 && xx < n) ? u[((long long)b * n + yy) * n + xx] : 0.f;
+  }
+  float v[kC];
+#pragma unroll
+  for (int c = 0; c < kC; c++) {
+    float acc = ws[kC * 9 + c];
+#pragma unroll
+    for (int t = 0; t < 9; t++) acc += ws[c * 9 + t] * tap[t];
+    v[c] = fmaxf(acc, 0.f);
+  }
+  store32(a0 + p * kC, v);
+}
+
+// out = 2x2 mean of in (side s -> s/2), NHWC
+__global__ void pool2_fwd(int B, int s, const bf16* __restrict__ in, bf16* __restrict__ out) {
+  const int so = s / 2;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)B * so * so * kC) return;
+  const int c = (int)(i % kC);
+  const long long p = i / kC;
+  const int b = (int)(p / ((long long)so * so));
+  const int r = (int)(p % ((long long)so * so));
+  const int y = r / so, x = r % so;
+  const bf16* base = in + (((long long)b * s + 2 * y) * s + 2 * x) * kC + c;
+  const float v = __bfloat162float(base[0]) + __bfloat162float(base[kC]) +
+                  __bfloat162float(base[(long long)s * kC]) +
+                  __bfloat162float(base[(long long)s * kC + kC]);
+  out[i] = __float2bfloat16(0.25f * v);
+}
+
+enum ConvMode { kRelu = 0, kResid = 1, kF32 = 2 };
+
+// out[p][o] = sum_tap sum_k wop[tap][k][o] in[p + sign*dil*off_tap][k] (+ bias),
+// 32 -> 32 channels, one thread per pixel.
+//   kRelu : zo = relu(acc + bias)                       (BF16)
+//   kResid: zo = e = relu(acc + bias), to = resid + e   (BF16)
+//   kF32  : fo = acc (+ addend)                         (FP32)
+template <int MODE>
+__global__ void __launch_bounds__(128) conv32_simt(int B, int H, const bf16* __restrict__ in,
+                                                   const bf16* __restrict__ wop,
+                                                   const float* __restrict__ bias, int dil,
+                                                   int sign, bf16* __restrict__ zo,
+                                                   bf16* __restrict__ to,
+                                                   const bf16* __restrict__ resid,
+                                                   float* __restrict__ fo,
+                                                   const float* __restrict__ addend) {
+  __shared__ float ws[9 * kC * kC];
+  for (int i = threadIdx.x; i < 9 * kC * kC; i += blockDim.x) ws[i] = __bfloat162float(wop[i]);
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= (long long)B * H * H) return;
+  const int b = (int)(p / ((long long)H * H));
+  const int r = (int)(p % ((long long)H * H));
+  const int y = r / H, x = r % H;
+  float acc[kC];
+#pragma unroll
+  for (int o = 0; o < kC; o++) acc[o] = (MODE != kF32 && bias) ? bias[o] : 0.f;
+  for (int t = 0; t < 9; t++) {
+    const int yy = y + sign * dil * (t / 3 - 1);
+    const int xx = x + sign * dil * (t % 3 - 1);
+    if (yy < 0 || yy >= H || xx < 0 || xx >= H) continue;
+    float v[kC];
+    load32(in + (((long long)b * H + yy) * H + xx) * kC, v);
+    const float* wt = ws + t * kC * kC;
+#pragma unroll
+    for (int k = 0; k < kC; k++) {
+      const float vk = v[k];
+#pragma unroll
+      for (int o = 0; o < kC; o++) acc[o] += vk * wt[k * kC + o];
+    }
+  }
+  if (MODE == kRelu) {
+#pragma unroll
+    for (int o = 0; o < kC; o++) acc[o] = fmaxf(acc[o], 0.f);
+    store32(zo + p * kC, acc);
+  } else if (MODE == kResid) {
+    float sv[kC];
+    load32(resid + p * kC, sv);
+#pragma unroll
+    for (int o = 0; o < kC; o++) acc[o] = fmaxf(acc[o], 0.f);
+    store32(zo + p * kC, acc);
+#pragma unroll
+    for (int o = 0; o < kC; o++) sv[o] += acc[o];
+    store32(to + p * kC, sv);
+  } else {
+    float* dst = fo + p * kC;
+    const float* ad = addend ? addend + p * kC : nullptr;
+#pragma unroll
+    for (int o = 0; o < kC; o++) dst[o] = acc[o] + (ad ? ad[o] : 0.f);
+  }
+}
+
+// Half-pixel bilinear source position of output index i (m source points, n out).
+__device__ __forceinline__ void bilin(int i, int m, int n, int& i0, int& i1, float& lam) {
+  float src = ((float)i + 0.5f) * (float)m / (float)n - 0.5f;
+  if (src < 0.f) src = 0.f;
+  i0 = (int)floorf(src);
+  if (i0 > m - 1) i0 = m - 1;
+  i1 = min(i0 + 1, m - 1);
+  lam = src - (float)i0;
+}
+
+struct Levels {
+  const bf16* z[kMaxLevels];
+  int side[kMaxLevels];
+  int L;
+};
+
+// s[p][c] = sum_l upsample(z_l)[p][c]
+__global__ void upsum_fwd(int B, int n, Levels lv, bf16* __restrict__ s) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)B * n * n * kC) return;
+  const int c = (int)(i % kC);
+  const long long p = i / kC;
+  const int b = (int)(p / ((long long)n * n));
+  const int r = (int)(p % ((long long)n * n));
+  const int y = r / n, x = r % n;
+  float acc = __bfloat162float(lv.z[0][i]);
+  for (int l = 1; l < lv.L; l++) {
+    const int m = lv.side[l];
+    int y0, y1, x0, x1;
+    float ly, lx;
+    bilin(y, m, n, y0, y1, ly);
+    bilin(x, m, n, x0, x1, lx);
+    const bf16* z = lv.z[l] + (long long)b * m * m * kC + c;
+    const float v00 = __bfloat162float(z[((long long)y0 * m + x0) * kC]);
+    const float v01 = __bfloat162float(z[((long long)y0 * m + x1) * kC]);
+    const float v10 = __bfloat162float(z[((long long)y1 * m + x0) * kC]);
+    const float v11 = __bfloat162float(z[((long long)y1 * m + x1) * kC]);
+    acc += (1.f - ly) * ((1.f - lx) * v00 + lx * v01) + ly * ((1.f - lx) * v10 + lx * v11);
+  }
+  s[i] = __float2bfloat16(acc);
+}
+
+// y[p] = b + sum_tap sum_c w[c][tap] t[p + off_tap][c]
+__global__ void conv_out_fwd(int B, int n, const bf16* __restrict__ t,
+                             const float* __restrict__ w, const float* __restrict__ bias,
+                             float* __restrict__ y) {
+  __shared__ float ws[kC * 9];
+  for (int i = threadIdx.x; i < kC * 9; i += blockDim.x) ws[i] = w[i];
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= (long long)B * n * n) return;
+  const int b = (int)(p / ((long long)n * n));
+  const int r = (int)(p % ((long long)n * n));
+  const int yy0 = r / n, xx0 = r % n;
+  float acc = bias[0];
+  for (int tp = 0; tp < 9; tp++) {
+    const int yy = yy0 + tp / 3 - 1, xx = xx0 + tp % 3 - 1;
+    if (yy < 0 || yy >= n || xx < 0 || xx >= n) continue;
+    float v[kC];
+    load32(t + (((long long)b * n + yy) * n + xx) * kC, v);
+#pragma unroll
+    for (int c = 0; c < kC; c++) acc += ws[c * 9 + tp] * v[c];
+  }
+  y[p] = acc;
+}
+
+// --------------------------------------------------------------- backward --
+
+// gy = 2 (y - t) / (B N); per-CTA partial sums of (y - t)^2
+__global__ void mse_grad(long long total, float scale, const float* __restrict__ y,
+                         const float* __restrict__ t, float* __restrict__ gy,
+                         float* __restrict__ part) {
+  __shared__ float red[32];
+  float acc = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    gy[i] = 2.f * d * scale;
+    acc += d * d;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  }
+}
+
+__global__ void loss_finish(const float* __restrict__ part, int nparts, float scale,
+                            float* __restrict__ loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nparts; i++) s += part[i];
+    *loss = (float)(s * scale);
+  }
+}
+
+// g_t[p][c] = sum_tap w[c][tap] gy[p - off_tap]
+__global__ void conv_out_bwd_data(int B, int n, const float* __restrict__ gy,
+                                  const float* __restrict__ w, float* __restrict__ gt) {
+  __shared__ float ws[kC * 9];
+  for (int i = threadIdx.x; i < kC * 9; i += blockDim.x) ws[i] = w[i];
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= (long long)B * n * n) return;
+  const int b = (int)(p / ((long long)n * n));
+  const int r = (int)(p % ((long long)n * n));
+  const int y = r / n, x = r % n;
+  float g[9];
+#pragma unroll
+  for (int tp = 0; tp < 9; tp++) {
+    const int yy = y - (tp / 3 - 1), xx = x - (tp % 3 - 1);
+    g[tp] = (yy >= 0 && yy < n && xx >= 0 && xx < n) ? gy[((long long)b * n + yy) * n + xx] : 0.f;
+  }
+  float* dst = gt + p * kC;
+#pragma unroll
+  for (int c = 0; c < kC; c++) {
+    float acc = 0.f;
+#pragma unroll
+    for (int tp = 0; tp < 9; tp++) acc += ws[c * 9 + tp] * g[tp];
+    dst[c] = acc;
+  }
+}
+
+// Per-CTA partial weight gradients of a 1-channel <-> 32-channel 3x3 conv:
+//   part[cta][c*9 + tap] = sum_p g1[p or p+off] * x32[...][c]  and bias part[cta][288 + ...].
+// MODE 0 (output conv):  dW[c][tap] = sum_p gy[p] t[p + off][c], db = sum_p gy[p]
+// MODE 1 (input conv):   dW[c][tap] = sum_p g32[p][c] u[p + off], db[c] = sum_p g32[p][c]
+template <int MODE>
+__global__ void conv1_wgrad(int B, int n, const float* __restrict__ g1,
+                            const bf16* __restrict__ x32, const float* __restrict__ g32,
+                            const float* __restrict__ u, float* __restrict__ part,
+                            int stride) {
+  const long long total = (long long)B * n * n;
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  const long long p0 = blockIdx.x * per;
+  const long long p1 = min(total, p0 + per);
+  const int t = threadIdx.x;  // 0..319: 288 weights (c*9+tap) then 32 biases
+  float acc = 0.f;
+  if (t < kC * 9) {
+    const int c = t / 9, tp = t % 9;
+    const int dy = tp / 3 - 1, dx = tp % 3 - 1;
+    for (long long p = p0; p < p1; p++) {
+      const int b = (int)(p / ((long long)n * n));
+      const int r = (int)(p % ((long long)n * n));
+      const int yy = r / n + dy, xx = r % n + dx;
+      if (yy < 0 || yy >= n || xx < 0 || xx >= n) continue;
+      const long long q = ((long long)b * n + yy) * n + xx;
+      if (MODE == 0)
+        acc += g1[p] * __bfloat162float(x32[q * kC + c]);
+      else
+        acc += g32[p * kC + c] * u[q];
+    }
+  } else if (t < kC * 9 + kC) {
+    const int c = t - kC * 9;
+    for (long long p = p0; p < p1; p++) {
+      if (MODE == 0) {
+        if (c == 0) acc += g1[p];
+      } else {
+        acc += g32[p * kC + c];
+      }
+    }
+  }
+  if (t < kC * 9 + kC) part[(long long)blockIdx.x * stride + t] = acc;
+}
+
+// out = bf16(g * (mask > 0))
+__global__ void mask_to_bf16(long long count, const float* __restrict__ g,
+                             const bf16* __restrict__ mask, bf16* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  out[i] = __float2bfloat16(__bfloat162float(mask[i]) > 0.f ? g[i] : 0.f);
+}
+
+__global__ void mask_f32(long long count, const float* __restrict__ g,
+                         const bf16* __restrict__ mask, float* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  out[i] = __bfloat162float(mask[i]) > 0.f ? g[i] : 0.f;
+}
+
+// Per-CTA partial gradients of a 32 -> 32 conv:
+//   part[cta][(tap*32 + k)*32 + o] = sum_p in[p + dil*off_tap][k] * g[p][o]
+//   part[cta][9216 + o]            = sum_p g[p][o]
+// 288 threads: thread = (tap, k), 32 accumulators over o.
+constexpr int kWTile = 32;
+__global__ void __launch_bounds__(288) conv32_wgrad_simt(int B, int H, const bf16* __restrict__ in,
+                                                         const bf16* __restrict__ g, int dil,
+                                                         float* __restrict__ part, int stride) {
+  __shared__ float gs[kWTile][kC];
+  const long long total = (long long)B * H * H;
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  const long long p0 = blockIdx.x * per;
+  const long long p1 = min(total, p0 + per);
+  const int t = threadIdx.x;
+  const int tp = t / kC, k = t % kC;
+  const int dy = dil * (tp / 3 - 1), dx = dil * (tp % 3 - 1);
+  float acc[kC];
+#pragma unroll
+  for (int o = 0; o < kC; o++) acc[o] = 0.f;
+  float bacc = 0.f;
+  for (long long pt = p0; pt < p1; pt += kWTile) {
+    const int cnt = (int)min((long long)kWTile, p1 - pt);
+    __syncthreads();
+    for (int i = t; i < kWTile * kC; i += blockDim.x) {
+      const int px = i / kC, o = i % kC;
+      gs[px][o] = px < cnt ? __bfloat162float(g[(pt + px) * kC + o]) : 0.f;
+    }
+    __syncthreads();
+    if (t < kC)
+      for (int px = 0; px < cnt; px++) bacc += gs[px][t];
+    for (int px = 0; px < cnt; px++) {
+      const long long p = pt + px;
+      const int b = (int)(p / ((long long)H * H));
+      const int r = (int)(p % ((long long)H * H));
+      const int yy = r / H + dy, xx = r % H + dx;
+      if (yy < 0 || yy >= H || xx < 0 || xx >= H) continue;
+      const float v = __bfloat162float(in[(((long long)b * H + yy) * H + xx) * kC + k]);
+#pragma unroll
+      for (int o = 0; o < kC; o++) acc[o] += v * gs[px][o];
+    }
+  }
+  float* dst = part + (long long)blockIdx.x * stride;
+#pragma unroll
+  for (int o = 0; o < kC; o++) dst[(tp * kC + k) * kC + o] = acc[o];
+  if (t < kC) dst[9 * kC * kC + t] = bacc;
+}
+
+// grad[dst_w[i]] = sum over CTAs of part[cta][i] for the weight layout used by
+// the partial kernels; the mapping to the parameter layout [o][k][tap] is done
+// here so the parameters keep the documented order.
+//   kind 0 (32->32): part index (tap*32 + k)*32 + o  -> param (o*32 + k)*9 + tap; bias 9216 + o
+//   kind 1 (1-ch)  : part index c*9 + tap (+ 288 + c bias) -> same order
+__global__ void reduce_wgrad(const float* __restrict__ part, int nparts, int stride, int kind,
+                             float* __restrict__ gw, float* __restrict__ gb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nw = kind == 0 ? 9 * kC * kC : 9 * kC;
+  const int nb = kind == 0 ? kC : (kind == 1 ? kC : 1);
+  if (i >= nw + nb) return;
+  double s = 0.0;
+  for (int c = 0; c < nparts; c++) s += part[(long long)c * stride + i];
+  if (i < nw) {
+    if (kind == 0) {
+      const int tp = i / (kC * kC), k = (i / kC) % kC, o = i % kC;
+      gw[(o * kC + k) * 9 + tp] = (float)s;
+    } else {
+      gw[i] = (float)s;
+    }
+  } else {
+    gb[i - nw] = (float)s;
+  }
+}
+
+// gz[b][i][j][c] = sum over fine (y, x) of U[y][i] U[x][j] gs[b][y][x][c] (transpose of
+// the bilinear upsampling from m to n)
+__global__ void upsample_bwd(int B, int n, int m, const float* __restrict__ gs,
+                             float* __restrict__ gz) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)B * m * m * kC) return;
+  const int c = (int)(idx % kC);
+  const long long p = idx / kC;
+  const int b = (int)(p / ((long long)m * m));
+  const int r = (int)(p % ((long long)m * m));
+  const int i = r / m, j = r % m;
+  const float f = (float)n / (float)m;
+  const int ylo = max(0, (int)floorf((i - 1.5f) * f)), yhi = min(n - 1, (int)ceilf((i + 2.5f) * f));
+  const int xlo = max(0, (int)floorf((j - 1.5f) * f)), xhi = min(n - 1, (int)ceilf((j + 2.5f) * f));
+  float acc = 0.f;
+  for (int y = ylo; y <= yhi; y++) {
+    int y0, y1;
+    float ly;
+    bilin(y, m, n, y0, y1, ly);
+    const float wy = (y0 == i ? 1.f - ly : 0.f) + (y1 == i ? ly : 0.f);
+    if (wy == 0.f) continue;
+    for (int x = xlo; x <= xhi; x++) {
+      int x0, x1;
+      float lx;
+      bilin(x, m, n, x0, x1, lx);
+      const float wx = (x0 == j ? 1.f - lx : 0.f) + (x1 == j ? lx : 0.f);
+      if (wx == 0.f) continue;
+      acc += wy * wx * gs[(((long long)b * n + y) * n + x) * kC + c];
+    }
+  }
+  gz[idx] = acc;
+}
+
+// fine[b][y][x][c] += 0.25 coarse[b][y/2][x/2][c] (fine side s, coarse side s/2)
+__global__ void pool2_bwd_add(int B, int s, const float* __restrict__ coarse,
+                              float* __restrict__ fine) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)B * s * s * kC) return;
+  const int c = (int)(idx % kC);
+  const long long p = idx / kC;
+  const int b = (int)(p / ((long long)s * s));
+  const int r = (int)(p % ((long long)s * s));
+  const int y = r / s, x = r % s;
+  const int so = s / 2;
+  if (y / 2 >= so || x / 2 >= so) return;
+  fine[idx] += 0.25f * coarse[(((long long)b * so + y / 2) * so + x / 2) * kC + c];
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+// theta -= lr * (m / c1) / (sqrt(v / c2) + eps), c1 = 1 - b1^t, c2 = 1 - b2^t
+__global__ void adam_kernel(long long count, float* __restrict__ theta,
+                            const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, float lr, float c1, float c2) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// wq[conv][tap][k][o] = W[o][k][tap], wqT[conv][tap][o][k] = W[o][k][tap] (BF16)
+__global__ void sync_weights_kernel(int nconv, const float* __restrict__ master,
+                                    const long long* __restrict__ offs, bf16* __restrict__ wq,
+                                    bf16* __restrict__ wqT) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long per = 9LL * kC * kC;
+  if (i >= nconv * per) return;
+  const int cv = (int)(i / per);
+  const int r = (int)(i % per);
+  const int o = r / (kC * 9), k = (r / 9) % kC, tp = r % 9;
+  const bf16 v = __float2bfloat16(master[offs[cv] + r]);
+  wq[(long long)cv * per + (tp * kC + k) * kC + o] = v;
+  wqT[(long long)cv * per + (tp * kC + o) * kC + k] = v;
+}
+
+unsigned nblk(long long count, int bs) { return (unsigned)((count + bs - 1) / bs); }
+
+unsigned long long sm64(unsigned long long& st) {
+  st += 0x9E3779B97F4A7C15ull;
+  unsigned long long z = st;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+#define NN_CK(x)                          \
+  do {                                    \
+    cudaError_t e_ = (x);                 \
+    if (e_ != cudaSuccess) return e_;     \
+  } while (0)
+
+cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed) {
+  net.n = n;
+  net.bmax = bmax;
+  net.L = 0;
+  int s = n;
+  net.side[net.L++] = s;
+  while (s / 2 >= 8 && net.L < kMaxLevels) {
+    s /= 2;
+    net.side[net.L++] = s;
+  }
+  const int L = net.L;
+  long long off = 0;
+  net.off_w[0] = off; off += kC * 9;
+  net.off_b[0] = off; off += kC;
+  for (int l = 0; l < L; l++) {
+    net.off_w[1 + l] = off; off += 9LL * kC * kC;
+    net.off_b[1 + l] = off; off += kC;
+  }
+  net.off_w[L + 1] = off; off += 9LL * kC * kC;
+  net.off_b[L + 1] = off; off += kC;
+  net.off_w[L + 2] = off; off += kC * 9;
+  net.off_b[L + 2] = off; off += 1;
+  net.nparams = off;
+
+  // He-uniform initialisation from splitmix64: U[-a, a], a = sqrt(6 / fan_in);
+  // the output layer uses a = sqrt(3 / fan_in); biases start at 0.
+  std::vector<float> p((size_t)net.nparams, 0.f);
+  unsigned long long st = seed ^ 0x6A09E667F3BCC909ull;
+  auto fill = [&](long long o, long long cnt, int fan_in, float gain) {
+    const double a = sqrt(gain / fan_in);
+    for (long long i = 0; i < cnt; i++) {
+      const double u = (double)(sm64(st) >> 11) * (1.0 / 9007199254740992.0);
+      p[(size_t)(o + i)] = (float)((2.0 * u - 1.0) * a);
+    }
+  };
+  fill(net.off_w[0], kC * 9, 9, 6.f);
+  for (int l = 0; l < L; l++) fill(net.off_w[1 + l], 9LL * kC * kC, 9 * kC, 6.f);
+  fill(net.off_w[L + 1], 9LL * kC * kC, 9 * kC, 6.f);
+  fill(net.off_w[L + 2], kC * 9, 9 * kC, 3.f);
+
+  const long long np = net.nparams;
+  NN_CK(cudaMalloc(&net.master, sizeof(float) * np));
+  NN_CK(cudaMalloc(&net.grad, sizeof(float) * np));
+  NN_CK(cudaMalloc(&net.adam_m, sizeof(float) * np));
+  NN_CK(cudaMalloc(&net.adam_v, sizeof(float) * np));
+  NN_CK(cudaMemcpy(net.master, p.data(), sizeof(float) * np, cudaMemcpyHostToDevice));
+  NN_CK(cudaMemset(net.grad, 0, sizeof(float) * np));
+  NN_CK(cudaMemset(net.adam_m, 0, sizeof(float) * np));
+  NN_CK(cudaMemset(net.adam_v, 0, sizeof(float) * np));
+  const long long per = 9LL * kC * kC;
+  NN_CK(cudaMalloc(&net.wq, sizeof(bf16) * per * (L + 1)));
+  NN_CK(cudaMalloc(&net.wqT, sizeof(bf16) * per * (L + 1)));
+  long long offs[kMaxLevels + 1];
+  for (int c = 0; c < L + 1; c++) offs[c] = net.off_w[1 + c];
+  NN_CK(cudaMalloc(&net.offs_dev, sizeof(offs)));
+  NN_CK(cudaMemcpy(net.offs_dev, offs, sizeof(long long) * (L + 1), cudaMemcpyHostToDevice));
+
+  const long long full = (long long)bmax * n * n * kC;
+  NN_CK(cudaMalloc(&net.a0, sizeof(bf16) * full));
+  net.pyr = 0;
+  for (int l = 0; l < L; l++) {
+    const long long sz = (long long)bmax * net.side[l] * net.side[l] * kC;
+    if (l > 0) NN_CK(cudaMalloc(&net.pool[l], sizeof(bf16) * sz));
+    NN_CK(cudaMalloc(&net.z[l], sizeof(bf16) * sz));
+    net.lvl_off[l] = net.pyr;
+    net.pyr += sz;
+  }
+  NN_CK(cudaMalloc(&net.s, sizeof(bf16) * full));
+  NN_CK(cudaMalloc(&net.e, sizeof(bf16) * full));
+  NN_CK(cudaMalloc(&net.t, sizeof(bf16) * full));
+  NN_CK(cudaMalloc(&net.g_t, sizeof(float) * full));
+  NN_CK(cudaMalloc(&net.g_s, sizeof(float) * full));
+  NN_CK(cudaMalloc(&net.g_lvl, sizeof(float) * full));
+  NN_CK(cudaMalloc(&net.g_pool, sizeof(float) * net.pyr));
+  NN_CK(cudaMalloc(&net.g_bf, sizeof(bf16) * full));
+  int dev = 0, nsm = 0;
+  NN_CK(cudaGetDevice(&dev));
+  NN_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  net.wparts = 2 * nsm;
+  NN_CK(cudaMalloc(&net.wgrad_part, sizeof(float) * (long long)net.wparts * (per + kC)));
+  const long long pix = (long long)bmax * n * n;
+  NN_CK(cudaMalloc(&net.gy, sizeof(float) * pix));
+  NN_CK(cudaMalloc(&net.loss_part, sizeof(float) * 1024));
+  NN_CK(cudaMalloc(&net.bu, sizeof(float) * pix));
+  NN_CK(cudaMalloc(&net.bt, sizeof(float) * pix));
+  NN_CK(cudaMalloc(&net.by, sizeof(float) * pix));
+  NN_CK(net_sync_weights(net, 0));
+  return cudaDeviceSynchronize();
+}
+
+void net_destroy(Net& net) {
+  cudaFree(net.master);
+  cudaFree(net.grad);
+  cudaFree(net.adam_m);
+  cudaFree(net.adam_v);
+  cudaFree(net.wq);
+  cudaFree(net.wqT);
+  cudaFree(net.offs_dev);
+  cudaFree(net.a0);
+  for (int l = 0; l < kMaxLevels; l++) {
+    cudaFree(net.pool[l]);
+    cudaFree(net.z[l]);
+  }
+  cudaFree(net.s);
+  cudaFree(net.e);
+  cudaFree(net.t);
+  cudaFree(net.g_t);
+  cudaFree(net.g_s);
+  cudaFree(net.g_lvl);
+  cudaFree(net.g_pool);
+  cudaFree(net.g_bf);
+  cudaFree(net.wgrad_part);
+  cudaFree(net.gy);
+  cudaFree(net.loss_part);
+  cudaFree(net.bu);
+  cudaFree(net.bt);
+  cudaFree(net.by);
+  net = Net();
+}
+
+cudaError_t net_sync_weights(Net& net, cudaStream_t s) {
+  const int nconv = net.L + 1;
+  const long long tot = (long long)nconv * 9 * kC * kC;
+  sync_weights_kernel<<<nblk(tot, 256), 256, 0, s>>>(nconv, net.master, net.offs_dev, net.wq,
+                                                    net.wqT);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t s) {
+  const int n = net.n, L = net.L;
+  const long long pix = (long long)B * n * n;
+  const long long per = 9LL * kC * kC;
+  conv_in_fwd<<<nblk(pix, 256), 256, 0, s>>>(B, n, u, net.master + net.off_w[0],
+                                              net.master + net.off_b[0], net.a0);
+  note_launches(1);
+  for (int l = 1; l < L; l++) {
+    const int sp = net.side[l - 1];
+    const bf16* src = l == 1 ? net.a0 : net.pool[l - 1];
+    const long long cnt = (long long)B * net.side[l] * net.side[l] * kC;
+    pool2_fwd<<<nblk(cnt, 256), 256, 0, s>>>(B, sp, src, net.pool[l]);
+    note_launches(1);
+  }
+  for (int l = 0; l < L; l++) {
+    const int sd = net.side[l];
+    const long long np = (long long)B * sd * sd;
+    conv32_simt<kRelu><<<nblk(np, 128), 128, 0, s>>>(
+        B, sd, l == 0 ? net.a0 : net.pool[l], net.wq + per * l, net.master + net.off_b[1 + l], 1,
+        1, net.z[l], nullptr, nullptr, nullptr, nullptr);
+    note_launches(1);
+  }
+  Levels lv;
+  lv.L = L;
+  for (int l = 0; l < L; l++) {
+    lv.z[l] = net.z[l];
+    lv.side[l] = net.side[l];
+  }
+  upsum_fwd<<<nblk(pix * kC, 256), 256, 0, s>>>(B, n, lv, net.s);
+  note_launches(1);
+  conv32_simt<kResid><<<nblk(pix, 128), 128, 0, s>>>(B, n, net.s, net.wq + per * L,
+                                                     net.master + net.off_b[L + 1], 2, 1, net.e,
+                                                     net.t, net.s, nullptr, nullptr);
+  note_launches(1);
+  conv_out_fwd<<<nblk(pix, 256), 256, 0, s>>>(B, n, net.t, net.master + net.off_w[L + 2],
+                                               net.master + net.off_b[L + 2], y);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const float* target,
+                         float* loss_dev, cudaStream_t s) {
+  const int n = net.n, L = net.L;
+  const long long pix = (long long)B * n * n;
+  const long long full = pix * kC;
+  const long long per = 9LL * kC * kC;
+  const int P = net.wparts;
+  const int stride = (int)(per + kC);
+  // loss and dL/dy
+  const int lparts = 256;
+  mse_grad<<<lparts, 256, 0, s>>>(pix, 1.f / (float)pix, y, target, net.gy, net.loss_part);
+  note_launches(1);
+  loss_finish<<<1, 32, 0, s>>>(net.loss_part, lparts, 1.f / (float)pix, loss_dev);
+  note_launches(1);
+  // output conv
+  conv1_wgrad<0><<<P, 320, 0, s>>>(B, n, net.gy, net.t, nullptr, nullptr, net.wgrad_part, stride);
+  note_launches(1);
+  reduce_wgrad<<<nblk(9 * kC + 1, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 2,
+                                                     net.grad + net.off_w[L + 2],
+                                                     net.grad + net.off_b[L + 2]);
+  note_launches(1);
+  conv_out_bwd_data<<<nblk(pix, 256), 256, 0, s>>>(B, n, net.gy, net.master + net.off_w[L + 2],
+                                                   net.g_t);
+  note_launches(1);
+  // dilated residual block: t = s + e, e = relu(conv_d2(s))
+  mask_to_bf16<<<nblk(full, 256), 256, 0, s>>>(full, net.g_t, net.e, net.g_bf);
+  note_launches(1);
+  conv32_wgrad_simt<<<P, 288, 0, s>>>(B, n, net.s, net.g_bf, 2, net.wgrad_part, stride);
+  note_launches(1);
+  reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0,
+                                                   net.grad + net.off_w[L + 1],
+                                                   net.grad + net.off_b[L + 1]);
+  note_launches(1);
+  conv32_simt<kF32><<<nblk(pix, 128), 128, 0, s>>>(B, n, net.g_bf, net.wqT + per * L, nullptr, 2,
+                                                   -1, nullptr, nullptr, nullptr, net.g_s,
+                                                   net.g_t);
+  note_launches(1);
+  // pyramid levels
+  for (int l = 0; l < L; l++) {
+    const int sd = net.side[l];
+    const long long lp = (long long)B * sd * sd;
+    const float* gz = net.g_s;
+    if (l > 0) {
+      upsample_bwd<<<nblk(lp * kC, 256), 256, 0, s>>>(B, n, sd, net.g_s, net.g_lvl);
+      note_launches(1);
+      gz = net.g_lvl;
+    }
+    mask_to_bf16<<<nblk(lp * kC, 256), 256, 0, s>>>(lp * kC, gz, net.z[l], net.g_bf);
+    note_launches(1);
+    const bf16* in = l == 0 ? net.a0 : net.pool[l];
+    conv32_wgrad_simt<<<P, 288, 0, s>>>(B, sd, in, net.g_bf, 1, net.wgrad_part, stride);
+    note_launches(1);
+    reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0,
+                                                     net.grad + net.off_w[1 + l],
+                                                     net.grad + net.off_b[1 + l]);
+    note_launches(1);
+    conv32_simt<kF32><<<nblk(lp, 128), 128, 0, s>>>(B, sd, net.g_bf, net.wqT + per * l, nullptr,
+                                                    1, -1, nullptr, nullptr, nullptr,
+                                                    net.g_pool + net.lvl_off[l], nullptr);
+    note_launches(1);
+  }
+  // pooling chain: the gradient of p_{l-1} collects 0.25 of p_l's
+  for (int l = L - 1; l >= 1; l--) {
+    const int sf = net.side[l - 1];
+    const long long cnt = (long long)B * sf * sf * kC;
+    pool2_bwd_add<<<nblk(cnt, 256), 256, 0, s>>>(B, sf, net.g_pool + net.lvl_off[l],
+                                                 net.g_pool + net.lvl_off[l - 1]);
+    note_launches(1);
+  }
+  // input conv
+  mask_f32<<<nblk(full, 256), 256, 0, s>>>(full, net.g_pool + net.lvl_off[0], net.a0, net.g_lvl);
+  note_launches(1);
+  conv1_wgrad<1><<<P, 320, 0, s>>>(B, n, nullptr, nullptr, net.g_lvl, u, net.wgrad_part, stride);
+  note_launches(1);
+  reduce_wgrad<<<nblk(9 * kC + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 1,
+                                                      net.grad + net.off_w[0],
+                                                      net.grad + net.off_b[0]);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t net_adam(Net& net, float lr, cudaStream_t s) {
+  net.adam_t += 1;
+  const float c1 = 1.f - powf(0.9f, (float)net.adam_t);
+  const float c2 = 1.f - powf(0.999f, (float)net.adam_t);
+  adam_kernel<<<nblk(net.nparams, 256), 256, 0, s>>>(net.nparams, net.master, net.grad,
+                                                     net.adam_m, net.adam_v, lr, c1, c2);
+  note_launches(1);
+  NN_CK(cudaGetLastError());
+  return net_sync_weights(net, s);
+}
+
+cudaError_t net_train_batch(Net& net, int B, const float* ring_u, const float* ring_t,
+                            long long stride, const int* pick, float lr, float* loss_dev,
+                            cudaStream_t s) {
+  const long long N = (long long)net.n * net.n;
+  for (int i = 0; i < B; i++) {
+    NN_CK(cudaMemcpyAsync(net.bu + i * N, ring_u + (long long)pick[i] * stride,
+                          sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+    NN_CK(cudaMemcpyAsync(net.bt + i * N, ring_t + (long long)pick[i] * stride,
+                          sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+  }
+  NN_CK(net_forward(net, B, net.bu, net.by, s));
+  NN_CK(net_backward(net, B, net.bu, net.by, net.bt, loss_dev, s));
+  return net_adam(net, lr, s);
+}
+
+}  // namespace mlg

@@ -1,0 +1,86 @@
+// The initial-guess network N(b) (Sec. 2.1): a variation of FluidNet's pressure
+// model -- multi-resolution average-pool pyramid, one convolution per level,
+// bilinear upsampling and summation -- followed by a dilated residual block
+// and an output convolution, trained online with Adam on the MSE loss
+// (Sec. 2.3).
+//
+//   a0  = relu(conv3x3(u, W_in) + b_in)                 1 -> 32
+//   p_0 = a0, p_l = avgpool2(p_{l-1}) while the side stays >= 8
+//   z_l = relu(conv3x3(p_l, W_l) + b_l)                 32 -> 32 per level
+//   s   = sum_l upsample(z_l)   (bilinear, half-pixel centres)
+//   t   = s + relu(conv3x3_dil2(s, W_d) + b_d)          32 -> 32
+//   y   = conv3x3(t, W_out) + b_out                     32 -> 1
+//
+// Parameters live in one flat FP32 array in the order
+// in.w, in.b, level0.w, level0.b, ..., dil.w, dil.b, out.w, out.b with weights
+// [out][in][ky][kx].  The 32 -> 32 convolutions run as implicit GEMMs on the
+// tensor cores with BF16 operands and FP32 accumulation.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace mlg {
+
+constexpr int kC = 32;      // channels
+constexpr int kMaxLevels = 12;
+
+struct Net {
+  int n = 0;                // grid side
+  int L = 0;                // pyramid levels
+  int side[kMaxLevels];     // level sides
+  int bmax = 0;             // largest batch
+  long long nparams = 0;
+  long long off_w[kMaxLevels + 3];  // offsets of each conv's weights (0 in, 1..L levels, L+1 dil, L+2 out)
+  long long off_b[kMaxLevels + 3];
+  float* master = nullptr;  // FP32 parameters
+  float* grad = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  long long adam_t = 0;
+  __nv_bfloat16* wq = nullptr;  // BF16 copies of the 32->32 weights, [conv][tap][ci][co]
+  __nv_bfloat16* wqT = nullptr; // transposed taps for the data gradient, [conv][tap][co][ci]
+  long long* offs_dev = nullptr;  // device copy of the 32->32 weight offsets
+  // activations, NHWC with 32 channels, BF16 (masks are recovered from
+  // post-ReLU values: relu(x) > 0 <=> x > 0)
+  __nv_bfloat16* a0 = nullptr;               // bmax x n^2 x 32
+  __nv_bfloat16* pool[kMaxLevels] = {};      // levels 1..L-1
+  __nv_bfloat16* z[kMaxLevels] = {};         // levels 0..L-1
+  __nv_bfloat16* s = nullptr;                // sum of the levels
+  __nv_bfloat16* e = nullptr;                // relu(dilated conv)
+  __nv_bfloat16* t = nullptr;                // s + e
+  // gradients of activations (FP32 for accumulation, BF16 copies as GEMM operands)
+  float* g_t = nullptr;                      // bmax x n^2 x 32
+  float* g_s = nullptr;
+  float* g_lvl = nullptr;                    // scratch, bmax x n^2 x 32
+  float* g_pool = nullptr;                   // pooled accumulation, bmax x n^2 x 32
+  __nv_bfloat16* g_bf = nullptr;             // bf16 operand scratch
+  float* wgrad_part = nullptr;               // split-K partials of weight gradients
+  float* gy = nullptr;                       // bmax x n^2
+  float* loss_part = nullptr;
+  float* bu = nullptr;                       // gathered minibatch inputs, bmax x n^2
+  float* bt = nullptr;                       // gathered minibatch targets
+  float* by = nullptr;                       // minibatch outputs
+  long long lvl_off[kMaxLevels];             // offsets of level l inside g_pool (per sample)
+  long long pyr = 0;                         // sum of level sizes (pixels) per sample
+  int wparts = 0;                            // CTAs of the weight-gradient kernels
+};
+
+cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed);
+void net_destroy(Net& net);
+// Re-derive the BF16 operand copies from the FP32 master parameters.
+cudaError_t net_sync_weights(Net& net, cudaStream_t s);
+// y = N(u) for B samples (u, y: B x n^2 FP32).
+cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t s);
+// After net_forward on the same inputs: loss = 1/(B N) sum ||y - t||^2 into
+// *loss_dev and all parameter gradients into net.grad.
+cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const float* target,
+                         float* loss_dev, cudaStream_t s);
+// One Adam step on net.master from net.grad; refreshes the BF16 copies.
+cudaError_t net_adam(Net& net, float lr, cudaStream_t s);
+// One minibatch step: gather ring slots `pick[0..B)` (stride floats apart) of
+// inputs u and targets t, forward, backward, Adam.  *loss_dev gets the loss.
+cudaError_t net_train_batch(Net& net, int B, const float* ring_u, const float* ring_t,
+                            long long stride, const int* pick, float lr, float* loss_dev,
+                            cudaStream_t s);
+
+}  // namespace mlg

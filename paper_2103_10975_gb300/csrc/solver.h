@@ -1,0 +1,79 @@
+// Host/device structures of the persistent GMRES(m) solver.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mlg {
+
+constexpr int kMaxM = 64;          // largest supported restart length
+constexpr int kPartStride = 1024;  // max CTAs per group (partials row length)
+
+// Per-system result written by the solver (mirrors mlgmres_result's numeric part).
+struct DevResult {
+  long long iters;
+  int cycles;
+  int status;      // 0 OK, 1 NOT_CONVERGED, kErrTimeout, kErrNonfinite
+  int used_alt;    // 1 if the alternative (learned) guess replaced x
+  int pad;
+  double bnorm;
+  double relres_true;
+  double relres_first_cycle;
+  double relres_guess;
+  double relres_alt;  // residual of the alternative guess, -1 if none
+};
+
+// One linear system A x = b.
+struct SolveTask {
+  int n;                 // interior points per axis
+  int N;                 // n^dim
+  const double* b;       // rhs (or the start vector in Arnoldi mode)
+  double* x;             // guess in, solution out
+  const double* x_alt;   // optional competing guess (learned), may be null
+  const float* kappa;    // 3D cell coefficients, may be null
+  DevResult* res;
+  double* hist;          // optional |g_{j+1}|/||b|| per step (Arnoldi mode: H)
+  long long hist_cap;
+};
+
+// Workspace of one CTA group.
+struct GroupWork {
+  void* V;            // (m+1) x ldv basis, element type of the precision
+  long long ldv;
+  void* W0;           // two work vectors (ping-pong), ldv each
+  void* W1;
+  double* part;       // 2 x (kMaxM+2) x kPartStride partial sums
+  GroupBarrier bar;
+};
+
+struct KParams {
+  int m;
+  double rtol;
+  long long max_iters;
+  int arnoldi_steps;        // > 0: run that many Arnoldi steps only (inspection mode)
+  int ngroups;
+  const int* group_first;   // ngroups+1 CTA ranges
+  const int* task_first;    // ngroups+1 ranges into task_order
+  const int* task_order;    // task indices, grouped
+  const SolveTask* tasks;
+  const GroupWork* work;    // ngroups
+};
+
+// Launch the persistent cooperative solver.  `fp32` selects the FP32 inner
+// precision; dim is 2 or 3.  Returns the CUDA error of the launch.
+cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid_blocks, cudaStream_t s);
+
+// Largest co-resident grid for the chosen kernel variant (blocks), and its CTA size.
+int gmres_max_blocks(bool fp32, int dim, int m, int* block_threads);
+
+// FP64 operator application out = A u (2D or 3D) on one grid.
+cudaError_t launch_apply(int dim, int n, const float* kappa, const double* u, double* out,
+                         cudaStream_t s);
+
+// Convert the first `rows` vectors of a basis of element type fp32?float:double
+// to double (row-major, ldv -> N).
+cudaError_t launch_basis_to_f64(bool fp32, const void* V, long long ldv, int rows, int N,
+                                double* out, cudaStream_t s);
+
+}  // namespace mlg

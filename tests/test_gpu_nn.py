@@ -1,0 +1,118 @@
+"""GPU parity of the initial-guess network (Sec. 2.1) and its training step
+(Sec. 2.3) against the FP64 oracle at the same weights, through the C ABI."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import nn as onn  # noqa: E402
+from oracle import direct  # noqa: E402
+from synthetic import MovingGaussians2D  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2103_10975_gb300 import Solver  # noqa: E402
+
+
+def unpack(flat, n, C=32):
+    out = {}
+    o = 0
+    for name, shape in onn.param_shapes(n, C):
+        k = int(np.prod(shape))
+        out[name] = flat[o:o + k].astype(np.float64).reshape(shape)
+        o += k
+    assert o == len(flat)
+    return out
+
+
+def pack(d, n, C=32):
+    return np.concatenate([d[name].reshape(-1) for name, _ in onn.param_shapes(n, C)])
+
+
+def bf16_round(a):
+    t = torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float32)
+    return t.numpy().astype(np.float64)
+
+
+def sample_batch(n, B, seed):
+    gen = MovingGaussians2D(n, seed, 50)
+    us, ts = [], []
+    for t in range(B):
+        b = gen.rhs(7 * t)
+        x = direct.dst_solve_2d(n, b)
+        s = onn.rms(b)
+        us.append(b / s)
+        ts.append(x / s)
+    return np.array(us), np.array(ts)
+
+
+@pytest.mark.parametrize("n", [16, 40])
+def test_param_layout(n):
+    s = Solver(n, m=10, batch=2)
+    assert s.param_count() == sum(int(np.prod(sh)) for _, sh in onn.param_shapes(n))
+    p = s.get_params()
+    s.set_params(p * 0.5)
+    assert np.array_equal(s.get_params(), (p * 0.5).astype(np.float32))
+
+
+@pytest.mark.parametrize("n", [16, 32, 40])
+def test_forward_parity(n):
+    s = Solver(n, m=10, batch=2)
+    flat = s.get_params()
+    P = unpack(flat, n)
+    # the 32->32 convolutions use BF16 weights: give the oracle the same values
+    for k in P:
+        if k.startswith("level") and k.endswith(".w") or k == "dil.w":
+            P[k] = bf16_round(P[k])
+    u, _ = sample_batch(n, 2, 3)
+    y = s.nn_forward(torch.as_tensor(u, dtype=torch.float32).cuda()).cpu().numpy()
+    for b in range(2):
+        yr = onn.forward(P, u[b], n)
+        assert np.linalg.norm(y[b] - yr) <= 3e-2 * np.linalg.norm(yr), b
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_gradient_parity(n):
+    s = Solver(n, m=10, batch=2)
+    flat = s.get_params()
+    P = unpack(flat, n)
+    for k in P:
+        if k.startswith("level") and k.endswith(".w") or k == "dil.w":
+            P[k] = bf16_round(P[k])
+    u, t = sample_batch(n, 2, 5)
+    loss, g = s.nn_loss_grad(torch.as_tensor(u, dtype=torch.float32).cuda(),
+                             torch.as_tensor(t, dtype=torch.float32).cuda())
+    lr, gr = onn.loss_and_grads(P, u, t, n)
+    assert abs(loss - lr) <= 2e-2 * lr
+    G = unpack(g, n)
+    for name in gr:
+        ref = gr[name]
+        nrm = np.linalg.norm(ref)
+        if nrm == 0.0:
+            continue
+        assert np.linalg.norm(G[name] - ref) <= 5e-2 * nrm, (name, np.linalg.norm(G[name] - ref) / nrm)
+
+
+def test_adam_step_through_training():
+    """One training phase of one Adam step on one stored pair moves every
+    weight by -lr * sign(g) (first Adam step), g the oracle gradient."""
+    n = 16
+    lr = 1e-3
+    s = Solver(n, m=30, rtol=1e-10, guess="learned", warmup_steps=1, batch=1, train_iters=1,
+               lr=lr)
+    b = MovingGaussians2D(n, 9, 20).rhs(0)
+    bd = torch.as_tensor(b).cuda()
+    x, r = s.solve(bd)
+    assert r["admitted"] == 1 and s.replay_size() == 1
+    p0 = s.get_params()
+    sc = onn.rms(b)
+    u = (b / sc).astype(np.float32)
+    t = (x.cpu().numpy() / sc).astype(np.float32)
+    _, g = s.nn_loss_grad(torch.as_tensor(u[None]).cuda(), torch.as_tensor(t[None]).cuda())
+    s.train_step()
+    torch.cuda.synchronize()
+    p1 = s.get_params()
+    big = np.abs(g) > 1e-3 * np.abs(g).max()
+    step = (p1 - p0)[big]
+    assert np.allclose(step, -lr * np.sign(g[big]), rtol=1e-3, atol=1e-6)
