@@ -94,6 +94,11 @@ typedef struct {
   unsigned long long seed;   /* network initialisation and minibatch sampling */
   int grid_blocks;           /* solver CTAs; 0 = pick from the problem size */
   double barrier_timeout_s;  /* limit of every device-side wait (> 0) */
+  int guess_smooth;          /* damped-Jacobi sweeps applied to the learned guess before it is
+                                scored (0 = the network output as it is).  The sweeps remove
+                                the white rounding noise of the BF16 network output, which A
+                                amplifies by up to its condition number in the residual */
+  float guess_omega;         /* damping of those sweeps (0 < omega <= 1) */
   int fault_inject;          /* test hook, 0 in normal use.  1: the solver's CTA-group
                                 barrier waits for one CTA more than is launched, so its
                                 first wait runs out after barrier_timeout_s and the solve
@@ -113,13 +118,13 @@ typedef struct {
   double relres_guess;       /* ||b - A x0|| / ||b|| of the guess used */
   double relres_learned;     /* same for the learned candidate (-1 if none was formed) */
   float tos_ms;              /* device time of the solve kernel (TOS, Sec. 2.2) */
-  float guess_ms;            /* device time of the learned-guess forward pass */
+  float guess_ms;            /* device time of the learned-guess forward pass and smoothing */
 } mlgmres_result;
 
 /* Fills *opt with the defaults: m = 30, rtol = 1e-10, max_iters = 10^7, FP64,
  * guess ZERO, fallback ZERO, replay_cap 64, warmup 50, p = 10, theta = 0.9,
  * deterministic_tos 0, train_iters 32, batch 8, lr 1e-3, seed 1,
- * grid_blocks 0, barrier_timeout_s 2, fault_inject 0. */
+ * grid_blocks 0, barrier_timeout_s 2, guess_smooth 8, guess_omega 0.8, fault_inject 0. */
 void mlgmres_default_options(mlgmres_options* opt);
 
 /* Creates a solver for one grid and allocates all workspace on the current
@@ -149,7 +154,9 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
                                    void* stream, mlgmres_result* out);
 
 /* One training phase (Sec. 2.3): opt.train_iters Adam steps on the MSE loss
- * ||N(b/s) - x/s||^2 over minibatches drawn from the replay ring, each batch
+ * ||N(b/s) - x/(c s)||^2 over minibatches drawn from the replay ring (c is the
+ * mean of rms(x)/rms(b) over the ring, so the targets have unit scale; the
+ * guess is then x0 = c s N(b/s)), each batch
  * holding every pair admitted since the previous call (up to opt.batch) and
  * uniform samples of the rest.  Runs on side_stream and returns once enqueued;
  * the next solve waits for it.  loss_host (may be NULL) receives the mean loss

@@ -51,6 +51,8 @@ class Options(ctypes.Structure):
         ("seed", ctypes.c_ulonglong),
         ("grid_blocks", ctypes.c_int),
         ("barrier_timeout_s", ctypes.c_double),
+        ("guess_smooth", ctypes.c_int),
+        ("guess_omega", ctypes.c_float),
         ("fault_inject", ctypes.c_int),
     ]
 

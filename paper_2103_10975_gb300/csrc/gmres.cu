@@ -82,55 +82,165 @@ __device__ __forceinline__ T stencil(const T* __restrict__ u, int i, int n,
 }
 
 // ----------------------------------------------------------- shared state --
-template <int MAXM, int BS>
+template <typename T, int MAXM, int BS>
 struct Smem {
-  double red[BS / 32][MAXM + 2];
+  T red[BS / 32][MAXM + 2];      // per-warp partials in the working precision
+  double redd[BS / 32][4];       // per-warp partials of the FP64 residual norms
   double tot[MAXM + 2];
-  double H[(MAXM + 1) * MAXM];  // column-major, leading dimension MAXM+1
+  double cr[MAXM], sr[MAXM];     // Givens products with the unrotated column
+  double Hu[(MAXM + 1) * MAXM];  // Hessenberg as built (Arnoldi relation), ld MAXM+1
+  double R[(MAXM + 1) * MAXM];   // the same columns after the Givens rotations
   double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
-  double hn, anorm, bnorm, beta;
-  int ctl;
-  int flag;
+  T HuT[(MAXM + 1) * MAXM];      // Hu in the working precision
+  T coef[MAXM + 2];              // h1 in the working precision (gather output)
+  T h2c[MAXM + 2];               // pending second-pass coefficients of w'
+  T cc[MAXM + 2];                // A w' -> A v_j correction coefficients
+  double hn, anorm2, h2sq;
+  T invT;                        // 1 / hn in the working precision
+  int ctl, stop, flag, fallback;
 };
 
 // Warp partial of slot k (lane 0 stores it); block_finish then adds the warp
 // partials of slots 0..L-1 and writes the CTA's sums to part[k*kPartStride + lb].
-template <int LMAX>
-__device__ __forceinline__ void warp_slot(double (*red)[LMAX], int k, double v) {
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+// All of it runs in the element type R (FP32 for the FP32 variant: the FP64
+// pipe of this GPU is ~1/64 of FP32 and would otherwise dominate).
+template <int LW, typename R, typename V>
+__device__ __forceinline__ void warp_slot(R (*red)[LW], int k, V v) {
+  R x = (R)v;
+  x = warp_sum(x);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = x;
 }
 
-template <int LMAX, int BS>
-__device__ __forceinline__ void block_finish(int L, double* part, int lb, double (*red)[LMAX]) {
+// Sums acc[k] over the warp for all k < MAXM at once (butterfly transpose
+// reduction: 31 shuffles per 32 slots instead of 5 per slot); lane l ends with
+// the warp total of slot l (+32 for the second half when MAXM = 64), which it
+// stores to red[warp][slot] for slot < L.
+template <int LMAX, int MAXM, typename T>
+__device__ __forceinline__ void warp_slots(T (*red)[LMAX], T (&acc)[MAXM], int L) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < MAXM / 32; g++) {
+    T v[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = acc[g * 32 + i];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      const bool up = (lane & off) != 0;
+#pragma unroll
+      for (int i = 0; i < off; i++) {
+        const T send = up ? v[i] : v[i + off];
+        const T keep = up ? v[i + off] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+    const int slot = g * 32 + lane;
+    if (slot < L) red[warp][slot] = v[0];
+  }
+}
+
+template <int LW, int BS, typename R>
+__device__ __forceinline__ void block_finish(int L, R* part, int lb, R (*red)[LW]) {
   __syncthreads();
   for (int k = threadIdx.x; k < L; k += BS) {
-    double s = 0.0;
+    R s = R(0);
+#pragma unroll
     for (int w = 0; w < BS / 32; w++) s += red[w][k];
     part[(long long)k * kPartStride + lb] = s;
   }
 }
 
-// Sum of the group's partials for k < L, identical in every CTA.
-template <int BS>
-__device__ __forceinline__ void gather(const double* part, int L, int nb, double* tot) {
+// Sum of the group's partials for k < L, identical in every CTA (same order);
+// tot gets the sums in FP64, coef the same values in the working precision.
+template <int BS, typename R, typename T>
+__device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot, T* coef) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = warp; k < L; k += BS / 32) {
-    double s = 0.0;
+    R s = R(0);
     for (int g = lane; g < nb; g += 32) s += ldcg(part + (long long)k * kPartStride + g);
     s = warp_sum(s);
-    if (lane == 0) tot[k] = s;
+    if (lane == 0) {
+      tot[k] = (double)s;
+      coef[k] = (T)s;
+    }
   }
   __syncthreads();
 }
 
+// Givens update of Hessenberg column c (Hu -> R): apply rotations 0..c-1, form
+// rotation c, update g, and return the stop code (0 go on, 1 end the cycle,
+// 2 non-finite).  Warp 0 only: the lanes form the products of the rotations
+// with the column's untouched entries in parallel, so lane 0's dependent chain
+// is one FMA per rotation.
+template <typename T, int MAXM, int BS>
+__device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, long long it,
+                             long long max_iters, int m, double* hist, long long hist_cap,
+                             double bnorm) {
+  constexpr int LD = MAXM + 1;
+  const int lane = threadIdx.x & 31;
+  const double* hc = sm.Hu + c * LD;
+  double* rc = sm.R + c * LD;
+  for (int i = lane; i < c; i += 32) {
+    sm.cr[i] = sm.cs[i] * hc[i + 1];
+    sm.sr[i] = sm.sn[i] * hc[i + 1];
+  }
+  __syncwarp();
+  int stop = 0;
+  if (lane == 0) {
+    double ri = hc[0];
+    for (int i = 0; i < c; i++) {
+      rc[i] = fma(sm.cs[i], ri, sm.sr[i]);
+      ri = fma(-sm.sn[i], ri, sm.cr[i]);
+    }
+    const double hsub = hc[c + 1];
+    const double rho = sqrt(fma(ri, ri, hsub * hsub));
+    if (rho == 0.0) {
+      sm.cs[c] = 1.0;
+      sm.sn[c] = 0.0;
+    } else {
+      const double inv = 1.0 / rho;
+      sm.cs[c] = ri * inv;
+      sm.sn[c] = hsub * inv;
+    }
+    rc[c] = rho;
+    rc[c + 1] = 0.0;
+    const double gc = sm.g[c];
+    sm.g[c + 1] = -sm.sn[c] * gc;
+    sm.g[c] = sm.cs[c] * gc;
+    const double res = fabs(sm.g[c + 1]);
+    if (hist && it <= hist_cap) hist[it - 1] = res / bnorm;
+    if (!isfinite(res) || !isfinite(hsub))
+      stop = 2;
+    else if (res <= rtol_bnorm || !(hsub * hsub > 1e-28 * sm.anorm2) || it >= max_iters ||
+             c + 1 >= m)
+      stop = 1;
+    sm.stop = stop;
+  }
+  __syncwarp();
+  return stop;
+}
+
 // --------------------------------------------------------------- one solve --
+// Arnoldi step j of a cycle (CGS2 with two group barriers).  Entering it, the
+// work vector W holds w', the previous step's vector after its first
+// projection (w'_0 = r), h2 = V^T w' are its still unapplied second-pass
+// coefficients, hn = ||w' - V h2|| (Pythagoras) and c are the coefficients
+// that turn A w' into A v_j through the Arnoldi relation
+// A v_k = sum_i Hu(i,k) v_i:
+//   X: v_j = (w' - V h2)/hn,  z = (A w' - sum_i c_i v_i)/hn  (= A v_j),
+//      h1 = V_{0..j}^T z, ||z||^2                                 -> barrier
+//   Y: w'_{j+1} = z - V h1, h2 = V_{0..j}^T w'_{j+1}, ||w'_{j+1}||^2 -> barrier
+//   Hu(:,j) = h1 + h2, Hu(j+1,j) = hn_{j+1} = sqrt(||w'||^2 - ||h2||^2)
+// When the Pythagorean difference cancels (||h2||^2 > ||w'||^2 / 2) an
+// explicit pass applies h2 and measures the norm instead.  The Givens update
+// of column j runs on thread 0 while the CTA already starts the next X pass;
+// if it ends the cycle, that speculative pass is discarded.
 template <typename T, int DIM, int MAXM, int BS>
 __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWork& w, int lb,
-                          int nb, unsigned long long& epoch, Smem<MAXM, BS>& sm) {
+                          int nb, unsigned long long& epoch, Smem<T, MAXM, BS>& sm) {
   constexpr int LD = MAXM + 1;
   constexpr int LMAX = MAXM + 2;
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const int n = tk.n;
   const int N = tk.N;
   const int m = kp.m;
@@ -141,9 +251,11 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   const int hi = min(N, lo + chunk);
   T* __restrict__ V = (T*)w.V;
   const long long ldv = w.ldv;
-  T* bufs[2] = {(T*)w.W0, (T*)w.W1};
+  T* __restrict__ WP = (T*)w.W0;  // w' (read by neighbours in X, rewritten in Y)
+  T* __restrict__ Z = (T*)w.W1;   // z = A v_j, own rows only
   const double h = 2.0 / (n + 1);
   const double s2 = 1.0 / (h * h);
+  const T s2t = (T)s2;
   const float* kappa = tk.kappa;
   int red = 0;
   auto part = [&]() { return w.part + (long long)(red & 1) * LMAX * kPartStride; };
@@ -154,7 +266,6 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   int status = 1;
   double relres = 0.0, relres_first = -1.0, relres_guess = -1.0, relres_alt = -1.0;
   int used_alt = 0;
-  int cur = 0;
   double bnorm = 0.0;
   bool ok = true;
 
@@ -175,15 +286,15 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         v2 += r1 * r1;
       }
     }
-    warp_slot<LMAX>(sm.red, 0, v0);
+    warp_slot<4>(sm.redd, 0, v0);
     if (alt) {
-      warp_slot<LMAX>(sm.red, 1, v1);
-      warp_slot<LMAX>(sm.red, 2, v2);
+      warp_slot<4>(sm.redd, 1, v1);
+      warp_slot<4>(sm.redd, 2, v2);
     }
-    block_finish<LMAX, BS>(alt ? 3 : 1, part(), lb, sm.red);
+    block_finish<4, BS, double>(alt ? 3 : 1, part(), lb, sm.redd);
     ok = group_sync(w.bar, epoch, &sm.flag);
     if (!ok) goto abort;
-    gather<BS>(part(), alt ? 3 : 1, nb, sm.tot);
+    gather<BS, double, T>(part(), alt ? 3 : 1, nb, sm.tot, sm.coef);
     red++;
     bnorm = sqrt(sm.tot[0]);
     if (bnorm == 0.0) {  // A x = 0 has the unique solution 0
@@ -207,10 +318,9 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   }
 
   for (;;) {
-    // ---- restart: P = r = b - A x (FP64), beta = ||r||
+    // ---- restart: w'_0 = r = b - A x (FP64), beta = ||r||
     {
       double v0 = 0.0;
-      T* P = bufs[cur];
       for (int i = lo + tid; i < hi; i += BS) {
         double ri;
         if (arnoldi) {
@@ -219,14 +329,18 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
           const double xc = ldcg(tk.x + i);
           ri = tk.b[i] - s2 * stencil<double, DIM>(tk.x, i, n, kappa, xc);
         }
-        P[i] = (T)ri;
+        WP[i] = (T)ri;
         v0 += ri * ri;
       }
-      warp_slot<LMAX>(sm.red, 0, v0);
-      block_finish<LMAX, BS>(1, part(), lb, sm.red);
+      for (int k = tid; k < LMAX; k += BS) {
+        sm.h2c[k] = T(0);
+        sm.cc[k] = T(0);
+      }
+      warp_slot<4>(sm.redd, 0, v0);
+      block_finish<4, BS, double>(1, part(), lb, sm.redd);
       ok = group_sync(w.bar, epoch, &sm.flag);
       if (!ok) goto abort;
-      gather<BS>(part(), 1, nb, sm.tot);
+      gather<BS, double, T>(part(), 1, nb, sm.tot, sm.coef);
       red++;
     }
     const double beta = sqrt(sm.tot[0]);
@@ -241,157 +355,183 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       if (iters >= kp.max_iters) { status = 1; break; }
     }
     if (beta == 0.0) { status = 0; break; }
-    double hn = beta;  // norm of the unnormalised vector in bufs[cur]
     if (tid == 0) {
       for (int k = 0; k <= MAXM; k++) sm.g[k] = 0.0;
       sm.g[0] = beta;
+      sm.hn = beta;
+      sm.invT = (T)(1.0 / beta);
+      sm.stop = 0;
     }
+    __syncthreads();
+    const double rtol_bnorm = kp.rtol * bnorm;
+    double* hist = (lb == 0) ? tk.hist : nullptr;
     int kcols = 0;
     const int jmax = arnoldi ? kp.arnoldi_steps : m;
-    for (int j = 0; j < jmax; j++) {
-      T* P = bufs[cur];
-      T* Q = bufs[cur ^ 1];
-      // ---- phase A: v_j = P/hn, w = A v_j, h1 = V^T w, ||w||^2
+    for (int j = 0;; j++) {
+      // ---- X: v_j and z = A v_j, h1 = V^T z; warp 0 first rotates column j-1
       {
         T acc[MAXM];
 #pragma unroll
         for (int k = 0; k < MAXM; k++) acc[k] = T(0);
-        T accA = T(0);
-        const T inv = (T)(1.0 / hn);
-        const T sc = (T)(s2 / hn);
+        T accZ = T(0);
+        const T inv = sm.invT;
+        const T cj = sm.cc[j];
+        if (tid < 32 && j > 0 && !arnoldi)
+          givens_column<T, MAXM, BS>(sm, j - 1, rtol_bnorm, iters, kp.max_iters, m, hist,
+                                     tk.hist_cap, bnorm);
         for (int i = lo + tid; i < hi; i += BS) {
-          const T pc = ldcg(P + i);
-          const T q = stencil<T, DIM>(P, i, n, kappa, pc) * sc;
-          const T vj = pc * inv;
+          const T wp = ldcg(WP + i);
+          T znum = s2t * stencil<T, DIM>(WP, i, n, kappa, wp);
+          T vnum = wp;
+          T col[MAXM];
+#pragma unroll
+          for (int k = 0; k < MAXM; k++) {
+            if (k < j) {
+              col[k] = V[(long long)k * ldv + i];
+              vnum -= sm.h2c[k] * col[k];
+              znum -= sm.cc[k] * col[k];
+            }
+          }
+          const T vj = vnum * inv;
+          const T z = (znum - cj * vj) * inv;
           V[(long long)j * ldv + i] = vj;
-          Q[i] = q;
-          accA += q * q;
+          Z[i] = z;
+          accZ += z * z;
 #pragma unroll
           for (int k = 0; k < MAXM; k++) {
             if (k < j)
-              acc[k] += V[(long long)k * ldv + i] * q;
+              acc[k] += col[k] * z;
             else if (k == j)
-              acc[k] += vj * q;
+              acc[k] += vj * z;
           }
         }
-#pragma unroll
-        for (int k = 0; k < MAXM; k++)
-          if (k <= j) warp_slot<LMAX>(sm.red, k, (double)acc[k]);
-        warp_slot<LMAX>(sm.red, j + 1, (double)accA);  // slot j+1 carries ||w||^2
-        block_finish<LMAX, BS>(j + 2, part(), lb, sm.red);
+        warp_slots<LMAX, MAXM, T>(sm.red, acc, min(j + 1, MAXM));
+        warp_slot<LMAX>(sm.red, min(j + 1, MAXM + 1), accZ);
+        block_finish<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red);
+        __syncthreads();
+        const int stop = sm.stop;
+        if (stop == 2) { status = kErrNonfinite; goto finish; }
+        if (stop == 1 || (arnoldi && j == jmax)) { kcols = j; break; }
         ok = group_sync(w.bar, epoch, &sm.flag);
         if (!ok) goto abort;
-        gather<BS>(part(), j + 2, nb, sm.tot);
+        gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef);
         red++;
-        if (tid <= j) sm.H[tid + j * LD] = sm.tot[tid];
-        if (tid == 0) sm.anorm = sqrt(sm.tot[j + 1]);
+        if (tid <= j) sm.Hu[tid + j * LD] = sm.tot[tid];
+        if (tid == 0) sm.anorm2 = sm.tot[j + 1];
       }
-      // ---- phase B: w -= V h1, h2 = V^T w
+      // ---- Y: w'_{j+1} = z - V h1, h2 = V^T w'_{j+1}, ||w'_{j+1}||^2
       {
         T acc[MAXM];
 #pragma unroll
         for (int k = 0; k < MAXM; k++) acc[k] = T(0);
+        T accN = T(0);
         for (int i = lo + tid; i < hi; i += BS) {
-          T q = Q[i];
+          T q = Z[i];
           T col[MAXM];
 #pragma unroll
           for (int k = 0; k < MAXM; k++) {
             if (k <= j) {
               col[k] = V[(long long)k * ldv + i];
-              q -= (T)sm.tot[k] * col[k];
+              q -= sm.coef[k] * col[k];
             }
           }
-          Q[i] = q;
+          WP[i] = q;
+          accN += q * q;
 #pragma unroll
           for (int k = 0; k < MAXM; k++)
             if (k <= j) acc[k] += col[k] * q;
         }
-#pragma unroll
-        for (int k = 0; k < MAXM; k++)
-          if (k <= j) warp_slot<LMAX>(sm.red, k, (double)acc[k]);
-        block_finish<LMAX, BS>(j + 1, part(), lb, sm.red);
+        warp_slots<LMAX, MAXM, T>(sm.red, acc, j + 1);
+        warp_slot<LMAX>(sm.red, j + 1, accN);
+        block_finish<LMAX, BS, T>(j + 2, (T*)part(), lb, sm.red);
         ok = group_sync(w.bar, epoch, &sm.flag);
         if (!ok) goto abort;
-        gather<BS>(part(), j + 1, nb, sm.tot);
-        red++;
-        if (tid <= j) sm.H[tid + j * LD] += sm.tot[tid];
-      }
-      // ---- phase C: w -= V h2, ||w||^2
-      {
-        T accN = T(0);
-        for (int i = lo + tid; i < hi; i += BS) {
-          T q = Q[i];
-#pragma unroll
-          for (int k = 0; k < MAXM; k++)
-            if (k <= j) q -= (T)sm.tot[k] * V[(long long)k * ldv + i];
-          Q[i] = q;
-          accN += q * q;
-        }
-        warp_slot<LMAX>(sm.red, 0, (double)accN);
-        block_finish<LMAX, BS>(1, part(), lb, sm.red);
-        ok = group_sync(w.bar, epoch, &sm.flag);
-        if (!ok) goto abort;
-        gather<BS>(part(), 1, nb, sm.tot);
+        gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef);
         red++;
       }
-      // ---- Hessenberg column j, Givens rotation, convergence test
-      hn = sqrt(sm.tot[0]);
       iters++;
-      kcols = j + 1;
-      if (tid == 0) {
-        double* hc = sm.H + j * LD;
-        hc[j + 1] = hn;
-        int stop = 0;
-        if (arnoldi) {
-          if (lb == 0 && tk.hist)  // unrotated column j, leading dimension jmax+1
-            for (int k = 0; k <= j + 1; k++) tk.hist[(long long)j * (jmax + 1) + k] = hc[k];
-          if (!(hn > 1e-14 * sm.anorm)) stop = 1;
-        } else {
-          for (int i = 0; i < j; i++) {
-            const double t = sm.cs[i] * hc[i] + sm.sn[i] * hc[i + 1];
-            hc[i + 1] = -sm.sn[i] * hc[i] + sm.cs[i] * hc[i + 1];
-            hc[i] = t;
-          }
-          const double rho = hypot(hc[j], hn);
-          if (rho == 0.0) {
-            sm.cs[j] = 1.0;
-            sm.sn[j] = 0.0;
-          } else {
-            sm.cs[j] = hc[j] / rho;
-            sm.sn[j] = hn / rho;
-          }
-          hc[j] = rho;
-          hc[j + 1] = 0.0;
-          sm.g[j + 1] = -sm.sn[j] * sm.g[j];
-          sm.g[j] = sm.cs[j] * sm.g[j];
-          const double res = fabs(sm.g[j + 1]);
-          if (lb == 0 && tk.hist && iters <= tk.hist_cap) tk.hist[iters - 1] = res / bnorm;
-          if (!isfinite(res) || !isfinite(hn)) stop = 2;
-          else if (res <= kp.rtol * bnorm || !(hn > 1e-14 * sm.anorm) || iters >= kp.max_iters)
-            stop = 1;
+      // ---- column j of Hu; hn_{j+1} = sqrt(||w'||^2 - ||h2||^2)
+      if (tid <= j) {
+        const double hv = sm.Hu[tid + j * LD] + sm.tot[tid];
+        sm.Hu[tid + j * LD] = hv;
+        sm.HuT[tid + j * LD] = (T)hv;
+        sm.h2c[tid] = sm.coef[tid];
+      }
+      if (tid < 32) {
+        T q = T(0);
+        for (int k = lane; k <= j; k += 32) q += sm.coef[k] * sm.coef[k];
+        q = warp_sum(q);
+        if (lane == 0) {
+          const double wn2 = sm.tot[j + 1];
+          const double hn2 = wn2 - (double)q;
+          sm.fallback = !(hn2 > 0.5 * wn2);
+          sm.h2sq = hn2;
         }
-        sm.ctl = stop;
       }
       __syncthreads();
-      const int stop = sm.ctl;
-      if (stop == 2) { status = kErrNonfinite; goto finish_x; }
-      cur ^= 1;
-      if (stop) break;
+      if (sm.fallback) {
+        // cancellation: apply h2 explicitly and measure ||w''||
+        T accN = T(0);
+        for (int i = lo + tid; i < hi; i += BS) {
+          T q = WP[i];
+#pragma unroll
+          for (int k = 0; k < MAXM; k++)
+            if (k <= j) q -= sm.h2c[k] * V[(long long)k * ldv + i];
+          WP[i] = q;
+          accN += q * q;
+        }
+        warp_slot<LMAX>(sm.red, 0, accN);
+        block_finish<LMAX, BS, T>(1, (T*)part(), lb, sm.red);
+        ok = group_sync(w.bar, epoch, &sm.flag);
+        if (!ok) goto abort;
+        gather<BS, T, T>((const T*)part(), 1, nb, sm.tot, sm.coef);
+        red++;
+        if (tid == 0) sm.h2sq = sm.tot[0];
+        if (tid <= j) sm.h2c[tid] = T(0);
+        __syncthreads();
+      }
+      if (tid < 32) {
+        if (lane == 0) {
+          const double hnext = sqrt(fmax(sm.h2sq, 0.0));
+          sm.hn = hnext;
+          sm.invT = (T)(1.0 / hnext);
+          sm.Hu[j + 1 + j * LD] = hnext;
+          sm.HuT[j + 1 + j * LD] = (T)hnext;
+          if (arnoldi) {
+            if (hist)
+              for (int k = 0; k <= j + 1; k++) hist[(long long)j * (jmax + 1) + k] = sm.Hu[k + j * LD];
+            sm.stop = !(hnext * hnext > 1e-28 * sm.anorm2) ? 1 : 0;
+          }
+        }
+        __syncwarp();
+        // c_i = sum_{k >= i-1} Hu(i,k) h2_k for the next X pass
+        for (int i = lane; i <= j + 1; i += 32) {
+          T c = T(0);
+          for (int k = (i > 0 ? i - 1 : 0); k <= j; k++) c += sm.HuT[i + k * LD] * sm.h2c[k];
+          sm.cc[i] = c;
+        }
+      }
+      __syncthreads();
+      if (!arnoldi && j + 1 >= m) {
+        // last column of the cycle: rotate it now (no further X pass)
+        if (tid < 32)
+          givens_column<T, MAXM, BS>(sm, j, rtol_bnorm, iters, kp.max_iters, m, hist,
+                                     tk.hist_cap, bnorm);
+        __syncthreads();
+        if (sm.stop == 2) { status = kErrNonfinite; goto finish; }
+        kcols = j + 1;
+        break;
+      }
     }
     if (arnoldi) {
-      // store the last basis vector too, so V_{k+1} is complete
-      const T inv = (T)(1.0 / hn);
-      const T* P = bufs[cur];
-      for (int i = lo + tid; i < hi; i += BS) V[(long long)kcols * ldv + i] = ldcg(P + i) * inv;
-      status = kcols;  // steps done
+      status = kcols;  // steps done; V_0..V_kcols written by the X passes
       break;
     }
-    // ---- cycle end: y = H^{-1} g (upper triangular), x += V y
+    // ---- cycle end: y = R^{-1} g (upper triangular), x += V y
     if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
       for (int i = kcols - 1; i >= 0; i--) {
-        const double yi = sm.g[i] / sm.H[i + i * LD];
-        for (int l = lane; l < i; l += 32) sm.g[l] -= sm.H[l + i * LD] * yi;
+        const double yi = sm.g[i] / sm.R[i + i * LD];
+        for (int l = lane; l < i; l += 32) sm.g[l] -= sm.R[l + i * LD] * yi;
         if (lane == 0) sm.y[i] = yi;
         __syncwarp();
       }
@@ -406,10 +546,6 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
     ok = group_sync(w.bar, epoch, &sm.flag);
     if (!ok) goto abort;
   }
-  goto finish;
-
-finish_x:
-  // non-finite Hessenberg data: keep x as it is
   goto finish;
 
 abort:
@@ -435,7 +571,8 @@ finish:
 
 template <typename T, int DIM, int MAXM, int BS>
 __global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
-  __shared__ Smem<MAXM, BS> sm;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<T, MAXM, BS>& sm = *reinterpret_cast<Smem<T, MAXM, BS>*>(smem_raw);
   int g = 0;
   while (g + 1 < kp.ngroups && (int)blockIdx.x >= kp.group_first[g + 1]) g++;
   const int lb = blockIdx.x - kp.group_first[g];
@@ -452,12 +589,22 @@ __global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
 }
 
 // ------------------------------------------------------------- host side --
+// The shared state lives in dynamic shared memory (up to ~107 KB for m <= 64).
+template <typename T, int DIM, int MAXM, int BS>
+static cudaError_t prepare_t() {
+  return cudaFuncSetAttribute(gmres_persistent<T, DIM, MAXM, BS>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(Smem<T, MAXM, BS>));
+}
+
 template <typename T, int DIM, int MAXM, int BS>
 static cudaError_t launch_t(const KParams& kp, int grid, cudaStream_t s) {
+  cudaError_t e = prepare_t<T, DIM, MAXM, BS>();
+  if (e != cudaSuccess) return e;
   void* args[] = {(void*)&kp};
   note_launches(1);
   return cudaLaunchCooperativeKernel((const void*)gmres_persistent<T, DIM, MAXM, BS>, dim3(grid),
-                                     dim3(BS), args, 0, s);
+                                     dim3(BS), args, sizeof(Smem<T, MAXM, BS>), s);
 }
 
 template <typename T, int DIM, int MAXM, int BS>
@@ -465,7 +612,9 @@ static int max_blocks_t(int* bs) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gmres_persistent<T, DIM, MAXM, BS>, BS, 0);
+  if (prepare_t<T, DIM, MAXM, BS>() != cudaSuccess) return 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gmres_persistent<T, DIM, MAXM, BS>, BS,
+                                                sizeof(Smem<T, MAXM, BS>));
   *bs = BS;
   return per * nsm;
 }

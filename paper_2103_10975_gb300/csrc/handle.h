@@ -58,6 +58,9 @@ struct mlgmres {
   int ring_head = 0;                  // next slot to write
   std::vector<int> fresh;             // slots admitted since the last train call (C_t)
   std::vector<double> E_hist, T_hist;
+  std::vector<double> ring_c;         // rms(x)/rms(b) of each stored pair
+  double c_train = 1.0;               // target scale used by the last training phase
+  double* x_tmp = nullptr;            // smoothing ping-pong buffer
   long long solves = 0;
   double* ddots = nullptr;            // device dots for the spread check
   double* hdots = nullptr;            // pinned

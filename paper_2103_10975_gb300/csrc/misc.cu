@@ -36,14 +36,32 @@ __global__ void normalise_kernel(const double* __restrict__ b, int N, const doub
   u[i] = (float)(b[i] / s);
 }
 
-// x = s y
+// x = scale s y
 __global__ void denormalise_kernel(const float* __restrict__ y, int N, const double* sumsq,
-                                   double* __restrict__ x) {
+                                   double scale, double* __restrict__ x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double s = sqrt(*sumsq / N);
   if (!(s > 0.0)) s = 1.0;
-  x[i] = s * (double)y[i];
+  x[i] = scale * s * (double)y[i];
+}
+
+// One damped-Jacobi sweep on the 2D operator: out = in + omega/d (b - A in),
+// d = 4/h^2 the diagonal of A.
+__global__ void jacobi_kernel(int n, const double* __restrict__ b, const double* __restrict__ xin,
+                              double* __restrict__ xout, double omega) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * n) return;
+  const int ix = i % n, iy = i / n;
+  const double c = xin[i];
+  const double l = ix > 0 ? xin[i - 1] : 0.0;
+  const double r = ix < n - 1 ? xin[i + 1] : 0.0;
+  const double d = iy > 0 ? xin[i - n] : 0.0;
+  const double t = iy < n - 1 ? xin[i + n] : 0.0;
+  const double h = 2.0 / (n + 1);
+  const double s2 = 1.0 / (h * h);
+  const double ax = s2 * (((c - l) + (c - r)) + ((c - d) + (c - t)));
+  xout[i] = c + omega / (4.0 * s2) * (b[i] - ax);
 }
 
 // ring pair: u = b/s, t = x/s
@@ -111,9 +129,15 @@ cudaError_t launch_normalise(const double* b, int N, const double* sumsq, float*
   note_launches(1);
   return cudaGetLastError();
 }
-cudaError_t launch_denormalise(const float* y, int N, const double* sumsq, double* x,
-                               cudaStream_t s) {
-  denormalise_kernel<<<blocks_for(N), 256, 0, s>>>(y, N, sumsq, x);
+cudaError_t launch_jacobi(int n, const double* b, const double* xin, double* xout, double omega,
+                          cudaStream_t s) {
+  jacobi_kernel<<<blocks_for(n * n), 256, 0, s>>>(n, b, xin, xout, omega);
+  note_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_denormalise(const float* y, int N, const double* sumsq, double scale,
+                               double* x, cudaStream_t s) {
+  denormalise_kernel<<<blocks_for(N), 256, 0, s>>>(y, N, sumsq, scale, x);
   note_launches(1);
   return cudaGetLastError();
 }

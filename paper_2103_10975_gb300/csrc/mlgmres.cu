@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -81,6 +82,8 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
   ARG(o->barrier_timeout_s > 0.0 && o->barrier_timeout_s <= 60.0,
       "barrier_timeout_s must be in (0, 60]");
   ARG(o->fault_inject == 0 || o->fault_inject == 1, "fault_inject must be 0 or 1");
+  ARG(o->guess_smooth >= 0 && o->guess_smooth <= 1000, "guess_smooth must be in 0..1000");
+  ARG(o->guess_omega > 0.0f && o->guess_omega <= 1.0f, "guess_omega must be in (0, 1]");
 }
 
 // Run the persistent kernel for `count` tasks already staged in h->htasks,
@@ -203,8 +206,17 @@ int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_r
   if (h->ring_count < h->opt.replay_cap) h->ring_count++;
   h->fresh.erase(std::remove(h->fresh.begin(), h->fresh.end(), slot), h->fresh.end());
   CK(launch_sumsq(b, h->N, h->scal + 1, s));
+  CK(launch_sumsq(x, h->N, h->scal + 2, s));
   CK(launch_store_pair(b, x, h->N, h->scal + 1, h->ring_u + (long long)slot * h->ldv,
                        h->ring_t + (long long)slot * h->ldv, s));
+  CK(cudaMemcpyAsync(h->hdots, h->scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  {
+    const double bb = h->hdots[0], xx = h->hdots[1];
+    const double ci = bb > 0.0 ? sqrt(xx / bb) : 1.0;
+    if ((int)h->ring_c.size() < h->opt.replay_cap) h->ring_c.resize(h->opt.replay_cap, 0.0);
+    h->ring_c[slot] = (std::isfinite(ci) && ci > 0.0) ? ci : 1.0;
+  }
   h->fresh.push_back(slot);
   return 1;
 }
@@ -233,6 +245,9 @@ void mlgmres_default_options(mlgmres_options* o) {
   o->seed = 1;
   o->grid_blocks = 0;
   o->barrier_timeout_s = 2.0;
+  o->guess_smooth = 8;
+  o->guess_omega = 0.8f;
+  o->fault_inject = 0;
 }
 
 mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* opt,
@@ -287,6 +302,7 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     if (grid->dim == 2) {
       // learned-guess machinery (the network is two-dimensional)
       CK(cudaMalloc(&h->x_alt, sizeof(double) * h->ldv));
+      CK(cudaMalloc(&h->x_tmp, sizeof(double) * h->ldv));
       CK(cudaMalloc(&h->u_in, sizeof(float) * h->ldv));
       CK(cudaMalloc(&h->y_out, sizeof(float) * h->ldv));
       CK(cudaMalloc(&h->ring_u, sizeof(float) * h->ldv * opt->replay_cap));
@@ -324,6 +340,7 @@ void mlgmres_destroy(mlgmres_t h) {
   cudaFreeHost(h->hwork);
   cudaFree(h->x_prev);
   cudaFree(h->x_alt);
+  cudaFree(h->x_tmp);
   cudaFree(h->u_in);
   cudaFree(h->y_out);
   cudaFree(h->scal);
@@ -376,8 +393,15 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
       CK(launch_sumsq(b, N, h->scal, s));
       CK(launch_normalise(b, N, h->scal, h->u_in, s));
       CK(net_forward(h->net, 1, h->u_in, h->y_out, s));
-      CK(launch_denormalise(h->y_out, N, h->scal, h->x_alt, s));
-      x_alt = h->x_alt;
+      // guess = c s N(b/s), then optional damped-Jacobi smoothing
+      double* cur = h->x_alt;
+      double* oth = h->x_tmp;
+      CK(launch_denormalise(h->y_out, N, h->scal, h->c_train, cur, s));
+      for (int k = 0; k < h->opt.guess_smooth; k++) {
+        CK(launch_jacobi(h->grid.n, b, cur, oth, (double)h->opt.guess_omega, s));
+        std::swap(cur, oth);
+      }
+      x_alt = cur;
     }
     SolveTask t;
     t.n = h->grid.n;
@@ -437,6 +461,11 @@ mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_ho
     // before returning, so everything they enqueued is complete here.
     const int B = std::min(h->opt.batch, std::max(1, h->ring_count));
     std::vector<int> pick(B);
+    // unit-scale targets: t / c with c the mean rms(x)/rms(b) over the ring
+    double csum = 0.0;
+    for (int i = 0; i < h->ring_count; i++) csum += h->ring_c[i];
+    h->c_train = csum > 0.0 ? csum / h->ring_count : 1.0;
+    const float tscale = (float)(1.0 / h->c_train);
     for (int it = 0; it < h->opt.train_iters; it++) {
       int k = 0;
       for (int f : h->fresh) {
@@ -444,8 +473,8 @@ mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_ho
         pick[k++] = f;
       }
       while (k < B) pick[k++] = (int)(splitmix_next(h->rng_state) % (unsigned long long)h->ring_count);
-      CK(net_train_batch(h->net, B, h->ring_u, h->ring_t, h->ldv, pick.data(), h->opt.lr,
-                         h->loss_dev, s));
+      CK(net_train_batch(h->net, B, h->ring_u, h->ring_t, h->ldv, pick.data(), tscale,
+                         h->opt.lr, h->loss_dev, s));
     }
     CK(cudaEventRecord(h->train_done, s));
     h->train_pending = true;
@@ -579,7 +608,7 @@ mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u, cons
     float* y = nullptr;
     CK(cudaMallocAsync(&y, sizeof(float) * (size_t)batch * h->N, s));
     CK(net_forward(h->net, batch, u, y, s));
-    CK(net_backward(h->net, batch, u, y, t, h->loss_dev, s));
+    CK(net_backward(h->net, batch, u, y, t, 1.0f, h->loss_dev, s));
     CK(cudaMemcpyAsync(loss_host, h->loss_dev, sizeof(float), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(grad_host, h->net.grad, sizeof(float) * h->net.nparams,
                        cudaMemcpyDeviceToHost, s));

@@ -221,15 +221,15 @@ __global__ void conv_out_fwd(int B, int n, const bf16* __restrict__ t,
 
 // --------------------------------------------------------------- backward --
 
-// gy = 2 (y - t) / (B N); per-CTA partial sums of (y - t)^2
-__global__ void mse_grad(long long total, float scale, const float* __restrict__ y,
+// gy = 2 (y - ts t) / (B N); per-CTA partial sums of (y - ts t)^2
+__global__ void mse_grad(long long total, float scale, float ts, const float* __restrict__ y,
                          const float* __restrict__ t, float* __restrict__ gy,
                          float* __restrict__ part) {
   __shared__ float red[32];
   float acc = 0.f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const float d = y[i] - t[i];
+    const float d = y[i] - ts * t[i];
     gy[i] = 2.f * d * scale;
     acc += d * d;
   }
@@ -675,7 +675,7 @@ cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t 
 }
 
 cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const float* target,
-                         float* loss_dev, cudaStream_t s) {
+                         float tscale, float* loss_dev, cudaStream_t s) {
   const int n = net.n, L = net.L;
   const long long pix = (long long)B * n * n;
   const long long full = pix * kC;
@@ -684,7 +684,8 @@ cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const 
   const int stride = (int)(per + kC);
   // loss and dL/dy
   const int lparts = 256;
-  mse_grad<<<lparts, 256, 0, s>>>(pix, 1.f / (float)pix, y, target, net.gy, net.loss_part);
+  mse_grad<<<lparts, 256, 0, s>>>(pix, 1.f / (float)pix, tscale, y, target, net.gy,
+                                  net.loss_part);
   note_launches(1);
   loss_finish<<<1, 32, 0, s>>>(net.loss_part, lparts, 1.f / (float)pix, loss_dev);
   note_launches(1);
@@ -767,8 +768,8 @@ cudaError_t net_adam(Net& net, float lr, cudaStream_t s) {
 }
 
 cudaError_t net_train_batch(Net& net, int B, const float* ring_u, const float* ring_t,
-                            long long stride, const int* pick, float lr, float* loss_dev,
-                            cudaStream_t s) {
+                            long long stride, const int* pick, float tscale, float lr,
+                            float* loss_dev, cudaStream_t s) {
   const long long N = (long long)net.n * net.n;
   for (int i = 0; i < B; i++) {
     NN_CK(cudaMemcpyAsync(net.bu + i * N, ring_u + (long long)pick[i] * stride,
@@ -777,7 +778,7 @@ cudaError_t net_train_batch(Net& net, int B, const float* ring_u, const float* r
                           sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
   }
   NN_CK(net_forward(net, B, net.bu, net.by, s));
-  NN_CK(net_backward(net, B, net.bu, net.by, net.bt, loss_dev, s));
+  NN_CK(net_backward(net, B, net.bu, net.by, net.bt, tscale, loss_dev, s));
   return net_adam(net, lr, s);
 }
 

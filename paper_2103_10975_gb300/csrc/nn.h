@@ -71,16 +71,16 @@ void net_destroy(Net& net);
 cudaError_t net_sync_weights(Net& net, cudaStream_t s);
 // y = N(u) for B samples (u, y: B x n^2 FP32).
 cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t s);
-// After net_forward on the same inputs: loss = 1/(B N) sum ||y - t||^2 into
-// *loss_dev and all parameter gradients into net.grad.
+// After net_forward on the same inputs: loss = 1/(B N) sum ||y - tscale t||^2
+// into *loss_dev and all parameter gradients into net.grad.
 cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const float* target,
-                         float* loss_dev, cudaStream_t s);
+                         float tscale, float* loss_dev, cudaStream_t s);
 // One Adam step on net.master from net.grad; refreshes the BF16 copies.
 cudaError_t net_adam(Net& net, float lr, cudaStream_t s);
 // One minibatch step: gather ring slots `pick[0..B)` (stride floats apart) of
 // inputs u and targets t, forward, backward, Adam.  *loss_dev gets the loss.
 cudaError_t net_train_batch(Net& net, int B, const float* ring_u, const float* ring_t,
-                            long long stride, const int* pick, float lr, float* loss_dev,
-                            cudaStream_t s);
+                            long long stride, const int* pick, float tscale, float lr,
+                            float* loss_dev, cudaStream_t s);
 
 }  // namespace mlg

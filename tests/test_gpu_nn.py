@@ -108,7 +108,9 @@ def test_adam_step_through_training():
     p0 = s.get_params()
     sc = onn.rms(b)
     u = (b / sc).astype(np.float32)
-    t = (x.cpu().numpy() / sc).astype(np.float32)
+    t = x.cpu().numpy() / sc
+    # the training phase scales targets to unit rms: t / (rms(x) / rms(b))
+    t = (t / onn.rms(t)).astype(np.float32)
     _, g = s.nn_loss_grad(torch.as_tensor(u[None]).cuda(), torch.as_tensor(t[None]).cuda())
     s.train_step()
     torch.cuda.synchronize()
