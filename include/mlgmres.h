@@ -212,6 +212,34 @@ mlgmres_status mlgmres_replay_size(mlgmres_t h, int* count);
  * handles).  Used to count the kernels inside a timed region. */
 mlgmres_status mlgmres_kernel_launches(long long* count);
 
+/* ---- solving without allocating ------------------------------------------ */
+
+/* The paper has no counterpart to this entry point.
+ *
+ * Solves A x = b on a 2D n x n grid like mlgmres_solve with guess ZERO and
+ * FP32-refined precision, but allocates no device memory at all: no handle is
+ * created, and the Krylov basis, work vectors, partial sums and barrier state
+ * live in one fixed array compiled into the library (about 10 MB, held on every
+ * GPU that loads the library until the process exits).  It is meant for
+ * callers that cannot call cudaMalloc -- a code whose memory pool has already
+ * taken all free device memory, a host thread that must not enter an
+ * allocator while it solves, or a plug-in that is not allowed to own device
+ * memory.
+ *   n, m:            n*n <= 65536 (grids up to 256 x 256) and 1 <= m <= 32;
+ *                    larger sizes return MLGMRES_ERR_ARG.
+ *   rtol, max_iters: as in mlgmres_options.
+ *   b_dev, x_dev:    caller-owned device arrays of n*n doubles (b input, x output).
+ *   res:             may be NULL.
+ * The first call on a device looks up the array's device address for that
+ * device; make that first call before capturing a stream into a CUDA graph.
+ * Every call uses the same array and it keeps the last call's contents (the
+ * barrier state is cleared at the start of each call): calls that overlap on
+ * the GPU -- from two streams or two threads -- race with each other and must
+ * be serialised by the caller.  Synchronises the stream before returning. */
+mlgmres_status mlgmres_solve_static(int n, int m, double rtol, long long max_iters,
+                                    const double* b_dev, double* x_dev, void* stream,
+                                    mlgmres_result* res);
+
 #ifdef __cplusplus
 }
 #endif

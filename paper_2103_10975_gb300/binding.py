@@ -105,6 +105,9 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_float), _vp]),
     "mlgmres_replay_size": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "mlgmres_kernel_launches": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong)]),
+    "mlgmres_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_longlong, _vp, _vp, _vp,
+                                            ctypes.POINTER(Result)]),
 }
 
 _lib = None
@@ -139,6 +142,16 @@ def kernel_launches():
     c = ctypes.c_longlong(0)
     load_library().mlgmres_kernel_launches(ctypes.byref(c))
     return c.value
+
+
+def solve_static(n, b, x, m=30, rtol=1e-10, max_iters=10 ** 7, stream=None):
+    """mlgmres_solve_static: the FP32-refined solve from x0 = 0 without any
+    device allocation (n*n <= 65536, m <= 32).  Returns (status, result dict)."""
+    r = Result()
+    st = load_library().mlgmres_solve_static(int(n), int(m), float(rtol), int(max_iters),
+                                             _ptr(b), _ptr(x), _stream_handle(stream),
+                                             ctypes.byref(r))
+    return st, r.as_dict()
 
 
 class MLGMRESError(RuntimeError):
