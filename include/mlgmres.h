@@ -93,6 +93,9 @@ typedef struct {
   float lr;                  /* Adam learning rate */
   unsigned long long seed;   /* network initialisation and minibatch sampling */
   int grid_blocks;           /* solver CTAs; 0 = pick from the problem size */
+  int batch_slots;           /* CTA groups reserved for mlgmres_solve_batch (0 = none); each
+                                holds a basis for the handle's grid, and at most the number
+                                of co-resident CTAs is used */
   double barrier_timeout_s;  /* limit of every device-side wait (> 0) */
   int guess_smooth;          /* damped-Jacobi sweeps applied to the learned guess before it is
                                 scored (0 = the network output as it is).  The sweeps remove
@@ -124,7 +127,8 @@ typedef struct {
 /* Fills *opt with the defaults: m = 30, rtol = 1e-10, max_iters = 10^7, FP64,
  * guess ZERO, fallback ZERO, replay_cap 64, warmup 50, p = 10, theta = 0.9,
  * deterministic_tos 0, train_iters 32, batch 8, lr 1e-3, seed 1,
- * grid_blocks 0, barrier_timeout_s 2, guess_smooth 8, guess_omega 0.8, fault_inject 0. */
+ * grid_blocks 0, batch_slots 0, barrier_timeout_s 2, guess_smooth 8, guess_omega 0.8,
+ * fault_inject 0. */
 void mlgmres_default_options(mlgmres_options* opt);
 
 /* Creates a solver for one grid and allocates all workspace on the current
@@ -143,12 +147,16 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
 mlgmres_status mlgmres_solve(mlgmres_t h, const double* b_dev, double* x_dev, void* stream,
                              mlgmres_result* res);
 
-/* Solves `count` independent systems, each on its own grid (grids[i].dim must
- * equal the handle's dim and grids[i].n must not exceed the handle's n), in one
- * persistent launch.  b_dev[i], x_dev[i]: device arrays of grids[i].n^dim
- * doubles; b_dev and x_dev themselves are HOST arrays of device pointers.
- * Guesses are ZERO (or USER when the handle's mode is USER); no pair is
- * collected.  out: `count` results (host).  Returns the worst status. */
+/* Solves `count` (1..4096) independent systems, each on its own grid
+ * (grids[i].dim must equal the handle's dim, grids[i].n must not exceed the
+ * handle's n; 3D grids may carry their own kappa), in one persistent launch.
+ * The handle must have been created with batch_slots > 0: every CTA group
+ * (one CTA each) works through a list of systems, the lists balanced
+ * largest-first by an n^(dim+2) cost estimate.  b_dev[i], x_dev[i]: device
+ * arrays of grids[i].n^dim doubles; b_dev and x_dev themselves are HOST arrays
+ * of device pointers.  Guesses are ZERO (USER when the handle's mode is USER);
+ * no pair is collected.  out: `count` results (host); tos_ms of each is the
+ * whole launch.  Returns the worst status. */
 mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* grids,
                                    const double* const* b_dev, double* const* x_dev,
                                    void* stream, mlgmres_result* out);

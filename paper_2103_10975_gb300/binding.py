@@ -50,6 +50,7 @@ class Options(ctypes.Structure):
         ("lr", ctypes.c_float),
         ("seed", ctypes.c_ulonglong),
         ("grid_blocks", ctypes.c_int),
+        ("batch_slots", ctypes.c_int),
         ("barrier_timeout_s", ctypes.c_double),
         ("guess_smooth", ctypes.c_int),
         ("guess_omega", ctypes.c_float),
@@ -243,12 +244,13 @@ class Solver:
         d["status_code"] = st
         return x, d
 
-    def solve_batch(self, ns, bs, xs=None, stream=None):
+    def solve_batch(self, ns, bs, xs=None, stream=None, kappas=None):
         import torch
         count = len(ns)
         grids = (Grid * count)()
         for i, n in enumerate(ns):
-            grids[i] = Grid(self.dim, int(n), None)
+            kp = None if kappas is None or kappas[i] is None else _ptr(kappas[i])
+            grids[i] = Grid(self.dim, int(n), kp)
         if xs is None:
             xs = [torch.empty_like(b) for b in bs]
         bp = (ctypes.c_void_p * count)(*[b.data_ptr() for b in bs])

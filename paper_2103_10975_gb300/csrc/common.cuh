@@ -58,9 +58,14 @@ struct GroupBarrier {
   unsigned long long timeout_ns;
 };
 
-__device__ __forceinline__ bool group_sync(const GroupBarrier& gb, unsigned long long& epoch,
-                                           int* s_flag) {
+// side() runs on warp 1 while thread 0 waits at the barrier (work that would
+// otherwise sit on the critical path between two barriers).
+template <typename Side>
+__device__ __forceinline__ bool group_sync_with(const GroupBarrier& gb,
+                                                unsigned long long& epoch, int* s_flag,
+                                                Side side) {
   __syncthreads();
+  if ((threadIdx.x >> 5) == 1) side();
   if (gb.nblocks == 1) {  // a one-CTA group only needs the CTA barrier
     if (threadIdx.x == 0) *s_flag = (*(volatile int*)gb.err == kErrNone);
     __syncthreads();
@@ -89,6 +94,15 @@ __device__ __forceinline__ bool group_sync(const GroupBarrier& gb, unsigned long
   }
   __syncthreads();
   return *s_flag != 0;
+}
+
+struct NoSide {
+  __device__ void operator()() const {}
+};
+
+__device__ __forceinline__ bool group_sync(const GroupBarrier& gb, unsigned long long& epoch,
+                                           int* s_flag) {
+  return group_sync_with(gb, epoch, s_flag, NoSide());
 }
 
 }  // namespace mlg

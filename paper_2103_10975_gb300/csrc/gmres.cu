@@ -97,6 +97,7 @@ struct Smem {
   T cc[MAXM + 2];                // A w' -> A v_j correction coefficients
   double hn, anorm2, h2sq;
   T invT;                        // 1 / hn in the working precision
+  T hn2T;                        // ||w'||^2 - ||h2||^2 in the working precision
   int ctl, stop, flag, fallback;
 };
 
@@ -139,28 +140,45 @@ __device__ __forceinline__ void warp_slots(T (*red)[LMAX], T (&acc)[MAXM], int L
 }
 
 template <int LW, int BS, typename R>
-__device__ __forceinline__ void block_finish(int L, R* part, int lb, R (*red)[LW]) {
+__device__ __forceinline__ void block_finish(int L, R* part, int lb, R (*red)[LW], int ps) {
   __syncthreads();
   for (int k = threadIdx.x; k < L; k += BS) {
     R s = R(0);
 #pragma unroll
     for (int w = 0; w < BS / 32; w++) s += red[w][k];
-    part[(long long)k * kPartStride + lb] = s;
+    part[(long long)k * ps + lb] = s;
   }
 }
 
 // Sum of the group's partials for k < L, identical in every CTA (same order);
 // tot gets the sums in FP64, coef the same values in the working precision.
+// Each warp takes up to four slots at a time so their loads are in flight
+// together.
 template <int BS, typename R, typename T>
-__device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot, T* coef) {
+__device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot, T* coef,
+                                       int ps) {
+  constexpr int NW = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = warp; k < L; k += BS / 32) {
-    R s = R(0);
-    for (int g = lane; g < nb; g += 32) s += ldcg(part + (long long)k * kPartStride + g);
-    s = warp_sum(s);
+  for (int k0 = warp; k0 < L; k0 += 4 * NW) {
+    R s[4] = {R(0), R(0), R(0), R(0)};
+    for (int g = lane; g < nb; g += 32) {
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int k = k0 + q * NW;
+        if (k < L) s[q] += ldcg(part + (long long)k * ps + g);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) s[q] = warp_sum(s[q]);
     if (lane == 0) {
-      tot[k] = (double)s;
-      coef[k] = (T)s;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int k = k0 + q * NW;
+        if (k < L) {
+          tot[k] = (double)s[q];
+          coef[k] = (T)s[q];
+        }
+      }
     }
   }
   __syncthreads();
@@ -239,6 +257,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
                           int nb, unsigned long long& epoch, Smem<T, MAXM, BS>& sm) {
   constexpr int LD = MAXM + 1;
   constexpr int LMAX = MAXM + 2;
+  // grid points per thread per loop trip (their loads are in flight together)
+  constexpr int U = (sizeof(T) * MAXM <= 128) ? 2 : 1;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int n = tk.n;
@@ -258,7 +278,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   const T s2t = (T)s2;
   const float* kappa = tk.kappa;
   int red = 0;
-  auto part = [&]() { return w.part + (long long)(red & 1) * LMAX * kPartStride; };
+  const int ps = w.pstride;
+  auto part = [&]() { return w.part + (long long)(red & 1) * LMAX * ps; };
   const bool leader = (lb == 0 && tid == 0);
 
   long long iters = 0;
@@ -277,6 +298,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
     for (int i = lo + tid; i < hi; i += BS) {
       const double bi = tk.b[i];
       v0 += bi * bi;
+      if (tk.zero_x) tk.x[i] = 0.0;
       if (alt) {
         const double xc = ldcg(tk.x + i);
         const double r0 = bi - s2 * stencil<double, DIM>(tk.x, i, n, kappa, xc);
@@ -291,10 +313,10 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       warp_slot<4>(sm.redd, 1, v1);
       warp_slot<4>(sm.redd, 2, v2);
     }
-    block_finish<4, BS, double>(alt ? 3 : 1, part(), lb, sm.redd);
+    block_finish<4, BS, double>(alt ? 3 : 1, part(), lb, sm.redd, ps);
     ok = group_sync(w.bar, epoch, &sm.flag);
     if (!ok) goto abort;
-    gather<BS, double, T>(part(), alt ? 3 : 1, nb, sm.tot, sm.coef);
+    gather<BS, double, T>(part(), alt ? 3 : 1, nb, sm.tot, sm.coef, ps);
     red++;
     bnorm = sqrt(sm.tot[0]);
     if (bnorm == 0.0) {  // A x = 0 has the unique solution 0
@@ -337,10 +359,10 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         sm.cc[k] = T(0);
       }
       warp_slot<4>(sm.redd, 0, v0);
-      block_finish<4, BS, double>(1, part(), lb, sm.redd);
+      block_finish<4, BS, double>(1, part(), lb, sm.redd, ps);
       ok = group_sync(w.bar, epoch, &sm.flag);
       if (!ok) goto abort;
-      gather<BS, double, T>(part(), 1, nb, sm.tot, sm.coef);
+      gather<BS, double, T>(part(), 1, nb, sm.tot, sm.coef, ps);
       red++;
     }
     const double beta = sqrt(sm.tot[0]);
@@ -368,7 +390,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
     int kcols = 0;
     const int jmax = arnoldi ? kp.arnoldi_steps : m;
     for (int j = 0;; j++) {
-      // ---- X: v_j and z = A v_j, h1 = V^T z; warp 0 first rotates column j-1
+      // ---- X: v_j and z = A v_j, h1 = V^T z; warp 1 rotates column j-1
+      // while thread 0 waits at the group barrier
       {
         T acc[MAXM];
 #pragma unroll
@@ -376,45 +399,65 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         T accZ = T(0);
         const T inv = sm.invT;
         const T cj = sm.cc[j];
-        if (tid < 32 && j > 0 && !arnoldi)
-          givens_column<T, MAXM, BS>(sm, j - 1, rtol_bnorm, iters, kp.max_iters, m, hist,
-                                     tk.hist_cap, bnorm);
-        for (int i = lo + tid; i < hi; i += BS) {
-          const T wp = ldcg(WP + i);
-          T znum = s2t * stencil<T, DIM>(WP, i, n, kappa, wp);
-          T vnum = wp;
-          T col[MAXM];
+        for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
+          int ii[U];
+          bool ok_[U];
+          T wp[U], znum[U], vnum[U];
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            ii[u] = i0 + u * BS;
+            ok_[u] = ii[u] < hi;
+            wp[u] = ok_[u] ? ldcg(WP + ii[u]) : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
+            vnum[u] = wp[u];
+          }
+          T col[U][MAXM];
 #pragma unroll
           for (int k = 0; k < MAXM; k++) {
             if (k < j) {
-              col[k] = V[(long long)k * ldv + i];
-              vnum -= sm.h2c[k] * col[k];
-              znum -= sm.cc[k] * col[k];
+#pragma unroll
+              for (int u = 0; u < U; u++) {
+                col[u][k] = ok_[u] ? V[(long long)k * ldv + ii[u]] : T(0);
+                vnum[u] -= sm.h2c[k] * col[u][k];
+                znum[u] -= sm.cc[k] * col[u][k];
+              }
             }
           }
-          const T vj = vnum * inv;
-          const T z = (znum - cj * vj) * inv;
-          V[(long long)j * ldv + i] = vj;
-          Z[i] = z;
-          accZ += z * z;
 #pragma unroll
-          for (int k = 0; k < MAXM; k++) {
-            if (k < j)
-              acc[k] += col[k] * z;
-            else if (k == j)
-              acc[k] += vj * z;
+          for (int u = 0; u < U; u++) {
+            const T vj = vnum[u] * inv;
+            const T z = (znum[u] - cj * vj) * inv;
+            if (ok_[u]) {
+              V[(long long)j * ldv + ii[u]] = vj;
+              Z[ii[u]] = z;
+            }
+            accZ += z * z;
+#pragma unroll
+            for (int k = 0; k < MAXM; k++) {
+              if (k < j)
+                acc[k] += col[u][k] * z;
+              else if (k == j)
+                acc[k] += vj * z;
+            }
           }
         }
         warp_slots<LMAX, MAXM, T>(sm.red, acc, min(j + 1, MAXM));
         warp_slot<LMAX>(sm.red, min(j + 1, MAXM + 1), accZ);
-        block_finish<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red);
-        __syncthreads();
+        block_finish<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red, ps);
+        if (arnoldi && j == jmax) { kcols = j; break; }
+        ok = group_sync_with(w.bar, epoch, &sm.flag, [&]() {
+          if (j > 0 && !arnoldi)
+            givens_column<T, MAXM, BS>(sm, j - 1, rtol_bnorm, iters, kp.max_iters, m, hist,
+                                       tk.hist_cap, bnorm);
+        });
+        if (!ok) goto abort;
         const int stop = sm.stop;
         if (stop == 2) { status = kErrNonfinite; goto finish; }
-        if (stop == 1 || (arnoldi && j == jmax)) { kcols = j; break; }
-        ok = group_sync(w.bar, epoch, &sm.flag);
-        if (!ok) goto abort;
-        gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef);
+        if (stop == 1) { kcols = j; break; }
+        gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef, ps);
         red++;
         if (tid <= j) sm.Hu[tid + j * LD] = sm.tot[tid];
         if (tid == 0) sm.anorm2 = sm.tot[j + 1];
@@ -425,32 +468,47 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
 #pragma unroll
         for (int k = 0; k < MAXM; k++) acc[k] = T(0);
         T accN = T(0);
-        for (int i = lo + tid; i < hi; i += BS) {
-          T q = Z[i];
-          T col[MAXM];
+        for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
+          int ii[U];
+          bool ok_[U];
+          T q[U];
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            ii[u] = i0 + u * BS;
+            ok_[u] = ii[u] < hi;
+            q[u] = ok_[u] ? Z[ii[u]] : T(0);
+          }
+          T col[U][MAXM];
 #pragma unroll
           for (int k = 0; k < MAXM; k++) {
             if (k <= j) {
-              col[k] = V[(long long)k * ldv + i];
-              q -= sm.coef[k] * col[k];
+#pragma unroll
+              for (int u = 0; u < U; u++) {
+                col[u][k] = ok_[u] ? V[(long long)k * ldv + ii[u]] : T(0);
+                q[u] -= sm.coef[k] * col[u][k];
+              }
             }
           }
-          WP[i] = q;
-          accN += q * q;
 #pragma unroll
-          for (int k = 0; k < MAXM; k++)
-            if (k <= j) acc[k] += col[k] * q;
+          for (int u = 0; u < U; u++) {
+            if (ok_[u]) WP[ii[u]] = q[u];
+            accN += q[u] * q[u];
+#pragma unroll
+            for (int k = 0; k < MAXM; k++)
+              if (k <= j) acc[k] += col[u][k] * q[u];
+          }
         }
         warp_slots<LMAX, MAXM, T>(sm.red, acc, j + 1);
         warp_slot<LMAX>(sm.red, j + 1, accN);
-        block_finish<LMAX, BS, T>(j + 2, (T*)part(), lb, sm.red);
+        block_finish<LMAX, BS, T>(j + 2, (T*)part(), lb, sm.red, ps);
         ok = group_sync(w.bar, epoch, &sm.flag);
         if (!ok) goto abort;
-        gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef);
+        gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef, ps);
         red++;
       }
       iters++;
-      // ---- column j of Hu; hn_{j+1} = sqrt(||w'||^2 - ||h2||^2)
+      // ---- column j of Hu; hn_{j+1} = sqrt(||w'||^2 - ||h2||^2), in the working
+      // precision (both terms come from reductions in that precision)
       if (tid <= j) {
         const double hv = sm.Hu[tid + j * LD] + sm.tot[tid];
         sm.Hu[tid + j * LD] = hv;
@@ -462,10 +520,10 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         for (int k = lane; k <= j; k += 32) q += sm.coef[k] * sm.coef[k];
         q = warp_sum(q);
         if (lane == 0) {
-          const double wn2 = sm.tot[j + 1];
-          const double hn2 = wn2 - (double)q;
-          sm.fallback = !(hn2 > 0.5 * wn2);
-          sm.h2sq = hn2;
+          const T wn2 = sm.coef[j + 1];
+          const T hn2 = wn2 - q;
+          sm.fallback = !(hn2 > T(0.5) * wn2);
+          sm.hn2T = hn2;
         }
       }
       __syncthreads();
@@ -481,22 +539,24 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
           accN += q * q;
         }
         warp_slot<LMAX>(sm.red, 0, accN);
-        block_finish<LMAX, BS, T>(1, (T*)part(), lb, sm.red);
+        block_finish<LMAX, BS, T>(1, (T*)part(), lb, sm.red, ps);
         ok = group_sync(w.bar, epoch, &sm.flag);
         if (!ok) goto abort;
-        gather<BS, T, T>((const T*)part(), 1, nb, sm.tot, sm.coef);
+        gather<BS, T, T>((const T*)part(), 1, nb, sm.tot, sm.coef, ps);
         red++;
-        if (tid == 0) sm.h2sq = sm.tot[0];
+        if (tid == 0) sm.hn2T = sm.coef[0];
         if (tid <= j) sm.h2c[tid] = T(0);
         __syncthreads();
       }
       if (tid < 32) {
         if (lane == 0) {
-          const double hnext = sqrt(fmax(sm.h2sq, 0.0));
+          const T h2v = sm.hn2T > T(0) ? sm.hn2T : T(0);
+          const T hnT = sqrt(h2v);
+          sm.invT = T(1) / hnT;
+          const double hnext = (double)hnT;
           sm.hn = hnext;
-          sm.invT = (T)(1.0 / hnext);
           sm.Hu[j + 1 + j * LD] = hnext;
-          sm.HuT[j + 1 + j * LD] = (T)hnext;
+          sm.HuT[j + 1 + j * LD] = hnT;
           if (arnoldi) {
             if (hist)
               for (int k = 0; k <= j + 1; k++) hist[(long long)j * (jmax + 1) + k] = sm.Hu[k + j * LD];

@@ -38,6 +38,11 @@ struct mlgmres {
   mlg::GroupWork* hwork = nullptr;    // pinned staging
   int cfg_cap = 0;                    // capacity (tasks) of the config buffers
   int group_cap = 0;                  // capacity (groups) of the group buffers
+  // batched solves: one-CTA groups with their own bases
+  int batch_groups = 0;
+  void* Vb = nullptr;
+  void* Wb = nullptr;                 // 2 work vectors per group
+  double* partb = nullptr;
 
   // ---- guess state ----
   double* x_prev = nullptr;

@@ -17,6 +17,8 @@ using namespace mlg;
 
 namespace {
 
+constexpr int kBatchCap = 4096;  // most systems per mlgmres_solve_batch call
+
 struct Fail {
   mlgmres_status st;
 };
@@ -79,6 +81,7 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
   ARG(o->batch >= 1 && o->batch <= 64, "batch must be in 1..64");
   ARG(o->lr > 0.0f, "lr must be positive");
   ARG(o->grid_blocks >= 0, "grid_blocks must be >= 0");
+  ARG(o->batch_slots >= 0 && o->batch_slots <= 4096, "batch_slots must be in 0..4096");
   ARG(o->barrier_timeout_s > 0.0 && o->barrier_timeout_s <= 60.0,
       "barrier_timeout_s must be in (0, 60]");
   ARG(o->fault_inject == 0 || o->fault_inject == 1, "fault_inject must be 0 or 1");
@@ -119,6 +122,7 @@ GroupWork single_group_work(mlgmres* h, int nblocks) {
   w.W0 = h->W0;
   w.W1 = h->W1;
   w.part = h->part;
+  w.pstride = kPartStride;
   w.bar.ctr = h->bar;
   w.bar.err = h->err;
   // fault_inject = 1 makes the barrier wait for a CTA that is never launched
@@ -244,6 +248,7 @@ void mlgmres_default_options(mlgmres_options* o) {
   o->lr = 1e-3f;
   o->seed = 1;
   o->grid_blocks = 0;
+  o->batch_slots = 0;
   o->barrier_timeout_s = 2.0;
   o->guess_smooth = 8;
   o->guess_omega = 0.8f;
@@ -282,6 +287,15 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     CK(cudaMalloc(&h->part, sizeof(double) * 2 * (kMaxM + 2) * kPartStride));
     h->group_cap = 1;
     h->cfg_cap = 1;
+    if (opt->batch_slots > 0) {
+      h->batch_groups = std::min(opt->batch_slots, h->max_blocks);
+      h->group_cap = std::max(h->group_cap, h->batch_groups);
+      h->cfg_cap = kBatchCap;
+      const size_t G = (size_t)h->batch_groups;
+      CK(cudaMalloc(&h->Vb, es * G * (size_t)(opt->m + 1) * h->ldv));
+      CK(cudaMalloc(&h->Wb, es * G * 2 * (size_t)h->ldv));
+      CK(cudaMalloc(&h->partb, sizeof(double) * G * 2 * (kMaxM + 2)));
+    }
     CK(cudaMalloc(&h->bar, sizeof(unsigned long long) * h->group_cap));
     CK(cudaMalloc(&h->err, sizeof(int) * h->group_cap));
     CK(cudaMalloc(&h->dres, sizeof(DevResult) * h->cfg_cap));
@@ -324,6 +338,9 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
 
 void mlgmres_destroy(mlgmres_t h) {
   if (!h) return;
+  cudaFree(h->Vb);
+  cudaFree(h->Wb);
+  cudaFree(h->partb);
   cudaFree(h->V);
   cudaFree(h->W0);
   cudaFree(h->W1);
@@ -413,6 +430,7 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
     t.res = h->dres;
     t.hist = nullptr;
     t.hist_cap = 0;
+    t.zero_x = 0;
     stage_single(h, t, h->blocks);
     CK(cudaEventRecord(h->ev0, s));
     run_solver(h, 1, 1, h->blocks, 0, s);
@@ -443,9 +461,99 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
                                    const double* const* b, double* const* x, void* stream,
                                    mlgmres_result* out) {
   if (!h) return MLGMRES_ERR_ARG;
-  h->last_error = "solve_batch is not available on this handle";
-  (void)count; (void)grids; (void)b; (void)x; (void)stream; (void)out;
-  return MLGMRES_ERR_ARG;
+  h->last_error.clear();
+  try {
+    ARG(h->batch_groups > 0, "the handle was created with batch_slots = 0");
+    ARG(count >= 1 && count <= kBatchCap, "count must be in 1..4096");
+    ARG(grids && b && x && out, "null argument");
+    for (int i = 0; i < count; i++) {
+      ARG(grids[i].dim == h->grid.dim, "every grid must have the handle's dim");
+      ARG(grids[i].n >= 1 && grids[i].n <= h->grid.n, "grid side out of range");
+      ARG(grids[i].dim == 3 || grids[i].kappa_dev == nullptr, "kappa is for 3D grids only");
+      ARG(b[i] && x[i] && b[i] != x[i], "b and x must be distinct device pointers");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int G = std::min(h->batch_groups, count);
+    const int dim = h->grid.dim;
+    // largest first onto the least-loaded group (iterations grow about like n^2,
+    // so the work of a system is about N n^2)
+    std::vector<int> order(count);
+    std::vector<double> cost(count);
+    for (int i = 0; i < count; i++) {
+      order[i] = i;
+      const double n = grids[i].n;
+      cost[i] = grid_points(dim, grids[i].n) * n * n;
+    }
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<double> load(G, 0.0);
+    std::vector<std::vector<int>> lists(G);
+    for (int i : order) {
+      int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      load[g] += cost[i];
+      lists[g].push_back(i);
+    }
+    int* gf = h->hcfg;
+    int* tf = h->hcfg + (G + 1);
+    int* to = h->hcfg + 2 * (G + 1);
+    int pos = 0;
+    for (int g = 0; g < G; g++) {
+      gf[g] = g;
+      tf[g] = pos;
+      for (int i : lists[g]) to[pos++] = i;
+    }
+    gf[G] = G;
+    tf[G] = pos;
+    const size_t es = h->fp32 ? sizeof(float) : sizeof(double);
+    for (int i = 0; i < count; i++) {
+      SolveTask t;
+      t.n = grids[i].n;
+      t.N = (int)grid_points(dim, grids[i].n);
+      t.b = b[i];
+      t.x = x[i];
+      t.x_alt = nullptr;
+      t.kappa = grids[i].kappa_dev;
+      t.res = h->dres + i;
+      t.hist = nullptr;
+      t.hist_cap = 0;
+      t.zero_x = h->opt.guess == MLGMRES_GUESS_USER ? 0 : 1;
+      h->htasks[i] = t;
+    }
+    for (int g = 0; g < G; g++) {
+      GroupWork w;
+      w.V = (char*)h->Vb + es * (size_t)g * (h->opt.m + 1) * h->ldv;
+      w.ldv = h->ldv;
+      w.W0 = (char*)h->Wb + es * (size_t)g * 2 * h->ldv;
+      w.W1 = (char*)w.W0 + es * h->ldv;
+      w.part = h->partb + (size_t)g * 2 * (kMaxM + 2);
+      w.pstride = 1;
+      w.bar.ctr = h->bar + g;
+      w.bar.err = h->err + g;
+      w.bar.nblocks = 1;
+      w.bar.timeout_ns = (unsigned long long)(h->opt.barrier_timeout_s * 1e9);
+      h->hwork[g] = w;
+    }
+    CK(cudaEventRecord(h->ev0, s));
+    run_solver(h, G, count, G, 0, s);
+    CK(cudaEventRecord(h->ev1, s));
+    CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult) * count, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    int worst = MLGMRES_OK;
+    for (int i = 0; i < count; i++) {
+      memset(&out[i], 0, sizeof(out[i]));
+      fill_result(h->hres[i], &out[i]);
+      out[i].guess_used = h->opt.guess == MLGMRES_GUESS_USER ? MLGMRES_GUESS_USER : MLGMRES_GUESS_ZERO;
+      out[i].relres_learned = -1.0;
+      out[i].tos_ms = ms;
+      const int st = out[i].status;
+      if (st < 0 && (worst >= 0 || st < worst)) worst = st;
+      else if (worst == MLGMRES_OK && st == MLGMRES_NOT_CONVERGED) worst = st;
+    }
+    return (mlgmres_status)worst;
+  } catch (const Fail& f) {
+    return f.st;
+  }
 }
 
 mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_host) {
@@ -526,6 +634,7 @@ mlgmres_status mlgmres_arnoldi(mlgmres_t h, const double* v0, int steps, double*
     t.res = h->dres;
     t.hist = Hd;
     t.hist_cap = (long long)(steps + 1) * steps;
+    t.zero_x = 0;
     stage_single(h, t, h->blocks);
     run_solver(h, 1, 1, h->blocks, steps, s);
     CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));

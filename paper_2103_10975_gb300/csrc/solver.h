@@ -35,6 +35,7 @@ struct SolveTask {
   DevResult* res;
   double* hist;          // optional |g_{j+1}|/||b|| per step (Arnoldi mode: H)
   long long hist_cap;
+  int zero_x;            // 1: the solve starts from x = 0 (written by the kernel)
 };
 
 // Workspace of one CTA group.
@@ -43,7 +44,8 @@ struct GroupWork {
   long long ldv;
   void* W0;           // two work vectors (ping-pong), ldv each
   void* W1;
-  double* part;       // 2 x (kMaxM+2) x kPartStride partial sums
+  double* part;       // 2 x (kMaxM+2) x pstride partial sums
+  int pstride;        // row length of part (>= the group's CTA count)
   GroupBarrier bar;
 };
 

@@ -101,12 +101,14 @@ extern "C" mlgmres_status mlgmres_solve_static(int n, int m, double rtol, long l
   t.res = dres;
   t.hist = nullptr;
   t.hist_cap = 0;
+  t.zero_x = 0;
   GroupWork w;
   w.V = V;
   w.ldv = kStaticLdv;
   w.W0 = W0;
   w.W1 = W1;
   w.part = part;
+  w.pstride = kPartStride;
   w.bar.ctr = bar;
   w.bar.err = err;
   w.bar.nblocks = (unsigned)blocks;

@@ -235,3 +235,60 @@ def test_3d_constant_kappa_vs_dst():
     s = Solver(n, dim=3, m=50, rtol=1e-10, precision="fp32_refine")
     x, r = s.solve(dev(b))
     assert r["status"] == 0 and rel(x.cpu().numpy(), direct.dst_solve_3d(n, b)) <= 1e-7
+
+
+def test_batched_uneven_grids():
+    """Many independent systems of uneven size in one persistent launch
+    (one CTA group per list of systems), each against its exact solution and
+    against a single solve of the same system."""
+    from synthetic import batched_instances
+    rng = np.random.default_rng(11)
+    sides = [int(v) for v in rng.integers(5, 72, size=13)] + [1, 2, 72]
+    bs, xs_exact = [], []
+    for i, n in enumerate(sides):
+        b = MovingGaussians2D(n, 4001 + i, 1).rhs(0) if n > 2 else rng.standard_normal(n * n)
+        bs.append(dev(b))
+        xs_exact.append(direct.dst_solve_2d(n, b))
+    s = Solver(72, m=30, rtol=1e-10, precision="fp32_refine", batch_slots=5)
+    xs, res = s.solve_batch(sides, bs)
+    for i, n in enumerate(sides):
+        assert res[i]["status"] == 0 and res[i]["relres_true"] <= 1e-10, (i, n, res[i])
+        assert rel(xs[i].cpu().numpy(), xs_exact[i]) <= 1e-7, (i, n)
+        single = Solver(n, m=30, rtol=1e-10, precision="fp32_refine")
+        _, r1 = single.solve(bs[i])
+        assert iters_close(res[i]["iters"], r1["iters"]), (n, res[i]["iters"], r1["iters"])
+    # the c4 generator: sides drawn from U{64..512}; a few of the smaller ones
+    inst = [(n, b) for n, b in batched_instances(40) if n <= 96][:4]
+    if inst:
+        s2 = Solver(96, m=30, rtol=1e-8, precision="fp32_refine", batch_slots=4)
+        xs2, res2 = s2.solve_batch([n for n, _ in inst], [dev(b) for _, b in inst])
+        for (n, b), x, r in zip(inst, xs2, res2):
+            assert r["status"] == 0 and r["relres_true"] <= 1e-8
+            assert rel(x.cpu().numpy(), direct.dst_solve_2d(n, b)) <= 1e-5
+
+
+def test_batched_3d_with_own_kappa():
+    sides = [6, 9, 12]
+    kaps, bs, refs = [], [], []
+    for i, n in enumerate(sides):
+        k = lognormal_kappa(n, 77 + i, smooth_sigma=1.5).astype(np.float32)
+        b = MovingGaussians3D(n, 5 + i, 10).rhs(0)
+        kaps.append(torch.as_tensor(k).cuda())
+        bs.append(dev(b))
+        xr, _, _ = native.gmres(3, n, b, m=50, rtol=1e-13, kappa=k.astype(np.float64))
+        refs.append(xr)
+    s = Solver(12, dim=3, m=50, rtol=1e-10, precision="fp64", batch_slots=2)
+    xs, res = s.solve_batch(sides, bs, kappas=kaps)
+    for x, r, xr in zip(xs, res, refs):
+        assert r["status"] == 0 and r["relres_true"] <= 1e-10
+        assert rel(x.cpu().numpy(), xr) <= 1e-7
+
+
+def test_batch_rejects_bad_arguments():
+    s = Solver(16, m=10, batch_slots=2)
+    b = dev(np.ones(17 * 17))
+    with pytest.raises(MLGMRESError):
+        s.solve_batch([17], [b])
+    s0 = Solver(16, m=10)
+    with pytest.raises(MLGMRESError):
+        s0.solve_batch([16], [dev(np.ones(256))])
