@@ -139,6 +139,30 @@ __device__ __forceinline__ void warp_slots(T (*red)[LMAX], T (&acc)[MAXM], int L
   }
 }
 
+// warp_slots for an accumulator array of K <= MAXM entries (padded to 32).
+template <int LMAX, int K, typename T>
+__device__ __forceinline__ void warp_slots_k(T (*red)[LMAX], const T (&acc)[K], int L) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < (K + 31) / 32; g++) {
+    T v[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = (g * 32 + i < K) ? acc[g * 32 + i] : T(0);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      const bool up = (lane & off) != 0;
+#pragma unroll
+      for (int i = 0; i < off; i++) {
+        const T send = up ? v[i] : v[i + off];
+        const T keep = up ? v[i + off] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+    const int slot = g * 32 + lane;
+    if (slot < L) red[warp][slot] = v[0];
+  }
+}
+
 template <int LW, int BS, typename R>
 __device__ __forceinline__ void block_finish(int L, R* part, int lb, R (*red)[LW], int ps) {
   __syncthreads();
@@ -237,6 +261,152 @@ __device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, lo
   return stop;
 }
 
+// ------------------------------------------------------------ the passes --
+// Grid points per thread per loop trip for an accumulator bucket of K slots:
+// small buckets take several points so that enough loads are in flight.
+template <typename T, int K>
+struct PointsPerTrip {
+  static constexpr int value = sizeof(T) == 4 ? (K <= 8 ? 4 : (K <= 24 ? 2 : 1)) : (K <= 8 ? 2 : 1);
+};
+
+// X pass for step j < K over this CTA's points [lo, hi): v_j = (w' - V h2)/hn,
+// z = (A w' - sum_i c_i v_i)/hn, then per-warp partials of h1 = V^T z (slots
+// 0..j) and ||z||^2 (slot j+1) into sm.red.
+template <typename T, int DIM, int MAXM, int BS, int K>
+__device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, int j, int n,
+                                       const T* __restrict__ WP, T* __restrict__ Z,
+                                       T* __restrict__ V, long long ldv,
+                                       const float* __restrict__ kappa, T s2t) {
+  constexpr int LMAX = MAXM + 2;
+  constexpr int U = PointsPerTrip<T, K>::value;
+  const int tid = threadIdx.x;
+  T acc[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) acc[k] = T(0);
+  T accZ = T(0);
+  const T inv = sm.invT;
+  const T cj = sm.cc[j];
+  for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
+    int ii[U];
+    bool ok_[U];
+    T wp[U], znum[U], vnum[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      ii[u] = i0 + u * BS;
+      ok_[u] = ii[u] < hi;
+      wp[u] = ok_[u] ? ldcg(WP + ii[u]) : T(0);
+    }
+    T col[U][K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      if (k < j) {
+#pragma unroll
+        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[(long long)k * ldv + ii[u]] : T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
+      vnum[u] = wp[u];
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      if (k < j) {
+        const T h2k = sm.h2c[k], ck = sm.cc[k];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          vnum[u] -= h2k * col[u][k];
+          znum[u] -= ck * col[u][k];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const T vj = vnum[u] * inv;
+      const T z = (znum[u] - cj * vj) * inv;
+      if (ok_[u]) {
+        V[(long long)j * ldv + ii[u]] = vj;
+        Z[ii[u]] = z;
+      }
+      accZ += z * z;
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        if (k < j)
+          acc[k] += col[u][k] * z;
+        else if (k == j)
+          acc[k] += vj * z;
+      }
+    }
+  }
+  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
+  warp_slot<LMAX>(sm.red, j + 1, accZ);
+}
+
+// Y pass for step j < K: w' = z - V h1 (stored), per-warp partials of
+// h2 = V^T w' (slots 0..j) and ||w'||^2 (slot j+1).
+template <typename T, int MAXM, int BS, int K>
+__device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, int j,
+                                       T* __restrict__ WP, const T* __restrict__ Z,
+                                       const T* __restrict__ V, long long ldv) {
+  constexpr int LMAX = MAXM + 2;
+  constexpr int U = PointsPerTrip<T, K>::value;
+  const int tid = threadIdx.x;
+  T acc[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) acc[k] = T(0);
+  T accN = T(0);
+  for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
+    int ii[U];
+    bool ok_[U];
+    T q[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      ii[u] = i0 + u * BS;
+      ok_[u] = ii[u] < hi;
+      q[u] = ok_[u] ? Z[ii[u]] : T(0);
+    }
+    T col[U][K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      if (k <= j) {
+#pragma unroll
+        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[(long long)k * ldv + ii[u]] : T(0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      if (k <= j) {
+        const T hk = sm.coef[k];
+#pragma unroll
+        for (int u = 0; u < U; u++) q[u] -= hk * col[u][k];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (ok_[u]) WP[ii[u]] = q[u];
+      accN += q[u] * q[u];
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        if (k <= j) acc[k] += col[u][k] * q[u];
+    }
+  }
+  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
+  warp_slot<LMAX>(sm.red, j + 1, accN);
+}
+
+// Bucket dispatch: the pass instantiated for the smallest multiple of 8 above j.
+#define MLG_BUCKETS(CALL)                   \
+  switch (j >> 3) {                         \
+    case 0: CALL(8); break;                 \
+    case 1: CALL(16); break;                \
+    case 2: CALL(24); break;                \
+    case 3: CALL(32); break;                \
+    case 4: CALL(40); break;                \
+    case 5: CALL(48); break;                \
+    case 6: CALL(56); break;                \
+    default: CALL(64); break;               \
+  }
+
 // --------------------------------------------------------------- one solve --
 // Arnoldi step j of a cycle (CGS2 with two group barriers).  Entering it, the
 // work vector W holds w', the previous step's vector after its first
@@ -257,8 +427,6 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
                           int nb, unsigned long long& epoch, Smem<T, MAXM, BS>& sm) {
   constexpr int LD = MAXM + 1;
   constexpr int LMAX = MAXM + 2;
-  // grid points per thread per loop trip (their loads are in flight together)
-  constexpr int U = (sizeof(T) * MAXM <= 128) ? 2 : 1;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int n = tk.n;
@@ -393,59 +561,9 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       // ---- X: v_j and z = A v_j, h1 = V^T z; warp 1 rotates column j-1
       // while thread 0 waits at the group barrier
       {
-        T acc[MAXM];
-#pragma unroll
-        for (int k = 0; k < MAXM; k++) acc[k] = T(0);
-        T accZ = T(0);
-        const T inv = sm.invT;
-        const T cj = sm.cc[j];
-        for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
-          int ii[U];
-          bool ok_[U];
-          T wp[U], znum[U], vnum[U];
-#pragma unroll
-          for (int u = 0; u < U; u++) {
-            ii[u] = i0 + u * BS;
-            ok_[u] = ii[u] < hi;
-            wp[u] = ok_[u] ? ldcg(WP + ii[u]) : T(0);
-          }
-#pragma unroll
-          for (int u = 0; u < U; u++) {
-            znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
-            vnum[u] = wp[u];
-          }
-          T col[U][MAXM];
-#pragma unroll
-          for (int k = 0; k < MAXM; k++) {
-            if (k < j) {
-#pragma unroll
-              for (int u = 0; u < U; u++) {
-                col[u][k] = ok_[u] ? V[(long long)k * ldv + ii[u]] : T(0);
-                vnum[u] -= sm.h2c[k] * col[u][k];
-                znum[u] -= sm.cc[k] * col[u][k];
-              }
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < U; u++) {
-            const T vj = vnum[u] * inv;
-            const T z = (znum[u] - cj * vj) * inv;
-            if (ok_[u]) {
-              V[(long long)j * ldv + ii[u]] = vj;
-              Z[ii[u]] = z;
-            }
-            accZ += z * z;
-#pragma unroll
-            for (int k = 0; k < MAXM; k++) {
-              if (k < j)
-                acc[k] += col[u][k] * z;
-              else if (k == j)
-                acc[k] += vj * z;
-            }
-          }
-        }
-        warp_slots<LMAX, MAXM, T>(sm.red, acc, min(j + 1, MAXM));
-        warp_slot<LMAX>(sm.red, min(j + 1, MAXM + 1), accZ);
+#define MLG_X(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, V, ldv, kappa, s2t)
+        MLG_BUCKETS(MLG_X)
+#undef MLG_X
         block_finish<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red, ps);
         if (arnoldi && j == jmax) { kcols = j; break; }
         ok = group_sync_with(w.bar, epoch, &sm.flag, [&]() {
@@ -464,42 +582,9 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       }
       // ---- Y: w'_{j+1} = z - V h1, h2 = V^T w'_{j+1}, ||w'_{j+1}||^2
       {
-        T acc[MAXM];
-#pragma unroll
-        for (int k = 0; k < MAXM; k++) acc[k] = T(0);
-        T accN = T(0);
-        for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
-          int ii[U];
-          bool ok_[U];
-          T q[U];
-#pragma unroll
-          for (int u = 0; u < U; u++) {
-            ii[u] = i0 + u * BS;
-            ok_[u] = ii[u] < hi;
-            q[u] = ok_[u] ? Z[ii[u]] : T(0);
-          }
-          T col[U][MAXM];
-#pragma unroll
-          for (int k = 0; k < MAXM; k++) {
-            if (k <= j) {
-#pragma unroll
-              for (int u = 0; u < U; u++) {
-                col[u][k] = ok_[u] ? V[(long long)k * ldv + ii[u]] : T(0);
-                q[u] -= sm.coef[k] * col[u][k];
-              }
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < U; u++) {
-            if (ok_[u]) WP[ii[u]] = q[u];
-            accN += q[u] * q[u];
-#pragma unroll
-            for (int k = 0; k < MAXM; k++)
-              if (k <= j) acc[k] += col[u][k] * q[u];
-          }
-        }
-        warp_slots<LMAX, MAXM, T>(sm.red, acc, j + 1);
-        warp_slot<LMAX>(sm.red, j + 1, accN);
+#define MLG_Y(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, V, ldv)
+        MLG_BUCKETS(MLG_Y)
+#undef MLG_Y
         block_finish<LMAX, BS, T>(j + 2, (T*)part(), lb, sm.red, ps);
         ok = group_sync(w.bar, epoch, &sm.flag);
         if (!ok) goto abort;
@@ -680,24 +765,16 @@ static int max_blocks_t(int* bs) {
 }
 
 // Variant table: 256-thread CTAs (the register budget of 255 per thread keeps the
-// V column and the dot accumulators of a CGS2 sweep in registers).
-#define MLG_DISPATCH(FN, ...)                                                              \
-  if (fp32) {                                                                              \
-    if (dim == 2) {                                                                        \
-      if (m <= 32) return FN<float, 2, 32, 256>(__VA_ARGS__);                              \
-      return FN<float, 2, 64, 256>(__VA_ARGS__);                                           \
-    } else {                                                                               \
-      if (m <= 32) return FN<float, 3, 32, 256>(__VA_ARGS__);                              \
-      return FN<float, 3, 64, 256>(__VA_ARGS__);                                           \
-    }                                                                                      \
-  } else {                                                                                 \
-    if (dim == 2) {                                                                        \
-      if (m <= 32) return FN<double, 2, 32, 256>(__VA_ARGS__);                             \
-      return FN<double, 2, 64, 256>(__VA_ARGS__);                                          \
-    } else {                                                                               \
-      if (m <= 32) return FN<double, 3, 32, 256>(__VA_ARGS__);                             \
-      return FN<double, 3, 64, 256>(__VA_ARGS__);                                          \
-    }                                                                                      \
+// V column and the dot accumulators of a pass in registers); the passes are
+// instantiated per bucket of j, so one variant per precision and dimension.
+#define MLG_DISPATCH(FN, ...)                                      \
+  (void)m;                                                         \
+  if (fp32) {                                                      \
+    if (dim == 2) return FN<float, 2, kMaxM, 256>(__VA_ARGS__);    \
+    return FN<float, 3, kMaxM, 256>(__VA_ARGS__);                  \
+  } else {                                                         \
+    if (dim == 2) return FN<double, 2, kMaxM, 256>(__VA_ARGS__);   \
+    return FN<double, 3, kMaxM, 256>(__VA_ARGS__);                 \
   }
 
 cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid, cudaStream_t s) {
