@@ -2,23 +2,23 @@
 // Sec. 1.4, Sec. 3 of arXiv 2103.10975), one cooperative launch per solve or
 // per batch of solves.
 //
-// Each CTA group (all CTAs for a single solve) owns one system at a time; the
-// grid points are split into contiguous per-CTA ranges.  One Arnoldi step j is
-// three fused passes separated by group barriers:
-//   A: w = A v_j (matrix-free stencil on the unnormalised previous vector,
-//      scaled by 1/h_{j,j-1} -- lazy normalisation), store v_j, and
-//      h1 = V_{0..j}^T w, ||w||^2 partial sums.
-//   B: w -= V h1 and h2 = V^T w in the same pass over V (each thread keeps its
-//      column of V in registers between the update and the dots).
-//   C: w -= V h2 and ||w||^2.
-// (classical Gram-Schmidt applied twice.)  After each barrier every CTA sums
-// the per-CTA partials in the same fixed order, so all CTAs hold bit-identical
-// coefficients and run the Givens update of the Hessenberg least-squares
-// problem redundantly in shared memory (FP64) with no extra synchronisation.
-// At a cycle end the back-substitution y = H^{-1} g runs in shared memory,
-// x += V y is accumulated in FP64 and the true residual b - A x is recomputed
-// in FP64 (the restart of GMRES(k)).  The FP32 variant stores V and w in FP32
-// and so runs every cycle as one step of mixed-precision iterative refinement.
+// Each CTA group (all CTAs for a single solve, or one CTA per system of a
+// batch) owns one system at a time; its grid points are split into contiguous
+// per-CTA ranges of whole 32-point tiles.  One Arnoldi step is classical
+// Gram-Schmidt applied twice, arranged as two fused passes over the CTA's
+// points with one group barrier each (see solve_one):
+//   X: v_j (lazy normalisation of the previous step's vector), z = A v_j
+//      obtained from the SpMV of the unnormalised vector through the Arnoldi
+//      relation, and the dots h1 = V^T z;
+//   Y: w' = z - V h1 with the dots h2 = V^T w' in the same pass.
+// After each barrier every CTA sums the per-CTA partials in the same fixed
+// order, so all CTAs hold bit-identical coefficients and run the scalar
+// recurrences (Pythagorean norm, Hessenberg column, Givens rotation) redundantly
+// in shared memory with no extra synchronisation.  At a cycle end the
+// back-substitution y = R^{-1} g runs in shared memory, x += V y is accumulated
+// in FP64 and the true residual b - A x is recomputed in FP64 (the restart of
+// GMRES(k)).  The FP32 variant stores V and the work vectors in FP32 and so
+// runs every cycle as one step of mixed-precision iterative refinement.
 #include <math.h>
 
 #include "solver.h"
@@ -79,6 +79,18 @@ __device__ __forceinline__ T stencil(const T* __restrict__ u, int i, int n,
     return stencil2d<T>(u, i, n, uc);
   else
     return stencil3d<T>(u, i, n, kappa, uc);
+}
+
+// ------------------------------------------------------------ basis layout --
+// V is stored tile-major: for every tile of 32 consecutive grid points the
+// `rows` basis values of each point follow each other, so a warp's column of
+// V (all k for its 32 points) is one contiguous run of rows * 32 elements and
+// each per-k access is one 128-byte (FP32) or 256-byte (FP64) segment.
+__host__ __device__ __forceinline__ long long vbase(int i, int rows) {
+  return ((long long)(i >> 5) * rows << 5) + (i & 31);
+}
+__host__ __device__ __forceinline__ long long vix(int k, int i, int rows) {
+  return vbase(i, rows) + ((long long)k << 5);
 }
 
 // ----------------------------------------------------------- shared state --
@@ -275,7 +287,7 @@ struct PointsPerTrip {
 template <typename T, int DIM, int MAXM, int BS, int K>
 __device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, int j, int n,
                                        const T* __restrict__ WP, T* __restrict__ Z,
-                                       T* __restrict__ V, long long ldv,
+                                       T* __restrict__ V, int rows, int voff,
                                        const float* __restrict__ kappa, T s2t) {
   constexpr int LMAX = MAXM + 2;
   constexpr int U = PointsPerTrip<T, K>::value;
@@ -296,12 +308,15 @@ __device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
       ok_[u] = ii[u] < hi;
       wp[u] = ok_[u] ? ldcg(WP + ii[u]) : T(0);
     }
+    long long vb[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) vb[u] = vbase(ii[u] - voff, rows);
     T col[U][K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
       if (k < j) {
 #pragma unroll
-        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[(long long)k * ldv + ii[u]] : T(0);
+        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[vb[u] + (k << 5)] : T(0);
       }
     }
 #pragma unroll
@@ -325,7 +340,7 @@ __device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
       const T vj = vnum[u] * inv;
       const T z = (znum[u] - cj * vj) * inv;
       if (ok_[u]) {
-        V[(long long)j * ldv + ii[u]] = vj;
+        V[vb[u] + ((long long)j << 5)] = vj;
         Z[ii[u]] = z;
       }
       accZ += z * z;
@@ -347,7 +362,7 @@ __device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
 template <typename T, int MAXM, int BS, int K>
 __device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, int j,
                                        T* __restrict__ WP, const T* __restrict__ Z,
-                                       const T* __restrict__ V, long long ldv) {
+                                       const T* __restrict__ V, int rows, int voff) {
   constexpr int LMAX = MAXM + 2;
   constexpr int U = PointsPerTrip<T, K>::value;
   const int tid = threadIdx.x;
@@ -365,12 +380,15 @@ __device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
       ok_[u] = ii[u] < hi;
       q[u] = ok_[u] ? Z[ii[u]] : T(0);
     }
+    long long vb[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) vb[u] = vbase(ii[u] - voff, rows);
     T col[U][K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
       if (k <= j) {
 #pragma unroll
-        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[(long long)k * ldv + ii[u]] : T(0);
+        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[vb[u] + (k << 5)] : T(0);
       }
     }
 #pragma unroll
@@ -434,11 +452,22 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   const int m = kp.m;
   const bool arnoldi = kp.arnoldi_steps > 0;
   int chunk = (N + nb - 1) / nb;
-  chunk = (chunk + 3) & ~3;
+  chunk = (chunk + 31) & ~31;  // whole tiles of the basis layout
   const int lo = min(N, lb * chunk);
   const int hi = min(N, lo + chunk);
-  T* __restrict__ V = (T*)w.V;
-  const long long ldv = w.ldv;
+  const int rows = m + 1;  // basis vectors per tile (V holds m+1 vectors)
+  // V lives in shared memory when this CTA's slice fits the reserved space
+  // (latency of a shared load instead of an L2 round trip); else in HBM.
+  // (only the FP32 2D variant has slices small enough to be worth a second
+  // instantiation of the passes; the global and the shared copies are kept
+  // apart so each pass uses the right address space)
+  const bool vshared = sizeof(T) == 4 && DIM == 2 && !arnoldi && kp.vsmem > 0 &&
+                       (long long)chunk * rows * (long long)sizeof(T) <= kp.vsmem;
+  T* __restrict__ Vg = (T*)w.V;
+  T* __restrict__ Vs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(&sm) +
+                                            sizeof(Smem<T, MAXM, BS>));
+  T* __restrict__ V = vshared ? Vs : Vg;  // cycle-end and fallback passes
+  const int voff = vshared ? lo : 0;
   T* __restrict__ WP = (T*)w.W0;  // w' (read by neighbours in X, rewritten in Y)
   T* __restrict__ Z = (T*)w.W1;   // z = A v_j, own rows only
   const double h = 2.0 / (n + 1);
@@ -561,16 +590,27 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       // ---- X: v_j and z = A v_j, h1 = V^T z; warp 1 rotates column j-1
       // while thread 0 waits at the group barrier
       {
-#define MLG_X(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, V, ldv, kappa, s2t)
-        MLG_BUCKETS(MLG_X)
+#define MLG_X(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vg, rows, 0, kappa, s2t)
+#define MLG_XS(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vs, rows, lo, kappa, s2t)
+        if constexpr (sizeof(T) == 4 && DIM == 2) {
+          if (vshared) {
+            MLG_BUCKETS(MLG_XS)
+          } else {
+            MLG_BUCKETS(MLG_X)
+          }
+        } else {
+          MLG_BUCKETS(MLG_X)
+        }
 #undef MLG_X
-        block_finish<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red, ps);
+#undef MLG_XS
         if (arnoldi && j == jmax) { kcols = j; break; }
-        ok = group_sync_with(w.bar, epoch, &sm.flag, [&]() {
+        auto givens_prev = [&]() {
           if (j > 0 && !arnoldi)
             givens_column<T, MAXM, BS>(sm, j - 1, rtol_bnorm, iters, kp.max_iters, m, hist,
                                        tk.hist_cap, bnorm);
-        });
+        };
+        block_finish<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red, ps);
+        ok = group_sync_with(w.bar, epoch, &sm.flag, givens_prev);
         if (!ok) goto abort;
         const int stop = sm.stop;
         if (stop == 2) { status = kErrNonfinite; goto finish; }
@@ -582,9 +622,19 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       }
       // ---- Y: w'_{j+1} = z - V h1, h2 = V^T w'_{j+1}, ||w'_{j+1}||^2
       {
-#define MLG_Y(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, V, ldv)
-        MLG_BUCKETS(MLG_Y)
+#define MLG_Y(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vg, rows, 0)
+#define MLG_YS(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vs, rows, lo)
+        if constexpr (sizeof(T) == 4 && DIM == 2) {
+          if (vshared) {
+            MLG_BUCKETS(MLG_YS)
+          } else {
+            MLG_BUCKETS(MLG_Y)
+          }
+        } else {
+          MLG_BUCKETS(MLG_Y)
+        }
 #undef MLG_Y
+#undef MLG_YS
         block_finish<LMAX, BS, T>(j + 2, (T*)part(), lb, sm.red, ps);
         ok = group_sync(w.bar, epoch, &sm.flag);
         if (!ok) goto abort;
@@ -619,7 +669,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
           T q = WP[i];
 #pragma unroll
           for (int k = 0; k < MAXM; k++)
-            if (k <= j) q -= sm.h2c[k] * V[(long long)k * ldv + i];
+            if (k <= j) q -= sm.h2c[k] * V[vix(k, i - voff, rows)];
           WP[i] = q;
           accN += q * q;
         }
@@ -684,7 +734,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
     __syncthreads();
     for (int i = lo + tid; i < hi; i += BS) {
       double d = 0.0;
-      for (int k = 0; k < kcols; k++) d += sm.y[k] * (double)V[(long long)k * ldv + i];
+      const long long vb = vbase(i - voff, rows);
+      for (int k = 0; k < kcols; k++) d += sm.y[k] * (double)V[vb + ((long long)k << 5)];
       tk.x[i] += d;
     }
     cycles++;
@@ -736,20 +787,20 @@ __global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
 // ------------------------------------------------------------- host side --
 // The shared state lives in dynamic shared memory (up to ~107 KB for m <= 64).
 template <typename T, int DIM, int MAXM, int BS>
-static cudaError_t prepare_t() {
+static cudaError_t prepare_t(int extra = 0) {
   return cudaFuncSetAttribute(gmres_persistent<T, DIM, MAXM, BS>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(Smem<T, MAXM, BS>));
+                              (int)sizeof(Smem<T, MAXM, BS>) + extra);
 }
 
 template <typename T, int DIM, int MAXM, int BS>
 static cudaError_t launch_t(const KParams& kp, int grid, cudaStream_t s) {
-  cudaError_t e = prepare_t<T, DIM, MAXM, BS>();
+  cudaError_t e = prepare_t<T, DIM, MAXM, BS>(kp.vsmem);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&kp};
   note_launches(1);
   return cudaLaunchCooperativeKernel((const void*)gmres_persistent<T, DIM, MAXM, BS>, dim3(grid),
-                                     dim3(BS), args, sizeof(Smem<T, MAXM, BS>), s);
+                                     dim3(BS), args, sizeof(Smem<T, MAXM, BS>) + kp.vsmem, s);
 }
 
 template <typename T, int DIM, int MAXM, int BS>
@@ -784,6 +835,15 @@ cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid, cudaSt
 
 int gmres_max_blocks(bool fp32, int dim, int m, int* bs) { MLG_DISPATCH(max_blocks_t, bs); }
 
+int gmres_vsmem_budget(bool fp32) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int own = fp32 ? (int)sizeof(Smem<float, kMaxM, 256>) : (int)sizeof(Smem<double, kMaxM, 256>);
+  const int left = optin - own - 1024;
+  return left > 0 ? left : 0;
+}
+
 // FP64 A u, one thread per point.
 template <int DIM>
 __global__ void apply_kernel(int n, int N, const float* kappa, const double* u, double* out) {
@@ -806,23 +866,23 @@ cudaError_t launch_apply(int dim, int n, const float* kappa, const double* u, do
 }
 
 template <typename T>
-__global__ void basis_to_f64(const T* V, long long ldv, int rows, int N, double* out) {
+__global__ void basis_to_f64(const T* V, int vrows, int rows, int N, double* out) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= (long long)rows * N) return;
   const int r = (int)(i / N), c = (int)(i % N);
-  out[i] = (double)V[r * ldv + c];
+  out[i] = (double)V[vix(r, c, vrows)];
 }
 
-cudaError_t launch_basis_to_f64(bool fp32, const void* V, long long ldv, int rows, int N,
+cudaError_t launch_basis_to_f64(bool fp32, const void* V, int vrows, int rows, int N,
                                 double* out, cudaStream_t s) {
   const long long tot = (long long)rows * N;
   const int bs = 256;
   const unsigned gr = (unsigned)((tot + bs - 1) / bs);
   note_launches(1);
   if (fp32)
-    basis_to_f64<float><<<gr, bs, 0, s>>>((const float*)V, ldv, rows, N, out);
+    basis_to_f64<float><<<gr, bs, 0, s>>>((const float*)V, vrows, rows, N, out);
   else
-    basis_to_f64<double><<<gr, bs, 0, s>>>((const double*)V, ldv, rows, N, out);
+    basis_to_f64<double><<<gr, bs, 0, s>>>((const double*)V, vrows, rows, N, out);
   return cudaGetLastError();
 }
 

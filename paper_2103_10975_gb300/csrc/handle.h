@@ -19,6 +19,7 @@ struct mlgmres {
   int blocks = 0;       // solver CTAs for a single solve
   int max_blocks = 0;   // co-resident limit of the kernel variant
   int bs = 0;
+  int vsmem = 0;        // shared-memory bytes for the V slice of a single solve
 
   // ---- solver workspace (one group for single solves) ----
   long long ldv = 0;

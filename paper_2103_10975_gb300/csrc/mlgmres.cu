@@ -92,7 +92,7 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
 // Run the persistent kernel for `count` tasks already staged in h->htasks,
 // with the group layout staged in h->hcfg / h->hwork.
 void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps,
-                cudaStream_t s) {
+                cudaStream_t s, int vsmem = 0) {
   const size_t cfg_bytes = sizeof(int) * (size_t)(2 * (ngroups + 1) + ntasks);
   CK(cudaMemcpyAsync(h->dcfg, h->hcfg, cfg_bytes, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(h->dtasks, h->htasks, sizeof(SolveTask) * ntasks, cudaMemcpyHostToDevice,
@@ -106,6 +106,7 @@ void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps
   kp.rtol = h->opt.rtol;
   kp.max_iters = h->opt.max_iters;
   kp.arnoldi_steps = arnoldi_steps;
+  kp.vsmem = arnoldi_steps > 0 ? 0 : vsmem;
   kp.ngroups = ngroups;
   kp.group_first = h->dcfg;
   kp.task_first = h->dcfg + (ngroups + 1);
@@ -280,11 +281,18 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
                                      : auto_blocks(h, h->N);
     h->blocks = std::min(h->blocks, kPartStride);
     h->ldv = ((long long)h->N + 63) / 64 * 64;
+    {
+      // shared-memory slice of V for single solves when it fits
+      const long long chunk = (((long long)h->N + h->blocks - 1) / h->blocks + 31) / 32 * 32;
+      const long long need = chunk * (opt->m + 1) * (h->fp32 ? 4 : 8);
+      const int budget = gmres_vsmem_budget(h->fp32);
+      h->vsmem = need <= budget ? (int)need : 0;
+    }
     const size_t es = h->fp32 ? sizeof(float) : sizeof(double);
     CK(cudaMalloc(&h->V, es * (size_t)(opt->m + 1) * h->ldv));
     CK(cudaMalloc(&h->W0, es * (size_t)h->ldv));
     CK(cudaMalloc(&h->W1, es * (size_t)h->ldv));
-    CK(cudaMalloc(&h->part, sizeof(double) * 2 * (kMaxM + 2) * kPartStride));
+    CK(cudaMalloc(&h->part, sizeof(double) * part_doubles(kPartStride)));
     h->group_cap = 1;
     h->cfg_cap = 1;
     if (opt->batch_slots > 0) {
@@ -294,7 +302,7 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
       const size_t G = (size_t)h->batch_groups;
       CK(cudaMalloc(&h->Vb, es * G * (size_t)(opt->m + 1) * h->ldv));
       CK(cudaMalloc(&h->Wb, es * G * 2 * (size_t)h->ldv));
-      CK(cudaMalloc(&h->partb, sizeof(double) * G * 2 * (kMaxM + 2)));
+      CK(cudaMalloc(&h->partb, sizeof(double) * G * part_doubles(1)));
     }
     CK(cudaMalloc(&h->bar, sizeof(unsigned long long) * h->group_cap));
     CK(cudaMalloc(&h->err, sizeof(int) * h->group_cap));
@@ -433,7 +441,7 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
     t.zero_x = 0;
     stage_single(h, t, h->blocks);
     CK(cudaEventRecord(h->ev0, s));
-    run_solver(h, 1, 1, h->blocks, 0, s);
+    run_solver(h, 1, 1, h->blocks, 0, s, h->vsmem);
     CK(cudaEventRecord(h->ev1, s));
     CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->x_prev, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
@@ -524,7 +532,7 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
       w.ldv = h->ldv;
       w.W0 = (char*)h->Wb + es * (size_t)g * 2 * h->ldv;
       w.W1 = (char*)w.W0 + es * h->ldv;
-      w.part = h->partb + (size_t)g * 2 * (kMaxM + 2);
+      w.part = h->partb + (size_t)g * part_doubles(1);
       w.pstride = 1;
       w.bar.ctr = h->bar + g;
       w.bar.err = h->err + g;
@@ -532,8 +540,18 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
       w.bar.timeout_ns = (unsigned long long)(h->opt.barrier_timeout_s * 1e9);
       h->hwork[g] = w;
     }
+    int vsmem = 0;
+    {
+      long long need = 0;
+      for (int i = 0; i < count; i++) {
+        const long long chunk = (grid_points(dim, grids[i].n) + 31) / 32 * 32;
+        need = std::max(need, chunk * (h->opt.m + 1) * (long long)es);
+      }
+      const int budget = gmres_vsmem_budget(h->fp32);
+      vsmem = need <= budget ? (int)need : 0;
+    }
     CK(cudaEventRecord(h->ev0, s));
-    run_solver(h, G, count, G, 0, s);
+    run_solver(h, G, count, G, 0, s, vsmem);
     CK(cudaEventRecord(h->ev1, s));
     CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult) * count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -644,7 +662,7 @@ mlgmres_status mlgmres_arnoldi(mlgmres_t h, const double* v0, int steps, double*
     const int k = h->hres[0].status;
     ARG(k >= 1, "Arnoldi run failed (barrier timeout or zero start vector)");
     *done = k;
-    CK(launch_basis_to_f64(h->fp32, h->V, h->ldv, k + 1, h->N, V_dev, s));
+    CK(launch_basis_to_f64(h->fp32, h->V, h->opt.m + 1, k + 1, h->N, V_dev, s));
     CK(cudaFreeAsync(Hd, s));
     CK(cudaStreamSynchronize(s));
     return MLGMRES_OK;

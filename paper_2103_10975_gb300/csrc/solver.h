@@ -9,6 +9,8 @@ namespace mlg {
 
 constexpr int kMaxM = 64;          // largest supported restart length
 constexpr int kPartStride = 1024;  // max CTAs per group (partials row length)
+// doubles in a group's partial-sum area (two alternating sets)
+constexpr long long part_doubles(int pstride) { return 2LL * (kMaxM + 2) * pstride; }
 
 // Per-system result written by the solver (mirrors mlgmres_result's numeric part).
 struct DevResult {
@@ -40,7 +42,7 @@ struct SolveTask {
 
 // Workspace of one CTA group.
 struct GroupWork {
-  void* V;            // (m+1) x ldv basis, element type of the precision
+  void* V;            // basis, tile-major (m+1 vectors per 32-point tile), ldv points
   long long ldv;
   void* W0;           // two work vectors (ping-pong), ldv each
   void* W1;
@@ -54,6 +56,7 @@ struct KParams {
   double rtol;
   long long max_iters;
   int arnoldi_steps;        // > 0: run that many Arnoldi steps only (inspection mode)
+  int vsmem;                // bytes of shared memory for a CTA's slice of V (0 = V in HBM)
   int ngroups;
   const int* group_first;   // ngroups+1 CTA ranges
   const int* task_first;    // ngroups+1 ranges into task_order
@@ -69,13 +72,17 @@ cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid_blocks,
 // Largest co-resident grid for the chosen kernel variant (blocks), and its CTA size.
 int gmres_max_blocks(bool fp32, int dim, int m, int* block_threads);
 
+// Shared-memory bytes a CTA may use for its slice of V (so that slice + the
+// solver's own state fit the per-CTA limit); 0 if none.
+int gmres_vsmem_budget(bool fp32);
+
 // FP64 operator application out = A u (2D or 3D) on one grid.
 cudaError_t launch_apply(int dim, int n, const float* kappa, const double* u, double* out,
                          cudaStream_t s);
 
-// Convert the first `rows` vectors of a basis of element type fp32?float:double
-// to double (row-major, ldv -> N).
-cudaError_t launch_basis_to_f64(bool fp32, const void* V, long long ldv, int rows, int N,
+// Convert the first `rows` vectors of a tile-major basis holding `vrows`
+// vectors per tile (element type fp32 ? float : double) to row-major doubles.
+cudaError_t launch_basis_to_f64(bool fp32, const void* V, int vrows, int rows, int N,
                                 double* out, cudaStream_t s);
 
 }  // namespace mlg

@@ -19,7 +19,7 @@ constexpr int kStaticMaxM = 32;
 constexpr long long kStaticLdv = kStaticMaxN;  // a multiple of 64
 constexpr size_t kStaticBasis = sizeof(float) * (size_t)(kStaticMaxM + 1) * kStaticLdv;
 constexpr size_t kStaticWork = 2 * sizeof(float) * (size_t)kStaticLdv;
-constexpr size_t kStaticPart = sizeof(double) * 2 * (kMaxM + 2) * kPartStride;
+constexpr size_t kStaticPart = sizeof(double) * part_doubles(kPartStride);
 constexpr size_t kStaticMisc = 4096;  // barrier counter, error flag, result, launch tables
 constexpr size_t kStaticBytes = kStaticBasis + kStaticWork + kStaticPart + kStaticMisc;
 
@@ -125,6 +125,7 @@ extern "C" mlgmres_status mlgmres_solve_static(int n, int m, double rtol, long l
   kp.rtol = rtol;
   kp.max_iters = max_iters;
   kp.arnoldi_steps = 0;
+  kp.vsmem = 0;
   kp.ngroups = 1;
   kp.group_first = cfg;
   kp.task_first = cfg + 2;
