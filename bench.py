@@ -34,6 +34,10 @@ SEED = 2001
 TAU0 = 50
 TRAIN_EVERY = 10
 METRIC = "time-to-solution per time step (ms) and GMRES iters, learned vs plain GMRES, rel res 1e-10"
+# DRAM bytes per Arnoldi step of gmres_persistent<float> on this workload, from
+# one ncu capture of a 300-step solve of the kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum = 79.3 MB); scaled to a launch by its steps.
+DRAM_BYTES_PER_STEP = 79.3e6 / 300
 WORKLOAD = ("2D Poisson -Lap u = f, 256x256 interior (N=65,536), zero Dirichlet, 5-point; "
             "3 moving signed Gaussians (sigma 0.1), 500-step series seed 2001; GMRES(30) "
             "rel tol 1e-10 (true FP64 residual)")
@@ -101,10 +105,10 @@ class Clocks:
 
 # --------------------------------------------------------------- helpers --
 def algorithmic_bytes(res, N, m, elem):
-    """Bytes one solve must move ('Roofline accounting'):
-    per Arnoldi step j: elem*N*(3j + 9); per cycle with k steps: elem*N*(k + 1)
-    (x += V y reads k basis vectors, the restart writes the new start vector)
-    + 32 N (x read/write, b read, x read by the FP64 residual)."""
+    """Bytes one solve must move: per Arnoldi step j the two CGS2 passes read
+    V_0..V_{j-1} and V_0..V_j, w' and z and write v_j, z and w': elem*N*(2j + 6);
+    per cycle with k steps x += V y reads k basis vectors and x (16 N with its
+    write), and the FP64 restart reads x and b (16 N) and writes w'_0 (elem*N)."""
     iters, cycles = int(res["iters"]), int(res["cycles"])
     total = 0.0
     left = iters
@@ -112,9 +116,10 @@ def algorithmic_bytes(res, N, m, elem):
     for c in range(ncyc):
         k = min(m, left) if c < ncyc - 1 else left
         left -= k
-        total += elem * N * (3.0 * k * (k - 1) / 2.0 + 9.0 * k)
-        total += elem * N * (k + 1) + 32.0 * N
-    total += 32.0 * N  # final residual check
+        total += elem * N * (k * (k - 1) + 6.0 * k)   # sum_j (2j + 6)
+        total += elem * N * k + 16.0 * N              # x += V y
+        total += 16.0 * N + elem * N                  # restart
+    total += 16.0 * N + elem * N                      # final residual check
     return total
 
 
@@ -273,6 +278,7 @@ def run_ours(args):
     byts = sum(algorithmic_bytes(r, N, M, 4) for r in res)
     tos = sum(r["tos_ms"] for r in res)
     achieved = byts / (tos * 1e-3) / 1e9
+    traffic = DRAM_BYTES_PER_STEP * statistics.mean(r["iters"] for r in res)
 
     # ---- end to end through the public API with host buffers
     Bh = torch.stack([torch.as_tensor(gen.rhs(t)) for t in range(TAU0 + W + K, TAU0 + W + 2 * K)])
@@ -332,7 +338,8 @@ def run_ours(args):
             "relres_true_max": max(r["relres_true"] for r in res),
             "compare": compare,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": byts / len(res),
                          "kernel": "gmres_persistent (FP32 variant)",
                          "peak_source": peak_kind,
                          "note": "V (8 MB) is L2-resident at 256^2: bytes served mostly by L2"},

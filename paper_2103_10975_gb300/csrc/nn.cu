@@ -91,68 +91,6 @@ __global__ void pool2_fwd(int B, int s, const bf16* __restrict__ in, bf16* __res
   out[i] = __float2bfloat16(0.25f * v);
 }
 
-enum ConvMode { kRelu = 0, kResid = 1, kF32 = 2 };
-
-// out[p][o] = sum_tap sum_k wop[tap][k][o] in[p + sign*dil*off_tap][k] (+ bias),
-// 32 -> 32 channels, one thread per pixel.
-//   kRelu : zo = relu(acc + bias)                       (BF16)
-//   kResid: zo = e = relu(acc + bias), to = resid + e   (BF16)
-//   kF32  : fo = acc (+ addend)                         (FP32)
-template <int MODE>
-__global__ void __launch_bounds__(128) conv32_simt(int B, int H, const bf16* __restrict__ in,
-                                                   const bf16* __restrict__ wop,
-                                                   const float* __restrict__ bias, int dil,
-                                                   int sign, bf16* __restrict__ zo,
-                                                   bf16* __restrict__ to,
-                                                   const bf16* __restrict__ resid,
-                                                   float* __restrict__ fo,
-                                                   const float* __restrict__ addend) {
-  __shared__ float ws[9 * kC * kC];
-  for (int i = threadIdx.x; i < 9 * kC * kC; i += blockDim.x) ws[i] = __bfloat162float(wop[i]);
-  __syncthreads();
-  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= (long long)B * H * H) return;
-  const int b = (int)(p / ((long long)H * H));
-  const int r = (int)(p % ((long long)H * H));
-  const int y = r / H, x = r % H;
-  float acc[kC];
-#pragma unroll
-  for (int o = 0; o < kC; o++) acc[o] = (MODE != kF32 && bias) ? bias[o] : 0.f;
-  for (int t = 0; t < 9; t++) {
-    const int yy = y + sign * dil * (t / 3 - 1);
-    const int xx = x + sign * dil * (t % 3 - 1);
-    if (yy < 0 || yy >= H || xx < 0 || xx >= H) continue;
-    float v[kC];
-    load32(in + (((long long)b * H + yy) * H + xx) * kC, v);
-    const float* wt = ws + t * kC * kC;
-#pragma unroll
-    for (int k = 0; k < kC; k++) {
-      const float vk = v[k];
-#pragma unroll
-      for (int o = 0; o < kC; o++) acc[o] += vk * wt[k * kC + o];
-    }
-  }
-  if (MODE == kRelu) {
-#pragma unroll
-    for (int o = 0; o < kC; o++) acc[o] = fmaxf(acc[o], 0.f);
-    store32(zo + p * kC, acc);
-  } else if (MODE == kResid) {
-    float sv[kC];
-    load32(resid + p * kC, sv);
-#pragma unroll
-    for (int o = 0; o < kC; o++) acc[o] = fmaxf(acc[o], 0.f);
-    store32(zo + p * kC, acc);
-#pragma unroll
-    for (int o = 0; o < kC; o++) sv[o] += acc[o];
-    store32(to + p * kC, sv);
-  } else {
-    float* dst = fo + p * kC;
-    const float* ad = addend ? addend + p * kC : nullptr;
-#pragma unroll
-    for (int o = 0; o < kC; o++) dst[o] = acc[o] + (ad ? ad[o] : 0.f);
-  }
-}
-
 // Half-pixel bilinear source position of output index i (m source points, n out).
 __device__ __forceinline__ void bilin(int i, int m, int n, int& i0, int& i1, float& lam) {
   float src = ((float)i + 0.5f) * (float)m / (float)n - 0.5f;
@@ -334,53 +272,6 @@ __global__ void mask_f32(long long count, const float* __restrict__ g,
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= count) return;
   out[i] = __bfloat162float(mask[i]) > 0.f ? g[i] : 0.f;
-}
-
-// Per-CTA partial gradients of a 32 -> 32 conv:
-//   part[cta][(tap*32 + k)*32 + o] = sum_p in[p + dil*off_tap][k] * g[p][o]
-//   part[cta][9216 + o]            = sum_p g[p][o]
-// 288 threads: thread = (tap, k), 32 accumulators over o.
-constexpr int kWTile = 32;
-__global__ void __launch_bounds__(288) conv32_wgrad_simt(int B, int H, const bf16* __restrict__ in,
-                                                         const bf16* __restrict__ g, int dil,
-                                                         float* __restrict__ part, int stride) {
-  __shared__ float gs[kWTile][kC];
-  const long long total = (long long)B * H * H;
-  const long long per = (total + gridDim.x - 1) / gridDim.x;
-  const long long p0 = blockIdx.x * per;
-  const long long p1 = min(total, p0 + per);
-  const int t = threadIdx.x;
-  const int tp = t / kC, k = t % kC;
-  const int dy = dil * (tp / 3 - 1), dx = dil * (tp % 3 - 1);
-  float acc[kC];
-#pragma unroll
-  for (int o = 0; o < kC; o++) acc[o] = 0.f;
-  float bacc = 0.f;
-  for (long long pt = p0; pt < p1; pt += kWTile) {
-    const int cnt = (int)min((long long)kWTile, p1 - pt);
-    __syncthreads();
-    for (int i = t; i < kWTile * kC; i += blockDim.x) {
-      const int px = i / kC, o = i % kC;
-      gs[px][o] = px < cnt ? __bfloat162float(g[(pt + px) * kC + o]) : 0.f;
-    }
-    __syncthreads();
-    if (t < kC)
-      for (int px = 0; px < cnt; px++) bacc += gs[px][t];
-    for (int px = 0; px < cnt; px++) {
-      const long long p = pt + px;
-      const int b = (int)(p / ((long long)H * H));
-      const int r = (int)(p % ((long long)H * H));
-      const int yy = r / H + dy, xx = r % H + dx;
-      if (yy < 0 || yy >= H || xx < 0 || xx >= H) continue;
-      const float v = __bfloat162float(in[(((long long)b * H + yy) * H + xx) * kC + k]);
-#pragma unroll
-      for (int o = 0; o < kC; o++) acc[o] += v * gs[px][o];
-    }
-  }
-  float* dst = part + (long long)blockIdx.x * stride;
-#pragma unroll
-  for (int o = 0; o < kC; o++) dst[(tp * kC + k) * kC + o] = acc[o];
-  if (t < kC) dst[9 * kC * kC + t] = bacc;
 }
 
 // grad[dst_w[i]] = sum over CTAs of part[cta][i] for the weight layout used by
@@ -651,10 +542,10 @@ cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t 
   for (int l = 0; l < L; l++) {
     const int sd = net.side[l];
     const long long np = (long long)B * sd * sd;
-    conv32_simt<kRelu><<<nblk(np, 128), 128, 0, s>>>(
-        B, sd, l == 0 ? net.a0 : net.pool[l], net.wq + per * l, net.master + net.off_b[1 + l], 1,
-        1, net.z[l], nullptr, nullptr, nullptr, nullptr);
-    note_launches(1);
+    (void)np;
+    NN_CK(launch_conv32_mma(0, B, sd, l == 0 ? net.a0 : net.pool[l], net.wqT + per * l,
+                            net.master + net.off_b[1 + l], 1, 1, net.z[l], nullptr, nullptr,
+                            nullptr, nullptr, s));
   }
   Levels lv;
   lv.L = L;
@@ -664,10 +555,8 @@ cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t 
   }
   upsum_fwd<<<nblk(pix * kC, 256), 256, 0, s>>>(B, n, lv, net.s);
   note_launches(1);
-  conv32_simt<kResid><<<nblk(pix, 128), 128, 0, s>>>(B, n, net.s, net.wq + per * L,
-                                                     net.master + net.off_b[L + 1], 2, 1, net.e,
-                                                     net.t, net.s, nullptr, nullptr);
-  note_launches(1);
+  NN_CK(launch_conv32_mma(1, B, n, net.s, net.wqT + per * L, net.master + net.off_b[L + 1], 2, 1,
+                          net.e, net.t, net.s, nullptr, nullptr, s));
   conv_out_fwd<<<nblk(pix, 256), 256, 0, s>>>(B, n, net.t, net.master + net.off_w[L + 2],
                                                net.master + net.off_b[L + 2], y);
   note_launches(1);
@@ -702,16 +591,13 @@ cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const 
   // dilated residual block: t = s + e, e = relu(conv_d2(s))
   mask_to_bf16<<<nblk(full, 256), 256, 0, s>>>(full, net.g_t, net.e, net.g_bf);
   note_launches(1);
-  conv32_wgrad_simt<<<P, 288, 0, s>>>(B, n, net.s, net.g_bf, 2, net.wgrad_part, stride);
-  note_launches(1);
+  NN_CK(launch_wgrad_mma(B, n, net.s, net.g_bf, 2, net.wgrad_part, stride, P, s));
   reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0,
                                                    net.grad + net.off_w[L + 1],
                                                    net.grad + net.off_b[L + 1]);
   note_launches(1);
-  conv32_simt<kF32><<<nblk(pix, 128), 128, 0, s>>>(B, n, net.g_bf, net.wqT + per * L, nullptr, 2,
-                                                   -1, nullptr, nullptr, nullptr, net.g_s,
-                                                   net.g_t);
-  note_launches(1);
+  NN_CK(launch_conv32_mma(2, B, n, net.g_bf, net.wq + per * L, nullptr, 2, -1, nullptr, nullptr,
+                          nullptr, net.g_s, net.g_t, s));
   // pyramid levels
   for (int l = 0; l < L; l++) {
     const int sd = net.side[l];
@@ -725,16 +611,13 @@ cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const 
     mask_to_bf16<<<nblk(lp * kC, 256), 256, 0, s>>>(lp * kC, gz, net.z[l], net.g_bf);
     note_launches(1);
     const bf16* in = l == 0 ? net.a0 : net.pool[l];
-    conv32_wgrad_simt<<<P, 288, 0, s>>>(B, sd, in, net.g_bf, 1, net.wgrad_part, stride);
-    note_launches(1);
+    NN_CK(launch_wgrad_mma(B, sd, in, net.g_bf, 1, net.wgrad_part, stride, P, s));
     reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0,
                                                      net.grad + net.off_w[1 + l],
                                                      net.grad + net.off_b[1 + l]);
     note_launches(1);
-    conv32_simt<kF32><<<nblk(lp, 128), 128, 0, s>>>(B, sd, net.g_bf, net.wqT + per * l, nullptr,
-                                                    1, -1, nullptr, nullptr, nullptr,
-                                                    net.g_pool + net.lvl_off[l], nullptr);
-    note_launches(1);
+    NN_CK(launch_conv32_mma(2, B, sd, net.g_bf, net.wq + per * l, nullptr, 1, -1, nullptr,
+                            nullptr, nullptr, net.g_pool + net.lvl_off[l], nullptr, s));
   }
   // pooling chain: the gradient of p_{l-1} collects 0.25 of p_l's
   for (int l = L - 1; l >= 1; l--) {

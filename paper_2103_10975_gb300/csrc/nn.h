@@ -38,7 +38,8 @@ struct Net {
   float* adam_v = nullptr;
   long long adam_t = 0;
   __nv_bfloat16* wq = nullptr;  // BF16 copies of the 32->32 weights, [conv][tap][ci][co]
-  __nv_bfloat16* wqT = nullptr; // transposed taps for the data gradient, [conv][tap][co][ci]
+                                // (B operand of the data gradient)
+  __nv_bfloat16* wqT = nullptr; // [conv][tap][co][ci] (B operand of the forward pass)
   long long* offs_dev = nullptr;  // device copy of the 32->32 weight offsets
   // activations, NHWC with 32 channels, BF16 (masks are recovered from
   // post-ReLU values: relu(x) > 0 <=> x > 0)
@@ -64,6 +65,16 @@ struct Net {
   long long pyr = 0;                         // sum of level sizes (pixels) per sample
   int wparts = 0;                            // CTAs of the weight-gradient kernels
 };
+
+// Tensor-core 32 -> 32 convolution (mode 0: relu(conv + b) -> zo; 1: e = relu(conv + b)
+// -> zo and resid + e -> to; 2: conv (+ addend) -> fo in FP32).  wop is [tap][n][k].
+cudaError_t launch_conv32_mma(int mode, int B, int H, const __nv_bfloat16* in,
+                              const __nv_bfloat16* wop, const float* bias, int dil, int sign,
+                              __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
+                              float* fo, const float* addend, cudaStream_t s);
+// Tensor-core weight gradient partials of a 32 -> 32 convolution (nparts CTAs).
+cudaError_t launch_wgrad_mma(int B, int H, const __nv_bfloat16* in, const __nv_bfloat16* g,
+                             int dil, float* part, int stride, int nparts, cudaStream_t s);
 
 cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed);
 void net_destroy(Net& net);

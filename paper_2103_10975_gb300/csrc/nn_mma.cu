@@ -1,0 +1,292 @@
+// Tensor-core (mma.sync m16n8k16, BF16 operands, FP32 accumulation) kernels
+// for the 32 -> 32 channel 3x3 convolutions of the initial-guess network, as
+// implicit GEMMs over NHWC activations:
+//   conv32_mma : out[p][n] = sum_{tap,k} in[p + sign*dil*off(tap)][k] * Wop[tap][n][k]
+//                (forward: Wop = transposed-tap copy; data gradient: sign = -1
+//                with the other copy), M = pixels, N = 32, K = 9 * 32
+//   wgrad_mma  : part[cta][(tap*32 + k)*32 + o] = sum_p in[p + dil*off(tap)][k] g[p][o]
+//                M = 32 output channels, N = 288 (tap, input channel), K = pixels
+// A CTA owns 64 consecutive pixels of one image row at a time; the three input
+// rows it needs (with a dil-wide halo, zero outside the image) are staged in
+// shared memory with an 80-byte pixel stride, which keeps ldmatrix conflict-free.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "nn.h"
+
+namespace mlg {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTileP = 64;          // pixels per tile
+constexpr int kPix = 40;            // bf16 per staged pixel (32 + 8 pad)
+constexpr int kMaxDil = 2;
+constexpr int kTileW = kTileP + 2 * kMaxDil;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Stage rows y + s*dil*(ty-1) (ty = 0..2), columns x0 - dil .. x0 + 63 + dil of
+// image b into tile[ty][c][kPix] (zero outside the image).
+__device__ __forceinline__ void stage_rows(bf16* tile, const bf16* __restrict__ in, int b, int H,
+                                           int y, int x0, int dil, int s) {
+  const int cols = kTileP + 2 * dil;
+  for (int idx = threadIdx.x; idx < 3 * cols * 4; idx += blockDim.x) {
+    const int q = idx & 3;
+    const int c = (idx >> 2) % cols;
+    const int ty = (idx >> 2) / cols;
+    const int yy = y + s * dil * (ty - 1);
+    const int xx = x0 - dil + c;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < H)
+      v = *reinterpret_cast<const uint4*>(in + (((long long)b * H + yy) * H + xx) * kC + q * 8);
+    *reinterpret_cast<uint4*>(tile + (ty * kTileW + c) * kPix + q * 8) = v;
+  }
+}
+
+enum { kRelu = 0, kResid = 1, kF32 = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(128) conv32_mma(int B, int H, const bf16* __restrict__ in,
+                                                  const bf16* __restrict__ wop,
+                                                  const float* __restrict__ bias, int dil,
+                                                  int sign, bf16* __restrict__ zo,
+                                                  bf16* __restrict__ to,
+                                                  const bf16* __restrict__ resid,
+                                                  float* __restrict__ fo,
+                                                  const float* __restrict__ addend) {
+  __shared__ __align__(16) bf16 ws[9 * kC * kPix];       // [tap][n][k]
+  __shared__ __align__(16) bf16 tile[3 * kTileW * kPix];  // [ty][c][k]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int idx = threadIdx.x; idx < 9 * kC * 4; idx += blockDim.x) {
+    const int q = idx & 3, row = idx >> 2;  // row = tap*32 + n
+    *reinterpret_cast<uint4*>(ws + row * kPix + q * 8) =
+        *reinterpret_cast<const uint4*>(wop + row * kC + q * 8);
+  }
+  float bv[4][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; nt++) {
+    const int o = nt * 8 + 2 * (lane & 3);
+    bv[nt][0] = (MODE != kF32 && bias) ? bias[o] : 0.f;
+    bv[nt][1] = (MODE != kF32 && bias) ? bias[o + 1] : 0.f;
+  }
+  const int tpr = (H + kTileP - 1) / kTileP;  // tiles per row
+  const long long ntiles = (long long)B * H * tpr;
+  for (long long tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
+    const int tx = (int)(tIdx % tpr);
+    const int y = (int)((tIdx / tpr) % H);
+    const int b = (int)(tIdx / ((long long)tpr * H));
+    const int x0 = tx * kTileP;
+    __syncthreads();  // previous tile's readers are done (and ws is staged)
+    stage_rows(tile, in, b, H, y, x0, dil, sign);
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) acc[nt][e] = 0.f;
+    // A row address of this lane (ldmatrix x4: matrix q = lane/8, row lane%8)
+    const int arow = warp * 16 + ((lane >> 3) & 1) * 8 + (lane & 7);
+    const int acol = (lane >> 4) * 8;
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+      const int ty = t / 3, txx = t % 3;
+      const int c = arow + dil + sign * dil * (txx - 1);
+      const bf16* abase = tile + (ty * kTileW + c) * kPix + acol;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        unsigned a[4];
+        ldsm_x4(a, abase + h * 16);
+        unsigned bb[2][4];
+#pragma unroll
+        for (int pr = 0; pr < 2; pr++) {
+          // n-tiles 2pr, 2pr+1: matrix q -> n = (2pr + q/2)*8 + lane%8, k = (q%2)*8 + 16h
+          const int n = (2 * pr + (lane >> 4)) * 8 + (lane & 7);
+          const int k = ((lane >> 3) & 1) * 8 + 16 * h;
+          ldsm_x4(bb[pr], ws + (t * kC + n) * kPix + k);
+        }
+        mma16816(acc[0], a, bb[0][0], bb[0][1]);
+        mma16816(acc[1], a, bb[0][2], bb[0][3]);
+        mma16816(acc[2], a, bb[1][0], bb[1][1]);
+        mma16816(acc[3], a, bb[1][2], bb[1][3]);
+      }
+    }
+    // epilogue: rows lane/4 and lane/4 + 8 of this warp's 16 pixels
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      const int p = warp * 16 + (lane >> 2) + half * 8;
+      const int x = x0 + p;
+      if (x >= H) continue;
+      const long long pix = ((long long)b * H + y) * H + x;
+#pragma unroll
+      for (int nt = 0; nt < 4; nt++) {
+        const int o = nt * 8 + 2 * (lane & 3);
+        float v0 = acc[nt][half * 2 + 0] + bv[nt][0];
+        float v1 = acc[nt][half * 2 + 1] + bv[nt][1];
+        if (MODE == kRelu) {
+          *reinterpret_cast<__nv_bfloat162*>(zo + pix * kC + o) =
+              __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+        } else if (MODE == kResid) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+          *reinterpret_cast<__nv_bfloat162*>(zo + pix * kC + o) = __floats2bfloat162_rn(v0, v1);
+          const float2 sv = __bfloat1622float2(
+              *reinterpret_cast<const __nv_bfloat162*>(resid + pix * kC + o));
+          *reinterpret_cast<__nv_bfloat162*>(to + pix * kC + o) =
+              __floats2bfloat162_rn(sv.x + v0, sv.y + v1);
+        } else {
+          if (addend) {
+            const float2 ad = *reinterpret_cast<const float2*>(addend + pix * kC + o);
+            v0 += ad.x;
+            v1 += ad.y;
+          }
+          *reinterpret_cast<float2*>(fo + pix * kC + o) = make_float2(v0, v1);
+        }
+      }
+    }
+  }
+}
+
+// Weight gradient: every CTA accumulates, over its tiles, the 32 x 288 product
+// g^T * im2col(in) in registers (warp w owns n-tiles 9w .. 9w+8 of the 36) and
+// the bias sums, then writes them as its partial (layout (tap*32 + k)*32 + o,
+// bias at 9216 + o).
+__global__ void __launch_bounds__(128) wgrad_mma(int B, int H, const bf16* __restrict__ in,
+                                                 const bf16* __restrict__ g, int dil,
+                                                 float* __restrict__ part, int stride) {
+  __shared__ __align__(16) bf16 tile[3 * kTileW * kPix];
+  __shared__ __align__(16) bf16 gt[kTileP * kPix];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[2][9][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+    for (int j = 0; j < 9; j++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) acc[mt][j][e] = 0.f;
+  float bsum = 0.f;  // thread t < 32: bias sum of channel t
+  const int tpr = (H + kTileP - 1) / kTileP;
+  const long long ntiles = (long long)B * H * tpr;
+  for (long long tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
+    const int tx = (int)(tIdx % tpr);
+    const int y = (int)((tIdx / tpr) % H);
+    const int b = (int)(tIdx / ((long long)tpr * H));
+    const int x0 = tx * kTileP;
+    __syncthreads();
+    stage_rows(tile, in, b, H, y, x0, dil, 1);
+    for (int idx = threadIdx.x; idx < kTileP * 4; idx += blockDim.x) {
+      const int q = idx & 3, p = idx >> 2;
+      const int x = x0 + p;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (x < H) v = *reinterpret_cast<const uint4*>(g + (((long long)b * H + y) * H + x) * kC + q * 8);
+      *reinterpret_cast<uint4*>(gt + p * kPix + q * 8) = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kC) {
+      for (int p = 0; p < kTileP; p++) bsum += __bfloat162float(gt[p * kPix + threadIdx.x]);
+    }
+#pragma unroll
+    for (int ks = 0; ks < kTileP / 16; ks++) {  // 16 pixels per step
+      // A = g^T (o x p): transposed 8x8 tiles from gt rows p
+      unsigned a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; mt++) {
+        // matrices: q0 (o 0-7, p 0-7), q1 (o 8-15, p 0-7), q2 (o 0-7, p 8-15), q3 (o 8-15, p 8-15)
+        const int q = lane >> 3;
+        const int p = ks * 16 + (q >> 1) * 8 + (lane & 7);
+        const int o = mt * 16 + (q & 1) * 8;
+        ldsm_x4_t(a[mt], gt + p * kPix + o);
+      }
+#pragma unroll
+      for (int jp = 0; jp < 9; jp += 2) {
+        // n-tiles nt = 9*warp + jp (+1): n = tap*32 + k, tap = nt/4, k block = nt%4
+        unsigned bb[4];
+        const int q = lane >> 3;
+        const int ntq = 9 * warp + jp + (q >> 1);
+        const int ntc = ntq < 36 ? ntq : 35;
+        const int tap = ntc >> 2, kb = ntc & 3;
+        const int ty = tap / 3, txx = tap % 3;
+        const int p = ks * 16 + (q & 1) * 8 + (lane & 7);
+        const int c = p + dil + dil * (txx - 1);
+        ldsm_x4_t(bb, tile + (ty * kTileW + c) * kPix + kb * 8);
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+          mma16816(acc[mt][jp], a[mt], bb[0], bb[1]);
+          if (jp + 1 < 9) mma16816(acc[mt][jp + 1], a[mt], bb[2], bb[3]);
+        }
+      }
+    }
+  }
+  // write the partial: c0,c1 -> (o = row, n = col, col+1), c2,c3 -> o + 8
+  float* dst = part + (long long)blockIdx.x * stride;
+#pragma unroll
+  for (int mt = 0; mt < 2; mt++) {
+#pragma unroll
+    for (int j = 0; j < 9; j++) {
+      const int nt = 9 * warp + j;
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int o = mt * 16 + (lane >> 2) + (e >> 1) * 8;
+        const int n = nt * 8 + 2 * (lane & 3) + (e & 1);
+        dst[(long long)n * kC + o] = acc[mt][j][e];
+      }
+    }
+  }
+  if (threadIdx.x < kC) dst[9 * kC * kC + threadIdx.x] = bsum;
+}
+
+}  // namespace
+
+cudaError_t launch_conv32_mma(int mode, int B, int H, const __nv_bfloat16* in,
+                              const __nv_bfloat16* wop, const float* bias, int dil, int sign,
+                              __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
+                              float* fo, const float* addend, cudaStream_t s) {
+  if (dil < 1 || dil > kMaxDil) return cudaErrorInvalidValue;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (long long)B * H * ((H + kTileP - 1) / kTileP);
+  const int grid = (int)(ntiles < 8LL * nsm ? ntiles : 8LL * nsm);
+  if (mode == kRelu)
+    conv32_mma<kRelu><<<grid, 128, 0, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
+                                            addend);
+  else if (mode == kResid)
+    conv32_mma<kResid><<<grid, 128, 0, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
+                                             addend);
+  else
+    conv32_mma<kF32><<<grid, 128, 0, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
+                                           addend);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad_mma(int B, int H, const __nv_bfloat16* in, const __nv_bfloat16* g,
+                             int dil, float* part, int stride, int nparts, cudaStream_t s) {
+  if (dil < 1 || dil > kMaxDil) return cudaErrorInvalidValue;
+  wgrad_mma<<<nparts, 128, 0, s>>>(B, H, in, g, dil, part, stride);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace mlg

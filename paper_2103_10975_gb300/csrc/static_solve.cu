@@ -86,7 +86,7 @@ extern "C" mlgmres_status mlgmres_solve_static(int n, int m, double rtol, long l
   int bs = 0;
   const int maxb = gmres_max_blocks(true, 2, m, &bs);
   if (maxb < 1) return MLGMRES_ERR_CUDA;
-  long long want = (N + (long long)bs * 4 - 1) / ((long long)bs * 4);
+  long long want = (N + 511) / 512;
   int blocks = (int)(want < 1 ? 1 : (want > maxb ? maxb : want));
   if (blocks > kPartStride) blocks = kPartStride;
 
