@@ -306,6 +306,20 @@ def run_ours(args):
     # ---- comparison arms on the same GPU and the same time steps
     compare = {}
     if not args.no_compare:
+        # the method against plain GMRES without the x_{t-1} fallback: the
+        # network's guess competes with x0 = 0 only
+        s3 = pkg.Solver(n, m=M, rtol=RTOL, precision="fp32_refine", guess="learned",
+                        fallback="zero", warmup_steps=TAU0, train_iters=32, batch=8,
+                        seed=11 + rank)
+        tmp = []
+        run_series(s3, 0, TAU0 + W, True, False, tmp)
+        rr = []
+        mm = run_series(s3, TAU0 + W, K, True, True, rr)
+        compare["learned_fallback_zero"] = {
+            "ms_per_step": statistics.mean(mm),
+            "iters_per_step": statistics.mean(r["iters"] for r in rr),
+            "learned_guess_used_fraction": sum(1 for r in rr if r["guess_used"] == 2) / len(rr)}
+        s3.close()
         for name, kw in (("plain_fp64_zero", dict(precision="fp64", guess="zero")),
                          ("plain_fp64_prev", dict(precision="fp64", guess="prev")),
                          ("fp32_refine_zero", dict(precision="fp32_refine", guess="zero"))):
@@ -339,7 +353,7 @@ def run_ours(args):
             "compare": compare,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": byts / len(res),
+                         "algorithmic_bytes_per_step": byts / len(res),
                          "kernel": "gmres_persistent (FP32 variant)",
                          "peak_source": peak_kind,
                          "note": "V (8 MB) is L2-resident at 256^2: bytes served mostly by L2"},

@@ -60,8 +60,9 @@ enum {
 enum {
   MLGMRES_GUESS_ZERO = 0,    /* x0 = 0 */
   MLGMRES_GUESS_PREV = 1,    /* x0 = solution of the previous solve on this handle */
-  MLGMRES_GUESS_LEARNED = 2, /* x0 = s N(b/s), s = rms(b); kept only if its residual is
-                                finite and below the fallback's */
+  MLGMRES_GUESS_LEARNED = 2, /* x0 = c s N(b/s), s = rms(b); kept only if its residual
+                                (after the first cycle, see guess_select) is finite and
+                                below the fallback's */
   MLGMRES_GUESS_USER = 3     /* x0 = the caller's x_dev contents */
 };
 
@@ -102,6 +103,12 @@ typedef struct {
                                 the white rounding noise of the BF16 network output, which A
                                 amplifies by up to its condition number in the residual */
   float guess_omega;         /* damping of those sweeps (0 < omega <= 1) */
+  int guess_select;          /* how the learned guess competes with the fallback:
+                                0 = by E_k (Sec. 2.2): one GMRES(m) cycle from each, the
+                                    smaller true residual after it wins and the solve
+                                    continues from there (the losing cycle counts in
+                                    iters);
+                                1 = by the initial residual ||b - A x0|| */
   int fault_inject;          /* test hook, 0 in normal use.  1: the solver's CTA-group
                                 barrier waits for one CTA more than is launched, so its
                                 first wait runs out after barrier_timeout_s and the solve
@@ -119,7 +126,8 @@ typedef struct {
   double relres_true;        /* ||b - A x|| / ||b||, FP64, at exit */
   double relres_first_cycle; /* E_k: true relative residual after the first cycle (Sec. 2.2) */
   double relres_guess;       /* ||b - A x0|| / ||b|| of the guess used */
-  double relres_learned;     /* same for the learned candidate (-1 if none was formed) */
+  double relres_learned;     /* initial relative residual of the learned candidate (-1 if
+                                none was formed) */
   float tos_ms;              /* device time of the solve kernel (TOS, Sec. 2.2) */
   float guess_ms;            /* device time of the learned-guess forward pass and smoothing */
 } mlgmres_result;
@@ -128,7 +136,7 @@ typedef struct {
  * guess ZERO, fallback ZERO, replay_cap 64, warmup 50, p = 10, theta = 0.9,
  * deterministic_tos 0, train_iters 32, batch 8, lr 1e-3, seed 1,
  * grid_blocks 0, batch_slots 0, barrier_timeout_s 2, guess_smooth 8, guess_omega 0.8,
- * fault_inject 0. */
+ * guess_select 0, fault_inject 0. */
 void mlgmres_default_options(mlgmres_options* opt);
 
 /* Creates a solver for one grid and allocates all workspace on the current

@@ -54,6 +54,7 @@ class Options(ctypes.Structure):
         ("barrier_timeout_s", ctypes.c_double),
         ("guess_smooth", ctypes.c_int),
         ("guess_omega", ctypes.c_float),
+        ("guess_select", ctypes.c_int),
         ("fault_inject", ctypes.c_int),
     ]
 

@@ -89,12 +89,13 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
   ARG(o->fault_inject == 0 || o->fault_inject == 1, "fault_inject must be 0 or 1");
   ARG(o->guess_smooth >= 0 && o->guess_smooth <= 1000, "guess_smooth must be in 0..1000");
   ARG(o->guess_omega > 0.0f && o->guess_omega <= 1.0f, "guess_omega must be in (0, 1]");
+  ARG(o->guess_select == 0 || o->guess_select == 1, "guess_select must be 0 or 1");
 }
 
 // Run the persistent kernel for `count` tasks already staged in h->htasks,
 // with the group layout staged in h->hcfg / h->hwork.
 void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps,
-                cudaStream_t s, int vsmem = 0) {
+                cudaStream_t s, int vsmem = 0, long long max_iters = -1) {
   const size_t cfg_bytes = sizeof(int) * (size_t)(2 * (ngroups + 1) + ntasks);
   CK(cudaMemcpyAsync(h->dcfg, h->hcfg, cfg_bytes, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(h->dtasks, h->htasks, sizeof(SolveTask) * ntasks, cudaMemcpyHostToDevice,
@@ -106,7 +107,7 @@ void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps
   KParams kp;
   kp.m = h->opt.m;
   kp.rtol = h->opt.rtol;
-  kp.max_iters = h->opt.max_iters;
+  kp.max_iters = max_iters > 0 ? max_iters : h->opt.max_iters;
   kp.arnoldi_steps = arnoldi_steps;
   kp.vsmem = arnoldi_steps > 0 ? 0 : vsmem;
   kp.ngroups = ngroups;
@@ -254,6 +255,7 @@ void mlgmres_default_options(mlgmres_options* o) {
   o->batch_slots = 0;
   o->barrier_timeout_s = 2.0;
   o->guess_smooth = 8;
+  o->guess_select = 0;
   o->guess_omega = 0.8f;
   o->fault_inject = 0;
 }
@@ -430,31 +432,73 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
       }
       x_alt = cur;
     }
-    SolveTask t;
-    t.n = h->grid.n;
-    t.N = N;
-    t.b = b;
-    t.x = x;
-    t.x_alt = x_alt;
-    t.kappa = h->grid.kappa_dev;
-    t.res = h->dres;
-    t.hist = nullptr;
-    t.hist_cap = 0;
-    t.zero_x = 0;
-    stage_single(h, t, h->blocks);
+    // one persistent launch from the guess in xs (optionally competing with
+    // alt by initial residual), capped at maxit Arnoldi steps
+    auto run_one = [&](double* xs, const double* alt, long long maxit) {
+      SolveTask t;
+      t.n = h->grid.n;
+      t.N = N;
+      t.b = b;
+      t.x = xs;
+      t.x_alt = alt;
+      t.kappa = h->grid.kappa_dev;
+      t.res = h->dres;
+      t.hist = nullptr;
+      t.hist_cap = 0;
+      t.zero_x = 0;
+      stage_single(h, t, h->blocks);
+      run_solver(h, 1, 1, h->blocks, 0, s, h->vsmem, maxit);
+      CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      return h->hres[0];
+    };
     CK(cudaEventRecord(h->ev0, s));
-    run_solver(h, 1, 1, h->blocks, 0, s, h->vsmem);
+    DevResult fin;
+    long long extra_iters = 0;
+    int extra_cycles = 0;
+    if (x_alt && h->opt.guess_select == 0) {
+      // E_k selection: one GMRES(m) cycle from each candidate, keep the one
+      // with the smaller true residual after it and continue from there
+      const long long cyc = std::min<long long>(h->opt.m, h->opt.max_iters);
+      double* xa = const_cast<double*>(x_alt);
+      const DevResult ra = run_one(xa, nullptr, cyc);
+      const DevResult rb = run_one(x, nullptr, cyc);
+      const bool learned = std::isfinite(ra.relres_true) && ra.status != kErrTimeout &&
+                           (!std::isfinite(rb.relres_true) || ra.relres_true < rb.relres_true);
+      const DevResult& w = learned ? ra : rb;
+      const DevResult& l = learned ? rb : ra;
+      if (learned) CK(cudaMemcpyAsync(x, xa, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      extra_iters = l.iters;
+      extra_cycles = l.cycles;
+      r.relres_learned = ra.relres_guess;
+      if (learned) r.guess_used = MLGMRES_GUESS_LEARNED;
+      if (w.status == 0 || w.status == kErrTimeout || w.status == kErrNonfinite ||
+          w.iters + l.iters >= h->opt.max_iters) {
+        fin = w;
+      } else {
+        fin = run_one(x, nullptr, h->opt.max_iters - w.iters - l.iters);
+        fin.iters += w.iters;
+        fin.cycles += w.cycles;
+        fin.relres_first_cycle = w.relres_true;  // E_k of the chosen guess
+        fin.relres_guess = w.relres_guess;
+      }
+    } else {
+      fin = run_one(x, x_alt, h->opt.max_iters);
+      if (fin.used_alt) r.guess_used = MLGMRES_GUESS_LEARNED;
+      if (x_alt) r.relres_learned = fin.relres_alt;
+    }
     CK(cudaEventRecord(h->ev1, s));
-    CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->x_prev, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
     h->have_prev = true;
-    fill_result(h->hres[0], &r);
-    if (h->hres[0].used_alt) r.guess_used = MLGMRES_GUESS_LEARNED;
-    if (x_alt) {
-      r.relres_learned = h->hres[0].relres_alt;
-      CK(cudaEventElapsedTime(&r.guess_ms, h->ev2, h->ev0));
-    }
+    const int guess_used = r.guess_used;
+    const double relres_learned = r.relres_learned;
+    fill_result(fin, &r);
+    r.iters += extra_iters;
+    r.cycles += extra_cycles;
+    r.guess_used = guess_used;
+    r.relres_learned = relres_learned;
+    if (x_alt) CK(cudaEventElapsedTime(&r.guess_ms, h->ev2, h->ev0));
     CK(cudaEventElapsedTime(&r.tos_ms, h->ev0, h->ev1));
     if (mode == MLGMRES_GUESS_LEARNED && h->grid.dim == 2 && r.status != MLGMRES_ERR_TIMEOUT)
       r.admitted = gate_and_store(h, b, x, r, s);
