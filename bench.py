@@ -104,6 +104,22 @@ class Clocks:
 
 
 # --------------------------------------------------------------- helpers --
+def max_over_ranks(value, dist, device=None):
+    """The largest `value` over all ranks (the job's time is its slowest rank's);
+    the value itself when not distributed."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_ms_per_step(total_ms_this_rank, steps, world, dist, device=None):
+    """Replicas: every rank runs its own series of `steps` time steps; the job
+    processed steps * world time steps in the slowest rank's time."""
+    return max_over_ranks(total_ms_this_rank, dist, device) / (steps * world)
+
 def algorithmic_bytes(res, N, m, elem):
     """Bytes one solve must move: per Arnoldi step j the two CGS2 passes read
     V_0..V_{j-1} and V_0..V_j, w' and z and write v_j, z and w': elem*N*(2j + 6);
@@ -266,12 +282,7 @@ def run_ours(args):
     t_wall = time.perf_counter() - t_wall0
     launches = pkg.kernel_launches() - l0
     clk = clocks.stop()
-    total_ms = sum(ms)
-    if dist is not None:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = total_ms / (K * world)
+    value = aggregate_ms_per_step(sum(ms), K, world, dist, dev)
 
     # roofline of the dominant kernel (the persistent solver)
     hbm, peak_kind = peaks()
@@ -297,11 +308,7 @@ def run_ours(args):
         xh.copy_(xd, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3
-    if dist is not None:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, dist, dev)
 
     # ---- comparison arms on the same GPU and the same time steps
     compare = {}

@@ -2,6 +2,8 @@
 
     python -m paper_2103_10975_gb300.profile_cases solve --n 256 --blocks 128 --max-iters 300
     python -m paper_2103_10975_gb300.profile_cases nn --n 256 --batch 8
+    python -m paper_2103_10975_gb300.profile_cases batch --count 512 --nmax 512
+    python -m paper_2103_10975_gb300.profile_cases cube --n 192 --max-iters 500
 
 `solve` runs the same capped solve twice on one moving-Gaussian right-hand
 side (the second launch is the one to capture) and prints the device time
@@ -53,6 +55,43 @@ def nn_case(n, batch):
                                                                1e3 * sum(times[2:]) / 5))
 
 
+def batch_case(count, nmin, nmax, rtol, m):
+    """Independent systems with sides drawn from U{nmin..nmax} (seed 4001 + i),
+    FP32-refined GMRES(m), all in one persistent launch."""
+    import torch
+    from paper_2103_10975_gb300 import Solver
+    from synthetic import batched_instances
+    inst = batched_instances(count, n_min=nmin, n_max=nmax)
+    ns = [n for n, _ in inst]
+    bs = [torch.as_tensor(b).cuda() for _, b in inst]
+    s = Solver(max(ns), m=m, rtol=rtol, precision="fp32_refine", batch_slots=4096,
+               max_iters=10 ** 7)
+    xs, res = s.solve_batch(ns, bs)
+    worst = max(r["relres_true"] for r in res)
+    iters = sum(r["iters"] for r in res)
+    unknowns = sum(n * n for n in ns)
+    print("batch of %d systems (sides %d..%d, %d unknowns): %.1f ms for the launch, "
+          "%d Arnoldi steps in total, worst relres %.2e, status %s"
+          % (count, min(ns), max(ns), unknowns, res[0]["tos_ms"], iters, worst,
+             sorted(set(r["status"] for r in res))))
+
+
+def cube_case(n, m, max_iters):
+    """192^3 variable-coefficient Poisson (log-normal kappa, seed 5001), FP32-refined
+    GMRES(m) capped at max_iters steps; prints the device time per step."""
+    import torch
+    from paper_2103_10975_gb300 import Solver
+    from synthetic import MovingGaussians3D, lognormal_kappa
+    kap = lognormal_kappa(n, 5001).astype("float32")
+    b = torch.as_tensor(MovingGaussians3D(n, 5001, 200).rhs(0)).cuda()
+    s = Solver(n, dim=3, kappa=kap, m=m, rtol=1e-10, precision="fp32_refine",
+               max_iters=max_iters)
+    s.solve(b)
+    _, r = s.solve(b)
+    print("n=%d^3 m=%d: %d steps, %.1f ms, %.1f us/step, relres %.3e"
+          % (n, m, r["iters"], r["tos_ms"], 1e3 * r["tos_ms"] / r["iters"], r["relres_true"]))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="case", required=True)
@@ -66,11 +105,25 @@ def main(argv=None):
     b = sub.add_parser("nn")
     b.add_argument("--n", type=int, default=256)
     b.add_argument("--batch", type=int, default=8)
+    c = sub.add_parser("batch")
+    c.add_argument("--count", type=int, default=512)
+    c.add_argument("--nmin", type=int, default=64)
+    c.add_argument("--nmax", type=int, default=512)
+    c.add_argument("--rtol", type=float, default=1e-8)
+    c.add_argument("--m", type=int, default=30)
+    d = sub.add_parser("cube")
+    d.add_argument("--n", type=int, default=192)
+    d.add_argument("--m", type=int, default=50)
+    d.add_argument("--max-iters", type=int, default=500)
     args = ap.parse_args(argv)
     if args.case == "solve":
         solve_case(args.n, args.blocks, args.max_iters, args.m, args.precision, args.source)
-    else:
+    elif args.case == "nn":
         nn_case(args.n, args.batch)
+    elif args.case == "batch":
+        batch_case(args.count, args.nmin, args.nmax, args.rtol, args.m)
+    else:
+        cube_case(args.n, args.m, args.max_iters)
 
 
 if __name__ == "__main__":
