@@ -94,9 +94,9 @@ typedef struct {
   float lr;                  /* Adam learning rate */
   unsigned long long seed;   /* network initialisation and minibatch sampling */
   int grid_blocks;           /* solver CTAs; 0 = pick from the problem size */
-  int batch_slots;           /* CTA groups reserved for mlgmres_solve_batch (0 = none); each
-                                holds a basis for the handle's grid, and at most the number
-                                of co-resident CTAs is used */
+  int batch_slots;           /* CTAs (and at most as many basis workspaces for the handle's
+                                grid) reserved for mlgmres_solve_batch (0 = none); at most
+                                the number of co-resident CTAs is used */
   double barrier_timeout_s;  /* limit of every device-side wait (> 0) */
   int guess_smooth;          /* damped-Jacobi sweeps applied to the learned guess before it is
                                 scored (0 = the network output as it is).  The sweeps remove
@@ -114,6 +114,10 @@ typedef struct {
                                 first wait runs out after barrier_timeout_s and the solve
                                 returns MLGMRES_ERR_TIMEOUT (exercises the bounded-wait
                                 path without faulting the GPU) */
+  int v_stages;              /* FP32 basis held in HBM: shared-memory stages per warp through
+                                which the passes stream V with bulk copies (2..4), or 0 for
+                                direct loads; -1 = automatic (the autotuned value if
+                                mlgmres_autotune ran, else 2 when they fit, else 0) */
 } mlgmres_options;
 
 typedef struct {
@@ -136,7 +140,7 @@ typedef struct {
  * guess ZERO, fallback ZERO, replay_cap 64, warmup 50, p = 10, theta = 0.9,
  * deterministic_tos 0, train_iters 32, batch 8, lr 1e-3, seed 1,
  * grid_blocks 0, batch_slots 0, barrier_timeout_s 2, guess_smooth 8, guess_omega 0.8,
- * guess_select 0, fault_inject 0. */
+ * guess_select 0, fault_inject 0, v_stages -1. */
 void mlgmres_default_options(mlgmres_options* opt);
 
 /* Creates a solver for one grid and allocates all workspace on the current
@@ -158,9 +162,11 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b_dev, double* x_dev, vo
 /* Solves `count` (1..4096) independent systems, each on its own grid
  * (grids[i].dim must equal the handle's dim, grids[i].n must not exceed the
  * handle's n; 3D grids may carry their own kappa), in one persistent launch.
- * The handle must have been created with batch_slots > 0: every CTA group
- * (one CTA each) works through a list of systems, the lists balanced
- * largest-first by an n^(dim+2) cost estimate.  b_dev[i], x_dev[i]: device
+ * The handle must have been created with batch_slots > 0.  Its CTAs are split
+ * into groups by mlgmres_batch_plan: a system whose n^(dim+2) cost estimate
+ * exceeds the ideal per-CTA share gets a group of several CTAs, the rest of
+ * the CTAs form one-CTA groups, and every group works through its list of
+ * systems largest first.  b_dev[i], x_dev[i]: device
  * arrays of grids[i].n^dim doubles; b_dev and x_dev themselves are HOST arrays
  * of device pointers.  Guesses are ZERO (USER when the handle's mode is USER);
  * no pair is collected.  out: `count` results (host); tos_ms of each is the
@@ -255,6 +261,49 @@ mlgmres_status mlgmres_kernel_launches(long long* count);
 mlgmres_status mlgmres_solve_static(int n, int m, double rtol, long long max_iters,
                                     const double* b_dev, double* x_dev, void* stream,
                                     mlgmres_result* res);
+
+/* Result of mlgmres_autotune. */
+typedef struct {
+  int grid_blocks;        /* chosen CTA count for single solves */
+  int v_stages;           /* chosen bulk-copy stages (0 = direct loads; -1 = not applicable:
+                             FP64, or V in shared memory) */
+  float us_per_step;      /* device time per Arnoldi step at the choice */
+  int candidates;         /* configurations timed (<= 32) */
+  int cand_blocks[32];
+  int cand_stages[32];
+  float cand_us_per_step[32];
+  int from_cache;         /* 1: taken from the process-wide cache, nothing was timed */
+} mlgmres_tuning;
+
+/* Autotuner (the paper has no counterpart).  Times capped solves of `steps`
+ * Arnoldi steps (0 = 2m) of A x = b_dev from x0 = 0, with the handle's
+ * precision and m, for candidate launch shapes -- CTA counts around one per
+ * 512 grid points (x1/2, x1, x2, and the co-resident maximum) and, for an FP32
+ * basis held in HBM, 0/2/3/4 bulk-copy stages -- and keeps the fastest per
+ * step for this handle's later solves (options grid_blocks and v_stages set
+ * explicitly at create still win).  Results are cached per process by
+ * (device, dim, n, m, precision); a cached shape is reused without timing
+ * unless `retune` is 1.  Writes into an internal scratch vector (allocated
+ * here and freed before returning), records no (b, x) pair, synchronises
+ * `stream`.  out may be NULL.  ERR_ARG on a NULL handle or b_dev, steps < 0. */
+mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b_dev, int steps, int retune,
+                                void* stream, mlgmres_tuning* out);
+
+/* The batch schedule mlgmres_solve_batch uses, computed on the host only (no
+ * device work; the paper has no counterpart: it solves one system at a time).
+ * Splits `ctas` CTAs into groups and assigns each of the `count` systems of
+ * sides n[0..count-1] (dim 2 or 3) to one group.  Cost of a system: N n^2
+ * (Arnoldi steps grow like n^2, each moves O(N) values).  Systems whose cost
+ * exceeds total / ctas get a dedicated group of ceil(cost / (total / ctas))
+ * CTAs (at most one per 512 points, and one CTA is kept back while systems
+ * remain); the remaining CTAs become one-CTA groups (no more than systems
+ * left); the remaining systems, largest first, go to the group on which they
+ * would finish earliest.  Outputs (host arrays): *groups = G;
+ * group_ctas[0..G-1] (room for `ctas` ints) sum to at most ctas;
+ * group_of[0..count-1] in 0..G-1.  ERR_ARG on a bad dim, count < 1, ctas < 1,
+ * a side < 1 or a NULL pointer. */
+mlgmres_status mlgmres_batch_plan(int dim, int count, const int* n, int ctas, int* groups,
+                                  int* group_ctas, int* group_of);
 
 #ifdef __cplusplus
 }

@@ -56,7 +56,28 @@ class Options(ctypes.Structure):
         ("guess_omega", ctypes.c_float),
         ("guess_select", ctypes.c_int),
         ("fault_inject", ctypes.c_int),
+        ("v_stages", ctypes.c_int),
     ]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("grid_blocks", ctypes.c_int),
+        ("v_stages", ctypes.c_int),
+        ("us_per_step", ctypes.c_float),
+        ("candidates", ctypes.c_int),
+        ("cand_blocks", ctypes.c_int * 32),
+        ("cand_stages", ctypes.c_int * 32),
+        ("cand_us_per_step", ctypes.c_float * 32),
+        ("from_cache", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        k = self.candidates
+        return {"grid_blocks": self.grid_blocks, "v_stages": self.v_stages,
+                "us_per_step": self.us_per_step, "from_cache": self.from_cache,
+                "candidates": [(self.cand_blocks[i], self.cand_stages[i],
+                                self.cand_us_per_step[i]) for i in range(k)]}
 
 
 class Result(ctypes.Structure):
@@ -110,6 +131,12 @@ _SIGS = {
     "mlgmres_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_longlong, _vp, _vp, _vp,
                                             ctypes.POINTER(Result)]),
+    "mlgmres_autotune": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
+                                        ctypes.POINTER(Tuning)]),
+    "mlgmres_batch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None
@@ -154,6 +181,20 @@ def solve_static(n, b, x, m=30, rtol=1e-10, max_iters=10 ** 7, stream=None):
                                              _ptr(b), _ptr(x), _stream_handle(stream),
                                              ctypes.byref(r))
     return st, r.as_dict()
+
+
+def batch_plan(dim, sides, ctas):
+    """mlgmres_batch_plan: the CTA groups a batched launch would use (host
+    only).  Returns (group_ctas list, group_of list)."""
+    count = len(sides)
+    n = (ctypes.c_int * count)(*[int(v) for v in sides])
+    G = ctypes.c_int(0)
+    gc = (ctypes.c_int * max(1, int(ctas)))()
+    go = (ctypes.c_int * count)()
+    st = load_library().mlgmres_batch_plan(int(dim), count, n, int(ctas), ctypes.byref(G), gc, go)
+    if st != MLGMRES_OK:
+        raise MLGMRESError(st, "batch_plan: invalid arguments")
+    return list(gc[:G.value]), list(go)
 
 
 class MLGMRESError(RuntimeError):
@@ -261,6 +302,14 @@ class Solver:
                                           res)
         self._check(st, "solve_batch", (MLGMRES_OK, MLGMRES_NOT_CONVERGED))
         return xs, [r.as_dict() for r in res]
+
+    def autotune(self, b, steps=0, retune=False, stream=None):
+        """mlgmres_autotune: returns the tuning record as a dict."""
+        t = Tuning()
+        self._check(self.lib.mlgmres_autotune(self.h, _ptr(b), int(steps), int(bool(retune)),
+                                              _stream_handle(stream), ctypes.byref(t)),
+                    "autotune")
+        return t.as_dict()
 
     def train_step(self, stream=None, want_loss=False):
         loss = ctypes.c_float(-1.0)

@@ -1,845 +1,51 @@
-// Persistent restarted GMRES(m) for the discrete Poisson operator (Sec. 1.2,
-// Sec. 1.4, Sec. 3 of arXiv 2103.10975), one cooperative launch per solve or
-// per batch of solves.
-//
-// Each CTA group (all CTAs for a single solve, or one CTA per system of a
-// batch) owns one system at a time; its grid points are split into contiguous
-// per-CTA ranges of whole 32-point tiles.  One Arnoldi step is classical
-// Gram-Schmidt applied twice, arranged as two fused passes over the CTA's
-// points with one group barrier each (see solve_one):
-//   X: v_j (lazy normalisation of the previous step's vector), z = A v_j
-//      obtained from the SpMV of the unnormalised vector through the Arnoldi
-//      relation, and the dots h1 = V^T z;
-//   Y: w' = z - V h1 with the dots h2 = V^T w' in the same pass.
-// After each barrier every CTA sums the per-CTA partials in the same fixed
-// order, so all CTAs hold bit-identical coefficients and run the scalar
-// recurrences (Pythagorean norm, Hessenberg column, Givens rotation) redundantly
-// in shared memory with no extra synchronisation.  At a cycle end the
-// back-substitution y = R^{-1} g runs in shared memory, x += V y is accumulated
-// in FP64 and the true residual b - A x is recomputed in FP64 (the restart of
-// GMRES(k)).  The FP32 variant stores V and the work vectors in FP32 and so
-// runs every cycle as one step of mixed-precision iterative refinement.
-#include <math.h>
-
-#include "solver.h"
+// Host side of the persistent GMRES(m) solver (the kernel and its passes are
+// in gmres_kernel.cuh): variant dispatch, shared-memory budgets, and the FP64
+// operator and basis-conversion kernels used for inspection.
+#include "gmres_kernel.cuh"
 
 namespace mlg {
 
-// ---------------------------------------------------------------- stencils --
-// Sum over faces of kappa_f (u_c - u_nb), unscaled; neighbours outside the grid
-// are 0 (zero Dirichlet).  Writing the 2D/3D Laplacian as a sum of differences
-// keeps the rounding error relative to |A u| instead of |u|.
-template <typename T>
-__device__ __forceinline__ T stencil2d(const T* __restrict__ u, int i, int n, T uc) {
-  const int ix = i % n;
-  const int iy = i / n;
-  const T l = ix > 0 ? ldcg(u + i - 1) : T(0);
-  const T r = ix < n - 1 ? ldcg(u + i + 1) : T(0);
-  const T d = iy > 0 ? ldcg(u + i - n) : T(0);
-  const T t = iy < n - 1 ? ldcg(u + i + n) : T(0);
-  return ((uc - l) + (uc - r)) + ((uc - d) + (uc - t));
-}
-
-template <typename T>
-__device__ __forceinline__ T face(T kc, T knb) { return T(2) * kc * knb / (kc + knb); }
-
-template <typename T>
-__device__ __forceinline__ T stencil3d(const T* __restrict__ u, int i, int n,
-                                       const float* __restrict__ kappa, T uc) {
-  const int ix = i % n;
-  const int t = i / n;
-  const int iy = t % n;
-  const int iz = t / n;
-  const int nn = n * n;
-  const int off[6] = {-1, 1, -n, n, -nn, nn};
-  const bool has[6] = {ix > 0, ix < n - 1, iy > 0, iy < n - 1, iz > 0, iz < n - 1};
-  T acc = T(0);
-  if (kappa) {
-    const T kc = (T)__ldg(kappa + i);
-#pragma unroll
-    for (int f = 0; f < 6; f++) {
-      if (has[f]) {
-        const T knb = (T)__ldg(kappa + i + off[f]);
-        acc += face(kc, knb) * (uc - ldcg(u + i + off[f]));
-      } else {
-        acc += kc * uc;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int f = 0; f < 6; f++) acc += has[f] ? (uc - ldcg(u + i + off[f])) : uc;
-  }
-  return acc;
-}
-
-template <typename T, int DIM>
-__device__ __forceinline__ T stencil(const T* __restrict__ u, int i, int n,
-                                     const float* __restrict__ kappa, T uc) {
-  if constexpr (DIM == 2)
-    return stencil2d<T>(u, i, n, uc);
-  else
-    return stencil3d<T>(u, i, n, kappa, uc);
-}
-
-// ------------------------------------------------------------ basis layout --
-// V is stored tile-major: for every tile of 32 consecutive grid points the
-// `rows` basis values of each point follow each other, so a warp's column of
-// V (all k for its 32 points) is one contiguous run of rows * 32 elements and
-// each per-k access is one 128-byte (FP32) or 256-byte (FP64) segment.
-__host__ __device__ __forceinline__ long long vbase(int i, int rows) {
-  return ((long long)(i >> 5) * rows << 5) + (i & 31);
-}
-__host__ __device__ __forceinline__ long long vix(int k, int i, int rows) {
-  return vbase(i, rows) + ((long long)k << 5);
-}
-
-// ----------------------------------------------------------- shared state --
-template <typename T, int MAXM, int BS>
-struct Smem {
-  T red[BS / 32][MAXM + 2];      // per-warp partials in the working precision
-  double redd[BS / 32][4];       // per-warp partials of the FP64 residual norms
-  double tot[MAXM + 2];
-  double cr[MAXM], sr[MAXM];     // Givens products with the unrotated column
-  double Hu[(MAXM + 1) * MAXM];  // Hessenberg as built (Arnoldi relation), ld MAXM+1
-  double R[(MAXM + 1) * MAXM];   // the same columns after the Givens rotations
-  double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
-  T HuT[(MAXM + 1) * MAXM];      // Hu in the working precision
-  T coef[MAXM + 2];              // h1 in the working precision (gather output)
-  T h2c[MAXM + 2];               // pending second-pass coefficients of w'
-  T cc[MAXM + 2];                // A w' -> A v_j correction coefficients
-  double hn, anorm2, h2sq;
-  T invT;                        // 1 / hn in the working precision
-  T hn2T;                        // ||w'||^2 - ||h2||^2 in the working precision
-  int ctl, stop, flag, fallback;
-};
-
-// Warp partial of slot k (lane 0 stores it); block_finish then adds the warp
-// partials of slots 0..L-1 and writes the CTA's sums to part[k*kPartStride + lb].
-// All of it runs in the element type R (FP32 for the FP32 variant: the FP64
-// pipe of this GPU is ~1/64 of FP32 and would otherwise dominate).
-template <int LW, typename R, typename V>
-__device__ __forceinline__ void warp_slot(R (*red)[LW], int k, V v) {
-  R x = (R)v;
-  x = warp_sum(x);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = x;
-}
-
-// Sums acc[k] over the warp for all k < MAXM at once (butterfly transpose
-// reduction: 31 shuffles per 32 slots instead of 5 per slot); lane l ends with
-// the warp total of slot l (+32 for the second half when MAXM = 64), which it
-// stores to red[warp][slot] for slot < L.
-template <int LMAX, int MAXM, typename T>
-__device__ __forceinline__ void warp_slots(T (*red)[LMAX], T (&acc)[MAXM], int L) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int g = 0; g < MAXM / 32; g++) {
-    T v[32];
-#pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = acc[g * 32 + i];
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      const bool up = (lane & off) != 0;
-#pragma unroll
-      for (int i = 0; i < off; i++) {
-        const T send = up ? v[i] : v[i + off];
-        const T keep = up ? v[i + off] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-      }
-    }
-    const int slot = g * 32 + lane;
-    if (slot < L) red[warp][slot] = v[0];
-  }
-}
-
-// warp_slots for an accumulator array of K <= MAXM entries (padded to 32).
-template <int LMAX, int K, typename T>
-__device__ __forceinline__ void warp_slots_k(T (*red)[LMAX], const T (&acc)[K], int L) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int g = 0; g < (K + 31) / 32; g++) {
-    T v[32];
-#pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = (g * 32 + i < K) ? acc[g * 32 + i] : T(0);
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      const bool up = (lane & off) != 0;
-#pragma unroll
-      for (int i = 0; i < off; i++) {
-        const T send = up ? v[i] : v[i + off];
-        const T keep = up ? v[i + off] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-      }
-    }
-    const int slot = g * 32 + lane;
-    if (slot < L) red[warp][slot] = v[0];
-  }
-}
-
-template <int LW, int BS, typename R>
-__device__ __forceinline__ void block_finish(int L, R* part, int lb, R (*red)[LW], int ps) {
-  __syncthreads();
-  for (int k = threadIdx.x; k < L; k += BS) {
-    R s = R(0);
-#pragma unroll
-    for (int w = 0; w < BS / 32; w++) s += red[w][k];
-    part[(long long)k * ps + lb] = s;
-  }
-}
-
-// Sum of the group's partials for k < L, identical in every CTA (same order);
-// tot gets the sums in FP64, coef the same values in the working precision.
-// Each warp takes up to four slots at a time so their loads are in flight
-// together.
-template <int BS, typename R, typename T>
-__device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot, T* coef,
-                                       int ps) {
-  constexpr int NW = BS / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k0 = warp; k0 < L; k0 += 4 * NW) {
-    R s[4] = {R(0), R(0), R(0), R(0)};
-    for (int g = lane; g < nb; g += 32) {
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int k = k0 + q * NW;
-        if (k < L) s[q] += ldcg(part + (long long)k * ps + g);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) s[q] = warp_sum(s[q]);
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int k = k0 + q * NW;
-        if (k < L) {
-          tot[k] = (double)s[q];
-          coef[k] = (T)s[q];
-        }
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// Givens update of Hessenberg column c (Hu -> R): apply rotations 0..c-1, form
-// rotation c, update g, and return the stop code (0 go on, 1 end the cycle,
-// 2 non-finite).  Warp 0 only: the lanes form the products of the rotations
-// with the column's untouched entries in parallel, so lane 0's dependent chain
-// is one FMA per rotation.
-template <typename T, int MAXM, int BS>
-__device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, long long it,
-                             long long max_iters, int m, double* hist, long long hist_cap,
-                             double bnorm) {
-  constexpr int LD = MAXM + 1;
-  const int lane = threadIdx.x & 31;
-  const double* hc = sm.Hu + c * LD;
-  double* rc = sm.R + c * LD;
-  for (int i = lane; i < c; i += 32) {
-    sm.cr[i] = sm.cs[i] * hc[i + 1];
-    sm.sr[i] = sm.sn[i] * hc[i + 1];
-  }
-  __syncwarp();
-  int stop = 0;
-  if (lane == 0) {
-    double ri = hc[0];
-    for (int i = 0; i < c; i++) {
-      rc[i] = fma(sm.cs[i], ri, sm.sr[i]);
-      ri = fma(-sm.sn[i], ri, sm.cr[i]);
-    }
-    const double hsub = hc[c + 1];
-    const double rho = sqrt(fma(ri, ri, hsub * hsub));
-    if (rho == 0.0) {
-      sm.cs[c] = 1.0;
-      sm.sn[c] = 0.0;
-    } else {
-      const double inv = 1.0 / rho;
-      sm.cs[c] = ri * inv;
-      sm.sn[c] = hsub * inv;
-    }
-    rc[c] = rho;
-    rc[c + 1] = 0.0;
-    const double gc = sm.g[c];
-    sm.g[c + 1] = -sm.sn[c] * gc;
-    sm.g[c] = sm.cs[c] * gc;
-    const double res = fabs(sm.g[c + 1]);
-    if (hist && it <= hist_cap) hist[it - 1] = res / bnorm;
-    if (!isfinite(res) || !isfinite(hsub))
-      stop = 2;
-    else if (res <= rtol_bnorm || !(hsub * hsub > 1e-28 * sm.anorm2) || it >= max_iters ||
-             c + 1 >= m)
-      stop = 1;
-    sm.stop = stop;
-  }
-  __syncwarp();
-  return stop;
-}
-
-// ------------------------------------------------------------ the passes --
-// Grid points per thread per loop trip for an accumulator bucket of K slots:
-// small buckets take several points so that enough loads are in flight.
-template <typename T, int K>
-struct PointsPerTrip {
-  static constexpr int value = sizeof(T) == 4 ? (K <= 8 ? 4 : (K <= 24 ? 2 : 1)) : (K <= 8 ? 2 : 1);
-};
-
-// X pass for step j < K over this CTA's points [lo, hi): v_j = (w' - V h2)/hn,
-// z = (A w' - sum_i c_i v_i)/hn, then per-warp partials of h1 = V^T z (slots
-// 0..j) and ||z||^2 (slot j+1) into sm.red.
-template <typename T, int DIM, int MAXM, int BS, int K>
-__device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, int j, int n,
-                                       const T* __restrict__ WP, T* __restrict__ Z,
-                                       T* __restrict__ V, int rows, int voff,
-                                       const float* __restrict__ kappa, T s2t) {
-  constexpr int LMAX = MAXM + 2;
-  constexpr int U = PointsPerTrip<T, K>::value;
-  const int tid = threadIdx.x;
-  T acc[K];
-#pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = T(0);
-  T accZ = T(0);
-  const T inv = sm.invT;
-  const T cj = sm.cc[j];
-  for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
-    int ii[U];
-    bool ok_[U];
-    T wp[U], znum[U], vnum[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      ii[u] = i0 + u * BS;
-      ok_[u] = ii[u] < hi;
-      wp[u] = ok_[u] ? ldcg(WP + ii[u]) : T(0);
-    }
-    long long vb[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) vb[u] = vbase(ii[u] - voff, rows);
-    T col[U][K];
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (k < j) {
-#pragma unroll
-        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[vb[u] + (k << 5)] : T(0);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
-      vnum[u] = wp[u];
-    }
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (k < j) {
-        const T h2k = sm.h2c[k], ck = sm.cc[k];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          vnum[u] -= h2k * col[u][k];
-          znum[u] -= ck * col[u][k];
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const T vj = vnum[u] * inv;
-      const T z = (znum[u] - cj * vj) * inv;
-      if (ok_[u]) {
-        V[vb[u] + ((long long)j << 5)] = vj;
-        Z[ii[u]] = z;
-      }
-      accZ += z * z;
-#pragma unroll
-      for (int k = 0; k < K; k++) {
-        if (k < j)
-          acc[k] += col[u][k] * z;
-        else if (k == j)
-          acc[k] += vj * z;
-      }
-    }
-  }
-  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
-  warp_slot<LMAX>(sm.red, j + 1, accZ);
-}
-
-// Y pass for step j < K: w' = z - V h1 (stored), per-warp partials of
-// h2 = V^T w' (slots 0..j) and ||w'||^2 (slot j+1).
-template <typename T, int MAXM, int BS, int K>
-__device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, int j,
-                                       T* __restrict__ WP, const T* __restrict__ Z,
-                                       const T* __restrict__ V, int rows, int voff) {
-  constexpr int LMAX = MAXM + 2;
-  constexpr int U = PointsPerTrip<T, K>::value;
-  const int tid = threadIdx.x;
-  T acc[K];
-#pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = T(0);
-  T accN = T(0);
-  for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
-    int ii[U];
-    bool ok_[U];
-    T q[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      ii[u] = i0 + u * BS;
-      ok_[u] = ii[u] < hi;
-      q[u] = ok_[u] ? Z[ii[u]] : T(0);
-    }
-    long long vb[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) vb[u] = vbase(ii[u] - voff, rows);
-    T col[U][K];
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (k <= j) {
-#pragma unroll
-        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[vb[u] + (k << 5)] : T(0);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (k <= j) {
-        const T hk = sm.coef[k];
-#pragma unroll
-        for (int u = 0; u < U; u++) q[u] -= hk * col[u][k];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      if (ok_[u]) WP[ii[u]] = q[u];
-      accN += q[u] * q[u];
-#pragma unroll
-      for (int k = 0; k < K; k++)
-        if (k <= j) acc[k] += col[u][k] * q[u];
-    }
-  }
-  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
-  warp_slot<LMAX>(sm.red, j + 1, accN);
-}
-
-// Bucket dispatch: the pass instantiated for the smallest multiple of 8 above j.
-#define MLG_BUCKETS(CALL)                   \
-  switch (j >> 3) {                         \
-    case 0: CALL(8); break;                 \
-    case 1: CALL(16); break;                \
-    case 2: CALL(24); break;                \
-    case 3: CALL(32); break;                \
-    case 4: CALL(40); break;                \
-    case 5: CALL(48); break;                \
-    case 6: CALL(56); break;                \
-    default: CALL(64); break;               \
-  }
-
-// --------------------------------------------------------------- one solve --
-// Arnoldi step j of a cycle (CGS2 with two group barriers).  Entering it, the
-// work vector W holds w', the previous step's vector after its first
-// projection (w'_0 = r), h2 = V^T w' are its still unapplied second-pass
-// coefficients, hn = ||w' - V h2|| (Pythagoras) and c are the coefficients
-// that turn A w' into A v_j through the Arnoldi relation
-// A v_k = sum_i Hu(i,k) v_i:
-//   X: v_j = (w' - V h2)/hn,  z = (A w' - sum_i c_i v_i)/hn  (= A v_j),
-//      h1 = V_{0..j}^T z, ||z||^2                                 -> barrier
-//   Y: w'_{j+1} = z - V h1, h2 = V_{0..j}^T w'_{j+1}, ||w'_{j+1}||^2 -> barrier
-//   Hu(:,j) = h1 + h2, Hu(j+1,j) = hn_{j+1} = sqrt(||w'||^2 - ||h2||^2)
-// When the Pythagorean difference cancels (||h2||^2 > ||w'||^2 / 2) an
-// explicit pass applies h2 and measures the norm instead.  The Givens update
-// of column j runs on thread 0 while the CTA already starts the next X pass;
-// if it ends the cycle, that speculative pass is discarded.
-template <typename T, int DIM, int MAXM, int BS>
-__device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWork& w, int lb,
-                          int nb, unsigned long long& epoch, Smem<T, MAXM, BS>& sm) {
-  constexpr int LD = MAXM + 1;
-  constexpr int LMAX = MAXM + 2;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int n = tk.n;
-  const int N = tk.N;
-  const int m = kp.m;
-  const bool arnoldi = kp.arnoldi_steps > 0;
-  int chunk = (N + nb - 1) / nb;
-  chunk = (chunk + 31) & ~31;  // whole tiles of the basis layout
-  const int lo = min(N, lb * chunk);
-  const int hi = min(N, lo + chunk);
-  const int rows = m + 1;  // basis vectors per tile (V holds m+1 vectors)
-  // V lives in shared memory when this CTA's slice fits the reserved space
-  // (latency of a shared load instead of an L2 round trip); else in HBM.
-  // (only the FP32 2D variant has slices small enough to be worth a second
-  // instantiation of the passes; the global and the shared copies are kept
-  // apart so each pass uses the right address space)
-  const bool vshared = sizeof(T) == 4 && DIM == 2 && !arnoldi && kp.vsmem > 0 &&
-                       (long long)chunk * rows * (long long)sizeof(T) <= kp.vsmem;
-  T* __restrict__ Vg = (T*)w.V;
-  T* __restrict__ Vs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(&sm) +
-                                            sizeof(Smem<T, MAXM, BS>));
-  T* __restrict__ V = vshared ? Vs : Vg;  // cycle-end and fallback passes
-  const int voff = vshared ? lo : 0;
-  T* __restrict__ WP = (T*)w.W0;  // w' (read by neighbours in X, rewritten in Y)
-  T* __restrict__ Z = (T*)w.W1;   // z = A v_j, own rows only
-  const double h = 2.0 / (n + 1);
-  const double s2 = 1.0 / (h * h);
-  const T s2t = (T)s2;
-  const float* kappa = tk.kappa;
-  int red = 0;
-  const int ps = w.pstride;
-  auto part = [&]() { return w.part + (long long)(red & 1) * LMAX * ps; };
-  const bool leader = (lb == 0 && tid == 0);
-
-  long long iters = 0;
-  int cycles = 0;
-  int status = 1;
-  double relres = 0.0, relres_first = -1.0, relres_guess = -1.0, relres_alt = -1.0;
-  int used_alt = 0;
-  double bnorm = 0.0;
-  bool ok = true;
-
-  // ---- phase 0: ||b||, and the residuals of both guesses when an alternative
-  // (learned) guess competes with the fallback already in x.
-  if (!arnoldi) {
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-    const bool alt = tk.x_alt != nullptr;
-    for (int i = lo + tid; i < hi; i += BS) {
-      const double bi = tk.b[i];
-      v0 += bi * bi;
-      if (tk.zero_x) tk.x[i] = 0.0;
-      if (alt) {
-        const double xc = ldcg(tk.x + i);
-        const double r0 = bi - s2 * stencil<double, DIM>(tk.x, i, n, kappa, xc);
-        const double ac = ldcg(tk.x_alt + i);
-        const double r1 = bi - s2 * stencil<double, DIM>(tk.x_alt, i, n, kappa, ac);
-        v1 += r0 * r0;
-        v2 += r1 * r1;
-      }
-    }
-    warp_slot<4>(sm.redd, 0, v0);
-    if (alt) {
-      warp_slot<4>(sm.redd, 1, v1);
-      warp_slot<4>(sm.redd, 2, v2);
-    }
-    block_finish<4, BS, double>(alt ? 3 : 1, part(), lb, sm.redd, ps);
-    ok = group_sync(w.bar, epoch, &sm.flag);
-    if (!ok) goto abort;
-    gather<BS, double, T>(part(), alt ? 3 : 1, nb, sm.tot, sm.coef, ps);
-    red++;
-    bnorm = sqrt(sm.tot[0]);
-    if (bnorm == 0.0) {  // A x = 0 has the unique solution 0
-      for (int i = lo + tid; i < hi; i += BS) tk.x[i] = 0.0;
-      status = 0;
-      relres = 0.0;
-      relres_guess = 0.0;
-      relres_first = 0.0;
-      goto finish;
-    }
-    if (alt) {
-      const double rx = sqrt(sm.tot[1]), ra = sqrt(sm.tot[2]);
-      relres_alt = ra / bnorm;
-      if (isfinite(ra) && ra < rx) {
-        used_alt = 1;
-        for (int i = lo + tid; i < hi; i += BS) tk.x[i] = tk.x_alt[i];
-        ok = group_sync(w.bar, epoch, &sm.flag);
-        if (!ok) goto abort;
-      }
-    }
-  }
-
-  for (;;) {
-    // ---- restart: w'_0 = r = b - A x (FP64), beta = ||r||
-    {
-      double v0 = 0.0;
-      for (int i = lo + tid; i < hi; i += BS) {
-        double ri;
-        if (arnoldi) {
-          ri = tk.b[i];
-        } else {
-          const double xc = ldcg(tk.x + i);
-          ri = tk.b[i] - s2 * stencil<double, DIM>(tk.x, i, n, kappa, xc);
-        }
-        WP[i] = (T)ri;
-        v0 += ri * ri;
-      }
-      for (int k = tid; k < LMAX; k += BS) {
-        sm.h2c[k] = T(0);
-        sm.cc[k] = T(0);
-      }
-      warp_slot<4>(sm.redd, 0, v0);
-      block_finish<4, BS, double>(1, part(), lb, sm.redd, ps);
-      ok = group_sync(w.bar, epoch, &sm.flag);
-      if (!ok) goto abort;
-      gather<BS, double, T>(part(), 1, nb, sm.tot, sm.coef, ps);
-      red++;
-    }
-    const double beta = sqrt(sm.tot[0]);
-    if (arnoldi) {
-      bnorm = beta;
-    } else {
-      relres = beta / bnorm;
-      if (cycles == 0) relres_guess = relres;
-      if (cycles == 1) relres_first = relres;
-      if (!isfinite(relres)) { status = kErrNonfinite; break; }
-      if (relres <= kp.rtol) { status = 0; break; }
-      if (iters >= kp.max_iters) { status = 1; break; }
-    }
-    if (beta == 0.0) { status = 0; break; }
-    if (tid == 0) {
-      for (int k = 0; k <= MAXM; k++) sm.g[k] = 0.0;
-      sm.g[0] = beta;
-      sm.hn = beta;
-      sm.invT = (T)(1.0 / beta);
-      sm.stop = 0;
-    }
-    __syncthreads();
-    const double rtol_bnorm = kp.rtol * bnorm;
-    double* hist = (lb == 0) ? tk.hist : nullptr;
-    int kcols = 0;
-    const int jmax = arnoldi ? kp.arnoldi_steps : m;
-    for (int j = 0;; j++) {
-      // ---- X: v_j and z = A v_j, h1 = V^T z; warp 1 rotates column j-1
-      // while thread 0 waits at the group barrier
-      {
-#define MLG_X(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vg, rows, 0, kappa, s2t)
-#define MLG_XS(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vs, rows, lo, kappa, s2t)
-        if constexpr (sizeof(T) == 4 && DIM == 2) {
-          if (vshared) {
-            MLG_BUCKETS(MLG_XS)
-          } else {
-            MLG_BUCKETS(MLG_X)
-          }
-        } else {
-          MLG_BUCKETS(MLG_X)
-        }
-#undef MLG_X
-#undef MLG_XS
-        if (arnoldi && j == jmax) { kcols = j; break; }
-        auto givens_prev = [&]() {
-          if (j > 0 && !arnoldi)
-            givens_column<T, MAXM, BS>(sm, j - 1, rtol_bnorm, iters, kp.max_iters, m, hist,
-                                       tk.hist_cap, bnorm);
-        };
-        block_finish<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red, ps);
-        ok = group_sync_with(w.bar, epoch, &sm.flag, givens_prev);
-        if (!ok) goto abort;
-        const int stop = sm.stop;
-        if (stop == 2) { status = kErrNonfinite; goto finish; }
-        if (stop == 1) { kcols = j; break; }
-        gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef, ps);
-        red++;
-        if (tid <= j) sm.Hu[tid + j * LD] = sm.tot[tid];
-        if (tid == 0) sm.anorm2 = sm.tot[j + 1];
-      }
-      // ---- Y: w'_{j+1} = z - V h1, h2 = V^T w'_{j+1}, ||w'_{j+1}||^2
-      {
-#define MLG_Y(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vg, rows, 0)
-#define MLG_YS(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vs, rows, lo)
-        if constexpr (sizeof(T) == 4 && DIM == 2) {
-          if (vshared) {
-            MLG_BUCKETS(MLG_YS)
-          } else {
-            MLG_BUCKETS(MLG_Y)
-          }
-        } else {
-          MLG_BUCKETS(MLG_Y)
-        }
-#undef MLG_Y
-#undef MLG_YS
-        block_finish<LMAX, BS, T>(j + 2, (T*)part(), lb, sm.red, ps);
-        ok = group_sync(w.bar, epoch, &sm.flag);
-        if (!ok) goto abort;
-        gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef, ps);
-        red++;
-      }
-      iters++;
-      // ---- column j of Hu; hn_{j+1} = sqrt(||w'||^2 - ||h2||^2), in the working
-      // precision (both terms come from reductions in that precision)
-      if (tid <= j) {
-        const double hv = sm.Hu[tid + j * LD] + sm.tot[tid];
-        sm.Hu[tid + j * LD] = hv;
-        sm.HuT[tid + j * LD] = (T)hv;
-        sm.h2c[tid] = sm.coef[tid];
-      }
-      if (tid < 32) {
-        T q = T(0);
-        for (int k = lane; k <= j; k += 32) q += sm.coef[k] * sm.coef[k];
-        q = warp_sum(q);
-        if (lane == 0) {
-          const T wn2 = sm.coef[j + 1];
-          const T hn2 = wn2 - q;
-          sm.fallback = !(hn2 > T(0.5) * wn2);
-          sm.hn2T = hn2;
-        }
-      }
-      __syncthreads();
-      if (sm.fallback) {
-        // cancellation: apply h2 explicitly and measure ||w''||
-        T accN = T(0);
-        for (int i = lo + tid; i < hi; i += BS) {
-          T q = WP[i];
-#pragma unroll
-          for (int k = 0; k < MAXM; k++)
-            if (k <= j) q -= sm.h2c[k] * V[vix(k, i - voff, rows)];
-          WP[i] = q;
-          accN += q * q;
-        }
-        warp_slot<LMAX>(sm.red, 0, accN);
-        block_finish<LMAX, BS, T>(1, (T*)part(), lb, sm.red, ps);
-        ok = group_sync(w.bar, epoch, &sm.flag);
-        if (!ok) goto abort;
-        gather<BS, T, T>((const T*)part(), 1, nb, sm.tot, sm.coef, ps);
-        red++;
-        if (tid == 0) sm.hn2T = sm.coef[0];
-        if (tid <= j) sm.h2c[tid] = T(0);
-        __syncthreads();
-      }
-      if (tid < 32) {
-        if (lane == 0) {
-          const T h2v = sm.hn2T > T(0) ? sm.hn2T : T(0);
-          const T hnT = sqrt(h2v);
-          sm.invT = T(1) / hnT;
-          const double hnext = (double)hnT;
-          sm.hn = hnext;
-          sm.Hu[j + 1 + j * LD] = hnext;
-          sm.HuT[j + 1 + j * LD] = hnT;
-          if (arnoldi) {
-            if (hist)
-              for (int k = 0; k <= j + 1; k++) hist[(long long)j * (jmax + 1) + k] = sm.Hu[k + j * LD];
-            sm.stop = !(hnext * hnext > 1e-28 * sm.anorm2) ? 1 : 0;
-          }
-        }
-        __syncwarp();
-        // c_i = sum_{k >= i-1} Hu(i,k) h2_k for the next X pass
-        for (int i = lane; i <= j + 1; i += 32) {
-          T c = T(0);
-          for (int k = (i > 0 ? i - 1 : 0); k <= j; k++) c += sm.HuT[i + k * LD] * sm.h2c[k];
-          sm.cc[i] = c;
-        }
-      }
-      __syncthreads();
-      if (!arnoldi && j + 1 >= m) {
-        // last column of the cycle: rotate it now (no further X pass)
-        if (tid < 32)
-          givens_column<T, MAXM, BS>(sm, j, rtol_bnorm, iters, kp.max_iters, m, hist,
-                                     tk.hist_cap, bnorm);
-        __syncthreads();
-        if (sm.stop == 2) { status = kErrNonfinite; goto finish; }
-        kcols = j + 1;
-        break;
-      }
-    }
-    if (arnoldi) {
-      status = kcols;  // steps done; V_0..V_kcols written by the X passes
-      break;
-    }
-    // ---- cycle end: y = R^{-1} g (upper triangular), x += V y
-    if (threadIdx.x < 32) {
-      for (int i = kcols - 1; i >= 0; i--) {
-        const double yi = sm.g[i] / sm.R[i + i * LD];
-        for (int l = lane; l < i; l += 32) sm.g[l] -= sm.R[l + i * LD] * yi;
-        if (lane == 0) sm.y[i] = yi;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int i = lo + tid; i < hi; i += BS) {
-      double d = 0.0;
-      const long long vb = vbase(i - voff, rows);
-      for (int k = 0; k < kcols; k++) d += sm.y[k] * (double)V[vb + ((long long)k << 5)];
-      tk.x[i] += d;
-    }
-    cycles++;
-    ok = group_sync(w.bar, epoch, &sm.flag);
-    if (!ok) goto abort;
-  }
-  goto finish;
-
-abort:
-  status = *(volatile int*)w.bar.err;
-  if (status == 0) status = kErrTimeout;
-
-finish:
-  if (leader) {
-    DevResult r;
-    r.iters = iters;
-    r.cycles = cycles;
-    r.status = status;
-    r.used_alt = used_alt;
-    r.pad = 0;
-    r.bnorm = bnorm;
-    r.relres_true = relres;
-    r.relres_first_cycle = relres_first < 0.0 ? relres : relres_first;
-    r.relres_guess = relres_guess;
-    r.relres_alt = relres_alt;
-    *tk.res = r;
-  }
-}
-
-template <typename T, int DIM, int MAXM, int BS>
-__global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<T, MAXM, BS>& sm = *reinterpret_cast<Smem<T, MAXM, BS>*>(smem_raw);
-  int g = 0;
-  while (g + 1 < kp.ngroups && (int)blockIdx.x >= kp.group_first[g + 1]) g++;
-  const int lb = blockIdx.x - kp.group_first[g];
-  const int nb = kp.group_first[g + 1] - kp.group_first[g];
-  const GroupWork w = kp.work[g];
-  unsigned long long epoch = 0;
-  for (int t = kp.task_first[g]; t < kp.task_first[g + 1]; t++) {
-    const SolveTask tk = kp.tasks[kp.task_order[t]];
-    solve_one<T, DIM, MAXM, BS>(kp, tk, w, lb, nb, epoch, sm);
-    if (*(volatile int*)w.bar.err != kErrNone) break;
-    // all CTAs finish with this task's data before the next task starts
-    if (!group_sync(w.bar, epoch, &sm.flag)) break;
-  }
-}
-
-// ------------------------------------------------------------- host side --
-// The shared state lives in dynamic shared memory (up to ~107 KB for m <= 64).
-template <typename T, int DIM, int MAXM, int BS>
-static cudaError_t prepare_t(int extra = 0) {
-  return cudaFuncSetAttribute(gmres_persistent<T, DIM, MAXM, BS>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(Smem<T, MAXM, BS>) + extra);
-}
-
-template <typename T, int DIM, int MAXM, int BS>
-static cudaError_t launch_t(const KParams& kp, int grid, cudaStream_t s) {
-  cudaError_t e = prepare_t<T, DIM, MAXM, BS>(kp.vsmem);
-  if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&kp};
-  note_launches(1);
-  return cudaLaunchCooperativeKernel((const void*)gmres_persistent<T, DIM, MAXM, BS>, dim3(grid),
-                                     dim3(BS), args, sizeof(Smem<T, MAXM, BS>) + kp.vsmem, s);
-}
-
-template <typename T, int DIM, int MAXM, int BS>
-static int max_blocks_t(int* bs) {
-  int dev = 0, nsm = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (prepare_t<T, DIM, MAXM, BS>() != cudaSuccess) return 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gmres_persistent<T, DIM, MAXM, BS>, BS,
-                                                sizeof(Smem<T, MAXM, BS>));
-  *bs = BS;
-  return per * nsm;
-}
-
 // Variant table: 256-thread CTAs (the register budget of 255 per thread keeps the
 // V column and the dot accumulators of a pass in registers); the passes are
-// instantiated per bucket of j, so one variant per precision and dimension.
-#define MLG_DISPATCH(FN, ...)                                      \
-  (void)m;                                                         \
-  if (fp32) {                                                      \
-    if (dim == 2) return FN<float, 2, kMaxM, 256>(__VA_ARGS__);    \
-    return FN<float, 3, kMaxM, 256>(__VA_ARGS__);                  \
-  } else {                                                         \
-    if (dim == 2) return FN<double, 2, kMaxM, 256>(__VA_ARGS__);   \
-    return FN<double, 3, kMaxM, 256>(__VA_ARGS__);                 \
-  }
+// instantiated per bucket of j, so one variant per precision and dimension,
+// each in its own translation unit (gmres_{f,d}{2,3}.cu).
+cudaError_t launch_gmres_f2(const KParams& kp, int grid, cudaStream_t s);
+cudaError_t launch_gmres_f3(const KParams& kp, int grid, cudaStream_t s);
+cudaError_t launch_gmres_d2(const KParams& kp, int grid, cudaStream_t s);
+cudaError_t launch_gmres_d3(const KParams& kp, int grid, cudaStream_t s);
+int max_blocks_f2(int* bs);
+int max_blocks_f3(int* bs);
+int max_blocks_d2(int* bs);
+int max_blocks_d3(int* bs);
 
 cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid, cudaStream_t s) {
-  const int m = kp.arnoldi_steps > 0 ? kp.arnoldi_steps : kp.m;
-  MLG_DISPATCH(launch_t, kp, grid, s);
+  if (fp32) return dim == 2 ? launch_gmres_f2(kp, grid, s) : launch_gmres_f3(kp, grid, s);
+  return dim == 2 ? launch_gmres_d2(kp, grid, s) : launch_gmres_d3(kp, grid, s);
 }
 
-int gmres_max_blocks(bool fp32, int dim, int m, int* bs) { MLG_DISPATCH(max_blocks_t, bs); }
+int gmres_max_blocks(bool fp32, int dim, int m, int* bs) {
+  (void)m;
+  if (fp32) return dim == 2 ? max_blocks_f2(bs) : max_blocks_f3(bs);
+  return dim == 2 ? max_blocks_d2(bs) : max_blocks_d3(bs);
+}
+
+bool gmres_stages_fit(int m, int P) {
+  return P >= 0 && P <= kMaxStages && 4LL * 8 * P * m * 32 <= gmres_vsmem_budget(true);
+}
+
+int gmres_bulk_stages(bool fp32, int m) {
+  // two stages measured fastest on GB300 at 1024^2 and 2048^2 (m = 40) and
+  // 192^3 (m = 50): 662 against 880 (three) and 860 (direct) us per step at 2048^2
+  if (!fp32) return 0;
+  return gmres_stages_fit(m, 2) ? 2 : 0;
+}
 
 int gmres_vsmem_budget(bool fp32) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int own = fp32 ? (int)sizeof(Smem<float, kMaxM, 256>) : (int)sizeof(Smem<double, kMaxM, 256>);
+  const int own = fp32 ? (int)smem_own_bytes<float, kMaxM, 256>()
+                       : (int)smem_own_bytes<double, kMaxM, 256>();
   const int left = optin - own - 1024;
   return left > 0 ? left : 0;
 }

@@ -20,6 +20,7 @@ struct mlgmres {
   int max_blocks = 0;   // co-resident limit of the kernel variant
   int bs = 0;
   int vsmem = 0;        // shared-memory bytes for the V slice of a single solve
+  int tuned_stages = -1;  // bulk-copy stages chosen by mlgmres_autotune (-1 = none)
 
   // ---- solver workspace (one group for single solves) ----
   long long ldv = 0;

@@ -8,9 +8,13 @@
 #include <cmath>
 #include <cstdio>
 #include <string>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "handle.h"
+#include "schedule.h"
 #include "misc.h"
 
 using namespace mlg;
@@ -90,12 +94,33 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
   ARG(o->guess_smooth >= 0 && o->guess_smooth <= 1000, "guess_smooth must be in 0..1000");
   ARG(o->guess_omega > 0.0f && o->guess_omega <= 1.0f, "guess_omega must be in (0, 1]");
   ARG(o->guess_select == 0 || o->guess_select == 1, "guess_select must be 0 or 1");
+  ARG(o->v_stages == -1 || o->v_stages == 0 || (o->v_stages >= 2 && o->v_stages <= 4),
+      "v_stages must be -1, 0 or 2..4");
+  ARG(o->v_stages <= 0 || o->precision == MLGMRES_FP64 || gmres_stages_fit(o->m, o->v_stages),
+      "v_stages: the stages do not fit in shared memory for this m");
+}
+
+// Bulk-copy stages the passes use for an FP32 basis in HBM.
+int effective_stages(const mlgmres* h) {
+  if (!h->fp32) return 0;
+  if (h->opt.v_stages >= 0) return h->opt.v_stages;
+  if (h->tuned_stages >= 0) return h->tuned_stages;
+  return gmres_bulk_stages(true, h->opt.m);
+}
+
+// Shared-memory bytes of a single solve's V slice at `blocks` CTAs (0 if the
+// slice does not fit).
+int single_vsmem(const mlgmres* h, int blocks) {
+  const long long chunk = (((long long)h->N + blocks - 1) / blocks + 31) / 32 * 32;
+  const long long need = chunk * (h->opt.m + 1) * (h->fp32 ? 4 : 8);
+  const int budget = gmres_vsmem_budget(h->fp32);
+  return need <= budget ? (int)need : 0;
 }
 
 // Run the persistent kernel for `count` tasks already staged in h->htasks,
 // with the group layout staged in h->hcfg / h->hwork.
 void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps,
-                cudaStream_t s, int vsmem = 0, long long max_iters = -1) {
+                cudaStream_t s, int vsmem = 0, long long max_iters = -1, int stages = -1) {
   const size_t cfg_bytes = sizeof(int) * (size_t)(2 * (ngroups + 1) + ntasks);
   CK(cudaMemcpyAsync(h->dcfg, h->hcfg, cfg_bytes, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(h->dtasks, h->htasks, sizeof(SolveTask) * ntasks, cudaMemcpyHostToDevice,
@@ -110,6 +135,7 @@ void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps
   kp.max_iters = max_iters > 0 ? max_iters : h->opt.max_iters;
   kp.arnoldi_steps = arnoldi_steps;
   kp.vsmem = arnoldi_steps > 0 ? 0 : vsmem;
+  kp.bulk_stages = stages >= 0 ? stages : effective_stages(h);
   kp.ngroups = ngroups;
   kp.group_first = h->dcfg;
   kp.task_first = h->dcfg + (ngroups + 1);
@@ -258,6 +284,7 @@ void mlgmres_default_options(mlgmres_options* o) {
   o->guess_select = 0;
   o->guess_omega = 0.8f;
   o->fault_inject = 0;
+  o->v_stages = -1;
 }
 
 mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* opt,
@@ -285,13 +312,7 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
                                      : auto_blocks(h, h->N);
     h->blocks = std::min(h->blocks, kPartStride);
     h->ldv = ((long long)h->N + 63) / 64 * 64;
-    {
-      // shared-memory slice of V for single solves when it fits
-      const long long chunk = (((long long)h->N + h->blocks - 1) / h->blocks + 31) / 32 * 32;
-      const long long need = chunk * (opt->m + 1) * (h->fp32 ? 4 : 8);
-      const int budget = gmres_vsmem_budget(h->fp32);
-      h->vsmem = need <= budget ? (int)need : 0;
-    }
+    h->vsmem = single_vsmem(h, h->blocks);  // V slice in shared memory when it fits
     const size_t es = h->fp32 ? sizeof(float) : sizeof(double);
     CK(cudaMalloc(&h->V, es * (size_t)(opt->m + 1) * h->ldv));
     CK(cudaMalloc(&h->W0, es * (size_t)h->ldv));
@@ -527,36 +548,26 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
       ARG(b[i] && x[i] && b[i] != x[i], "b and x must be distinct device pointers");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const int G = std::min(h->batch_groups, count);
     const int dim = h->grid.dim;
-    // largest first onto the least-loaded group (iterations grow about like n^2,
-    // so the work of a system is about N n^2)
-    std::vector<int> order(count);
-    std::vector<double> cost(count);
-    for (int i = 0; i < count; i++) {
-      order[i] = i;
-      const double n = grids[i].n;
-      cost[i] = grid_points(dim, grids[i].n) * n * n;
-    }
-    std::sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-    std::vector<double> load(G, 0.0);
-    std::vector<std::vector<int>> lists(G);
-    for (int i : order) {
-      int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-      load[g] += cost[i];
-      lists[g].push_back(i);
-    }
+    // CTA groups in proportion to the systems' cost (see schedule.cu)
+    std::vector<int> sides(count), gctas, gof, order;
+    for (int i = 0; i < count; i++) sides[i] = grids[i].n;
+    const int G = plan_batch(dim, count, sides.data(), h->batch_groups, gctas, gof, order);
+    ARG(G >= 1 && G <= h->batch_groups, "batch schedule failed");
     int* gf = h->hcfg;
     int* tf = h->hcfg + (G + 1);
     int* to = h->hcfg + 2 * (G + 1);
-    int pos = 0;
+    int pos = 0, cta = 0;
     for (int g = 0; g < G; g++) {
-      gf[g] = g;
+      gf[g] = cta;
+      cta += gctas[g];
       tf[g] = pos;
-      for (int i : lists[g]) to[pos++] = i;
+      for (int i : order)
+        if (gof[i] == g) to[pos++] = i;
     }
-    gf[G] = G;
+    gf[G] = cta;
     tf[G] = pos;
+    const int grid_ctas = cta;
     const size_t es = h->fp32 ? sizeof(float) : sizeof(double);
     for (int i = 0; i < count; i++) {
       SolveTask t;
@@ -572,17 +583,19 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
       t.zero_x = h->opt.guess == MLGMRES_GUESS_USER ? 0 : 1;
       h->htasks[i] = t;
     }
+    long long part_off = 0;
     for (int g = 0; g < G; g++) {
       GroupWork w;
       w.V = (char*)h->Vb + es * (size_t)g * (h->opt.m + 1) * h->ldv;
       w.ldv = h->ldv;
       w.W0 = (char*)h->Wb + es * (size_t)g * 2 * h->ldv;
       w.W1 = (char*)w.W0 + es * h->ldv;
-      w.part = h->partb + (size_t)g * part_doubles(1);
-      w.pstride = 1;
+      w.part = h->partb + part_off;
+      part_off += part_doubles(gctas[g]);
+      w.pstride = gctas[g];
       w.bar.ctr = h->bar + g;
       w.bar.err = h->err + g;
-      w.bar.nblocks = 1;
+      w.bar.nblocks = (unsigned)gctas[g];
       w.bar.timeout_ns = (unsigned long long)(h->opt.barrier_timeout_s * 1e9);
       h->hwork[g] = w;
     }
@@ -590,14 +603,16 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
     {
       long long need = 0;
       for (int i = 0; i < count; i++) {
-        const long long chunk = (grid_points(dim, grids[i].n) + 31) / 32 * 32;
+        const long long N = grid_points(dim, grids[i].n);
+        const long long k = gctas[gof[i]];
+        const long long chunk = ((N + k - 1) / k + 31) / 32 * 32;
         need = std::max(need, chunk * (h->opt.m + 1) * (long long)es);
       }
       const int budget = gmres_vsmem_budget(h->fp32);
       vsmem = need <= budget ? (int)need : 0;
     }
     CK(cudaEventRecord(h->ev0, s));
-    run_solver(h, G, count, G, 0, s, vsmem);
+    run_solver(h, G, count, grid_ctas, 0, s, vsmem);
     CK(cudaEventRecord(h->ev1, s));
     CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult) * count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -659,6 +674,138 @@ mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_ho
     }
     return MLGMRES_OK;
   } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+namespace {
+struct TuneKey {
+  int dev, dim, n, m, fp32;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, dim, n, m, fp32) < std::tie(o.dev, o.dim, o.n, o.m, o.fp32);
+  }
+};
+struct TuneVal {
+  int blocks, stages;
+  float us;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+}  // namespace
+
+mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int retune, void* stream,
+                                mlgmres_tuning* out) {
+  if (!h) return MLGMRES_ERR_ARG;
+  h->last_error.clear();
+  double* xs = nullptr;
+  try {
+    ARG(b != nullptr, "null b");
+    ARG(steps >= 0, "steps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (steps == 0) steps = 2 * h->opt.m;
+    const TuneKey key{h->dev, h->grid.dim, h->grid.n, h->opt.m, h->fp32 ? 1 : 0};
+    mlgmres_tuning t;
+    memset(&t, 0, sizeof(t));
+    auto apply = [&](int blocks, int stages) {
+      if (h->opt.grid_blocks == 0) {
+        h->blocks = blocks;
+        h->vsmem = single_vsmem(h, blocks);
+      }
+      h->tuned_stages = stages;
+    };
+    if (!retune) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        apply(it->second.blocks, it->second.stages);
+        t.grid_blocks = h->blocks;
+        t.v_stages = it->second.stages;
+        t.us_per_step = it->second.us;
+        t.from_cache = 1;
+        if (out) *out = t;
+        return MLGMRES_OK;
+      }
+    }
+    if (h->train_pending) CK(cudaStreamWaitEvent(s, h->train_done, 0));
+    CK(cudaMalloc(&xs, sizeof(double) * (size_t)h->N));
+    // candidate CTA counts around one per 512 points, and the co-resident limit
+    std::vector<int> blocks;
+    const int cap = std::min(h->max_blocks, kPartStride);
+    if (h->opt.grid_blocks > 0) {
+      blocks.push_back(h->blocks);
+    } else {
+      const int base = auto_blocks(h, h->N);
+      for (int c : {base / 2, base, base * 2, cap}) {
+        c = std::max(1, std::min(c, cap));
+        if (std::find(blocks.begin(), blocks.end(), c) == blocks.end()) blocks.push_back(c);
+      }
+    }
+    int best_b = h->blocks, best_p = -1;
+    float best_us = INFINITY;
+    for (int nb : blocks) {
+      const int vs = single_vsmem(h, nb);
+      // the FP32 2D passes keep V in shared memory when the slice fits
+      const bool shared = h->fp32 && h->grid.dim == 2 && vs > 0;
+      std::vector<int> stages;
+      if (!h->fp32 || shared) {
+        stages.push_back(-1);
+      } else if (h->opt.v_stages >= 0) {
+        stages.push_back(h->opt.v_stages);
+      } else {
+        for (int P : {0, 2, 3, 4})
+          if (P == 0 || gmres_stages_fit(h->opt.m, P)) stages.push_back(P);
+      }
+      for (int P : stages) {
+        if (t.candidates >= 32) break;
+        SolveTask tk;
+        tk.n = h->grid.n;
+        tk.N = h->N;
+        tk.b = b;
+        tk.x = xs;
+        tk.x_alt = nullptr;
+        tk.kappa = h->grid.kappa_dev;
+        tk.res = h->dres;
+        tk.hist = nullptr;
+        tk.hist_cap = 0;
+        tk.zero_x = 1;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; rep++) {  // the first run warms up
+          stage_single(h, tk, nb);
+          CK(cudaEventRecord(h->ev0, s));
+          run_solver(h, 1, 1, nb, 0, s, vs, steps, P < 0 ? 0 : P);
+          CK(cudaEventRecord(h->ev1, s));
+          CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        }
+        const DevResult r = h->hres[0];
+        ARG(r.status == 0 || r.status == 1, "autotune: a timed solve failed");
+        const float us = r.iters > 0 ? 1000.f * ms / (float)r.iters : INFINITY;
+        t.cand_blocks[t.candidates] = nb;
+        t.cand_stages[t.candidates] = P;
+        t.cand_us_per_step[t.candidates] = us;
+        t.candidates++;
+        if (us < best_us) {
+          best_us = us;
+          best_b = nb;
+          best_p = P;
+        }
+      }
+    }
+    CK(cudaFree(xs));
+    xs = nullptr;
+    apply(best_b, best_p);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = TuneVal{best_b, best_p, best_us};
+    }
+    t.grid_blocks = h->blocks;
+    t.v_stages = best_p;
+    t.us_per_step = best_us;
+    if (out) *out = t;
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    if (xs) cudaFree(xs);
     return f.st;
   }
 }

@@ -57,6 +57,7 @@ struct KParams {
   long long max_iters;
   int arnoldi_steps;        // > 0: run that many Arnoldi steps only (inspection mode)
   int vsmem;                // bytes of shared memory for a CTA's slice of V (0 = V in HBM)
+  int bulk_stages;          // bulk-copy stages per warp when V is in HBM (FP32; 0 = off)
   int ngroups;
   const int* group_first;   // ngroups+1 CTA ranges
   const int* task_first;    // ngroups+1 ranges into task_order
@@ -75,6 +76,13 @@ int gmres_max_blocks(bool fp32, int dim, int m, int* block_threads);
 // Shared-memory bytes a CTA may use for its slice of V (so that slice + the
 // solver's own state fit the per-CTA limit); 0 if none.
 int gmres_vsmem_budget(bool fp32);
+
+// Default bulk-copy stages per warp for an FP32 basis in HBM: 2 when they fit
+// next to the solver's state, else 0 (FP64: 0).
+int gmres_bulk_stages(bool fp32, int m);
+
+// Whether P bulk-copy stages per warp (of m 32-point rows each) fit.
+bool gmres_stages_fit(int m, int P);
 
 // FP64 operator application out = A u (2D or 3D) on one grid.
 cudaError_t launch_apply(int dim, int n, const float* kappa, const double* u, double* out,

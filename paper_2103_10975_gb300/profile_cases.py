@@ -5,6 +5,9 @@
     python -m paper_2103_10975_gb300.profile_cases batch --count 512 --nmax 512
     python -m paper_2103_10975_gb300.profile_cases cube --n 192 --max-iters 500
 
+--stages selects the bulk-copy depth for an FP32 basis in HBM (0 = direct
+loads, -1 = automatic); --autotune runs mlgmres_autotune first.
+
 `solve` runs the same capped solve twice on one moving-Gaussian right-hand
 side (the second launch is the one to capture) and prints the device time
 per Arnoldi step; `nn` runs the network's forward + backward seven times on
@@ -21,7 +24,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def solve_case(n, blocks, max_iters, m, precision, source):
+def solve_case(n, blocks, max_iters, m, precision, source, stages=-1, autotune=False):
     import torch
     from paper_2103_10975_gb300 import Solver
     from synthetic import MovingGaussians2D, RandomWalkSources2D
@@ -30,11 +33,16 @@ def solve_case(n, blocks, max_iters, m, precision, source):
     else:
         b = MovingGaussians2D(n, 2001, 500).rhs(0)
     bd = torch.as_tensor(b).cuda()
-    s = Solver(n, m=m, rtol=1e-10, precision=precision, grid_blocks=blocks, max_iters=max_iters)
+    s = Solver(n, m=m, rtol=1e-10, precision=precision, grid_blocks=blocks, max_iters=max_iters,
+               v_stages=stages)
+    if autotune:
+        t = s.autotune(bd, retune=True)
+        print("autotune:", t)
     s.solve(bd)
     _, r = s.solve(bd)
-    print("n=%d m=%d %s blocks=%d: %d steps, %.3f ms, %.2f us/step"
-          % (n, m, precision, blocks, r["iters"], r["tos_ms"], 1e3 * r["tos_ms"] / r["iters"]))
+    print("n=%d m=%d %s blocks=%d stages=%d: %d steps, %.3f ms, %.2f us/step"
+          % (n, m, precision, blocks, stages, r["iters"], r["tos_ms"],
+             1e3 * r["tos_ms"] / r["iters"]))
 
 
 def nn_case(n, batch):
@@ -55,7 +63,7 @@ def nn_case(n, batch):
                                                                1e3 * sum(times[2:]) / 5))
 
 
-def batch_case(count, nmin, nmax, rtol, m):
+def batch_case(count, nmin, nmax, rtol, m, stages=-1):
     """Independent systems with sides drawn from U{nmin..nmax} (seed 4001 + i),
     FP32-refined GMRES(m), all in one persistent launch."""
     import torch
@@ -65,7 +73,7 @@ def batch_case(count, nmin, nmax, rtol, m):
     ns = [n for n, _ in inst]
     bs = [torch.as_tensor(b).cuda() for _, b in inst]
     s = Solver(max(ns), m=m, rtol=rtol, precision="fp32_refine", batch_slots=4096,
-               max_iters=10 ** 7)
+               max_iters=10 ** 7, v_stages=stages)
     xs, res = s.solve_batch(ns, bs)
     worst = max(r["relres_true"] for r in res)
     iters = sum(r["iters"] for r in res)
@@ -76,7 +84,7 @@ def batch_case(count, nmin, nmax, rtol, m):
              sorted(set(r["status"] for r in res))))
 
 
-def cube_case(n, m, max_iters):
+def cube_case(n, m, max_iters, stages=-1, autotune=False):
     """192^3 variable-coefficient Poisson (log-normal kappa, seed 5001), FP32-refined
     GMRES(m) capped at max_iters steps; prints the device time per step."""
     import torch
@@ -85,7 +93,9 @@ def cube_case(n, m, max_iters):
     kap = lognormal_kappa(n, 5001).astype("float32")
     b = torch.as_tensor(MovingGaussians3D(n, 5001, 200).rhs(0)).cuda()
     s = Solver(n, dim=3, kappa=kap, m=m, rtol=1e-10, precision="fp32_refine",
-               max_iters=max_iters)
+               max_iters=max_iters, v_stages=stages)
+    if autotune:
+        print("autotune:", s.autotune(b, retune=True))
     s.solve(b)
     _, r = s.solve(b)
     print("n=%d^3 m=%d: %d steps, %.1f ms, %.1f us/step, relres %.3e"
@@ -102,6 +112,8 @@ def main(argv=None):
     a.add_argument("--m", type=int, default=30)
     a.add_argument("--precision", default="fp32_refine")
     a.add_argument("--source", default="moving", choices=["moving", "walk"])
+    a.add_argument("--stages", type=int, default=-1)
+    a.add_argument("--autotune", action="store_true")
     b = sub.add_parser("nn")
     b.add_argument("--n", type=int, default=256)
     b.add_argument("--batch", type=int, default=8)
@@ -111,19 +123,23 @@ def main(argv=None):
     c.add_argument("--nmax", type=int, default=512)
     c.add_argument("--rtol", type=float, default=1e-8)
     c.add_argument("--m", type=int, default=30)
+    c.add_argument("--stages", type=int, default=-1)
     d = sub.add_parser("cube")
     d.add_argument("--n", type=int, default=192)
     d.add_argument("--m", type=int, default=50)
     d.add_argument("--max-iters", type=int, default=500)
+    d.add_argument("--stages", type=int, default=-1)
+    d.add_argument("--autotune", action="store_true")
     args = ap.parse_args(argv)
     if args.case == "solve":
-        solve_case(args.n, args.blocks, args.max_iters, args.m, args.precision, args.source)
+        solve_case(args.n, args.blocks, args.max_iters, args.m, args.precision, args.source,
+                   args.stages, args.autotune)
     elif args.case == "nn":
         nn_case(args.n, args.batch)
     elif args.case == "batch":
-        batch_case(args.count, args.nmin, args.nmax, args.rtol, args.m)
+        batch_case(args.count, args.nmin, args.nmax, args.rtol, args.m, args.stages)
     else:
-        cube_case(args.n, args.m, args.max_iters)
+        cube_case(args.n, args.m, args.max_iters, args.stages, args.autotune)
 
 
 if __name__ == "__main__":

@@ -18,6 +18,7 @@ from .sources import (
     RandomWalkSources2D,
     MovingGaussians3D,
     batched_instances,
+    batched_sides,
     lognormal_kappa,
     mode_rhs_2d,
 )
@@ -25,5 +26,5 @@ from .sources import (
 __all__ = [
     "SplitMix64", "splitmix64_stream", "uniform_stream", "normal_stream",
     "grid_coords", "MovingGaussians2D", "RandomWalkSources2D", "MovingGaussians3D",
-    "batched_instances", "lognormal_kappa", "mode_rhs_2d",
+    "batched_instances", "batched_sides", "lognormal_kappa", "mode_rhs_2d",
 ]

@@ -167,6 +167,11 @@ class MovingGaussians3D:
         return b.reshape(-1)
 
 
+def batched_sides(count, base_seed=4001, n_min=64, n_max=512):
+    """The sides of batched_instances without building the right-hand sides."""
+    return [SplitMix64(base_seed + i).randint(n_min, n_max) for i in range(count)]
+
+
 def batched_instances(count, base_seed=4001, n_min=64, n_max=512):
     """Independent instances for the batched workload: instance i uses seed
     base_seed + i; its first draw is the side n_i ~ U{n_min..n_max}, the rest
