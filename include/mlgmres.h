@@ -114,10 +114,17 @@ typedef struct {
                                 first wait runs out after barrier_timeout_s and the solve
                                 returns MLGMRES_ERR_TIMEOUT (exercises the bounded-wait
                                 path without faulting the GPU) */
-  int v_stages;              /* FP32 basis held in HBM: shared-memory stages per warp through
-                                which the passes stream V with bulk copies (2..4), or 0 for
-                                direct loads; -1 = automatic (the autotuned value if
-                                mlgmres_autotune ran, else 2 when they fit, else 0) */
+  int v_stages;              /* FP32 basis held in HBM: most shared-memory stages per warp
+                                through which the passes stream V with bulk copies (2..16;
+                                a pass uses as many as fit in the warp's share of shared
+                                memory for its j rows), or 0 for direct loads; -1 =
+                                automatic (the autotuned value if mlgmres_autotune ran,
+                                else 16) */
+  int retrain_after;         /* f_r of Algorithm 1 (Sec. 2.2): when > 0, mlgmres_solve itself
+                                starts a training phase (as mlgmres_train_step, on a stream
+                                of the handle) once f_r pairs have been admitted since the
+                                previous phase, and from tau0 on; 0 = the caller decides
+                                when to call mlgmres_train_step (fixed cadence) */
 } mlgmres_options;
 
 typedef struct {
@@ -134,13 +141,14 @@ typedef struct {
                                 none was formed) */
   float tos_ms;              /* device time of the solve kernel (TOS, Sec. 2.2) */
   float guess_ms;            /* device time of the learned-guess forward pass and smoothing */
+  int trained;               /* 1 if this solve started a training phase (retrain_after) */
 } mlgmres_result;
 
 /* Fills *opt with the defaults: m = 30, rtol = 1e-10, max_iters = 10^7, FP64,
  * guess ZERO, fallback ZERO, replay_cap 64, warmup 50, p = 10, theta = 0.9,
  * deterministic_tos 0, train_iters 32, batch 8, lr 1e-3, seed 1,
  * grid_blocks 0, batch_slots 0, barrier_timeout_s 2, guess_smooth 8, guess_omega 0.8,
- * guess_select 0, fault_inject 0, v_stages -1. */
+ * guess_select 0, fault_inject 0, v_stages -1, retrain_after 0. */
 void mlgmres_default_options(mlgmres_options* opt);
 
 /* Creates a solver for one grid and allocates all workspace on the current
@@ -279,7 +287,7 @@ typedef struct {
  * Arnoldi steps (0 = 2m) of A x = b_dev from x0 = 0, with the handle's
  * precision and m, for candidate launch shapes -- CTA counts around one per
  * 512 grid points (x1/2, x1, x2, and the co-resident maximum) and, for an FP32
- * basis held in HBM, 0/2/3/4 bulk-copy stages -- and keeps the fastest per
+ * basis held in HBM, 0/2/4/8/16 bulk-copy stages -- and keeps the fastest per
  * step for this handle's later solves (options grid_blocks and v_stages set
  * explicitly at create still win).  Results are cached per process by
  * (device, dim, n, m, precision); a cached shape is reused without timing

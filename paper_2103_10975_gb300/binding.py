@@ -57,6 +57,7 @@ class Options(ctypes.Structure):
         ("guess_select", ctypes.c_int),
         ("fault_inject", ctypes.c_int),
         ("v_stages", ctypes.c_int),
+        ("retrain_after", ctypes.c_int),
     ]
 
 
@@ -94,6 +95,7 @@ class Result(ctypes.Structure):
         ("relres_learned", ctypes.c_double),
         ("tos_ms", ctypes.c_float),
         ("guess_ms", ctypes.c_float),
+        ("trained", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -14,6 +14,7 @@ long long launches_so_far();
 constexpr int kErrNone = 0;
 constexpr int kErrTimeout = -4;
 constexpr int kErrNonfinite = -5;
+constexpr int kErrConfig = -6;  // launch parameters inconsistent with a task (reported as ERR_CUDA)
 
 // Loads of data that another CTA wrote before a grid barrier go through L2
 // (ld.global.cg) so a stale L1 line can never be read.
@@ -72,9 +73,12 @@ __device__ __forceinline__ bool group_sync_with(const GroupBarrier& gb,
     return *s_flag != 0;
   }
   if (threadIdx.x == 0) {
+    // the CTA's writes are ordered before this release by the CTA barrier
+    // above; the acquire loads below order the other CTAs' writes before the
+    // CTA barrier that ends the wait (release/acquire at gpu scope, cumulative
+    // through bar.sync), so no separate fences are needed
     epoch += 1;
     const unsigned long long target = epoch * (unsigned long long)gb.nblocks;
-    __threadfence();
     red_release_add_u64(gb.ctr, 1ull);
     int ok = 1;
     if (ld_acquire_u64(gb.ctr) < target) {
@@ -89,7 +93,6 @@ __device__ __forceinline__ bool group_sync_with(const GroupBarrier& gb,
       }
     }
     if (ok && *(volatile int*)gb.err != kErrNone) ok = 0;
-    __threadfence();
     *s_flag = ok;
   }
   __syncthreads();

@@ -7,37 +7,54 @@ namespace mlg {
 
 // Variant table: 256-thread CTAs (the register budget of 255 per thread keeps the
 // V column and the dot accumulators of a pass in registers); the passes are
-// instantiated per bucket of j, so one variant per precision and dimension,
-// each in its own translation unit (gmres_{f,d}{2,3}.cu).
-cudaError_t launch_gmres_f2(const KParams& kp, int grid, cudaStream_t s);
-cudaError_t launch_gmres_f3(const KParams& kp, int grid, cudaStream_t s);
-cudaError_t launch_gmres_d2(const KParams& kp, int grid, cudaStream_t s);
-cudaError_t launch_gmres_d3(const KParams& kp, int grid, cudaStream_t s);
-int max_blocks_f2(int* bs);
-int max_blocks_f3(int* bs);
-int max_blocks_d2(int* bs);
-int max_blocks_d3(int* bs);
+// instantiated per bucket of j; one variant per precision, dimension and
+// placement of V, each in its own translation unit (gmres_<variant>.cu).
+#define MLG_VARIANT(tag)                                                \
+  cudaError_t launch_gmres_##tag(const KParams& kp, int grid, cudaStream_t s); \
+  int max_blocks_##tag(int* bs);
+MLG_VARIANT(f2d)
+MLG_VARIANT(f2s)
+MLG_VARIANT(f2b)
+MLG_VARIANT(f3d)
+MLG_VARIANT(f3b)
+MLG_VARIANT(d2)
+MLG_VARIANT(d3)
+#undef MLG_VARIANT
 
 cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid, cudaStream_t s) {
-  if (fp32) return dim == 2 ? launch_gmres_f2(kp, grid, s) : launch_gmres_f3(kp, grid, s);
-  return dim == 2 ? launch_gmres_d2(kp, grid, s) : launch_gmres_d3(kp, grid, s);
+  if (!fp32) {
+    if (kp.vmode != kVDirect) return cudaErrorInvalidValue;
+    return dim == 2 ? launch_gmres_d2(kp, grid, s) : launch_gmres_d3(kp, grid, s);
+  }
+  if (dim == 2) {
+    if (kp.vmode == kVShared) return launch_gmres_f2s(kp, grid, s);
+    if (kp.vmode == kVBulk) return launch_gmres_f2b(kp, grid, s);
+    return launch_gmres_f2d(kp, grid, s);
+  }
+  if (kp.vmode == kVShared) return cudaErrorInvalidValue;
+  if (kp.vmode == kVBulk) return launch_gmres_f3b(kp, grid, s);
+  return launch_gmres_f3d(kp, grid, s);
 }
 
+// The co-resident limit of the direct variant (every variant runs one 256-thread
+// CTA per SM: 255 registers per thread).
 int gmres_max_blocks(bool fp32, int dim, int m, int* bs) {
   (void)m;
-  if (fp32) return dim == 2 ? max_blocks_f2(bs) : max_blocks_f3(bs);
+  if (fp32) return dim == 2 ? max_blocks_f2d(bs) : max_blocks_f3d(bs);
   return dim == 2 ? max_blocks_d2(bs) : max_blocks_d3(bs);
 }
 
-bool gmres_stages_fit(int m, int P) {
-  return P >= 0 && P <= kMaxStages && 4LL * 8 * P * m * 32 <= gmres_vsmem_budget(true);
+int gmres_bulk_cap(int m, int P) {
+  if (P <= 0) return 0;
+  const long long share = (long long)gmres_vsmem_budget(true) / 4 / 8 / 32 * 32;  // floats
+  const long long want = (long long)P * m * 32;
+  const long long cap = want < share ? want : share;
+  return cap >= (long long)m * 32 ? (int)cap : 0;
 }
 
 int gmres_bulk_stages(bool fp32, int m) {
-  // two stages measured fastest on GB300 at 1024^2 and 2048^2 (m = 40) and
-  // 192^3 (m = 50): 662 against 880 (three) and 860 (direct) us per step at 2048^2
   if (!fp32) return 0;
-  return gmres_stages_fit(m, 2) ? 2 : 0;
+  return gmres_bulk_cap(m, kMaxStages) > 0 ? kMaxStages : 0;
 }
 
 int gmres_vsmem_budget(bool fp32) {

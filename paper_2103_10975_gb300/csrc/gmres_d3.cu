@@ -1,13 +1,13 @@
-// One variant of the persistent GMRES(m) kernel (FP64, 3D
-// operator), compiled on its own so that the variants build in parallel.
+// One variant of the persistent GMRES(m) kernel (FP64, 3D),
+// compiled on its own so that the variants build in parallel.
 #include "gmres_kernel.cuh"
 
 namespace mlg {
 
 cudaError_t launch_gmres_d3(const KParams& kp, int grid, cudaStream_t s) {
-  return launch_t<double, 3, kMaxM, 256>(kp, grid, s);
+  return launch_t<double, 3, kMaxM, 256, kVDirect>(kp, grid, s);
 }
 
-int max_blocks_d3(int* bs) { return max_blocks_t<double, 3, kMaxM, 256>(bs); }
+int max_blocks_d3(int* bs) { return max_blocks_t<double, 3, kMaxM, 256, kVDirect>(bs); }
 
 }  // namespace mlg

@@ -95,7 +95,7 @@ __host__ __device__ __forceinline__ long long vix(int k, int i, int rows) {
 }
 
 // ----------------------------------------------------------- shared state --
-constexpr int kMaxStages = 4;  // bulk-copy stages per warp (upper bound)
+constexpr int kMaxStages = 16;  // bulk-copy stages per warp (upper bound)
 
 template <typename T, int MAXM, int BS>
 struct Smem {
@@ -335,10 +335,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phas
 }
 
 struct BulkPipe {
-  float* stage;                // [warp][P][cap] tiles of V
+  float* stage;                // [warp][cap] staging area of each warp
   unsigned long long* bar;     // [warp][kMaxStages]
-  int P;                       // stages per warp
-  int cap;                     // elements per stage (m * 32)
+  int P;                       // most stages per warp
+  int cap;                     // floats of staging area per warp (>= m * 32)
   int* err;
   unsigned long long timeout_ns;
 };
@@ -482,7 +482,53 @@ __device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
   warp_slot<LMAX>(sm.red, j + 1, accN);
 }
 
-// X pass with V in HBM, staged per warp through the bulk-copy pipeline (FP32).
+// Per-warp ring of bulk-copy stages for one pass that needs `rows` rows of V
+// per tile: as many stages as fit in the warp's share of the staging buffer
+// (up to pp.P), so that small j keep more tiles in flight.
+struct BulkRing {
+  float* st;                  // the warp's staging area
+  unsigned long long* bars;   // the warp's stage barriers
+  unsigned bytes;             // bytes per stage (rows * 32 * 4)
+  int P;                      // stages in use for this pass
+};
+
+__device__ __forceinline__ BulkRing bulk_ring(const BulkPipe& pp, int rows) {
+  BulkRing r;
+  const int warp = threadIdx.x >> 5;
+  r.st = pp.stage + (size_t)warp * pp.cap;
+  r.bars = pp.bar + warp * kMaxStages;
+  r.bytes = (unsigned)rows * 32u * 4u;
+  const int fit = rows > 0 ? pp.cap / (rows * 32) : pp.P;
+  r.P = max(1, min(pp.P, fit));
+  return r;
+}
+
+// Lane 0 issues the copy of tile q (rows 0..rows-1 of tile lo/32 + warp + NW q)
+// into stage q mod P.  The stage's previous contents were consumed by this
+// warp's shared loads before the __syncwarp that precedes every re-issue.
+template <int NW>
+__device__ __forceinline__ void bulk_issue(const BulkRing& r, const float* V, int lo, int rows,
+                                           int q) {
+  const int sidx = q % r.P;
+  const int i0 = lo + (int)((threadIdx.x >> 5) + NW * q) * 32;
+  mbar_expect_tx(&r.bars[sidx], r.bytes);
+  bulk_g2s(r.st + (size_t)sidx * (r.bytes >> 2), V + vbase(i0, rows), r.bytes, &r.bars[sidx]);
+}
+
+// Waits (bounded) for the copies this warp issued for trips q+1 .. last, so
+// that none is left in flight when a pass is abandoned.
+__device__ __forceinline__ void bulk_drain(const BulkRing& r, const BulkPipe& pp, int q, int nq,
+                                           unsigned& phase) {
+  for (int t = q + 1; t < nq && t < q + r.P; t++) {
+    const int sidx = t % r.P;
+    if (mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns))
+      phase ^= 1u << sidx;
+  }
+}
+
+// X pass with V in HBM, staged per warp through the bulk-copy ring (FP32).
+// The V column of a point is read from the stage twice (update, then dots)
+// instead of being held in registers.
 template <int DIM, int MAXM, int BS, int K>
 __device__ __forceinline__ void x_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, int hi, int j,
                                             int n, const float* __restrict__ WP,
@@ -500,44 +546,35 @@ __device__ __forceinline__ void x_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, i
   const float cj = sm.cc[j];
   const int ntile = (hi - lo + 31) >> 5;
   const int nq = ntile > warp ? (ntile - warp + NW - 1) / NW : 0;
-  const unsigned bytes = (unsigned)j * 32u * 4u;
-  float* st = pp.stage + (size_t)warp * pp.P * pp.cap;
-  unsigned long long* bars = pp.bar + warp * kMaxStages;
-  auto issue = [&](int q) {
-    const int sidx = q % pp.P;
-    const int i0 = lo + (warp + NW * q) * 32;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&bars[sidx], bytes);
-    bulk_g2s(st + (size_t)sidx * pp.cap, V + vbase(i0, rows), bytes, &bars[sidx]);
-  };
+  const BulkRing r = bulk_ring(pp, j);
   if (j > 0 && lane == 0)
-    for (int q = 0; q < pp.P && q < nq; q++) issue(q);
+    for (int q = 0; q < r.P && q < nq; q++) bulk_issue<NW>(r, V, lo, rows, q);
   bool good = true;
   int q = 0;
   for (; q < nq; q++) {
-    const int sidx = q % pp.P;
+    const int sidx = q % r.P;
     const int i = lo + (warp + NW * q) * 32 + lane;
     const bool ok = i < hi;
     // the operator part first: its loads overlap the wait for the stage
     const float wp = ok ? ldcg(WP + i) : 0.f;
     float znum = ok ? s2t * stencil<float, DIM>(WP, i, n, kappa, wp) : 0.f;
     float vnum = wp;
+    const float* sc = r.st + (size_t)sidx * (r.bytes >> 2) + lane;
     if (j > 0) {
-      if (!mbar_wait(&bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
+      if (!mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
         good = false;
         break;
       }
       phase ^= 1u << sidx;
-    }
-    const float* sc = st + (size_t)sidx * pp.cap + lane;
-    float col[K];
+      if (ok) {
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (k < j) {
-        // points past the end of a ragged last tile hold stale values: zero
-        col[k] = ok ? sc[k << 5] : 0.f;
-        vnum -= sm.h2c[k] * col[k];
-        znum -= sm.cc[k] * col[k];
+        for (int k = 0; k < K; k++) {
+          if (k < j) {
+            const float v = sc[k << 5];
+            vnum -= sm.h2c[k] * v;
+            znum -= sm.cc[k] * v;
+          }
+        }
       }
     }
     const float vj = vnum * inv;
@@ -545,33 +582,27 @@ __device__ __forceinline__ void x_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, i
     if (ok) {
       V[vbase(i, rows) + ((long long)j << 5)] = vj;
       Z[i] = z;
-    }
-    accZ += z * z;
+      // points past the end of a ragged last tile hold stale values: skipped
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (k < j)
-        acc[k] += col[k] * z;
-      else if (k == j)
-        acc[k] += vj * z;
+      for (int k = 0; k < K; k++) {
+        if (k < j)
+          acc[k] += sc[k << 5] * z;
+        else if (k == j)
+          acc[k] += vj * z;
+      }
+      accZ += z * z;
     }
     __syncwarp();
-    if (j > 0 && lane == 0 && q + pp.P < nq) issue(q + pp.P);
+    if (j > 0 && lane == 0 && q + r.P < nq) bulk_issue<NW>(r, V, lo, rows, q + r.P);
   }
-  if (!good && j > 0) {
-    // leave no copy in flight: wait (bounded) for the ones already issued
-    for (int r = q + 1; r < nq && r < q + pp.P; r++) {
-      const int sidx = r % pp.P;
-      if (mbar_wait(&bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns))
-        phase ^= 1u << sidx;
-    }
-  }
+  if (!good && j > 0) bulk_drain(r, pp, q, nq, phase);
   // the V_j stores above are read by later bulk copies (async proxy)
   asm volatile("fence.proxy.async.global;" ::: "memory");
   warp_slots_k<LMAX, K, float>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accZ);
 }
 
-// Y pass with V in HBM through the bulk-copy pipeline (FP32).
+// Y pass with V in HBM through the bulk-copy ring (FP32).
 template <int MAXM, int BS, int K>
 __device__ __forceinline__ void y_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, int hi, int j,
                                             float* __restrict__ WP, const float* __restrict__ Z,
@@ -586,54 +617,36 @@ __device__ __forceinline__ void y_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, i
   float accN = 0.f;
   const int ntile = (hi - lo + 31) >> 5;
   const int nq = ntile > warp ? (ntile - warp + NW - 1) / NW : 0;
-  const unsigned bytes = (unsigned)(j + 1) * 32u * 4u;
-  float* st = pp.stage + (size_t)warp * pp.P * pp.cap;
-  unsigned long long* bars = pp.bar + warp * kMaxStages;
-  auto issue = [&](int q) {
-    const int sidx = q % pp.P;
-    const int i0 = lo + (warp + NW * q) * 32;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&bars[sidx], bytes);
-    bulk_g2s(st + (size_t)sidx * pp.cap, V + vbase(i0, rows), bytes, &bars[sidx]);
-  };
+  const BulkRing r = bulk_ring(pp, j + 1);
   if (lane == 0)
-    for (int q = 0; q < pp.P && q < nq; q++) issue(q);
+    for (int q = 0; q < r.P && q < nq; q++) bulk_issue<NW>(r, V, lo, rows, q);
   bool good = true;
   int q = 0;
   for (; q < nq; q++) {
-    const int sidx = q % pp.P;
+    const int sidx = q % r.P;
     const int i = lo + (warp + NW * q) * 32 + lane;
     const bool ok = i < hi;
     float qv = ok ? Z[i] : 0.f;
-    if (!mbar_wait(&bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
+    if (!mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
       good = false;
       break;
     }
     phase ^= 1u << sidx;
-    const float* sc = st + (size_t)sidx * pp.cap + lane;
-    float col[K];
+    const float* sc = r.st + (size_t)sidx * (r.bytes >> 2) + lane;
+    if (ok) {
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (k <= j) {
-        col[k] = ok ? sc[k << 5] : 0.f;
-        qv -= sm.coef[k] * col[k];
-      }
+      for (int k = 0; k < K; k++)
+        if (k <= j) qv -= sm.coef[k] * sc[k << 5];
+      WP[i] = qv;
+      accN += qv * qv;
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        if (k <= j) acc[k] += sc[k << 5] * qv;
     }
-    if (ok) WP[i] = qv;
-    accN += qv * qv;
-#pragma unroll
-    for (int k = 0; k < K; k++)
-      if (k <= j) acc[k] += col[k] * qv;
     __syncwarp();
-    if (lane == 0 && q + pp.P < nq) issue(q + pp.P);
+    if (lane == 0 && q + r.P < nq) bulk_issue<NW>(r, V, lo, rows, q + r.P);
   }
-  if (!good) {
-    for (int r = q + 1; r < nq && r < q + pp.P; r++) {
-      const int sidx = r % pp.P;
-      if (mbar_wait(&bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns))
-        phase ^= 1u << sidx;
-    }
-  }
+  if (!good) bulk_drain(r, pp, q, nq, phase);
   warp_slots_k<LMAX, K, float>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accN);
 }
@@ -666,7 +679,7 @@ __device__ __forceinline__ void y_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, i
 // explicit pass applies h2 and measures the norm instead.  The Givens update
 // of column j runs on thread 0 while the CTA already starts the next X pass;
 // if it ends the cycle, that speculative pass is discarded.
-template <typename T, int DIM, int MAXM, int BS>
+template <typename T, int DIM, int MAXM, int BS, int VM>
 __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWork& w, int lb,
                           int nb, unsigned long long& epoch, unsigned& bphase,
                           Smem<T, MAXM, BS>& sm) {
@@ -685,22 +698,22 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   const int rows = m + 1;  // basis vectors per tile (V holds m+1 vectors)
   // V lives in shared memory when this CTA's slice fits the reserved space
   // (latency of a shared load instead of an L2 round trip); else in HBM.
-  // (only the FP32 2D variant has slices small enough to be worth a second
-  // instantiation of the passes; the global and the shared copies are kept
-  // apart so each pass uses the right address space)
-  const bool vshared = sizeof(T) == 4 && DIM == 2 && !arnoldi && kp.vsmem > 0 &&
-                       (long long)chunk * rows * (long long)sizeof(T) <= kp.vsmem;
+  // (only the FP32 2D variant has slices small enough to be worth it; each
+  // placement of V is its own kernel variant, so every pass uses the right
+  // address space and registers are allocated per variant)
+  const bool vshared = VM == kVShared;
   T* __restrict__ Vg = (T*)w.V;
   T* __restrict__ Vs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(&sm) +
                                             smem_own_bytes<T, MAXM, BS>());
   T* __restrict__ V = vshared ? Vs : Vg;  // cycle-end and fallback passes
   const int voff = vshared ? lo : 0;
   // bulk-copy staging of V (FP32, V in HBM): stages follow the shared state
-  const bool bulk = sizeof(T) == 4 && !vshared && kp.bulk_stages > 0;
+  const bool bulk = VM == kVBulk;
+  (void)bulk;
   BulkPipe pipe;
   pipe.stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&sm) + smem_own_bytes<T, MAXM, BS>());
   pipe.P = kp.bulk_stages;
-  pipe.cap = m * 32;
+  pipe.cap = kp.bulk_cap;
   pipe.bar = &sm.bbar[0][0];
   pipe.err = w.bar.err;
   pipe.timeout_ns = w.bar.timeout_ns;
@@ -722,6 +735,11 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   int used_alt = 0;
   double bnorm = 0.0;
   bool ok = true;
+
+  if (VM == kVShared && (long long)chunk * rows * (long long)sizeof(T) > kp.vsmem) {
+    status = kErrConfig;  // the slice would overrun the shared-memory reservation
+    goto finish;
+  }
 
   // ---- phase 0: ||b||, and the residuals of both guesses when an alternative
   // (learned) guess competes with the fallback already in x.
@@ -832,14 +850,10 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   x_pass_bulk<DIM, MAXM, BS, KK>(*reinterpret_cast<Smem<float, MAXM, BS>*>(&sm), lo, hi, j, n, \
                                  (const float*)WP, (float*)Z, (float*)Vg, rows, kappa,       \
                                  (float)s2t, pipe, bphase)
-        if constexpr (sizeof(T) == 4) {
-          if (vshared) {
-            if constexpr (DIM == 2) { MLG_BUCKETS(MLG_XS) }
-          } else if (bulk) {
-            MLG_BUCKETS(MLG_XB)
-          } else {
-            MLG_BUCKETS(MLG_X)
-          }
+        if constexpr (VM == kVShared) {
+          MLG_BUCKETS(MLG_XS)
+        } else if constexpr (VM == kVBulk) {
+          MLG_BUCKETS(MLG_XB)
         } else {
           MLG_BUCKETS(MLG_X)
         }
@@ -870,14 +884,10 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
 #define MLG_YB(KK)                                                                          \
   y_pass_bulk<MAXM, BS, KK>(*reinterpret_cast<Smem<float, MAXM, BS>*>(&sm), lo, hi, j,         \
                             (float*)WP, (const float*)Z, (const float*)Vg, rows, pipe, bphase)
-        if constexpr (sizeof(T) == 4) {
-          if (vshared) {
-            if constexpr (DIM == 2) { MLG_BUCKETS(MLG_YS) }
-          } else if (bulk) {
-            MLG_BUCKETS(MLG_YB)
-          } else {
-            MLG_BUCKETS(MLG_Y)
-          }
+        if constexpr (VM == kVShared) {
+          MLG_BUCKETS(MLG_YS)
+        } else if constexpr (VM == kVBulk) {
+          MLG_BUCKETS(MLG_YB)
         } else {
           MLG_BUCKETS(MLG_Y)
         }
@@ -947,13 +957,20 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
             sm.stop = !(hnext * hnext > 1e-28 * sm.anorm2) ? 1 : 0;
           }
         }
-        __syncwarp();
-        // c_i = sum_{k >= i-1} Hu(i,k) h2_k for the next X pass
-        for (int i = lane; i <= j + 1; i += 32) {
-          T c = T(0);
-          for (int k = (i > 0 ? i - 1 : 0); k <= j; k++) c += sm.HuT[i + k * LD] * sm.h2c[k];
-          sm.cc[i] = c;
-        }
+      }
+      __syncthreads();
+      // c_i = sum_{k >= i-1} Hu(i,k) h2_k for the next X pass: eight lanes per
+      // row, each a strided part of the sum, added in a fixed order
+      for (int i0 = 0; i0 <= j + 1; i0 += BS / 8) {
+        const int i = i0 + (tid >> 3);
+        const int sub = tid & 7;
+        T c = T(0);
+        if (i <= j + 1)
+          for (int k = (i > 0 ? i - 1 : 0) + sub; k <= j; k += 8) c += sm.HuT[i + k * LD] * sm.h2c[k];
+        c += __shfl_xor_sync(0xffffffffu, c, 4);
+        c += __shfl_xor_sync(0xffffffffu, c, 2);
+        c += __shfl_xor_sync(0xffffffffu, c, 1);
+        if (sub == 0 && i <= j + 1) sm.cc[i] = c;
       }
       __syncthreads();
       if (!arnoldi && j + 1 >= m) {
@@ -1014,7 +1031,7 @@ finish:
   }
 }
 
-template <typename T, int DIM, int MAXM, int BS>
+template <typename T, int DIM, int MAXM, int BS, int VM>
 __global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<T, MAXM, BS>& sm = *reinterpret_cast<Smem<T, MAXM, BS>*>(smem_raw);
@@ -1025,7 +1042,7 @@ __global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
   const GroupWork w = kp.work[g];
   unsigned long long epoch = 0;
   unsigned bphase = 0;  // parity of each bulk-copy stage of this thread's warp
-  if (sizeof(T) == 4 && kp.bulk_stages > 0) {
+  if (VM == kVBulk) {
     for (int i = threadIdx.x; i < (BS / 32) * kMaxStages; i += BS)
       mbar_init(&sm.bbar[0][0] + i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1033,7 +1050,7 @@ __global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
   }
   for (int t = kp.task_first[g]; t < kp.task_first[g + 1]; t++) {
     const SolveTask tk = kp.tasks[kp.task_order[t]];
-    solve_one<T, DIM, MAXM, BS>(kp, tk, w, lb, nb, epoch, bphase, sm);
+    solve_one<T, DIM, MAXM, BS, VM>(kp, tk, w, lb, nb, epoch, bphase, sm);
     if (*(volatile int*)w.bar.err != kErrNone) break;
     // all CTAs finish with this task's data before the next task starts
     if (!group_sync(w.bar, epoch, &sm.flag)) break;
@@ -1041,35 +1058,37 @@ __global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
 }
 
 // ------------------------------------------------------------- host side --
-// The shared state lives in dynamic shared memory (up to ~107 KB for m <= 64).
-template <typename T, int DIM, int MAXM, int BS>
+// The shared state lives in dynamic shared memory (about 90 KB for m <= 64),
+// followed by the CTA's slice of V (VM = kVShared) or the warps' bulk-copy
+// stages (VM = kVBulk).
+template <typename T, int DIM, int MAXM, int BS, int VM>
 cudaError_t prepare_t(int extra = 0) {
-  return cudaFuncSetAttribute(gmres_persistent<T, DIM, MAXM, BS>,
+  return cudaFuncSetAttribute(gmres_persistent<T, DIM, MAXM, BS, VM>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_own_bytes<T, MAXM, BS>() + extra);
 }
 
-template <typename T, int DIM, int MAXM, int BS>
+template <typename T, int DIM, int MAXM, int BS, int VM>
 cudaError_t launch_t(const KParams& kp, int grid, cudaStream_t s) {
-  const int bulk = (sizeof(T) == 4 && kp.bulk_stages > 0)
-                       ? (int)(sizeof(float) * (size_t)(BS / 32) * kp.bulk_stages * kp.m * 32)
-                       : 0;
-  const int extra = kp.vsmem > bulk ? kp.vsmem : bulk;
-  cudaError_t e = prepare_t<T, DIM, MAXM, BS>(extra);
+  int extra = 0;
+  if (VM == kVShared) extra = kp.vsmem;
+  if (VM == kVBulk) extra = (int)(sizeof(float) * (size_t)(BS / 32) * kp.bulk_cap);
+  cudaError_t e = prepare_t<T, DIM, MAXM, BS, VM>(extra);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&kp};
   note_launches(1);
-  return cudaLaunchCooperativeKernel((const void*)gmres_persistent<T, DIM, MAXM, BS>, dim3(grid),
-                                     dim3(BS), args, smem_own_bytes<T, MAXM, BS>() + extra, s);
+  return cudaLaunchCooperativeKernel((const void*)gmres_persistent<T, DIM, MAXM, BS, VM>,
+                                     dim3(grid), dim3(BS), args,
+                                     smem_own_bytes<T, MAXM, BS>() + extra, s);
 }
 
-template <typename T, int DIM, int MAXM, int BS>
+template <typename T, int DIM, int MAXM, int BS, int VM>
 int max_blocks_t(int* bs) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (prepare_t<T, DIM, MAXM, BS>() != cudaSuccess) return 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gmres_persistent<T, DIM, MAXM, BS>, BS,
+  if (prepare_t<T, DIM, MAXM, BS, VM>() != cudaSuccess) return 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gmres_persistent<T, DIM, MAXM, BS, VM>, BS,
                                                 smem_own_bytes<T, MAXM, BS>());
   *bs = BS;
   return per * nsm;

@@ -73,6 +73,7 @@ struct mlgmres {
   double* hdots = nullptr;            // pinned
   unsigned long long rng_state = 0;
   cudaEvent_t train_done = nullptr;
+  cudaStream_t train_stream = nullptr;  // training phases started by solve (retrain_after)
   bool train_pending = false;
   float* loss_dev = nullptr;
 

@@ -94,10 +94,11 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
   ARG(o->guess_smooth >= 0 && o->guess_smooth <= 1000, "guess_smooth must be in 0..1000");
   ARG(o->guess_omega > 0.0f && o->guess_omega <= 1.0f, "guess_omega must be in (0, 1]");
   ARG(o->guess_select == 0 || o->guess_select == 1, "guess_select must be 0 or 1");
-  ARG(o->v_stages == -1 || o->v_stages == 0 || (o->v_stages >= 2 && o->v_stages <= 4),
-      "v_stages must be -1, 0 or 2..4");
-  ARG(o->v_stages <= 0 || o->precision == MLGMRES_FP64 || gmres_stages_fit(o->m, o->v_stages),
-      "v_stages: the stages do not fit in shared memory for this m");
+  ARG(o->v_stages == -1 || o->v_stages == 0 || (o->v_stages >= 2 && o->v_stages <= 16),
+      "v_stages must be -1, 0 or 2..16");
+  ARG(o->v_stages <= 0 || o->precision == MLGMRES_FP64 || gmres_bulk_cap(o->m, o->v_stages) > 0,
+      "v_stages: no stage of m rows fits in shared memory");
+  ARG(o->retrain_after >= 0, "retrain_after must be >= 0");
 }
 
 // Bulk-copy stages the passes use for an FP32 basis in HBM.
@@ -136,6 +137,15 @@ void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps
   kp.arnoldi_steps = arnoldi_steps;
   kp.vsmem = arnoldi_steps > 0 ? 0 : vsmem;
   kp.bulk_stages = stages >= 0 ? stages : effective_stages(h);
+  kp.bulk_cap = h->fp32 ? gmres_bulk_cap(h->opt.m, kp.bulk_stages) : 0;
+  if (kp.bulk_cap == 0) kp.bulk_stages = 0;
+  // placement of V: shared-memory slices when every task's slice fits (FP32 2D
+  // solves), else bulk-copy stages, else direct loads
+  kp.vmode = kVDirect;
+  if (h->fp32) {
+    if (kp.vsmem > 0 && h->grid.dim == 2) kp.vmode = kVShared;
+    else if (kp.bulk_stages > 0) kp.vmode = kVBulk;
+  }
   kp.ngroups = ngroups;
   kp.group_first = h->dcfg;
   kp.task_first = h->dcfg + (ngroups + 1);
@@ -255,6 +265,40 @@ int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_r
   return 1;
 }
 
+// One training phase (Sec. 2.3) on stream s; see mlgmres_train_step.
+void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
+  if (loss_host) *loss_host = -1.0f;
+  if (h->ring_count == 0 || h->solves < h->opt.warmup_steps || h->opt.train_iters == 0) return;
+  // the ring was written on the solve streams; the handle's solves synchronise
+  // before returning, so everything they enqueued is complete here.
+  const int B = std::min(h->opt.batch, std::max(1, h->ring_count));
+  std::vector<int> pick(B);
+  // unit-scale targets: t / c with c the mean rms(x)/rms(b) over the ring
+  double csum = 0.0;
+  for (int i = 0; i < h->ring_count; i++) csum += h->ring_c[i];
+  h->c_train = csum > 0.0 ? csum / h->ring_count : 1.0;
+  const float tscale = (float)(1.0 / h->c_train);
+  for (int it = 0; it < h->opt.train_iters; it++) {
+    int k = 0;
+    for (int f : h->fresh) {
+      if (k >= B) break;
+      pick[k++] = f;
+    }
+    while (k < B) pick[k++] = (int)(splitmix_next(h->rng_state) % (unsigned long long)h->ring_count);
+    CK(net_train_batch(h->net, B, h->ring_u, h->ring_t, h->ldv, pick.data(), tscale, h->opt.lr,
+                       h->loss_dev, s));
+  }
+  CK(cudaEventRecord(h->train_done, s));
+  h->train_pending = true;
+  h->net_ready = true;
+  h->train_calls++;
+  h->fresh.clear();
+  if (loss_host) {
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(loss_host, h->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -285,6 +329,7 @@ void mlgmres_default_options(mlgmres_options* o) {
   o->guess_omega = 0.8f;
   o->fault_inject = 0;
   o->v_stages = -1;
+  o->retrain_after = 0;
 }
 
 mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* opt,
@@ -345,6 +390,8 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     CK(cudaEventCreate(&h->ev1));
     CK(cudaEventCreate(&h->ev2));
     CK(cudaEventCreateWithFlags(&h->train_done, cudaEventDisableTiming));
+    if (opt->guess == MLGMRES_GUESS_LEARNED && opt->retrain_after > 0)
+      CK(cudaStreamCreateWithFlags(&h->train_stream, cudaStreamNonBlocking));
     h->rng_state = opt->seed;
     if (grid->dim == 2) {
       // learned-guess machinery (the network is two-dimensional)
@@ -404,6 +451,7 @@ void mlgmres_destroy(mlgmres_t h) {
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev2) cudaEventDestroy(h->ev2);
   if (h->train_done) cudaEventDestroy(h->train_done);
+  if (h->train_stream) cudaStreamDestroy(h->train_stream);
   delete h;
 }
 
@@ -523,6 +571,16 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
     CK(cudaEventElapsedTime(&r.tos_ms, h->ev0, h->ev1));
     if (mode == MLGMRES_GUESS_LEARNED && h->grid.dim == 2 && r.status != MLGMRES_ERR_TIMEOUT)
       r.admitted = gate_and_store(h, b, x, r, s);
+    // Algorithm 1's trigger: retrain once f_r pairs were admitted since the
+    // previous phase (the first phase at tau0 takes the warm-up pairs)
+    r.trained = 0;
+    if (h->opt.guess == MLGMRES_GUESS_LEARNED && h->opt.retrain_after > 0 &&
+        h->solves >= h->opt.warmup_steps &&
+        ((int)h->fresh.size() >= h->opt.retrain_after || h->train_calls == 0)) {
+      const int before = h->train_calls;
+      train_phase(h, h->train_stream, nullptr);
+      r.trained = h->train_calls > before ? 1 : 0;
+    }
     if (res_out) *res_out = r;
     if (r.status == MLGMRES_ERR_TIMEOUT) h->last_error = "device barrier wait timed out";
     if (r.status == MLGMRES_ERR_NONFINITE) h->last_error = "non-finite residual";
@@ -640,38 +698,7 @@ mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_ho
   h->last_error.clear();
   try {
     ARG(h->grid.dim == 2, "the learned guess is available for 2D grids only");
-    if (loss_host) *loss_host = -1.0f;
-    if (h->ring_count == 0 || h->solves < h->opt.warmup_steps || h->opt.train_iters == 0)
-      return MLGMRES_OK;
-    cudaStream_t s = (cudaStream_t)side_stream;
-    // the ring was written on the solve streams; the handle's solves synchronise
-    // before returning, so everything they enqueued is complete here.
-    const int B = std::min(h->opt.batch, std::max(1, h->ring_count));
-    std::vector<int> pick(B);
-    // unit-scale targets: t / c with c the mean rms(x)/rms(b) over the ring
-    double csum = 0.0;
-    for (int i = 0; i < h->ring_count; i++) csum += h->ring_c[i];
-    h->c_train = csum > 0.0 ? csum / h->ring_count : 1.0;
-    const float tscale = (float)(1.0 / h->c_train);
-    for (int it = 0; it < h->opt.train_iters; it++) {
-      int k = 0;
-      for (int f : h->fresh) {
-        if (k >= B) break;
-        pick[k++] = f;
-      }
-      while (k < B) pick[k++] = (int)(splitmix_next(h->rng_state) % (unsigned long long)h->ring_count);
-      CK(net_train_batch(h->net, B, h->ring_u, h->ring_t, h->ldv, pick.data(), tscale,
-                         h->opt.lr, h->loss_dev, s));
-    }
-    CK(cudaEventRecord(h->train_done, s));
-    h->train_pending = true;
-    h->net_ready = true;
-    h->train_calls++;
-    h->fresh.clear();
-    if (loss_host) {
-      CK(cudaStreamSynchronize(s));
-      CK(cudaMemcpy(loss_host, h->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
-    }
+    train_phase(h, (cudaStream_t)side_stream, loss_host);
     return MLGMRES_OK;
   } catch (const Fail& f) {
     return f.st;
@@ -752,8 +779,8 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
       } else if (h->opt.v_stages >= 0) {
         stages.push_back(h->opt.v_stages);
       } else {
-        for (int P : {0, 2, 3, 4})
-          if (P == 0 || gmres_stages_fit(h->opt.m, P)) stages.push_back(P);
+        for (int P : {0, 2, 4, 8, 16})
+          if (P == 0 || gmres_bulk_cap(h->opt.m, P) > 0) stages.push_back(P);
       }
       for (int P : stages) {
         if (t.candidates >= 32) break;

@@ -221,42 +221,54 @@ __global__ void conv_out_bwd_data(int B, int n, const float* __restrict__ gy,
 //   part[cta][c*9 + tap] = sum_p g1[p or p+off] * x32[...][c]  and bias part[cta][288 + ...].
 // MODE 0 (output conv):  dW[c][tap] = sum_p gy[p] t[p + off][c], db = sum_p gy[p]
 // MODE 1 (input conv):   dW[c][tap] = sum_p g32[p][c] u[p + off], db[c] = sum_p g32[p][c]
+// Lane = channel (coalesced 32-channel rows), warp = one of 8 interleaved pixel
+// streams of the CTA's range; the 8 warp sums are added in a fixed order.
 template <int MODE>
-__global__ void conv1_wgrad(int B, int n, const float* __restrict__ g1,
-                            const bf16* __restrict__ x32, const float* __restrict__ g32,
-                            const float* __restrict__ u, float* __restrict__ part,
-                            int stride) {
-  const long long total = (long long)B * n * n;
+__global__ void __launch_bounds__(256) conv1_wgrad(int B, int n, const float* __restrict__ g1,
+                                                   const bf16* __restrict__ x32,
+                                                   const float* __restrict__ g32,
+                                                   const float* __restrict__ u,
+                                                   float* __restrict__ part, int stride) {
+  __shared__ float red[8][kC * 10];
+  const long long nn = (long long)n * n;
+  const long long total = (long long)B * nn;
   const long long per = (total + gridDim.x - 1) / gridDim.x;
   const long long p0 = blockIdx.x * per;
   const long long p1 = min(total, p0 + per);
-  const int t = threadIdx.x;  // 0..319: 288 weights (c*9+tap) then 32 biases
-  float acc = 0.f;
-  if (t < kC * 9) {
-    const int c = t / 9, tp = t % 9;
-    const int dy = tp / 3 - 1, dx = tp % 3 - 1;
-    for (long long p = p0; p < p1; p++) {
-      const int b = (int)(p / ((long long)n * n));
-      const int r = (int)(p % ((long long)n * n));
-      const int yy = r / n + dy, xx = r % n + dx;
+  const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float acc[9];
+#pragma unroll
+  for (int t = 0; t < 9; t++) acc[t] = 0.f;
+  float accb = 0.f;
+  for (long long p = p0 + w; p < p1; p += 8) {
+    const int b = (int)(p / nn);
+    const int r = (int)(p - (long long)b * nn);
+    const int y = r / n, x = r - (r / n) * n;
+    const float gp = MODE == 0 ? g1[p] : g32[p * kC + c];
+    accb += gp;
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+      const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
       if (yy < 0 || yy >= n || xx < 0 || xx >= n) continue;
       const long long q = ((long long)b * n + yy) * n + xx;
-      if (MODE == 0)
-        acc += g1[p] * __bfloat162float(x32[q * kC + c]);
-      else
-        acc += g32[p * kC + c] * u[q];
-    }
-  } else if (t < kC * 9 + kC) {
-    const int c = t - kC * 9;
-    for (long long p = p0; p < p1; p++) {
-      if (MODE == 0) {
-        if (c == 0) acc += g1[p];
-      } else {
-        acc += g32[p * kC + c];
-      }
+      const float v = MODE == 0 ? __bfloat162float(x32[q * kC + c]) : u[q];
+      acc[t] += gp * v;
     }
   }
-  if (t < kC * 9 + kC) part[(long long)blockIdx.x * stride + t] = acc;
+#pragma unroll
+  for (int t = 0; t < 9; t++) red[w][c * 10 + t] = acc[t];
+  red[w][c * 10 + 9] = accb;
+  __syncthreads();
+  for (int t = threadIdx.x; t < kC * 9 + kC; t += blockDim.x) {
+    // t < 288: weight c*9+tap; t >= 288: bias of channel t-288 (MODE 0: one bias)
+    const int cc = t < kC * 9 ? t / 9 : t - kC * 9;
+    const int k = t < kC * 9 ? t % 9 : 9;
+    float v = 0.f;
+    if (!(MODE == 0 && k == 9 && cc != 0))
+      for (int ww = 0; ww < 8; ww++) v += red[ww][(MODE == 0 && k == 9 ? 0 : cc) * 10 + k];
+    if (MODE == 0 && k == 9) v = cc == 0 ? v : 0.f;
+    part[(long long)blockIdx.x * stride + t] = v;
+  }
 }
 
 // out = bf16(g * (mask > 0))
@@ -299,35 +311,50 @@ __global__ void reduce_wgrad(const float* __restrict__ part, int nparts, int str
   }
 }
 
-// gz[b][i][j][c] = sum over fine (y, x) of U[y][i] U[x][j] gs[b][y][x][c] (transpose of
-// the bilinear upsampling from m to n)
-__global__ void upsample_bwd(int B, int n, int m, const float* __restrict__ gs,
-                             float* __restrict__ gz) {
+// Transpose of the bilinear upsampling from m to n, separably:
+//   tx[b][y][j][c] = sum_x U[x][j] gs[b][y][x][c]      (upsample_bwd_x, n x m)
+//   gz[b][i][j][c] = sum_y U[y][i] tx[b][y][j][c]      (upsample_bwd_y, m x m)
+// U[x][j] = the weight of coarse j in fine x's half-pixel interpolation.
+__device__ __forceinline__ float up_weight(int f_idx, int m, int n, int j) {
+  int i0, i1;
+  float l;
+  bilin(f_idx, m, n, i0, i1, l);
+  return (i0 == j ? 1.f - l : 0.f) + (i1 == j ? l : 0.f);
+}
+
+__global__ void upsample_bwd_x(int B, int n, int m, const float* __restrict__ gs,
+                               float* __restrict__ tx) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)B * n * m * kC) return;
+  const int c = (int)(idx % kC);
+  const long long p = idx / kC;  // (b, y, j)
+  const int j = (int)(p % m);
+  const long long by = p / m;    // b * n + y
+  const float f = (float)n / (float)m;
+  const int xlo = max(0, (int)floorf((j - 1.5f) * f)), xhi = min(n - 1, (int)ceilf((j + 2.5f) * f));
+  float acc = 0.f;
+  for (int x = xlo; x <= xhi; x++) {
+    const float wx = up_weight(x, m, n, j);
+    if (wx != 0.f) acc += wx * gs[(by * n + x) * kC + c];
+  }
+  tx[idx] = acc;
+}
+
+__global__ void upsample_bwd_y(int B, int n, int m, const float* __restrict__ tx,
+                               float* __restrict__ gz) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)B * m * m * kC) return;
   const int c = (int)(idx % kC);
-  const long long p = idx / kC;
+  const long long p = idx / kC;  // (b, i, j)
+  const int j = (int)(p % m);
+  const int i = (int)((p / m) % m);
   const int b = (int)(p / ((long long)m * m));
-  const int r = (int)(p % ((long long)m * m));
-  const int i = r / m, j = r % m;
   const float f = (float)n / (float)m;
   const int ylo = max(0, (int)floorf((i - 1.5f) * f)), yhi = min(n - 1, (int)ceilf((i + 2.5f) * f));
-  const int xlo = max(0, (int)floorf((j - 1.5f) * f)), xhi = min(n - 1, (int)ceilf((j + 2.5f) * f));
   float acc = 0.f;
   for (int y = ylo; y <= yhi; y++) {
-    int y0, y1;
-    float ly;
-    bilin(y, m, n, y0, y1, ly);
-    const float wy = (y0 == i ? 1.f - ly : 0.f) + (y1 == i ? ly : 0.f);
-    if (wy == 0.f) continue;
-    for (int x = xlo; x <= xhi; x++) {
-      int x0, x1;
-      float lx;
-      bilin(x, m, n, x0, x1, lx);
-      const float wx = (x0 == j ? 1.f - lx : 0.f) + (x1 == j ? lx : 0.f);
-      if (wx == 0.f) continue;
-      acc += wy * wx * gs[(((long long)b * n + y) * n + x) * kC + c];
-    }
+    const float wy = up_weight(y, m, n, i);
+    if (wy != 0.f) acc += wy * tx[(((long long)b * n + y) * m + j) * kC + c];
   }
   gz[idx] = acc;
 }
@@ -579,7 +606,7 @@ cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const 
   loss_finish<<<1, 32, 0, s>>>(net.loss_part, lparts, 1.f / (float)pix, loss_dev);
   note_launches(1);
   // output conv
-  conv1_wgrad<0><<<P, 320, 0, s>>>(B, n, net.gy, net.t, nullptr, nullptr, net.wgrad_part, stride);
+  conv1_wgrad<0><<<P, 256, 0, s>>>(B, n, net.gy, net.t, nullptr, nullptr, net.wgrad_part, stride);
   note_launches(1);
   reduce_wgrad<<<nblk(9 * kC + 1, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 2,
                                                      net.grad + net.off_w[L + 2],
@@ -604,8 +631,11 @@ cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const 
     const long long lp = (long long)B * sd * sd;
     const float* gz = net.g_s;
     if (l > 0) {
-      upsample_bwd<<<nblk(lp * kC, 256), 256, 0, s>>>(B, n, sd, net.g_s, net.g_lvl);
-      note_launches(1);
+      // g_t is free here (the residual block's gradient is already in g_s)
+      upsample_bwd_x<<<nblk((long long)B * n * sd * kC, 256), 256, 0, s>>>(B, n, sd, net.g_s,
+                                                                            net.g_t);
+      upsample_bwd_y<<<nblk(lp * kC, 256), 256, 0, s>>>(B, n, sd, net.g_t, net.g_lvl);
+      note_launches(2);
       gz = net.g_lvl;
     }
     mask_to_bf16<<<nblk(lp * kC, 256), 256, 0, s>>>(lp * kC, gz, net.z[l], net.g_bf);
@@ -630,7 +660,7 @@ cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const 
   // input conv
   mask_f32<<<nblk(full, 256), 256, 0, s>>>(full, net.g_pool + net.lvl_off[0], net.a0, net.g_lvl);
   note_launches(1);
-  conv1_wgrad<1><<<P, 320, 0, s>>>(B, n, nullptr, nullptr, net.g_lvl, u, net.wgrad_part, stride);
+  conv1_wgrad<1><<<P, 256, 0, s>>>(B, n, nullptr, nullptr, net.g_lvl, u, net.wgrad_part, stride);
   note_launches(1);
   reduce_wgrad<<<nblk(9 * kC + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 1,
                                                       net.grad + net.off_w[0],

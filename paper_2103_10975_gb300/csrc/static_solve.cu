@@ -127,6 +127,8 @@ extern "C" mlgmres_status mlgmres_solve_static(int n, int m, double rtol, long l
   kp.arnoldi_steps = 0;
   kp.vsmem = 0;
   kp.bulk_stages = 0;
+  kp.bulk_cap = 0;
+  kp.vmode = kVDirect;
   kp.ngroups = 1;
   kp.group_first = cfg;
   kp.task_first = cfg + 2;

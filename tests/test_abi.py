@@ -37,11 +37,11 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     # sizes of the C structs as laid out by a C compiler on this ABI
     assert ctypes.sizeof(binding.Grid) == 16
-    assert ctypes.sizeof(binding.Result) == 8 + 4 * 4 + 5 * 8 + 2 * 4
+    assert ctypes.sizeof(binding.Result) == 8 + 4 * 4 + 5 * 8 + 2 * 4 + 4 + 4  # + trained, pad
     o = binding.default_options()
     assert o.m == 30 and o.rtol == 1e-10 and o.replay_cap == 64 and o.warmup_steps == 50
     assert o.window_p == 10 and abs(o.ortho_theta - 0.9) < 1e-15 and o.batch == 8
-    assert o.fault_inject == 0
+    assert o.fault_inject == 0 and o.v_stages == -1 and o.retrain_after == 0
 
 
 def test_create_without_gpu_fails_cleanly():

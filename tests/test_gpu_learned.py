@@ -45,3 +45,30 @@ def test_learned_guess_reduces_iterations():
                                                        hi, 100 * np.mean(used)))
     assert np.mean(used) > 0.5
     assert lo > 0.0
+
+
+def test_retraining_triggered_by_f_r_admitted_pairs():
+    """Algorithm 1's trigger (retrain_after = f_r): the solve itself starts a
+    training phase at tau0 and then each time f_r pairs have entered the
+    replay ring since the previous phase, and at no other step."""
+    from paper_2103_10975_gb300 import Solver
+    n, T, tau0, f_r = 32, 80, 10, 3
+    gen = MovingGaussians2D(n, 1001, 80)
+    s = Solver(n, m=20, rtol=1e-8, guess="learned", fallback="prev", warmup_steps=tau0,
+               retrain_after=f_r, deterministic_tos=1, train_iters=2, batch=4, seed=5)
+    fresh, phases, admitted = 0, 0, 0
+    for t in range(T):
+        x, r = s.solve(torch.as_tensor(gen.rhs(t)).cuda())
+        assert r["status"] == 0
+        fresh += r["admitted"]
+        if t + 1 > tau0:
+            admitted += r["admitted"]
+        due = t + 1 >= tau0 and (phases == 0 or fresh >= f_r)
+        assert r["trained"] == int(due), (t, fresh, phases, r["trained"])
+        if r["trained"]:
+            phases += 1
+            fresh = 0
+    assert phases >= 2
+    # the gate keeps only part of the post-warm-up pairs (the paper reports
+    # about one in ten on its workload)
+    assert 0 < admitted < T - tau0
