@@ -114,7 +114,7 @@ typedef struct {
                                 first wait runs out after barrier_timeout_s and the solve
                                 returns MLGMRES_ERR_TIMEOUT (exercises the bounded-wait
                                 path without faulting the GPU) */
-  int v_stages;              /* FP32 basis held in HBM: most shared-memory stages per warp
+  int v_stages;              /* basis held in HBM: most shared-memory stages per warp
                                 through which the passes stream V with bulk copies (2..16;
                                 a pass uses as many as fit in the warp's share of shared
                                 memory for its j rows), or 0 for direct loads; -1 =

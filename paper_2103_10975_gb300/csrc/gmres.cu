@@ -17,23 +17,31 @@ MLG_VARIANT(f2s)
 MLG_VARIANT(f2b)
 MLG_VARIANT(f3d)
 MLG_VARIANT(f3b)
-MLG_VARIANT(d2)
-MLG_VARIANT(d3)
+MLG_VARIANT(d2d)
+MLG_VARIANT(d2s)
+MLG_VARIANT(d2b)
+MLG_VARIANT(d3d)
+MLG_VARIANT(d3b)
 #undef MLG_VARIANT
 
 cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid, cudaStream_t s) {
-  if (!fp32) {
-    if (kp.vmode != kVDirect) return cudaErrorInvalidValue;
-    return dim == 2 ? launch_gmres_d2(kp, grid, s) : launch_gmres_d3(kp, grid, s);
+  if (dim == 3 && kp.vmode == kVShared) return cudaErrorInvalidValue;
+  if (fp32) {
+    if (dim == 2) {
+      if (kp.vmode == kVShared) return launch_gmres_f2s(kp, grid, s);
+      if (kp.vmode == kVBulk) return launch_gmres_f2b(kp, grid, s);
+      return launch_gmres_f2d(kp, grid, s);
+    }
+    if (kp.vmode == kVBulk) return launch_gmres_f3b(kp, grid, s);
+    return launch_gmres_f3d(kp, grid, s);
   }
   if (dim == 2) {
-    if (kp.vmode == kVShared) return launch_gmres_f2s(kp, grid, s);
-    if (kp.vmode == kVBulk) return launch_gmres_f2b(kp, grid, s);
-    return launch_gmres_f2d(kp, grid, s);
+    if (kp.vmode == kVShared) return launch_gmres_d2s(kp, grid, s);
+    if (kp.vmode == kVBulk) return launch_gmres_d2b(kp, grid, s);
+    return launch_gmres_d2d(kp, grid, s);
   }
-  if (kp.vmode == kVShared) return cudaErrorInvalidValue;
-  if (kp.vmode == kVBulk) return launch_gmres_f3b(kp, grid, s);
-  return launch_gmres_f3d(kp, grid, s);
+  if (kp.vmode == kVBulk) return launch_gmres_d3b(kp, grid, s);
+  return launch_gmres_d3d(kp, grid, s);
 }
 
 // The co-resident limit of the direct variant (every variant runs one 256-thread
@@ -41,20 +49,20 @@ cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid, cudaSt
 int gmres_max_blocks(bool fp32, int dim, int m, int* bs) {
   (void)m;
   if (fp32) return dim == 2 ? max_blocks_f2d(bs) : max_blocks_f3d(bs);
-  return dim == 2 ? max_blocks_d2(bs) : max_blocks_d3(bs);
+  return dim == 2 ? max_blocks_d2d(bs) : max_blocks_d3d(bs);
 }
 
-int gmres_bulk_cap(int m, int P) {
+int gmres_bulk_cap(bool fp32, int m, int P) {
   if (P <= 0) return 0;
-  const long long share = (long long)gmres_vsmem_budget(true) / 4 / 8 / 32 * 32;  // floats
-  const long long want = (long long)P * m * 32;
+  const long long row = 32LL * (fp32 ? 4 : 8);                                  // bytes
+  const long long share = (long long)gmres_vsmem_budget(fp32) / 8 / 128 * 128;  // per warp
+  const long long want = (long long)P * m * row;
   const long long cap = want < share ? want : share;
-  return cap >= (long long)m * 32 ? (int)cap : 0;
+  return cap >= (long long)m * row ? (int)cap : 0;
 }
 
 int gmres_bulk_stages(bool fp32, int m) {
-  if (!fp32) return 0;
-  return gmres_bulk_cap(m, kMaxStages) > 0 ? kMaxStages : 0;
+  return gmres_bulk_cap(fp32, m, kMaxStages) > 0 ? kMaxStages : 0;
 }
 
 int gmres_vsmem_budget(bool fp32) {

@@ -1,0 +1,13 @@
+// One variant of the persistent GMRES(m) kernel (FP64, 2D, V in HBM loaded by the passes),
+// compiled on its own so that the variants build in parallel.
+#include "gmres_kernel.cuh"
+
+namespace mlg {
+
+cudaError_t launch_gmres_d2d(const KParams& kp, int grid, cudaStream_t s) {
+  return launch_t<double, 2, kMaxM, 256, kVDirect>(kp, grid, s);
+}
+
+int max_blocks_d2d(int* bs) { return max_blocks_t<double, 2, kMaxM, 256, kVDirect>(bs); }
+
+}  // namespace mlg

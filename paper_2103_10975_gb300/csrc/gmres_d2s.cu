@@ -1,0 +1,13 @@
+// One variant of the persistent GMRES(m) kernel (FP64, 2D, V slices in shared memory),
+// compiled on its own so that the variants build in parallel.
+#include "gmres_kernel.cuh"
+
+namespace mlg {
+
+cudaError_t launch_gmres_d2s(const KParams& kp, int grid, cudaStream_t s) {
+  return launch_t<double, 2, kMaxM, 256, kVShared>(kp, grid, s);
+}
+
+int max_blocks_d2s(int* bs) { return max_blocks_t<double, 2, kMaxM, 256, kVShared>(bs); }
+
+}  // namespace mlg

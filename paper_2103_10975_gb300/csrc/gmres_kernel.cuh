@@ -202,8 +202,8 @@ __device__ __forceinline__ void block_finish(int L, R* part, int lb, R (*red)[LW
 
 // Sum of the group's partials for k < L, identical in every CTA (same order);
 // tot gets the sums in FP64, coef the same values in the working precision.
-// Each warp takes up to four slots at a time so their loads are in flight
-// together.
+// Each warp takes up to four slots at a time, four partials per lane each, so
+// that sixteen loads per lane are in flight together.
 template <int BS, typename R, typename T>
 __device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot, T* coef,
                                        int ps) {
@@ -211,12 +211,20 @@ __device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k0 = warp; k0 < L; k0 += 4 * NW) {
     R s[4] = {R(0), R(0), R(0), R(0)};
-    for (int g = lane; g < nb; g += 32) {
+    // 128 partials per round, all 16 loads of a lane issued before any is used
+    for (int g0 = 0; g0 < nb; g0 += 128) {
+      R v[4][4];
 #pragma unroll
       for (int q = 0; q < 4; q++) {
         const int k = k0 + q * NW;
-        if (k < L) s[q] += ldcg(part + (long long)k * ps + g);
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          const int g = g0 + r * 32 + lane;
+          v[q][r] = (k < L && g < nb) ? ldcg(part + (long long)k * ps + g) : R(0);
+        }
       }
+#pragma unroll
+      for (int q = 0; q < 4; q++) s[q] += (v[q][0] + v[q][1]) + (v[q][2] + v[q][3]);
     }
 #pragma unroll
     for (int q = 0; q < 4; q++) s[q] = warp_sum(s[q]);
@@ -335,10 +343,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phas
 }
 
 struct BulkPipe {
-  float* stage;                // [warp][cap] staging area of each warp
+  unsigned char* stage;        // [warp][cap] staging area of each warp
   unsigned long long* bar;     // [warp][kMaxStages]
   int P;                       // most stages per warp
-  int cap;                     // floats of staging area per warp (>= m * 32)
+  int cap;                     // bytes of staging area per warp (>= m 32-point rows)
   int* err;
   unsigned long long timeout_ns;
 };
@@ -482,23 +490,128 @@ __device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
   warp_slot<LMAX>(sm.red, j + 1, accN);
 }
 
+// X and Y passes with the CTA's slice of V in shared memory (2D): the same
+// arithmetic as x_pass / y_pass, but a point's V column is read from shared
+// memory twice (update, then dots) instead of being held in registers, so
+// registers only carry the accumulators; U points per trip keep the
+// stencil's global loads in flight together.
+template <typename T, int DIM, int MAXM, int BS, int K>
+__device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi, int j, int n,
+                                          const T* __restrict__ WP, T* __restrict__ Z,
+                                          T* __restrict__ Vs, int rows,
+                                          const float* __restrict__ kappa, T s2t) {
+  constexpr int LMAX = MAXM + 2;
+  constexpr int U = 2;
+  const int tid = threadIdx.x;
+  T acc[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) acc[k] = T(0);
+  T accZ = T(0);
+  const T inv = sm.invT;
+  const T cj = sm.cc[j];
+  for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
+    int ii[U];
+    bool ok_[U];
+    T wp[U], znum[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      ii[u] = i0 + u * BS;
+      ok_[u] = ii[u] < hi;
+      wp[u] = ok_[u] ? ldcg(WP + ii[u]) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (!ok_[u]) continue;
+      const T* vc = Vs + vbase(ii[u] - lo, rows);
+      T vnum = wp[u], zn = znum[u];
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        if (k < j) {
+          const T v = vc[k << 5];
+          vnum -= sm.h2c[k] * v;
+          zn -= sm.cc[k] * v;
+        }
+      }
+      const T vj = vnum * inv;
+      const T z = (zn - cj * vj) * inv;
+      Vs[vbase(ii[u] - lo, rows) + (j << 5)] = vj;
+      Z[ii[u]] = z;
+      accZ += z * z;
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        if (k < j)
+          acc[k] += vc[k << 5] * z;
+        else if (k == j)
+          acc[k] += vj * z;
+      }
+    }
+  }
+  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
+  warp_slot<LMAX>(sm.red, j + 1, accZ);
+}
+
+template <typename T, int MAXM, int BS, int K>
+__device__ __forceinline__ void y_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi, int j,
+                                          T* __restrict__ WP, const T* __restrict__ Z,
+                                          const T* __restrict__ Vs, int rows) {
+  constexpr int LMAX = MAXM + 2;
+  constexpr int U = 2;
+  const int tid = threadIdx.x;
+  T acc[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) acc[k] = T(0);
+  T accN = T(0);
+  for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
+    int ii[U];
+    bool ok_[U];
+    T q[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      ii[u] = i0 + u * BS;
+      ok_[u] = ii[u] < hi;
+      q[u] = ok_[u] ? Z[ii[u]] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (!ok_[u]) continue;
+      const T* vc = Vs + vbase(ii[u] - lo, rows);
+      T qv = q[u];
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        if (k <= j) qv -= sm.coef[k] * vc[k << 5];
+      WP[ii[u]] = qv;
+      accN += qv * qv;
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        if (k <= j) acc[k] += vc[k << 5] * qv;
+    }
+  }
+  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
+  warp_slot<LMAX>(sm.red, j + 1, accN);
+}
+
 // Per-warp ring of bulk-copy stages for one pass that needs `rows` rows of V
 // per tile: as many stages as fit in the warp's share of the staging buffer
 // (up to pp.P), so that small j keep more tiles in flight.
+template <typename T>
 struct BulkRing {
-  float* st;                  // the warp's staging area
+  T* st;                      // the warp's staging area
   unsigned long long* bars;   // the warp's stage barriers
-  unsigned bytes;             // bytes per stage (rows * 32 * 4)
+  unsigned bytes;             // bytes per stage (rows * 32 * sizeof(T))
   int P;                      // stages in use for this pass
 };
 
-__device__ __forceinline__ BulkRing bulk_ring(const BulkPipe& pp, int rows) {
-  BulkRing r;
+template <typename T>
+__device__ __forceinline__ BulkRing<T> bulk_ring(const BulkPipe& pp, int rows) {
+  BulkRing<T> r;
   const int warp = threadIdx.x >> 5;
-  r.st = pp.stage + (size_t)warp * pp.cap;
+  r.st = reinterpret_cast<T*>(pp.stage + (size_t)warp * pp.cap);
   r.bars = pp.bar + warp * kMaxStages;
-  r.bytes = (unsigned)rows * 32u * 4u;
-  const int fit = rows > 0 ? pp.cap / (rows * 32) : pp.P;
+  r.bytes = (unsigned)rows * 32u * (unsigned)sizeof(T);
+  const int fit = rows > 0 ? pp.cap / (int)r.bytes : pp.P;
   r.P = max(1, min(pp.P, fit));
   return r;
 }
@@ -506,18 +619,20 @@ __device__ __forceinline__ BulkRing bulk_ring(const BulkPipe& pp, int rows) {
 // Lane 0 issues the copy of tile q (rows 0..rows-1 of tile lo/32 + warp + NW q)
 // into stage q mod P.  The stage's previous contents were consumed by this
 // warp's shared loads before the __syncwarp that precedes every re-issue.
-template <int NW>
-__device__ __forceinline__ void bulk_issue(const BulkRing& r, const float* V, int lo, int rows,
+template <int NW, typename T>
+__device__ __forceinline__ void bulk_issue(const BulkRing<T>& r, const T* V, int lo, int rows,
                                            int q) {
   const int sidx = q % r.P;
   const int i0 = lo + (int)((threadIdx.x >> 5) + NW * q) * 32;
   mbar_expect_tx(&r.bars[sidx], r.bytes);
-  bulk_g2s(r.st + (size_t)sidx * (r.bytes >> 2), V + vbase(i0, rows), r.bytes, &r.bars[sidx]);
+  bulk_g2s(r.st + (size_t)sidx * (r.bytes / sizeof(T)), V + vbase(i0, rows), r.bytes,
+           &r.bars[sidx]);
 }
 
 // Waits (bounded) for the copies this warp issued for trips q+1 .. last, so
 // that none is left in flight when a pass is abandoned.
-__device__ __forceinline__ void bulk_drain(const BulkRing& r, const BulkPipe& pp, int q, int nq,
+template <typename T>
+__device__ __forceinline__ void bulk_drain(const BulkRing<T>& r, const BulkPipe& pp, int q, int nq,
                                            unsigned& phase) {
   for (int t = q + 1; t < nq && t < q + r.P; t++) {
     const int sidx = t % r.P;
@@ -526,27 +641,27 @@ __device__ __forceinline__ void bulk_drain(const BulkRing& r, const BulkPipe& pp
   }
 }
 
-// X pass with V in HBM, staged per warp through the bulk-copy ring (FP32).
+// X pass with V in HBM, staged per warp through the bulk-copy ring.
 // The V column of a point is read from the stage twice (update, then dots)
 // instead of being held in registers.
-template <int DIM, int MAXM, int BS, int K>
-__device__ __forceinline__ void x_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, int hi, int j,
-                                            int n, const float* __restrict__ WP,
-                                            float* __restrict__ Z, float* __restrict__ V,
+template <typename T, int DIM, int MAXM, int BS, int K>
+__device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int hi, int j,
+                                            int n, const T* __restrict__ WP,
+                                            T* __restrict__ Z, T* __restrict__ V,
                                             int rows, const float* __restrict__ kappa,
-                                            float s2t, const BulkPipe& pp, unsigned& phase) {
+                                            T s2t, const BulkPipe& pp, unsigned& phase) {
   constexpr int LMAX = MAXM + 2;
   constexpr int NW = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float acc[K];
+  T acc[K];
 #pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = 0.f;
-  float accZ = 0.f;
-  const float inv = sm.invT;
-  const float cj = sm.cc[j];
+  for (int k = 0; k < K; k++) acc[k] = T(0);
+  T accZ = T(0);
+  const T inv = sm.invT;
+  const T cj = sm.cc[j];
   const int ntile = (hi - lo + 31) >> 5;
   const int nq = ntile > warp ? (ntile - warp + NW - 1) / NW : 0;
-  const BulkRing r = bulk_ring(pp, j);
+  const BulkRing<T> r = bulk_ring<T>(pp, j);
   if (j > 0 && lane == 0)
     for (int q = 0; q < r.P && q < nq; q++) bulk_issue<NW>(r, V, lo, rows, q);
   bool good = true;
@@ -556,10 +671,10 @@ __device__ __forceinline__ void x_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, i
     const int i = lo + (warp + NW * q) * 32 + lane;
     const bool ok = i < hi;
     // the operator part first: its loads overlap the wait for the stage
-    const float wp = ok ? ldcg(WP + i) : 0.f;
-    float znum = ok ? s2t * stencil<float, DIM>(WP, i, n, kappa, wp) : 0.f;
-    float vnum = wp;
-    const float* sc = r.st + (size_t)sidx * (r.bytes >> 2) + lane;
+    const T wp = ok ? ldcg(WP + i) : T(0);
+    T znum = ok ? s2t * stencil<T, DIM>(WP, i, n, kappa, wp) : T(0);
+    T vnum = wp;
+    const T* sc = r.st + (size_t)sidx * (r.bytes / sizeof(T)) + lane;
     if (j > 0) {
       if (!mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
         good = false;
@@ -570,15 +685,15 @@ __device__ __forceinline__ void x_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, i
 #pragma unroll
         for (int k = 0; k < K; k++) {
           if (k < j) {
-            const float v = sc[k << 5];
+            const T v = sc[k << 5];
             vnum -= sm.h2c[k] * v;
             znum -= sm.cc[k] * v;
           }
         }
       }
     }
-    const float vj = vnum * inv;
-    const float z = (znum - cj * vj) * inv;
+    const T vj = vnum * inv;
+    const T z = (znum - cj * vj) * inv;
     if (ok) {
       V[vbase(i, rows) + ((long long)j << 5)] = vj;
       Z[i] = z;
@@ -598,26 +713,26 @@ __device__ __forceinline__ void x_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, i
   if (!good && j > 0) bulk_drain(r, pp, q, nq, phase);
   // the V_j stores above are read by later bulk copies (async proxy)
   asm volatile("fence.proxy.async.global;" ::: "memory");
-  warp_slots_k<LMAX, K, float>(sm.red, acc, j + 1);
+  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accZ);
 }
 
-// Y pass with V in HBM through the bulk-copy ring (FP32).
-template <int MAXM, int BS, int K>
-__device__ __forceinline__ void y_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, int hi, int j,
-                                            float* __restrict__ WP, const float* __restrict__ Z,
-                                            const float* __restrict__ V, int rows,
+// Y pass with V in HBM through the bulk-copy ring.
+template <typename T, int MAXM, int BS, int K>
+__device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int hi, int j,
+                                            T* __restrict__ WP, const T* __restrict__ Z,
+                                            const T* __restrict__ V, int rows,
                                             const BulkPipe& pp, unsigned& phase) {
   constexpr int LMAX = MAXM + 2;
   constexpr int NW = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float acc[K];
+  T acc[K];
 #pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = 0.f;
-  float accN = 0.f;
+  for (int k = 0; k < K; k++) acc[k] = T(0);
+  T accN = T(0);
   const int ntile = (hi - lo + 31) >> 5;
   const int nq = ntile > warp ? (ntile - warp + NW - 1) / NW : 0;
-  const BulkRing r = bulk_ring(pp, j + 1);
+  const BulkRing<T> r = bulk_ring<T>(pp, j + 1);
   if (lane == 0)
     for (int q = 0; q < r.P && q < nq; q++) bulk_issue<NW>(r, V, lo, rows, q);
   bool good = true;
@@ -626,13 +741,13 @@ __device__ __forceinline__ void y_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, i
     const int sidx = q % r.P;
     const int i = lo + (warp + NW * q) * 32 + lane;
     const bool ok = i < hi;
-    float qv = ok ? Z[i] : 0.f;
+    T qv = ok ? Z[i] : T(0);
     if (!mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
       good = false;
       break;
     }
     phase ^= 1u << sidx;
-    const float* sc = r.st + (size_t)sidx * (r.bytes >> 2) + lane;
+    const T* sc = r.st + (size_t)sidx * (r.bytes / sizeof(T)) + lane;
     if (ok) {
 #pragma unroll
       for (int k = 0; k < K; k++)
@@ -647,7 +762,7 @@ __device__ __forceinline__ void y_pass_bulk(Smem<float, MAXM, BS>& sm, int lo, i
     if (lane == 0 && q + r.P < nq) bulk_issue<NW>(r, V, lo, rows, q + r.P);
   }
   if (!good) bulk_drain(r, pp, q, nq, phase);
-  warp_slots_k<LMAX, K, float>(sm.red, acc, j + 1);
+  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accN);
 }
 
@@ -711,7 +826,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   const bool bulk = VM == kVBulk;
   (void)bulk;
   BulkPipe pipe;
-  pipe.stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&sm) + smem_own_bytes<T, MAXM, BS>());
+  pipe.stage = reinterpret_cast<unsigned char*>(&sm) + smem_own_bytes<T, MAXM, BS>();
   pipe.P = kp.bulk_stages;
   pipe.cap = kp.bulk_cap;
   pipe.bar = &sm.bbar[0][0];
@@ -845,11 +960,9 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       // while thread 0 waits at the group barrier
       {
 #define MLG_X(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vg, rows, 0, kappa, s2t)
-#define MLG_XS(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vs, rows, lo, kappa, s2t)
-#define MLG_XB(KK)                                                                          \
-  x_pass_bulk<DIM, MAXM, BS, KK>(*reinterpret_cast<Smem<float, MAXM, BS>*>(&sm), lo, hi, j, n, \
-                                 (const float*)WP, (float*)Z, (float*)Vg, rows, kappa,       \
-                                 (float)s2t, pipe, bphase)
+#define MLG_XS(KK) x_pass_sm<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vs, rows, kappa, s2t)
+#define MLG_XB(KK) \
+  x_pass_bulk<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vg, rows, kappa, s2t, pipe, bphase)
         if constexpr (VM == kVShared) {
           MLG_BUCKETS(MLG_XS)
         } else if constexpr (VM == kVBulk) {
@@ -880,10 +993,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       // ---- Y: w'_{j+1} = z - V h1, h2 = V^T w'_{j+1}, ||w'_{j+1}||^2
       {
 #define MLG_Y(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vg, rows, 0)
-#define MLG_YS(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vs, rows, lo)
-#define MLG_YB(KK)                                                                          \
-  y_pass_bulk<MAXM, BS, KK>(*reinterpret_cast<Smem<float, MAXM, BS>*>(&sm), lo, hi, j,         \
-                            (float*)WP, (const float*)Z, (const float*)Vg, rows, pipe, bphase)
+#define MLG_YS(KK) y_pass_sm<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vs, rows)
+#define MLG_YB(KK) y_pass_bulk<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vg, rows, pipe, bphase)
         if constexpr (VM == kVShared) {
           MLG_BUCKETS(MLG_YS)
         } else if constexpr (VM == kVBulk) {
@@ -1072,7 +1183,7 @@ template <typename T, int DIM, int MAXM, int BS, int VM>
 cudaError_t launch_t(const KParams& kp, int grid, cudaStream_t s) {
   int extra = 0;
   if (VM == kVShared) extra = kp.vsmem;
-  if (VM == kVBulk) extra = (int)(sizeof(float) * (size_t)(BS / 32) * kp.bulk_cap);
+  if (VM == kVBulk) extra = (BS / 32) * kp.bulk_cap;
   cudaError_t e = prepare_t<T, DIM, MAXM, BS, VM>(extra);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&kp};

@@ -96,17 +96,17 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
   ARG(o->guess_select == 0 || o->guess_select == 1, "guess_select must be 0 or 1");
   ARG(o->v_stages == -1 || o->v_stages == 0 || (o->v_stages >= 2 && o->v_stages <= 16),
       "v_stages must be -1, 0 or 2..16");
-  ARG(o->v_stages <= 0 || o->precision == MLGMRES_FP64 || gmres_bulk_cap(o->m, o->v_stages) > 0,
+  ARG(o->v_stages <= 0 ||
+          gmres_bulk_cap(o->precision == MLGMRES_FP32_REFINE, o->m, o->v_stages) > 0,
       "v_stages: no stage of m rows fits in shared memory");
   ARG(o->retrain_after >= 0, "retrain_after must be >= 0");
 }
 
 // Bulk-copy stages the passes use for an FP32 basis in HBM.
 int effective_stages(const mlgmres* h) {
-  if (!h->fp32) return 0;
   if (h->opt.v_stages >= 0) return h->opt.v_stages;
   if (h->tuned_stages >= 0) return h->tuned_stages;
-  return gmres_bulk_stages(true, h->opt.m);
+  return gmres_bulk_stages(h->fp32, h->opt.m);
 }
 
 // Shared-memory bytes of a single solve's V slice at `blocks` CTAs (0 if the
@@ -137,15 +137,13 @@ void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps
   kp.arnoldi_steps = arnoldi_steps;
   kp.vsmem = arnoldi_steps > 0 ? 0 : vsmem;
   kp.bulk_stages = stages >= 0 ? stages : effective_stages(h);
-  kp.bulk_cap = h->fp32 ? gmres_bulk_cap(h->opt.m, kp.bulk_stages) : 0;
+  kp.bulk_cap = gmres_bulk_cap(h->fp32, h->opt.m, kp.bulk_stages);
   if (kp.bulk_cap == 0) kp.bulk_stages = 0;
-  // placement of V: shared-memory slices when every task's slice fits (FP32 2D
-  // solves), else bulk-copy stages, else direct loads
+  // placement of V: shared-memory slices when every task's slice fits (2D),
+  // else bulk-copy stages, else direct loads
   kp.vmode = kVDirect;
-  if (h->fp32) {
-    if (kp.vsmem > 0 && h->grid.dim == 2) kp.vmode = kVShared;
-    else if (kp.bulk_stages > 0) kp.vmode = kVBulk;
-  }
+  if (kp.vsmem > 0 && h->grid.dim == 2) kp.vmode = kVShared;
+  else if (kp.bulk_stages > 0) kp.vmode = kVBulk;
   kp.ngroups = ngroups;
   kp.group_first = h->dcfg;
   kp.task_first = h->dcfg + (ngroups + 1);
@@ -771,16 +769,16 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
     float best_us = INFINITY;
     for (int nb : blocks) {
       const int vs = single_vsmem(h, nb);
-      // the FP32 2D passes keep V in shared memory when the slice fits
-      const bool shared = h->fp32 && h->grid.dim == 2 && vs > 0;
+      // 2D passes keep V in shared memory when the slice fits
+      const bool shared = h->grid.dim == 2 && vs > 0;
       std::vector<int> stages;
-      if (!h->fp32 || shared) {
+      if (shared) {
         stages.push_back(-1);
       } else if (h->opt.v_stages >= 0) {
         stages.push_back(h->opt.v_stages);
       } else {
         for (int P : {0, 2, 4, 8, 16})
-          if (P == 0 || gmres_bulk_cap(h->opt.m, P) > 0) stages.push_back(P);
+          if (P == 0 || gmres_bulk_cap(h->fp32, h->opt.m, P) > 0) stages.push_back(P);
       }
       for (int P : stages) {
         if (t.candidates >= 32) break;

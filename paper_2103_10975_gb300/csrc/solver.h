@@ -10,8 +10,8 @@ namespace mlg {
 constexpr int kMaxM = 64;          // largest supported restart length
 // Where a launch keeps the basis V (one kernel variant each):
 constexpr int kVDirect = 0;  // HBM, loaded into registers by the passes
-constexpr int kVShared = 1;  // each CTA's slice in shared memory (FP32 2D)
-constexpr int kVBulk = 2;    // HBM, streamed through per-warp bulk-copy stages (FP32)
+constexpr int kVShared = 1;  // each CTA's slice in shared memory (2D)
+constexpr int kVBulk = 2;    // HBM, streamed through per-warp bulk-copy stages
 constexpr int kPartStride = 1024;  // max CTAs per group (partials row length)
 // doubles in a group's partial-sum area (two alternating sets)
 constexpr long long part_doubles(int pstride) { return 2LL * (kMaxM + 2) * pstride; }
@@ -61,8 +61,8 @@ struct KParams {
   long long max_iters;
   int arnoldi_steps;        // > 0: run that many Arnoldi steps only (inspection mode)
   int vsmem;                // bytes of shared memory for a CTA's slice of V (0 = V in HBM)
-  int bulk_stages;          // most bulk-copy stages per warp when V is in HBM (FP32; 0 = off)
-  int bulk_cap;             // floats of staging area per warp (>= m * 32 when bulk_stages > 0)
+  int bulk_stages;          // most bulk-copy stages per warp when V is in HBM (0 = off)
+  int bulk_cap;             // bytes of staging area per warp (>= m 32-point rows)
   int vmode;                // kVDirect | kVShared | kVBulk (the kernel variant launched)
   int ngroups;
   const int* group_first;   // ngroups+1 CTA ranges
@@ -83,14 +83,14 @@ int gmres_max_blocks(bool fp32, int dim, int m, int* block_threads);
 // solver's own state fit the per-CTA limit); 0 if none.
 int gmres_vsmem_budget(bool fp32);
 
-// Most bulk-copy stages per warp (kMaxStages) for an FP32 basis in HBM; 0 for
-// FP64.  A pass uses as many as fit in a warp's staging area for its rows.
+// Most bulk-copy stages per warp (kMaxStages) for a basis in HBM.  A pass uses
+// as many as fit in a warp's staging area for its rows.
 int gmres_bulk_stages(bool fp32, int m);
 
-// Floats of staging area per warp for at most P stages of m rows each: the
+// Bytes of staging area per warp for at most P stages of m rows each: the
 // warp's share of the shared memory left next to the solver's state, capped
-// at P * m * 32; 0 if not even one stage of m rows fits.
-int gmres_bulk_cap(int m, int P);
+// at P m rows; 0 if not even one stage of m rows fits.
+int gmres_bulk_cap(bool fp32, int m, int P);
 
 // FP64 operator application out = A u (2D or 3D) on one grid.
 cudaError_t launch_apply(int dim, int n, const float* kappa, const double* u, double* out,
