@@ -59,6 +59,28 @@ struct GroupBarrier {
   unsigned long long timeout_ns;
 };
 
+// Thread 0's half of the group barrier: arrive (release) and wait (acquire,
+// bounded); returns 0 on a timeout or a raised error flag.
+__device__ __forceinline__ int group_arrive_wait(const GroupBarrier& gb, unsigned long long& epoch) {
+  epoch += 1;
+  const unsigned long long target = epoch * (unsigned long long)gb.nblocks;
+  red_release_add_u64(gb.ctr, 1ull);
+  int ok = 1;
+  if (ld_acquire_u64(gb.ctr) < target) {
+    const unsigned long long t0 = globaltimer_ns();
+    while (ld_acquire_u64(gb.ctr) < target) {
+      if (*(volatile int*)gb.err != kErrNone) { ok = 0; break; }
+      if (globaltimer_ns() - t0 > gb.timeout_ns) {
+        atomicCAS(gb.err, kErrNone, kErrTimeout);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  if (ok && *(volatile int*)gb.err != kErrNone) ok = 0;
+  return ok;
+}
+
 // side() runs on warp 1 while thread 0 waits at the barrier (work that would
 // otherwise sit on the critical path between two barriers).
 template <typename Side>
@@ -74,26 +96,10 @@ __device__ __forceinline__ bool group_sync_with(const GroupBarrier& gb,
   }
   if (threadIdx.x == 0) {
     // the CTA's writes are ordered before this release by the CTA barrier
-    // above; the acquire loads below order the other CTAs' writes before the
-    // CTA barrier that ends the wait (release/acquire at gpu scope, cumulative
+    // above; the acquire loads order the other CTAs' writes before the CTA
+    // barrier that ends the wait (release/acquire at gpu scope, cumulative
     // through bar.sync), so no separate fences are needed
-    epoch += 1;
-    const unsigned long long target = epoch * (unsigned long long)gb.nblocks;
-    red_release_add_u64(gb.ctr, 1ull);
-    int ok = 1;
-    if (ld_acquire_u64(gb.ctr) < target) {
-      const unsigned long long t0 = globaltimer_ns();
-      while (ld_acquire_u64(gb.ctr) < target) {
-        if (*(volatile int*)gb.err != kErrNone) { ok = 0; break; }
-        if (globaltimer_ns() - t0 > gb.timeout_ns) {
-          atomicCAS(gb.err, kErrNone, kErrTimeout);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    if (ok && *(volatile int*)gb.err != kErrNone) ok = 0;
-    *s_flag = ok;
+    *s_flag = group_arrive_wait(gb, epoch);
   }
   __syncthreads();
   return *s_flag != 0;

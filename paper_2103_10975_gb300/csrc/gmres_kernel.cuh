@@ -200,6 +200,35 @@ __device__ __forceinline__ void block_finish(int L, R* part, int lb, R (*red)[LW
   }
 }
 
+// block_finish and the group barrier in one: after one CTA barrier, warp 0
+// adds the warp partials, stores the CTA's sums, and (its lanes' stores ordered
+// by __syncwarp before lane 0's release) arrives and waits at the group
+// barrier, while warp 1 runs `side`; a second CTA barrier ends it.  Saves the
+// CTA barrier that separates the two when they are done one after the other.
+template <int LW, int BS, typename R, typename Side>
+__device__ __forceinline__ bool finish_and_sync(int L, R* part, int lb, R (*red)[LW], int ps,
+                                                const GroupBarrier& gb, unsigned long long& epoch,
+                                                int* s_flag, Side side) {
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    for (int k = lane; k < L; k += 32) {
+      R s = R(0);
+#pragma unroll
+      for (int w = 0; w < BS / 32; w++) s += red[w][k];
+      part[(long long)k * ps + lb] = s;
+    }
+    __syncwarp();
+    if (lane == 0)
+      *s_flag = gb.nblocks == 1 ? (*(volatile int*)gb.err == kErrNone)
+                                : group_arrive_wait(gb, epoch);
+  } else if (warp == 1) {
+    side();
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
 // Sum of the group's partials for k < L, identical in every CTA (same order);
 // tot gets the sums in FP64, coef the same values in the working precision.
 // Each warp takes up to four slots at a time, four partials per lane each, so
@@ -268,14 +297,19 @@ __device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, lo
       ri = fma(-sm.sn[i], ri, sm.cr[i]);
     }
     const double hsub = hc[c + 1];
-    const double rho = sqrt(fma(ri, ri, hsub * hsub));
-    if (rho == 0.0) {
-      sm.cs[c] = 1.0;
-      sm.sn[c] = 0.0;
-    } else {
-      const double inv = 1.0 / rho;
+    const double r2 = fma(ri, ri, hsub * hsub);
+    double rho;
+    if (r2 > 1e-300 && r2 < 1e300) {
+      // one reciprocal square root instead of a square root and a division
+      // (each a long dependent chain on this GPU's FP64 pipe)
+      const double inv = rsqrt(r2);
       sm.cs[c] = ri * inv;
       sm.sn[c] = hsub * inv;
+      rho = r2 * inv;
+    } else {
+      rho = sqrt(r2);
+      sm.cs[c] = rho == 0.0 ? 1.0 : ri / rho;
+      sm.sn[c] = rho == 0.0 ? 0.0 : hsub / rho;
     }
     rc[c] = rho;
     rc[c + 1] = 0.0;
@@ -979,8 +1013,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
             givens_column<T, MAXM, BS>(sm, j - 1, rtol_bnorm, iters, kp.max_iters, m, hist,
                                        tk.hist_cap, bnorm);
         };
-        block_finish<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red, ps);
-        ok = group_sync_with(w.bar, epoch, &sm.flag, givens_prev);
+        ok = finish_and_sync<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red, ps, w.bar,
+                                          epoch, &sm.flag, givens_prev);
         if (!ok) goto abort;
         const int stop = sm.stop;
         if (stop == 2) { status = kErrNonfinite; goto finish; }
@@ -1005,8 +1039,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
 #undef MLG_Y
 #undef MLG_YS
 #undef MLG_YB
-        block_finish<LMAX, BS, T>(j + 2, (T*)part(), lb, sm.red, ps);
-        ok = group_sync(w.bar, epoch, &sm.flag);
+        ok = finish_and_sync<LMAX, BS, T>(j + 2, (T*)part(), lb, sm.red, ps, w.bar, epoch,
+                                          &sm.flag, NoSide());
         if (!ok) goto abort;
         gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef, ps);
         red++;
