@@ -23,6 +23,11 @@ each 2x2 block.  Bilinear upsampling from m to n points per axis uses
 half-pixel centres: src = (i + 0.5) m/n - 0.5 clamped below at 0, i0 = floor(src),
 i1 = min(i0 + 1, m - 1), weight src - i0 on i1.
 
+The 3D network (dim = 3, the variable-coefficient workload) is the same with
+3x3x3 kernels, 2x2x2 average pooling (mean of each 2x2x2 block, down to 8^3)
+and trilinear upsampling (the 1D interpolation applied along each axis).
+Arrays are (C, n, n) in 2D and (C, n, n, n) in 3D, x the last axis.
+
 Scaling (the paper leaves it open): the network sees u = b/s and is trained
 towards x/s, s = rms(b); the guess is x0 = s * y.  Loss: the squared 2-norm of
 Sec. 2.3 averaged over the batch and the grid points,
@@ -31,6 +36,7 @@ Adam (Kingma & Ba 2015): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
 theta -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
 """
 
+import itertools
 import math
 
 import numpy as np
@@ -45,56 +51,71 @@ def level_sizes(n, min_size=8):
     return sizes
 
 
-def param_shapes(n, C=32):
+def param_shapes(n, C=32, dim=2):
     """Ordered (name, shape) list of the network's parameters."""
-    shapes = [("in.w", (C, 1, 3, 3)), ("in.b", (C,))]
+    k = (3,) * dim
+    shapes = [("in.w", (C, 1) + k), ("in.b", (C,))]
     for l in range(len(level_sizes(n))):
-        shapes += [("level%d.w" % l, (C, C, 3, 3)), ("level%d.b" % l, (C,))]
-    shapes += [("dil.w", (C, C, 3, 3)), ("dil.b", (C,)), ("out.w", (1, C, 3, 3)), ("out.b", (1,))]
+        shapes += [("level%d.w" % l, (C, C) + k), ("level%d.b" % l, (C,))]
+    shapes += [("dil.w", (C, C) + k), ("dil.b", (C,)), ("out.w", (1, C) + k), ("out.b", (1,))]
     return shapes
 
 
+def _taps(dim):
+    return list(itertools.product(range(3), repeat=dim))
+
+
+def _window(pad, tap, d, size):
+    return pad[(slice(None),) + tuple(slice(t * d, t * d + sz) for t, sz in zip(tap, size))]
+
+
 def conv_fwd(inp, W, bias, d):
-    C, H, Wd = inp.shape
-    pad = np.zeros((C, H + 2 * d, Wd + 2 * d))
-    pad[:, d:d + H, d:d + Wd] = inp
-    out = np.zeros((W.shape[0], H, Wd)) + bias[:, None, None]
-    for ky in range(3):
-        for kx in range(3):
-            patch = pad[:, ky * d:ky * d + H, kx * d:kx * d + Wd]
-            out += np.einsum("oc,chw->ohw", W[:, :, ky, kx], patch)
+    """Cross-correlation with dilation d over the spatial axes of inp (C, ...),
+    zeros outside the grid; W is (O, C, 3, ..., 3)."""
+    size = inp.shape[1:]
+    pad = np.zeros((inp.shape[0],) + tuple(sz + 2 * d for sz in size))
+    pad[(slice(None),) + tuple(slice(d, d + sz) for sz in size)] = inp
+    out = np.zeros((W.shape[0],) + size) + bias.reshape((-1,) + (1,) * len(size))
+    for tap in _taps(len(size)):
+        patch = _window(pad, tap, d, size)
+        out += np.tensordot(W[(slice(None), slice(None)) + tap], patch, axes=([1], [0]))
     return out
 
 
 def conv_bwd(inp, W, d, gout):
     """Returns (grad_in, grad_W, grad_bias) of conv_fwd for upstream gout."""
-    C, H, Wd = inp.shape
-    pad = np.zeros((C, H + 2 * d, Wd + 2 * d))
-    pad[:, d:d + H, d:d + Wd] = inp
+    size = inp.shape[1:]
+    dim = len(size)
+    pad = np.zeros((inp.shape[0],) + tuple(sz + 2 * d for sz in size))
+    inner = (slice(None),) + tuple(slice(d, d + sz) for sz in size)
+    pad[inner] = inp
     gpad = np.zeros_like(pad)
     gW = np.zeros_like(W)
-    for ky in range(3):
-        for kx in range(3):
-            patch = pad[:, ky * d:ky * d + H, kx * d:kx * d + Wd]
-            gW[:, :, ky, kx] = np.einsum("ohw,chw->oc", gout, patch)
-            gpad[:, ky * d:ky * d + H, kx * d:kx * d + Wd] += np.einsum(
-                "oc,ohw->chw", W[:, :, ky, kx], gout)
-    return gpad[:, d:d + H, d:d + Wd], gW, gout.sum(axis=(1, 2))
+    sp = tuple(range(1, dim + 1))
+    for tap in _taps(dim):
+        patch = _window(pad, tap, d, size)
+        gW[(slice(None), slice(None)) + tap] = np.tensordot(gout, patch, axes=(sp, sp))
+        win = (slice(None),) + tuple(slice(t * d, t * d + sz) for t, sz in zip(tap, size))
+        gpad[win] += np.tensordot(W[(slice(None), slice(None)) + tap], gout, axes=([0], [0]))
+    return gpad[inner], gW, gout.sum(axis=sp)
 
 
 def avgpool2(x):
-    C, H, W = x.shape
-    h, w = H // 2, W // 2
-    return 0.25 * (x[:, 0:2 * h:2, 0:2 * w:2] + x[:, 1:2 * h:2, 0:2 * w:2]
-                   + x[:, 0:2 * h:2, 1:2 * w:2] + x[:, 1:2 * h:2, 1:2 * w:2])
+    """Mean of each 2x2 (2x2x2) block; size s -> floor(s/2) per axis."""
+    dim = x.ndim - 1
+    h = [sz // 2 for sz in x.shape[1:]]
+    out = np.zeros((x.shape[0],) + tuple(h))
+    for off in itertools.product(range(2), repeat=dim):
+        out += x[(slice(None),) + tuple(slice(o, 2 * hh, 2) for o, hh in zip(off, h))]
+    return out / 2 ** dim
 
 
-def avgpool2_bwd(g, H, W):
-    C, h, w = g.shape
-    out = np.zeros((C, H, W))
-    for a in range(2):
-        for b in range(2):
-            out[:, a:2 * h:2, b:2 * w:2] += 0.25 * g
+def avgpool2_bwd(g, *size):
+    dim = g.ndim - 1
+    h = g.shape[1:]
+    out = np.zeros((g.shape[0],) + tuple(size))
+    for off in itertools.product(range(2), repeat=dim):
+        out[(slice(None),) + tuple(slice(o, 2 * hh, 2) for o, hh in zip(off, h))] += g / 2 ** dim
     return out
 
 
@@ -115,27 +136,36 @@ def interp_matrix(m, n):
     return U
 
 
+def _along(U, x, axis):
+    """Apply the matrix U (n x m) along spatial axis `axis` (1-based) of x."""
+    return np.moveaxis(np.tensordot(U, x, axes=([1], [axis])), 0, axis)
+
+
 def upsample(z, n):
-    C, m, _ = z.shape
-    U = interp_matrix(m, n)
-    return np.einsum("im,cmk,jk->cij", U, z, U)
+    """Half-pixel (bi/tri)linear upsampling of z (C, m, ...) to n points per axis."""
+    U = interp_matrix(z.shape[1], n)
+    for ax in range(1, z.ndim):
+        z = _along(U, z, ax)
+    return z
 
 
 def upsample_bwd(g, m):
-    C, n, _ = g.shape
-    U = interp_matrix(m, n)
-    return np.einsum("im,cij,jk->cmk", U, g, U)
+    """Adjoint of upsample: g (C, n, ...) -> (C, m, ...)."""
+    U = interp_matrix(m, g.shape[1]).T
+    for ax in range(1, g.ndim):
+        g = _along(U, g, ax)
+    return g
 
 
 def relu(x):
     return np.maximum(x, 0.0)
 
 
-def forward(params, u, n, keep=False):
-    """params: dict name -> array; u: (n*n,) normalised input.  Returns y (n*n,)
-    and, with keep=True, the activations needed by backward."""
+def forward(params, u, n, keep=False, dim=2):
+    """params: dict name -> array; u: (n^dim,) normalised input.  Returns y
+    (n^dim,) and, with keep=True, the activations needed by backward."""
     sizes = level_sizes(n)
-    x = np.asarray(u, dtype=np.float64).reshape(1, n, n)
+    x = np.asarray(u, dtype=np.float64).reshape((1,) + (n,) * dim)
     pre0 = conv_fwd(x, params["in.w"], params["in.b"], 1)
     a0 = relu(pre0)
     pools = [a0]
@@ -156,11 +186,11 @@ def forward(params, u, n, keep=False):
     return y.reshape(-1)
 
 
-def backward(params, cache, gy, n):
-    """Gradients of all parameters for upstream gradient gy (n*n,)."""
+def backward(params, cache, gy, n, dim=2):
+    """Gradients of all parameters for upstream gradient gy (n^dim,)."""
     sizes = level_sizes(n)
     g = {}
-    gy = np.asarray(gy, dtype=np.float64).reshape(1, n, n)
+    gy = np.asarray(gy, dtype=np.float64).reshape((1,) + (n,) * dim)
     gt, g["out.w"], g["out.b"] = conv_bwd(cache["t"], params["out.w"], 1, gy)
     gpred = gt * (cache["pred"] > 0)
     gs_d, g["dil.w"], g["dil.b"] = conv_bwd(cache["s"], params["dil.w"], 2, gpred)
@@ -175,25 +205,25 @@ def backward(params, cache, gy, n):
     # pooling chain: p_l = avgpool2(p_{l-1}); accumulate from the coarsest level
     acc = gpools[-1]
     for l in range(len(sizes) - 1, 0, -1):
-        acc = gpools[l - 1] + avgpool2_bwd(acc, sizes[l - 1], sizes[l - 1])
+        acc = gpools[l - 1] + avgpool2_bwd(acc, *((sizes[l - 1],) * dim))
     ga0 = acc
     gpre0 = ga0 * (cache["pre0"] > 0)
     _, g["in.w"], g["in.b"] = conv_bwd(cache["x"], params["in.w"], 1, gpre0)
     return g
 
 
-def loss_and_grads(params, inputs, targets, n):
+def loss_and_grads(params, inputs, targets, n, dim=2):
     """Batch MSE L = 1/(B N) sum ||y_b - target_b||^2 and its gradients.
-    inputs / targets: (B, n*n) normalised arrays."""
+    inputs / targets: (B, n^dim) normalised arrays."""
     B = len(inputs)
-    N = n * n
+    N = n ** dim
     total = 0.0
     grads = {k: np.zeros_like(v) for k, v in params.items()}
     for b in range(B):
-        y, cache = forward(params, inputs[b], n, keep=True)
+        y, cache = forward(params, inputs[b], n, keep=True, dim=dim)
         diff = y - np.asarray(targets[b], dtype=np.float64)
         total += float(diff @ diff)
-        gb = backward(params, cache, 2.0 * diff / (B * N), n)
+        gb = backward(params, cache, 2.0 * diff / (B * N), n, dim=dim)
         for k in grads:
             grads[k] += gb[k]
     return total / (B * N), grads

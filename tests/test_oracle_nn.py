@@ -1,4 +1,4 @@
-"""Pins of the FP64 network reference: convolution against scipy's 2D
+"""Pins of the FP64 network reference (2D and 3D): convolution against scipy's
 correlation, pooling / upsampling against their closed forms, the analytic
 backward pass against central finite differences, Adam against its formula."""
 import math
@@ -133,3 +133,86 @@ def test_training_reduces_loss():
             state[k] = (m, v)
     l1, _ = nn.loss_and_grads(params, u, t, n)
     assert l1 < 0.5 * l0
+
+
+# ---------------------------------------------------------------- 3D network
+
+def _params3(n, C, seed):
+    rng = np.random.default_rng(seed)
+    return {k: rng.standard_normal(s) * (0.3 if k.endswith(".w") else 0.1)
+            for k, s in nn.param_shapes(n, C, dim=3)}
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_conv3d_matches_scipy_correlate(d):
+    import scipy.ndimage
+    rng = np.random.default_rng(10 + d)
+    C, O, H = 2, 2, 7
+    inp = rng.standard_normal((C, H, H, H))
+    W = rng.standard_normal((O, C, 3, 3, 3))
+    bias = rng.standard_normal(O)
+    got = nn.conv_fwd(inp, W, bias, d)
+    for o in range(O):
+        ref = np.full((H, H, H), bias[o])
+        for c in range(C):
+            k = np.zeros((2 * d + 1,) * 3)
+            k[::d, ::d, ::d] = W[o, c]
+            ref += scipy.ndimage.correlate(inp[c], k, mode="constant", cval=0.0)
+        assert np.allclose(got[o], ref, atol=1e-12)
+
+
+def test_pool3d_and_trilinear_closed_forms():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((2, 8, 8, 8))
+    p = nn.avgpool2(x)
+    assert p.shape == (2, 4, 4, 4)
+    assert np.isclose(p[1, 2, 1, 3], x[1, 4:6, 2:4, 6:8].mean())
+    assert np.allclose(nn.avgpool2(np.full((1, 7, 7, 7), 3.0)), 3.0)
+    # trilinear upsampling written out corner by corner at sampled points
+    z = rng.standard_normal((1, 5, 5, 5))
+    n = 12
+    u = nn.upsample(z, n)
+
+    def src(i):
+        s = max((i + 0.5) * 5 / n - 0.5, 0.0)
+        i0 = min(int(math.floor(s)), 4)
+        return i0, min(i0 + 1, 4), s - i0
+
+    for (i, j, k) in [(0, 0, 0), (3, 7, 11), (11, 5, 2), (6, 6, 6)]:
+        z0, z1, lz = src(i)
+        y0, y1, ly = src(j)
+        x0, x1, lx = src(k)
+        ref = 0.0
+        for zz, wz in ((z0, 1 - lz), (z1, lz)):
+            for yy, wy in ((y0, 1 - ly), (y1, ly)):
+                for xx, wx in ((x0, 1 - lx), (x1, lx)):
+                    ref += wz * wy * wx * z[0, zz, yy, xx]
+        assert abs(u[0, i, j, k] - ref) < 1e-13
+    assert np.allclose(nn.upsample(np.full((1, 4, 4, 4), 2.0), 9), 2.0)
+    g = rng.standard_normal((1, n, n, n))
+    assert np.isclose((u * g).sum(), (z * nn.upsample_bwd(g, 5)).sum())
+    g4 = rng.standard_normal((2, 4, 4, 4))
+    assert np.isclose((p * g4).sum(), (x * nn.avgpool2_bwd(g4, 8, 8, 8)).sum())
+
+
+def test_3d_gradients_vs_central_differences():
+    n, C = 8, 3
+    params = _params3(n, C, 7)
+    rng = np.random.default_rng(8)
+    inputs = rng.standard_normal((1, n ** 3))
+    targets = rng.standard_normal((1, n ** 3))
+    _, grads = nn.loss_and_grads(params, inputs, targets, n, dim=3)
+    eps = 1e-6
+    for name in params:
+        flat = params[name].reshape(-1)
+        idx = rng.choice(flat.size, size=min(3, flat.size), replace=False)
+        for i in idx:
+            old = flat[i]
+            flat[i] = old + eps
+            lp, _ = nn.loss_and_grads(params, inputs, targets, n, dim=3)
+            flat[i] = old - eps
+            lm, _ = nn.loss_and_grads(params, inputs, targets, n, dim=3)
+            flat[i] = old
+            fd = (lp - lm) / (2 * eps)
+            an = grads[name].reshape(-1)[i]
+            assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-3), (name, i, fd, an)
