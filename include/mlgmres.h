@@ -25,7 +25,8 @@
  *    ABI.  mlgmres_last_error() gives a text for the last failing call.
  *  - The library allocates all of its workspace (Krylov basis, Hessenberg
  *    state, network weights, Adam state, replay buffer) in mlgmres_create;
- *    solves allocate no device memory.
+ *    solves allocate no device memory.  (A handle whose guess mode is not
+ *    LEARNED allocates the network only on its first mlgmres_nn_* call.)
  *  - A handle is not thread safe; use one handle per host thread.
  */
 #ifndef MLGMRES_H
@@ -214,12 +215,16 @@ mlgmres_status mlgmres_apply(mlgmres_t h, const double* u_dev, double* out_dev, 
 mlgmres_status mlgmres_arnoldi(mlgmres_t h, const double* v0_dev, int steps, double* H_host,
                                double* V_dev, int* done, void* stream);
 
-/* Number of network parameters (FP32 master copy). */
+/* The network of Sec. 2.1 exists in 2D (3x3 kernels, 2x2 average pooling,
+ * bilinear upsampling) and, for dim = 3 handles, in 3D (3x3x3 kernels, 2x2x2
+ * pooling, trilinear upsampling); inputs are n^dim values per sample.
+ * Number of network parameters (FP32 master copy). */
 mlgmres_status mlgmres_nn_param_count(mlgmres_t h, long long* count);
 
 /* Copies the FP32 master parameters out / in, in the order
  * in.w, in.b, level[0].w, level[0].b, ..., dil.w, dil.b, out.w, out.b
- * (weights as [out][in][ky][kx]).  Setting them also resets Adam's moments. */
+ * (weights as [out][in][ky][kx], 3D [out][in][kz][ky][kx]).  Setting them also
+ * resets Adam's moments. */
 mlgmres_status mlgmres_nn_get_params(mlgmres_t h, float* params_host, long long count);
 mlgmres_status mlgmres_nn_set_params(mlgmres_t h, const float* params_host, long long count);
 

@@ -64,6 +64,37 @@ __global__ void jacobi_kernel(int n, const double* __restrict__ b, const double*
   xout[i] = c + omega / (4.0 * s2) * (b[i] - ax);
 }
 
+// 3D: A u = (1/h^2) sum_faces k_f (u_c - u_nb), k_f the harmonic mean of the
+// two cells' kappa (kappa_c on a wall face, u = 0 beyond it; kappa = NULL
+// means 1); the diagonal is (1/h^2) sum_faces k_f.
+__global__ void jacobi3d_kernel(int n, const float* __restrict__ kappa,
+                                const double* __restrict__ b, const double* __restrict__ xin,
+                                double* __restrict__ xout, double omega) {
+  const long long N = (long long)n * n * n;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
+  const long long nn = (long long)n * n;
+  const long long off[6] = {-1, 1, -(long long)n, (long long)n, -nn, nn};
+  const bool has[6] = {ix > 0, ix < n - 1, iy > 0, iy < n - 1, iz > 0, iz < n - 1};
+  const double c = xin[i];
+  const double kc = kappa ? (double)kappa[i] : 1.0;
+  double au = 0.0, diag = 0.0;
+  for (int f = 0; f < 6; f++) {
+    double kf = kc, unb = 0.0;
+    if (has[f]) {
+      const double kn = kappa ? (double)kappa[i + off[f]] : 1.0;
+      kf = 2.0 * kc * kn / (kc + kn);
+      unb = xin[i + off[f]];
+    }
+    au += kf * (c - unb);
+    diag += kf;
+  }
+  const double h = 2.0 / (n + 1);
+  const double s2 = 1.0 / (h * h);
+  xout[i] = c + omega * (b[i] - s2 * au) / (s2 * diag);
+}
+
 // ring pair: u = b/s, t = x/s
 __global__ void store_pair_kernel(const double* __restrict__ b, const double* __restrict__ x,
                                   int N, const double* sumsq, float* __restrict__ u,
@@ -129,9 +160,12 @@ cudaError_t launch_normalise(const double* b, int N, const double* sumsq, float*
   note_launches(1);
   return cudaGetLastError();
 }
-cudaError_t launch_jacobi(int n, const double* b, const double* xin, double* xout, double omega,
-                          cudaStream_t s) {
-  jacobi_kernel<<<blocks_for(n * n), 256, 0, s>>>(n, b, xin, xout, omega);
+cudaError_t launch_jacobi(int dim, int n, const float* kappa, const double* b, const double* xin,
+                          double* xout, double omega, cudaStream_t s) {
+  if (dim == 3)
+    jacobi3d_kernel<<<blocks_for(n * n * n), 256, 0, s>>>(n, kappa, b, xin, xout, omega);
+  else
+    jacobi_kernel<<<blocks_for(n * n), 256, 0, s>>>(n, b, xin, xout, omega);
   note_launches(1);
   return cudaGetLastError();
 }

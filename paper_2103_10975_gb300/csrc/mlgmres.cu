@@ -109,6 +109,23 @@ int effective_stages(const mlgmres* h) {
   return gmres_bulk_stages(h->fp32, h->opt.m);
 }
 
+// Allocates the network, its replay ring and the learned-guess buffers (2D
+// and 3D networks; once per handle).
+void ensure_net(mlgmres* h) {
+  if (h->net.master) return;
+  const mlgmres_options* opt = &h->opt;
+  CK(cudaMalloc(&h->x_alt, sizeof(double) * h->ldv));
+  CK(cudaMalloc(&h->x_tmp, sizeof(double) * h->ldv));
+  CK(cudaMalloc(&h->u_in, sizeof(float) * h->ldv));
+  CK(cudaMalloc(&h->y_out, sizeof(float) * h->ldv));
+  CK(cudaMalloc(&h->ring_u, sizeof(float) * h->ldv * opt->replay_cap));
+  CK(cudaMalloc(&h->ring_t, sizeof(float) * h->ldv * opt->replay_cap));
+  CK(cudaMalloc(&h->ddots, sizeof(double) * (2 * opt->replay_cap + 1)));
+  CK(cudaMallocHost(&h->hdots, sizeof(double) * (2 * opt->replay_cap + 1)));
+  CK(cudaMalloc(&h->loss_dev, sizeof(float) * 4));
+  CK(net_create(h->net, h->grid.n, opt->batch, opt->seed, h->grid.dim));
+}
+
 // Shared-memory bytes of a single solve's V slice at `blocks` CTAs (0 if the
 // slice does not fit).
 int single_vsmem(const mlgmres* h, int blocks) {
@@ -391,19 +408,9 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     if (opt->guess == MLGMRES_GUESS_LEARNED && opt->retrain_after > 0)
       CK(cudaStreamCreateWithFlags(&h->train_stream, cudaStreamNonBlocking));
     h->rng_state = opt->seed;
-    if (grid->dim == 2) {
-      // learned-guess machinery (the network is two-dimensional)
-      CK(cudaMalloc(&h->x_alt, sizeof(double) * h->ldv));
-      CK(cudaMalloc(&h->x_tmp, sizeof(double) * h->ldv));
-      CK(cudaMalloc(&h->u_in, sizeof(float) * h->ldv));
-      CK(cudaMalloc(&h->y_out, sizeof(float) * h->ldv));
-      CK(cudaMalloc(&h->ring_u, sizeof(float) * h->ldv * opt->replay_cap));
-      CK(cudaMalloc(&h->ring_t, sizeof(float) * h->ldv * opt->replay_cap));
-      CK(cudaMalloc(&h->ddots, sizeof(double) * (2 * opt->replay_cap + 1)));
-      CK(cudaMallocHost(&h->hdots, sizeof(double) * (2 * opt->replay_cap + 1)));
-      CK(cudaMalloc(&h->loss_dev, sizeof(float) * 4));
-      CK(net_create(h->net, grid->n, opt->batch, opt->seed));
-    }
+    // learned-guess machinery: at create for the LEARNED mode, else on the
+    // first call of an nn_* inspection entry point
+    if (opt->guess == MLGMRES_GUESS_LEARNED) ensure_net(h);
     CK(cudaDeviceSynchronize());
   } catch (const Fail& f) {
     fprintf(stderr, "mlgmres_create: %s\n", h->last_error.c_str());
@@ -480,7 +487,7 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
     } else {
       r.guess_used = MLGMRES_GUESS_USER;
     }
-    if (mode == MLGMRES_GUESS_LEARNED && h->net_ready && h->grid.dim == 2) {
+    if (mode == MLGMRES_GUESS_LEARNED && h->net_ready) {
       if (h->train_pending) {
         CK(cudaStreamWaitEvent(s, h->train_done, 0));
         h->train_pending = false;
@@ -494,7 +501,8 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
       double* oth = h->x_tmp;
       CK(launch_denormalise(h->y_out, N, h->scal, h->c_train, cur, s));
       for (int k = 0; k < h->opt.guess_smooth; k++) {
-        CK(launch_jacobi(h->grid.n, b, cur, oth, (double)h->opt.guess_omega, s));
+        CK(launch_jacobi(h->grid.dim, h->grid.n, h->grid.kappa_dev, b, cur, oth,
+                         (double)h->opt.guess_omega, s));
         std::swap(cur, oth);
       }
       x_alt = cur;
@@ -567,7 +575,7 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
     r.relres_learned = relres_learned;
     if (x_alt) CK(cudaEventElapsedTime(&r.guess_ms, h->ev2, h->ev0));
     CK(cudaEventElapsedTime(&r.tos_ms, h->ev0, h->ev1));
-    if (mode == MLGMRES_GUESS_LEARNED && h->grid.dim == 2 && r.status != MLGMRES_ERR_TIMEOUT)
+    if (mode == MLGMRES_GUESS_LEARNED && r.status != MLGMRES_ERR_TIMEOUT)
       r.admitted = gate_and_store(h, b, x, r, s);
     // Algorithm 1's trigger: retrain once f_r pairs were admitted since the
     // previous phase (the first phase at tau0 takes the warm-up pairs)
@@ -695,7 +703,10 @@ mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_ho
   if (!h) return MLGMRES_ERR_ARG;
   h->last_error.clear();
   try {
-    ARG(h->grid.dim == 2, "the learned guess is available for 2D grids only");
+    if (!h->net.master) {  // no learned guess on this handle: nothing to train
+      if (loss_host) *loss_host = -1.0f;
+      return MLGMRES_OK;
+    }
     train_phase(h, (cudaStream_t)side_stream, loss_host);
     return MLGMRES_OK;
   } catch (const Fail& f) {
@@ -891,9 +902,10 @@ mlgmres_status mlgmres_arnoldi(mlgmres_t h, const double* v0, int steps, double*
 
 mlgmres_status mlgmres_nn_param_count(mlgmres_t h, long long* count) {
   if (!h || !count) return MLGMRES_ERR_ARG;
-  if (h->grid.dim != 2) {
-    h->last_error = "the network exists for 2D grids only";
-    return MLGMRES_ERR_ARG;
+  try {
+    ensure_net(h);
+  } catch (const Fail& f) {
+    return f.st;
   }
   *count = h->net.nparams;
   return MLGMRES_OK;
@@ -902,7 +914,8 @@ mlgmres_status mlgmres_nn_param_count(mlgmres_t h, long long* count) {
 mlgmres_status mlgmres_nn_get_params(mlgmres_t h, float* p, long long count) {
   if (!h) return MLGMRES_ERR_ARG;
   try {
-    ARG(h->grid.dim == 2 && p && count == h->net.nparams, "bad parameter buffer");
+    ensure_net(h);
+    ARG(p && count == h->net.nparams, "bad parameter buffer");
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(p, h->net.master, sizeof(float) * count, cudaMemcpyDeviceToHost));
     return MLGMRES_OK;
@@ -914,7 +927,8 @@ mlgmres_status mlgmres_nn_get_params(mlgmres_t h, float* p, long long count) {
 mlgmres_status mlgmres_nn_set_params(mlgmres_t h, const float* p, long long count) {
   if (!h) return MLGMRES_ERR_ARG;
   try {
-    ARG(h->grid.dim == 2 && p && count == h->net.nparams, "bad parameter buffer");
+    ensure_net(h);
+    ARG(p && count == h->net.nparams, "bad parameter buffer");
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(h->net.master, p, sizeof(float) * count, cudaMemcpyHostToDevice));
     CK(cudaMemset(h->net.adam_m, 0, sizeof(float) * count));
@@ -932,7 +946,8 @@ mlgmres_status mlgmres_nn_forward(mlgmres_t h, int batch, const float* u, float*
                                   void* stream) {
   if (!h) return MLGMRES_ERR_ARG;
   try {
-    ARG(h->grid.dim == 2 && u && y, "bad arguments");
+    ensure_net(h);
+    ARG(u && y, "bad arguments");
     ARG(batch >= 1 && batch <= h->opt.batch, "batch must be in 1..opt.batch");
     cudaStream_t s = (cudaStream_t)stream;
     CK(net_forward(h->net, batch, u, y, s));
@@ -947,7 +962,8 @@ mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u, cons
                                     float* loss_host, float* grad_host, void* stream) {
   if (!h) return MLGMRES_ERR_ARG;
   try {
-    ARG(h->grid.dim == 2 && u && t && loss_host && grad_host, "bad arguments");
+    ensure_net(h);
+    ARG(u && t && loss_host && grad_host, "bad arguments");
     ARG(batch >= 1 && batch <= h->opt.batch, "batch must be in 1..opt.batch");
     cudaStream_t s = (cudaStream_t)stream;
     float* y = nullptr;

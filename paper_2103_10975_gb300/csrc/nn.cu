@@ -42,56 +42,97 @@ __device__ __forceinline__ void store32(bf16* p, const float* v) {
   }
 }
 
+// --------------------------------------------------------------- geometry --
+// Grid points of a cubic grid of side n: p = ((b n + z) n + y) n + x in 3D,
+// (b n + y) n + x in 2D.  Tap t of a 3^D stencil: kz = t / 9 (3D), ky = (t / 3) % 3,
+// kx = t % 3, offsets k - 1 (times the dilation).
+template <int D>
+struct Geo {
+  static constexpr int T = D == 3 ? 27 : 9;
+  __device__ static void decode(long long p, int n, int& b, int& z, int& y, int& x) {
+    x = (int)(p % n);
+    long long r = p / n;
+    y = (int)(r % n);
+    r /= n;
+    if (D == 3) {
+      z = (int)(r % n);
+      r /= n;
+    } else {
+      z = 0;
+    }
+    b = (int)r;
+  }
+  // index of (b, z + dz, y + dy, x + dx), or -1 outside the grid
+  __device__ static long long nb(int b, int z, int y, int x, int dz, int dy, int dx, int n) {
+    const int zz = z + dz, yy = y + dy, xx = x + dx;
+    if (yy < 0 || yy >= n || xx < 0 || xx >= n) return -1;
+    if (D == 3 && (zz < 0 || zz >= n)) return -1;
+    return D == 3 ? (((long long)b * n + zz) * n + yy) * n + xx : ((long long)b * n + yy) * n + xx;
+  }
+  __device__ static void tap(int t, int& dz, int& dy, int& dx) {
+    dz = D == 3 ? t / 9 - 1 : 0;
+    dy = (t / 3) % 3 - 1;
+    dx = t % 3 - 1;
+  }
+  __host__ __device__ static long long pts(int n) {
+    return D == 3 ? (long long)n * n * n : (long long)n * n;
+  }
+};
+
 // ---------------------------------------------------------------- forward --
 
 // a0[p][c] = relu(b[c] + sum_tap w[c][tap] u[p + off_tap])
+template <int D>
 __global__ void conv_in_fwd(int B, int n, const float* __restrict__ u,
                             const float* __restrict__ w, const float* __restrict__ bias,
                             bf16* __restrict__ a0) {
-  __shared__ float ws[kC * 9 + kC];
-  for (int i = threadIdx.x; i < kC * 9; i += blockDim.x) ws[i] = w[i];
-  for (int i = threadIdx.x; i < kC; i += blockDim.x) ws[kC * 9 + i] = bias[i];
+  constexpr int T = Geo<D>::T;
+  __shared__ float ws[kC * T + kC];
+  for (int i = threadIdx.x; i < kC * T; i += blockDim.x) ws[i] = w[i];
+  for (int i = threadIdx.x; i < kC; i += blockDim.x) ws[kC * T + i] = bias[i];
   __syncthreads();
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= (long long)B * n * n) return;
-  const int b = (int)(p / ((long long)n * n));
-  const int r = (int)(p % ((long long)n * n));
-  const int y = r / n, x = r % n;
-  float tap[9];
+  if (p >= B * Geo<D>::pts(n)) return;
+  int b, z, y, x;
+  Geo<D>::decode(p, n, b, z, y, x);
+  float tp[T];
 #pragma unroll
-  for (int t = 0; t < 9; t++) {
-    const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-    tap[t] = (yy >= 0 && yy < n && xx >= 0 && xx < n) ? u[((long long)b * n + yy) * n + xx] : 0.f;
+  for (int t = 0; t < T; t++) {
+    int dz, dy, dx;
+    Geo<D>::tap(t, dz, dy, dx);
+    const long long q = Geo<D>::nb(b, z, y, x, dz, dy, dx, n);
+    tp[t] = q >= 0 ? u[q] : 0.f;
   }
   float v[kC];
 #pragma unroll
   for (int c = 0; c < kC; c++) {
-    float acc = ws[kC * 9 + c];
+    float acc = ws[kC * T + c];
 #pragma unroll
-    for (int t = 0; t < 9; t++) acc += ws[c * 9 + t] * tap[t];
+    for (int t = 0; t < T; t++) acc += ws[c * T + t] * tp[t];
     v[c] = fmaxf(acc, 0.f);
   }
   store32(a0 + p * kC, v);
 }
 
-// out = 2x2 mean of in (side s -> s/2), NHWC
+// out = mean of each 2^D block of in (side s -> s/2), channels last
+template <int D>
 __global__ void pool2_fwd(int B, int s, const bf16* __restrict__ in, bf16* __restrict__ out) {
   const int so = s / 2;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= (long long)B * so * so * kC) return;
+  if (i >= B * Geo<D>::pts(so) * kC) return;
   const int c = (int)(i % kC);
-  const long long p = i / kC;
-  const int b = (int)(p / ((long long)so * so));
-  const int r = (int)(p % ((long long)so * so));
-  const int y = r / so, x = r % so;
-  const bf16* base = in + (((long long)b * s + 2 * y) * s + 2 * x) * kC + c;
-  const float v = __bfloat162float(base[0]) + __bfloat162float(base[kC]) +
-                  __bfloat162float(base[(long long)s * kC]) +
-                  __bfloat162float(base[(long long)s * kC + kC]);
-  out[i] = __float2bfloat16(0.25f * v);
+  int b, z, y, x;
+  Geo<D>::decode(i / kC, so, b, z, y, x);
+  float v = 0.f;
+#pragma unroll
+  for (int k = 0; k < (1 << D); k++) {
+    const long long q = Geo<D>::nb(b, 2 * z, 2 * y, 2 * x, (k >> 2) & 1, (k >> 1) & 1, k & 1, s);
+    v += __bfloat162float(in[q * kC + c]);
+  }
+  out[i] = __float2bfloat16(v * (1.f / (1 << D)));
 }
 
-// Half-pixel bilinear source position of output index i (m source points, n out).
+// Half-pixel linear source position of output index i (m source points, n out).
 __device__ __forceinline__ void bilin(int i, int m, int n, int& i0, int& i1, float& lam) {
   float src = ((float)i + 0.5f) * (float)m / (float)n - 0.5f;
   if (src < 0.f) src = 0.f;
@@ -107,52 +148,60 @@ struct Levels {
   int L;
 };
 
-// s[p][c] = sum_l upsample(z_l)[p][c]
+// s[p][c] = sum_l upsample(z_l)[p][c]  (bilinear in 2D, trilinear in 3D)
+template <int D>
 __global__ void upsum_fwd(int B, int n, Levels lv, bf16* __restrict__ s) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= (long long)B * n * n * kC) return;
+  if (i >= B * Geo<D>::pts(n) * kC) return;
   const int c = (int)(i % kC);
-  const long long p = i / kC;
-  const int b = (int)(p / ((long long)n * n));
-  const int r = (int)(p % ((long long)n * n));
-  const int y = r / n, x = r % n;
+  int b, z, y, x;
+  Geo<D>::decode(i / kC, n, b, z, y, x);
   float acc = __bfloat162float(lv.z[0][i]);
   for (int l = 1; l < lv.L; l++) {
     const int m = lv.side[l];
-    int y0, y1, x0, x1;
-    float ly, lx;
+    int z0 = 0, z1 = 0, y0, y1, x0, x1;
+    float lz = 0.f, ly, lx;
+    if (D == 3) bilin(z, m, n, z0, z1, lz);
     bilin(y, m, n, y0, y1, ly);
     bilin(x, m, n, x0, x1, lx);
-    const bf16* z = lv.z[l] + (long long)b * m * m * kC + c;
-    const float v00 = __bfloat162float(z[((long long)y0 * m + x0) * kC]);
-    const float v01 = __bfloat162float(z[((long long)y0 * m + x1) * kC]);
-    const float v10 = __bfloat162float(z[((long long)y1 * m + x0) * kC]);
-    const float v11 = __bfloat162float(z[((long long)y1 * m + x1) * kC]);
-    acc += (1.f - ly) * ((1.f - lx) * v00 + lx * v01) + ly * ((1.f - lx) * v10 + lx * v11);
+    const bf16* zl = lv.z[l] + c;
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < (1 << D); k++) {
+      const int zz = (k >> 2) & 1 ? z1 : z0, yy = (k >> 1) & 1 ? y1 : y0, xx = k & 1 ? x1 : x0;
+      const float wz = D == 3 ? ((k >> 2) & 1 ? lz : 1.f - lz) : 1.f;
+      const float wy = (k >> 1) & 1 ? ly : 1.f - ly, wx = k & 1 ? lx : 1.f - lx;
+      const long long q = Geo<D>::nb(b, zz, yy, xx, 0, 0, 0, m);
+      v += wz * wy * wx * __bfloat162float(zl[q * kC]);
+    }
+    acc += v;
   }
   s[i] = __float2bfloat16(acc);
 }
 
 // y[p] = b + sum_tap sum_c w[c][tap] t[p + off_tap][c]
+template <int D>
 __global__ void conv_out_fwd(int B, int n, const bf16* __restrict__ t,
                              const float* __restrict__ w, const float* __restrict__ bias,
                              float* __restrict__ y) {
-  __shared__ float ws[kC * 9];
-  for (int i = threadIdx.x; i < kC * 9; i += blockDim.x) ws[i] = w[i];
+  constexpr int T = Geo<D>::T;
+  __shared__ float ws[kC * T];
+  for (int i = threadIdx.x; i < kC * T; i += blockDim.x) ws[i] = w[i];
   __syncthreads();
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= (long long)B * n * n) return;
-  const int b = (int)(p / ((long long)n * n));
-  const int r = (int)(p % ((long long)n * n));
-  const int yy0 = r / n, xx0 = r % n;
+  if (p >= B * Geo<D>::pts(n)) return;
+  int b, z, yy0, xx0;
+  Geo<D>::decode(p, n, b, z, yy0, xx0);
   float acc = bias[0];
-  for (int tp = 0; tp < 9; tp++) {
-    const int yy = yy0 + tp / 3 - 1, xx = xx0 + tp % 3 - 1;
-    if (yy < 0 || yy >= n || xx < 0 || xx >= n) continue;
+  for (int tp = 0; tp < T; tp++) {
+    int dz, dy, dx;
+    Geo<D>::tap(tp, dz, dy, dx);
+    const long long q = Geo<D>::nb(b, z, yy0, xx0, dz, dy, dx, n);
+    if (q < 0) continue;
     float v[kC];
-    load32(t + (((long long)b * n + yy) * n + xx) * kC, v);
+    load32(t + q * kC, v);
 #pragma unroll
-    for (int c = 0; c < kC; c++) acc += ws[c * 9 + tp] * v[c];
+    for (int c = 0; c < kC; c++) acc += ws[c * T + tp] * v[c];
   }
   y[p] = acc;
 }
@@ -191,82 +240,84 @@ __global__ void loss_finish(const float* __restrict__ part, int nparts, float sc
 }
 
 // g_t[p][c] = sum_tap w[c][tap] gy[p - off_tap]
+template <int D>
 __global__ void conv_out_bwd_data(int B, int n, const float* __restrict__ gy,
                                   const float* __restrict__ w, float* __restrict__ gt) {
-  __shared__ float ws[kC * 9];
-  for (int i = threadIdx.x; i < kC * 9; i += blockDim.x) ws[i] = w[i];
+  constexpr int T = Geo<D>::T;
+  __shared__ float ws[kC * T];
+  for (int i = threadIdx.x; i < kC * T; i += blockDim.x) ws[i] = w[i];
   __syncthreads();
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= (long long)B * n * n) return;
-  const int b = (int)(p / ((long long)n * n));
-  const int r = (int)(p % ((long long)n * n));
-  const int y = r / n, x = r % n;
-  float g[9];
+  if (p >= B * Geo<D>::pts(n)) return;
+  int b, z, y, x;
+  Geo<D>::decode(p, n, b, z, y, x);
+  float g[T];
 #pragma unroll
-  for (int tp = 0; tp < 9; tp++) {
-    const int yy = y - (tp / 3 - 1), xx = x - (tp % 3 - 1);
-    g[tp] = (yy >= 0 && yy < n && xx >= 0 && xx < n) ? gy[((long long)b * n + yy) * n + xx] : 0.f;
+  for (int tp = 0; tp < T; tp++) {
+    int dz, dy, dx;
+    Geo<D>::tap(tp, dz, dy, dx);
+    const long long q = Geo<D>::nb(b, z, y, x, -dz, -dy, -dx, n);
+    g[tp] = q >= 0 ? gy[q] : 0.f;
   }
   float* dst = gt + p * kC;
 #pragma unroll
   for (int c = 0; c < kC; c++) {
     float acc = 0.f;
 #pragma unroll
-    for (int tp = 0; tp < 9; tp++) acc += ws[c * 9 + tp] * g[tp];
+    for (int tp = 0; tp < T; tp++) acc += ws[c * T + tp] * g[tp];
     dst[c] = acc;
   }
 }
 
-// Per-CTA partial weight gradients of a 1-channel <-> 32-channel 3x3 conv:
-//   part[cta][c*9 + tap] = sum_p g1[p or p+off] * x32[...][c]  and bias part[cta][288 + ...].
+// Per-CTA partial weight gradients of a 1-channel <-> 32-channel 3^D conv:
+//   part[cta][c*T + tap] and the biases at part[cta][32 T + c].
 // MODE 0 (output conv):  dW[c][tap] = sum_p gy[p] t[p + off][c], db = sum_p gy[p]
 // MODE 1 (input conv):   dW[c][tap] = sum_p g32[p][c] u[p + off], db[c] = sum_p g32[p][c]
 // Lane = channel (coalesced 32-channel rows), warp = one of 8 interleaved pixel
 // streams of the CTA's range; the 8 warp sums are added in a fixed order.
-template <int MODE>
+template <int MODE, int D>
 __global__ void __launch_bounds__(256) conv1_wgrad(int B, int n, const float* __restrict__ g1,
                                                    const bf16* __restrict__ x32,
                                                    const float* __restrict__ g32,
                                                    const float* __restrict__ u,
                                                    float* __restrict__ part, int stride) {
-  __shared__ float red[8][kC * 10];
-  const long long nn = (long long)n * n;
-  const long long total = (long long)B * nn;
+  constexpr int T = Geo<D>::T;
+  __shared__ float red[8][kC * (T + 1)];
+  const long long total = B * Geo<D>::pts(n);
   const long long per = (total + gridDim.x - 1) / gridDim.x;
   const long long p0 = blockIdx.x * per;
   const long long p1 = min(total, p0 + per);
   const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float acc[9];
+  float acc[T];
 #pragma unroll
-  for (int t = 0; t < 9; t++) acc[t] = 0.f;
+  for (int t = 0; t < T; t++) acc[t] = 0.f;
   float accb = 0.f;
   for (long long p = p0 + w; p < p1; p += 8) {
-    const int b = (int)(p / nn);
-    const int r = (int)(p - (long long)b * nn);
-    const int y = r / n, x = r - (r / n) * n;
+    int b, z, y, x;
+    Geo<D>::decode(p, n, b, z, y, x);
     const float gp = MODE == 0 ? g1[p] : g32[p * kC + c];
     accb += gp;
 #pragma unroll
-    for (int t = 0; t < 9; t++) {
-      const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-      if (yy < 0 || yy >= n || xx < 0 || xx >= n) continue;
-      const long long q = ((long long)b * n + yy) * n + xx;
+    for (int t = 0; t < T; t++) {
+      int dz, dy, dx;
+      Geo<D>::tap(t, dz, dy, dx);
+      const long long q = Geo<D>::nb(b, z, y, x, dz, dy, dx, n);
+      if (q < 0) continue;
       const float v = MODE == 0 ? __bfloat162float(x32[q * kC + c]) : u[q];
       acc[t] += gp * v;
     }
   }
 #pragma unroll
-  for (int t = 0; t < 9; t++) red[w][c * 10 + t] = acc[t];
-  red[w][c * 10 + 9] = accb;
+  for (int t = 0; t < T; t++) red[w][c * (T + 1) + t] = acc[t];
+  red[w][c * (T + 1) + T] = accb;
   __syncthreads();
-  for (int t = threadIdx.x; t < kC * 9 + kC; t += blockDim.x) {
-    // t < 288: weight c*9+tap; t >= 288: bias of channel t-288 (MODE 0: one bias)
-    const int cc = t < kC * 9 ? t / 9 : t - kC * 9;
-    const int k = t < kC * 9 ? t % 9 : 9;
+  for (int t = threadIdx.x; t < kC * T + kC; t += blockDim.x) {
+    // t < 32 T: weight c*T + tap; t >= 32 T: bias of channel t - 32 T (MODE 0: one bias)
+    const int cc = t < kC * T ? t / T : t - kC * T;
+    const int k = t < kC * T ? t % T : T;
     float v = 0.f;
-    if (!(MODE == 0 && k == 9 && cc != 0))
-      for (int ww = 0; ww < 8; ww++) v += red[ww][(MODE == 0 && k == 9 ? 0 : cc) * 10 + k];
-    if (MODE == 0 && k == 9) v = cc == 0 ? v : 0.f;
+    if (!(MODE == 0 && k == T && cc != 0))
+      for (int ww = 0; ww < 8; ww++) v += red[ww][cc * (T + 1) + k];
     part[(long long)blockIdx.x * stride + t] = v;
   }
 }
@@ -288,13 +339,13 @@ __global__ void mask_f32(long long count, const float* __restrict__ g,
 
 // grad[dst_w[i]] = sum over CTAs of part[cta][i] for the weight layout used by
 // the partial kernels; the mapping to the parameter layout [o][k][tap] is done
-// here so the parameters keep the documented order.
-//   kind 0 (32->32): part index (tap*32 + k)*32 + o  -> param (o*32 + k)*9 + tap; bias 9216 + o
-//   kind 1 (1-ch)  : part index c*9 + tap (+ 288 + c bias) -> same order
+// here so the parameters keep the documented order (T taps).
+//   kind 0 (32->32): part index (tap*32 + k)*32 + o  -> param (o*32 + k)*T + tap; bias 1024 T + o
+//   kind 1/2 (1-ch): part index c*T + tap (+ 32 T + c bias) -> same order
 __global__ void reduce_wgrad(const float* __restrict__ part, int nparts, int stride, int kind,
-                             float* __restrict__ gw, float* __restrict__ gb) {
+                             int T, float* __restrict__ gw, float* __restrict__ gb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nw = kind == 0 ? 9 * kC * kC : 9 * kC;
+  const int nw = kind == 0 ? T * kC * kC : T * kC;
   const int nb = kind == 0 ? kC : (kind == 1 ? kC : 1);
   if (i >= nw + nb) return;
   double s = 0.0;
@@ -302,7 +353,7 @@ __global__ void reduce_wgrad(const float* __restrict__ part, int nparts, int str
   if (i < nw) {
     if (kind == 0) {
       const int tp = i / (kC * kC), k = (i / kC) % kC, o = i % kC;
-      gw[(o * kC + k) * 9 + tp] = (float)s;
+      gw[(o * kC + k) * T + tp] = (float)s;
     } else {
       gw[i] = (float)s;
     }
@@ -311,10 +362,11 @@ __global__ void reduce_wgrad(const float* __restrict__ part, int nparts, int str
   }
 }
 
-// Transpose of the bilinear upsampling from m to n, separably:
-//   tx[b][y][j][c] = sum_x U[x][j] gs[b][y][x][c]      (upsample_bwd_x, n x m)
-//   gz[b][i][j][c] = sum_y U[y][i] tx[b][y][j][c]      (upsample_bwd_y, m x m)
-// U[x][j] = the weight of coarse j in fine x's half-pixel interpolation.
+// Transpose of the linear upsampling from m to n along one axis of a tensor
+// viewed as (outer, n, inner) -> (outer, m, inner):
+//   out[o][j][c] = sum_x U[x][j] in[o][x][c],  U[x][j] = the weight of coarse j
+// in fine x's half-pixel interpolation.  The D-dimensional transpose is D such
+// passes, one per axis.
 __device__ __forceinline__ float up_weight(int f_idx, int m, int n, int j) {
   int i0, i1;
   float l;
@@ -322,56 +374,37 @@ __device__ __forceinline__ float up_weight(int f_idx, int m, int n, int j) {
   return (i0 == j ? 1.f - l : 0.f) + (i1 == j ? l : 0.f);
 }
 
-__global__ void upsample_bwd_x(int B, int n, int m, const float* __restrict__ gs,
-                               float* __restrict__ tx) {
+__global__ void upsample_bwd_axis(long long outer, int n, int m, long long inner,
+                                  const float* __restrict__ in, float* __restrict__ out) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * n * m * kC) return;
-  const int c = (int)(idx % kC);
-  const long long p = idx / kC;  // (b, y, j)
+  if (idx >= outer * m * inner) return;
+  const long long c = idx % inner;
+  const long long p = idx / inner;
   const int j = (int)(p % m);
-  const long long by = p / m;    // b * n + y
+  const long long o = p / m;
   const float f = (float)n / (float)m;
   const int xlo = max(0, (int)floorf((j - 1.5f) * f)), xhi = min(n - 1, (int)ceilf((j + 2.5f) * f));
   float acc = 0.f;
   for (int x = xlo; x <= xhi; x++) {
     const float wx = up_weight(x, m, n, j);
-    if (wx != 0.f) acc += wx * gs[(by * n + x) * kC + c];
+    if (wx != 0.f) acc += wx * in[(o * n + x) * inner + c];
   }
-  tx[idx] = acc;
+  out[idx] = acc;
 }
 
-__global__ void upsample_bwd_y(int B, int n, int m, const float* __restrict__ tx,
-                               float* __restrict__ gz) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * m * m * kC) return;
-  const int c = (int)(idx % kC);
-  const long long p = idx / kC;  // (b, i, j)
-  const int j = (int)(p % m);
-  const int i = (int)((p / m) % m);
-  const int b = (int)(p / ((long long)m * m));
-  const float f = (float)n / (float)m;
-  const int ylo = max(0, (int)floorf((i - 1.5f) * f)), yhi = min(n - 1, (int)ceilf((i + 2.5f) * f));
-  float acc = 0.f;
-  for (int y = ylo; y <= yhi; y++) {
-    const float wy = up_weight(y, m, n, i);
-    if (wy != 0.f) acc += wy * tx[(((long long)b * n + y) * m + j) * kC + c];
-  }
-  gz[idx] = acc;
-}
-
-// fine[b][y][x][c] += 0.25 coarse[b][y/2][x/2][c] (fine side s, coarse side s/2)
+// fine[p][c] += coarse[p / 2][c] / 2^D (fine side s, coarse side s/2)
+template <int D>
 __global__ void pool2_bwd_add(int B, int s, const float* __restrict__ coarse,
                               float* __restrict__ fine) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * s * s * kC) return;
+  if (idx >= B * Geo<D>::pts(s) * kC) return;
   const int c = (int)(idx % kC);
-  const long long p = idx / kC;
-  const int b = (int)(p / ((long long)s * s));
-  const int r = (int)(p % ((long long)s * s));
-  const int y = r / s, x = r % s;
+  int b, z, y, x;
+  Geo<D>::decode(idx / kC, s, b, z, y, x);
   const int so = s / 2;
-  if (y / 2 >= so || x / 2 >= so) return;
-  fine[idx] += 0.25f * coarse[(((long long)b * so + y / 2) * so + x / 2) * kC + c];
+  if (y / 2 >= so || x / 2 >= so || (D == 3 && z / 2 >= so)) return;
+  const long long q = Geo<D>::nb(b, z / 2, y / 2, x / 2, 0, 0, 0, so);
+  fine[idx] += (1.f / (1 << D)) * coarse[q * kC + c];
 }
 
 // Adam (Kingma & Ba): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
@@ -391,15 +424,15 @@ __global__ void adam_kernel(long long count, float* __restrict__ theta,
 }
 
 // wq[conv][tap][k][o] = W[o][k][tap], wqT[conv][tap][o][k] = W[o][k][tap] (BF16)
-__global__ void sync_weights_kernel(int nconv, const float* __restrict__ master,
+__global__ void sync_weights_kernel(int nconv, int T, const float* __restrict__ master,
                                     const long long* __restrict__ offs, bf16* __restrict__ wq,
                                     bf16* __restrict__ wqT) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long per = 9LL * kC * kC;
+  const long long per = (long long)T * kC * kC;
   if (i >= nconv * per) return;
   const int cv = (int)(i / per);
   const int r = (int)(i % per);
-  const int o = r / (kC * 9), k = (r / 9) % kC, tp = r % 9;
+  const int o = r / (kC * T), k = (r / T) % kC, tp = r % T;
   const bf16 v = __float2bfloat16(master[offs[cv] + r]);
   wq[(long long)cv * per + (tp * kC + k) * kC + o] = v;
   wqT[(long long)cv * per + (tp * kC + o) * kC + k] = v;
@@ -423,8 +456,12 @@ unsigned long long sm64(unsigned long long& st) {
     if (e_ != cudaSuccess) return e_;     \
   } while (0)
 
-cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed) {
+cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int dim) {
+  if (dim != 2 && dim != 3) return cudaErrorInvalidValue;
   net.n = n;
+  net.dim = dim;
+  net.taps = dim == 3 ? 27 : 9;
+  const int T = net.taps;
   net.bmax = bmax;
   net.L = 0;
   int s = n;
@@ -434,16 +471,17 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed) {
     net.side[net.L++] = s;
   }
   const int L = net.L;
+  const long long per = (long long)T * kC * kC;
   long long off = 0;
-  net.off_w[0] = off; off += kC * 9;
+  net.off_w[0] = off; off += kC * T;
   net.off_b[0] = off; off += kC;
   for (int l = 0; l < L; l++) {
-    net.off_w[1 + l] = off; off += 9LL * kC * kC;
+    net.off_w[1 + l] = off; off += per;
     net.off_b[1 + l] = off; off += kC;
   }
-  net.off_w[L + 1] = off; off += 9LL * kC * kC;
+  net.off_w[L + 1] = off; off += per;
   net.off_b[L + 1] = off; off += kC;
-  net.off_w[L + 2] = off; off += kC * 9;
+  net.off_w[L + 2] = off; off += kC * T;
   net.off_b[L + 2] = off; off += 1;
   net.nparams = off;
 
@@ -458,10 +496,10 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed) {
       p[(size_t)(o + i)] = (float)((2.0 * u - 1.0) * a);
     }
   };
-  fill(net.off_w[0], kC * 9, 9, 6.f);
-  for (int l = 0; l < L; l++) fill(net.off_w[1 + l], 9LL * kC * kC, 9 * kC, 6.f);
-  fill(net.off_w[L + 1], 9LL * kC * kC, 9 * kC, 6.f);
-  fill(net.off_w[L + 2], kC * 9, 9 * kC, 3.f);
+  fill(net.off_w[0], kC * T, T, 6.f);
+  for (int l = 0; l < L; l++) fill(net.off_w[1 + l], per, T * kC, 6.f);
+  fill(net.off_w[L + 1], per, T * kC, 6.f);
+  fill(net.off_w[L + 2], kC * T, T * kC, 3.f);
 
   const long long np = net.nparams;
   NN_CK(cudaMalloc(&net.master, sizeof(float) * np));
@@ -472,7 +510,6 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed) {
   NN_CK(cudaMemset(net.grad, 0, sizeof(float) * np));
   NN_CK(cudaMemset(net.adam_m, 0, sizeof(float) * np));
   NN_CK(cudaMemset(net.adam_v, 0, sizeof(float) * np));
-  const long long per = 9LL * kC * kC;
   NN_CK(cudaMalloc(&net.wq, sizeof(bf16) * per * (L + 1)));
   NN_CK(cudaMalloc(&net.wqT, sizeof(bf16) * per * (L + 1)));
   long long offs[kMaxLevels + 1];
@@ -480,11 +517,14 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed) {
   NN_CK(cudaMalloc(&net.offs_dev, sizeof(offs)));
   NN_CK(cudaMemcpy(net.offs_dev, offs, sizeof(long long) * (L + 1), cudaMemcpyHostToDevice));
 
-  const long long full = (long long)bmax * n * n * kC;
+  auto pts = [dim](int side) {
+    return dim == 3 ? (long long)side * side * side : (long long)side * side;
+  };
+  const long long full = (long long)bmax * pts(n) * kC;
   NN_CK(cudaMalloc(&net.a0, sizeof(bf16) * full));
   net.pyr = 0;
   for (int l = 0; l < L; l++) {
-    const long long sz = (long long)bmax * net.side[l] * net.side[l] * kC;
+    const long long sz = (long long)bmax * pts(net.side[l]) * kC;
     if (l > 0) NN_CK(cudaMalloc(&net.pool[l], sizeof(bf16) * sz));
     NN_CK(cudaMalloc(&net.z[l], sizeof(bf16) * sz));
     net.lvl_off[l] = net.pyr;
@@ -503,7 +543,7 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed) {
   NN_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   net.wparts = 2 * nsm;
   NN_CK(cudaMalloc(&net.wgrad_part, sizeof(float) * (long long)net.wparts * (per + kC)));
-  const long long pix = (long long)bmax * n * n;
+  const long long pix = (long long)bmax * pts(n);
   NN_CK(cudaMalloc(&net.gy, sizeof(float) * pix));
   NN_CK(cudaMalloc(&net.loss_part, sizeof(float) * 1024));
   NN_CK(cudaMalloc(&net.bu, sizeof(float) * pix));
@@ -545,34 +585,34 @@ void net_destroy(Net& net) {
 
 cudaError_t net_sync_weights(Net& net, cudaStream_t s) {
   const int nconv = net.L + 1;
-  const long long tot = (long long)nconv * 9 * kC * kC;
-  sync_weights_kernel<<<nblk(tot, 256), 256, 0, s>>>(nconv, net.master, net.offs_dev, net.wq,
-                                                    net.wqT);
+  const long long tot = (long long)nconv * net.taps * kC * kC;
+  sync_weights_kernel<<<nblk(tot, 256), 256, 0, s>>>(nconv, net.taps, net.master, net.offs_dev,
+                                                    net.wq, net.wqT);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t s) {
+namespace {
+
+template <int D>
+cudaError_t forward_t(Net& net, int B, const float* u, float* y, cudaStream_t s) {
   const int n = net.n, L = net.L;
-  const long long pix = (long long)B * n * n;
-  const long long per = 9LL * kC * kC;
-  conv_in_fwd<<<nblk(pix, 256), 256, 0, s>>>(B, n, u, net.master + net.off_w[0],
-                                              net.master + net.off_b[0], net.a0);
+  const long long pix = B * Geo<D>::pts(n);
+  const long long per = (long long)Geo<D>::T * kC * kC;
+  conv_in_fwd<D><<<nblk(pix, 256), 256, 0, s>>>(B, n, u, net.master + net.off_w[0],
+                                                 net.master + net.off_b[0], net.a0);
   note_launches(1);
   for (int l = 1; l < L; l++) {
     const int sp = net.side[l - 1];
     const bf16* src = l == 1 ? net.a0 : net.pool[l - 1];
-    const long long cnt = (long long)B * net.side[l] * net.side[l] * kC;
-    pool2_fwd<<<nblk(cnt, 256), 256, 0, s>>>(B, sp, src, net.pool[l]);
+    const long long cnt = B * Geo<D>::pts(net.side[l]) * kC;
+    pool2_fwd<D><<<nblk(cnt, 256), 256, 0, s>>>(B, sp, src, net.pool[l]);
     note_launches(1);
   }
   for (int l = 0; l < L; l++) {
-    const int sd = net.side[l];
-    const long long np = (long long)B * sd * sd;
-    (void)np;
-    NN_CK(launch_conv32_mma(0, B, sd, l == 0 ? net.a0 : net.pool[l], net.wqT + per * l,
-                            net.master + net.off_b[1 + l], 1, 1, net.z[l], nullptr, nullptr,
-                            nullptr, nullptr, s));
+    NN_CK(launch_conv32_mma(D, 0, B, net.side[l], l == 0 ? net.a0 : net.pool[l],
+                            net.wqT + per * l, net.master + net.off_b[1 + l], 1, 1, net.z[l],
+                            nullptr, nullptr, nullptr, nullptr, s));
   }
   Levels lv;
   lv.L = L;
@@ -580,22 +620,24 @@ cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t 
     lv.z[l] = net.z[l];
     lv.side[l] = net.side[l];
   }
-  upsum_fwd<<<nblk(pix * kC, 256), 256, 0, s>>>(B, n, lv, net.s);
+  upsum_fwd<D><<<nblk(pix * kC, 256), 256, 0, s>>>(B, n, lv, net.s);
   note_launches(1);
-  NN_CK(launch_conv32_mma(1, B, n, net.s, net.wqT + per * L, net.master + net.off_b[L + 1], 2, 1,
-                          net.e, net.t, net.s, nullptr, nullptr, s));
-  conv_out_fwd<<<nblk(pix, 256), 256, 0, s>>>(B, n, net.t, net.master + net.off_w[L + 2],
-                                               net.master + net.off_b[L + 2], y);
+  NN_CK(launch_conv32_mma(D, 1, B, n, net.s, net.wqT + per * L, net.master + net.off_b[L + 1], 2,
+                          1, net.e, net.t, net.s, nullptr, nullptr, s));
+  conv_out_fwd<D><<<nblk(pix, 256), 256, 0, s>>>(B, n, net.t, net.master + net.off_w[L + 2],
+                                                  net.master + net.off_b[L + 2], y);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const float* target,
-                         float tscale, float* loss_dev, cudaStream_t s) {
+template <int D>
+cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const float* target,
+                       float tscale, float* loss_dev, cudaStream_t s) {
+  constexpr int T = Geo<D>::T;
   const int n = net.n, L = net.L;
-  const long long pix = (long long)B * n * n;
+  const long long pix = B * Geo<D>::pts(n);
   const long long full = pix * kC;
-  const long long per = 9LL * kC * kC;
+  const long long per = (long long)T * kC * kC;
   const int P = net.wparts;
   const int stride = (int)(per + kC);
   // loss and dL/dy
@@ -606,67 +648,95 @@ cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const 
   loss_finish<<<1, 32, 0, s>>>(net.loss_part, lparts, 1.f / (float)pix, loss_dev);
   note_launches(1);
   // output conv
-  conv1_wgrad<0><<<P, 256, 0, s>>>(B, n, net.gy, net.t, nullptr, nullptr, net.wgrad_part, stride);
+  conv1_wgrad<0, D><<<P, 256, 0, s>>>(B, n, net.gy, net.t, nullptr, nullptr, net.wgrad_part,
+                                      stride);
   note_launches(1);
-  reduce_wgrad<<<nblk(9 * kC + 1, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 2,
+  reduce_wgrad<<<nblk(T * kC + 1, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 2, T,
                                                      net.grad + net.off_w[L + 2],
                                                      net.grad + net.off_b[L + 2]);
   note_launches(1);
-  conv_out_bwd_data<<<nblk(pix, 256), 256, 0, s>>>(B, n, net.gy, net.master + net.off_w[L + 2],
-                                                   net.g_t);
+  conv_out_bwd_data<D><<<nblk(pix, 256), 256, 0, s>>>(B, n, net.gy,
+                                                      net.master + net.off_w[L + 2], net.g_t);
   note_launches(1);
   // dilated residual block: t = s + e, e = relu(conv_d2(s))
   mask_to_bf16<<<nblk(full, 256), 256, 0, s>>>(full, net.g_t, net.e, net.g_bf);
   note_launches(1);
-  NN_CK(launch_wgrad_mma(B, n, net.s, net.g_bf, 2, net.wgrad_part, stride, P, s));
-  reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0,
+  NN_CK(launch_wgrad_mma(D, B, n, net.s, net.g_bf, 2, net.wgrad_part, stride, P, s));
+  reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
                                                    net.grad + net.off_w[L + 1],
                                                    net.grad + net.off_b[L + 1]);
   note_launches(1);
-  NN_CK(launch_conv32_mma(2, B, n, net.g_bf, net.wq + per * L, nullptr, 2, -1, nullptr, nullptr,
-                          nullptr, net.g_s, net.g_t, s));
+  NN_CK(launch_conv32_mma(D, 2, B, n, net.g_bf, net.wq + per * L, nullptr, 2, -1, nullptr,
+                          nullptr, nullptr, net.g_s, net.g_t, s));
   // pyramid levels
   for (int l = 0; l < L; l++) {
     const int sd = net.side[l];
-    const long long lp = (long long)B * sd * sd;
+    const long long lp = B * Geo<D>::pts(sd);
     const float* gz = net.g_s;
     if (l > 0) {
-      // g_t is free here (the residual block's gradient is already in g_s)
-      upsample_bwd_x<<<nblk((long long)B * n * sd * kC, 256), 256, 0, s>>>(B, n, sd, net.g_s,
-                                                                            net.g_t);
-      upsample_bwd_y<<<nblk(lp * kC, 256), 256, 0, s>>>(B, n, sd, net.g_t, net.g_lvl);
-      note_launches(2);
-      gz = net.g_lvl;
+      // transposed upsampling, one axis at a time (x, y, then z); g_t and
+      // g_lvl are free here (the residual block's gradient is already in g_s)
+      const long long nn = n, m = sd;
+      if (D == 2) {
+        upsample_bwd_axis<<<nblk(B * nn * m * kC, 256), 256, 0, s>>>(B * nn, n, sd, kC, net.g_s,
+                                                                     net.g_t);
+        upsample_bwd_axis<<<nblk(B * m * m * kC, 256), 256, 0, s>>>(B, n, sd, m * kC, net.g_t,
+                                                                    net.g_lvl);
+        note_launches(2);
+        gz = net.g_lvl;
+      } else {
+        upsample_bwd_axis<<<nblk(B * nn * nn * m * kC, 256), 256, 0, s>>>(B * nn * nn, n, sd, kC,
+                                                                          net.g_s, net.g_t);
+        upsample_bwd_axis<<<nblk(B * nn * m * m * kC, 256), 256, 0, s>>>(B * nn, n, sd, m * kC,
+                                                                         net.g_t, net.g_lvl);
+        upsample_bwd_axis<<<nblk(B * m * m * m * kC, 256), 256, 0, s>>>(B, n, sd, m * m * kC,
+                                                                        net.g_lvl, net.g_t);
+        note_launches(3);
+        gz = net.g_t;
+      }
     }
     mask_to_bf16<<<nblk(lp * kC, 256), 256, 0, s>>>(lp * kC, gz, net.z[l], net.g_bf);
     note_launches(1);
     const bf16* in = l == 0 ? net.a0 : net.pool[l];
-    NN_CK(launch_wgrad_mma(B, sd, in, net.g_bf, 1, net.wgrad_part, stride, P, s));
-    reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0,
+    NN_CK(launch_wgrad_mma(D, B, sd, in, net.g_bf, 1, net.wgrad_part, stride, P, s));
+    reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
                                                      net.grad + net.off_w[1 + l],
                                                      net.grad + net.off_b[1 + l]);
     note_launches(1);
-    NN_CK(launch_conv32_mma(2, B, sd, net.g_bf, net.wq + per * l, nullptr, 1, -1, nullptr,
+    NN_CK(launch_conv32_mma(D, 2, B, sd, net.g_bf, net.wq + per * l, nullptr, 1, -1, nullptr,
                             nullptr, nullptr, net.g_pool + net.lvl_off[l], nullptr, s));
   }
-  // pooling chain: the gradient of p_{l-1} collects 0.25 of p_l's
+  // pooling chain: the gradient of p_{l-1} collects 1/2^D of p_l's
   for (int l = L - 1; l >= 1; l--) {
     const int sf = net.side[l - 1];
-    const long long cnt = (long long)B * sf * sf * kC;
-    pool2_bwd_add<<<nblk(cnt, 256), 256, 0, s>>>(B, sf, net.g_pool + net.lvl_off[l],
-                                                 net.g_pool + net.lvl_off[l - 1]);
+    const long long cnt = B * Geo<D>::pts(sf) * kC;
+    pool2_bwd_add<D><<<nblk(cnt, 256), 256, 0, s>>>(B, sf, net.g_pool + net.lvl_off[l],
+                                                    net.g_pool + net.lvl_off[l - 1]);
     note_launches(1);
   }
   // input conv
   mask_f32<<<nblk(full, 256), 256, 0, s>>>(full, net.g_pool + net.lvl_off[0], net.a0, net.g_lvl);
   note_launches(1);
-  conv1_wgrad<1><<<P, 256, 0, s>>>(B, n, nullptr, nullptr, net.g_lvl, u, net.wgrad_part, stride);
+  conv1_wgrad<1, D><<<P, 256, 0, s>>>(B, n, nullptr, nullptr, net.g_lvl, u, net.wgrad_part,
+                                      stride);
   note_launches(1);
-  reduce_wgrad<<<nblk(9 * kC + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 1,
+  reduce_wgrad<<<nblk(T * kC + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 1, T,
                                                       net.grad + net.off_w[0],
                                                       net.grad + net.off_b[0]);
   note_launches(1);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t s) {
+  return net.dim == 3 ? forward_t<3>(net, B, u, y, s) : forward_t<2>(net, B, u, y, s);
+}
+
+cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const float* target,
+                         float tscale, float* loss_dev, cudaStream_t s) {
+  return net.dim == 3 ? backward_t<3>(net, B, u, y, target, tscale, loss_dev, s)
+                      : backward_t<2>(net, B, u, y, target, tscale, loss_dev, s);
 }
 
 cudaError_t net_adam(Net& net, float lr, cudaStream_t s) {
@@ -683,7 +753,7 @@ cudaError_t net_adam(Net& net, float lr, cudaStream_t s) {
 cudaError_t net_train_batch(Net& net, int B, const float* ring_u, const float* ring_t,
                             long long stride, const int* pick, float tscale, float lr,
                             float* loss_dev, cudaStream_t s) {
-  const long long N = (long long)net.n * net.n;
+  const long long N = net.dim == 3 ? (long long)net.n * net.n * net.n : (long long)net.n * net.n;
   for (int i = 0; i < B; i++) {
     NN_CK(cudaMemcpyAsync(net.bu + i * N, ring_u + (long long)pick[i] * stride,
                           sizeof(float) * N, cudaMemcpyDeviceToDevice, s));

@@ -2,7 +2,9 @@
 // model -- multi-resolution average-pool pyramid, one convolution per level,
 // bilinear upsampling and summation -- followed by a dilated residual block
 // and an output convolution, trained online with Adam on the MSE loss
-// (Sec. 2.3).
+// (Sec. 2.3).  The same network in 3D (dim = 3, for the variable-coefficient
+// workload) uses 3x3x3 kernels, 2x2x2 pooling down to 8^3 and trilinear
+// upsampling; weights are then [out][in][kz][ky][kx].
 //
 //   a0  = relu(conv3x3(u, W_in) + b_in)                 1 -> 32
 //   p_0 = a0, p_l = avgpool2(p_{l-1}) while the side stays >= 8
@@ -26,6 +28,8 @@ constexpr int kMaxLevels = 12;
 
 struct Net {
   int n = 0;                // grid side
+  int dim = 2;              // 2: 3x3 kernels, 2x2 pooling; 3: 3x3x3, 2x2x2
+  int taps = 9;             // 3^dim
   int L = 0;                // pyramid levels
   int side[kMaxLevels];     // level sides
   int bmax = 0;             // largest batch
@@ -41,7 +45,7 @@ struct Net {
                                 // (B operand of the data gradient)
   __nv_bfloat16* wqT = nullptr; // [conv][tap][co][ci] (B operand of the forward pass)
   long long* offs_dev = nullptr;  // device copy of the 32->32 weight offsets
-  // activations, NHWC with 32 channels, BF16 (masks are recovered from
+  // activations, channels last (NHWC / NDHWC) with 32 channels, BF16 (masks are recovered from
   // post-ReLU values: relu(x) > 0 <=> x > 0)
   __nv_bfloat16* a0 = nullptr;               // bmax x n^2 x 32
   __nv_bfloat16* pool[kMaxLevels] = {};      // levels 1..L-1
@@ -66,17 +70,19 @@ struct Net {
   int wparts = 0;                            // CTAs of the weight-gradient kernels
 };
 
-// Tensor-core 32 -> 32 convolution (mode 0: relu(conv + b) -> zo; 1: e = relu(conv + b)
-// -> zo and resid + e -> to; 2: conv (+ addend) -> fo in FP32).  wop is [tap][n][k].
-cudaError_t launch_conv32_mma(int mode, int B, int H, const __nv_bfloat16* in,
+// Tensor-core 32 -> 32 convolution (dim 2: 3x3, dim 3: 3x3x3; mode 0:
+// relu(conv + b) -> zo; 1: e = relu(conv + b) -> zo and resid + e -> to;
+// 2: conv (+ addend) -> fo in FP32).  wop is [tap][n][k].
+cudaError_t launch_conv32_mma(int dim, int mode, int B, int H, const __nv_bfloat16* in,
                               const __nv_bfloat16* wop, const float* bias, int dil, int sign,
                               __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                               float* fo, const float* addend, cudaStream_t s);
 // Tensor-core weight gradient partials of a 32 -> 32 convolution (nparts CTAs).
-cudaError_t launch_wgrad_mma(int B, int H, const __nv_bfloat16* in, const __nv_bfloat16* g,
-                             int dil, float* part, int stride, int nparts, cudaStream_t s);
+cudaError_t launch_wgrad_mma(int dim, int B, int H, const __nv_bfloat16* in,
+                             const __nv_bfloat16* g, int dil, float* part, int stride, int nparts,
+                             cudaStream_t s);
 
-cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed);
+cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int dim = 2);
 void net_destroy(Net& net);
 // Re-derive the BF16 operand copies from the FP32 master parameters.
 cudaError_t net_sync_weights(Net& net, cudaStream_t s);

@@ -1,14 +1,16 @@
 // Tensor-core (mma.sync m16n8k16, BF16 operands, FP32 accumulation) kernels
-// for the 32 -> 32 channel 3x3 convolutions of the initial-guess network, as
-// implicit GEMMs over NHWC activations:
+// for the 32 -> 32 channel 3x3 (2D) and 3x3x3 (3D) convolutions of the
+// initial-guess network, as implicit GEMMs over channels-last activations:
 //   conv32_mma : out[p][n] = sum_{tap,k} in[p + sign*dil*off(tap)][k] * Wop[tap][n][k]
 //                (forward: Wop = transposed-tap copy; data gradient: sign = -1
-//                with the other copy), M = pixels, N = 32, K = 9 * 32
+//                with the other copy), M = pixels, N = 32, K = T * 32 (T = 9 or 27)
 //   wgrad_mma  : part[cta][(tap*32 + k)*32 + o] = sum_p in[p + dil*off(tap)][k] g[p][o]
-//                M = 32 output channels, N = 288 (tap, input channel), K = pixels
-// A CTA owns 64 consecutive pixels of one image row at a time; the three input
-// rows it needs (with a dil-wide halo, zero outside the image) are staged in
-// shared memory with an 80-byte pixel stride, which keeps ldmatrix conflict-free.
+//                M = 32 output channels, N = 288 (the 9 taps of one kz plane x input
+//                channel; 3D runs it once per plane), K = pixels
+// A CTA owns 64 consecutive pixels of one grid row at a time; the 3 (2D) or 9
+// (3D) input rows it needs (with a dil-wide halo, zero outside the grid) are
+// staged in shared memory with an 80-byte pixel stride, which keeps ldmatrix
+// conflict-free.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -47,27 +49,51 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Stage rows y + s*dil*(ty-1) (ty = 0..2), columns x0 - dil .. x0 + 63 + dil of
-// image b into tile[ty][c][kPix] (zero outside the image).
-__device__ __forceinline__ void stage_rows(bf16* tile, const bf16* __restrict__ in, int b, int H,
-                                           int y, int x0, int dil, int s) {
+// Stage the input rows a tile of row (b, z, y), columns x0 .. x0+63, reads:
+// rows y + s*dil*(ty-1) (and planes z + s*dil*(tz-1) in 3D), columns
+// x0 - dil .. x0 + 63 + dil, into tile[r][c][kPix], r = tz*3 + ty (zero
+// outside the grid).  zoff selects one plane offset only (wgrad, 3D).
+template <int D>
+__device__ __forceinline__ void stage_rows(bf16* tile, const bf16* __restrict__ in, int b, int n,
+                                           int z, int y, int x0, int dil, int s, int nplanes,
+                                           int zoff) {
   const int cols = kTileP + 2 * dil;
-  for (int idx = threadIdx.x; idx < 3 * cols * 4; idx += blockDim.x) {
+  const int rows = 3 * nplanes;
+  for (int idx = threadIdx.x; idx < rows * cols * 4; idx += blockDim.x) {
     const int q = idx & 3;
     const int c = (idx >> 2) % cols;
-    const int ty = (idx >> 2) / cols;
+    const int r = (idx >> 2) / cols;
+    const int ty = r % 3, tz = r / 3;
     const int yy = y + s * dil * (ty - 1);
+    const int zz = D == 3 ? z + s * dil * ((nplanes == 3 ? tz : zoff) - 1) : 0;
     const int xx = x0 - dil + c;
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (yy >= 0 && yy < H && xx >= 0 && xx < H)
-      v = *reinterpret_cast<const uint4*>(in + (((long long)b * H + yy) * H + xx) * kC + q * 8);
-    *reinterpret_cast<uint4*>(tile + (ty * kTileW + c) * kPix + q * 8) = v;
+    if (yy >= 0 && yy < n && xx >= 0 && xx < n && (D == 2 || (zz >= 0 && zz < n))) {
+      const long long pix = D == 3 ? (((long long)b * n + zz) * n + yy) * n + xx
+                                   : ((long long)b * n + yy) * n + xx;
+      v = *reinterpret_cast<const uint4*>(in + pix * kC + q * 8);
+    }
+    *reinterpret_cast<uint4*>(tile + (r * kTileW + c) * kPix + q * 8) = v;
   }
+}
+
+// row index (b, z, y) of a grid with rows = B n^(D-1)
+template <int D>
+__device__ __forceinline__ void decode_row(long long row, int n, int& b, int& z, int& y) {
+  y = (int)(row % n);
+  const long long r2 = row / n;
+  z = D == 3 ? (int)(r2 % n) : 0;
+  b = D == 3 ? (int)(r2 / n) : (int)r2;
 }
 
 enum { kRelu = 0, kResid = 1, kF32 = 2 };
 
-template <int MODE>
+template <int D>
+constexpr int conv_smem_bytes() {
+  return (int)sizeof(bf16) * ((D == 3 ? 27 : 9) * kC * kPix + (D == 3 ? 9 : 3) * kTileW * kPix);
+}
+
+template <int MODE, int D>
 __global__ void __launch_bounds__(128) conv32_mma(int B, int H, const bf16* __restrict__ in,
                                                   const bf16* __restrict__ wop,
                                                   const float* __restrict__ bias, int dil,
@@ -76,10 +102,12 @@ __global__ void __launch_bounds__(128) conv32_mma(int B, int H, const bf16* __re
                                                   const bf16* __restrict__ resid,
                                                   float* __restrict__ fo,
                                                   const float* __restrict__ addend) {
-  __shared__ __align__(16) bf16 ws[9 * kC * kPix];       // [tap][n][k]
-  __shared__ __align__(16) bf16 tile[3 * kTileW * kPix];  // [ty][c][k]
+  constexpr int T = D == 3 ? 27 : 9;
+  extern __shared__ __align__(16) unsigned char nn_smem[];
+  bf16* ws = reinterpret_cast<bf16*>(nn_smem);   // [tap][n][k]
+  bf16* tile = ws + T * kC * kPix;               // [r][c][k]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int idx = threadIdx.x; idx < 9 * kC * 4; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < T * kC * 4; idx += blockDim.x) {
     const int q = idx & 3, row = idx >> 2;  // row = tap*32 + n
     *reinterpret_cast<uint4*>(ws + row * kPix + q * 8) =
         *reinterpret_cast<const uint4*>(wop + row * kC + q * 8);
@@ -92,14 +120,16 @@ __global__ void __launch_bounds__(128) conv32_mma(int B, int H, const bf16* __re
     bv[nt][1] = (MODE != kF32 && bias) ? bias[o + 1] : 0.f;
   }
   const int tpr = (H + kTileP - 1) / kTileP;  // tiles per row
-  const long long ntiles = (long long)B * H * tpr;
+  long long nrows = (long long)B * H;
+  if (D == 3) nrows *= H;
+  const long long ntiles = nrows * tpr;
   for (long long tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
     const int tx = (int)(tIdx % tpr);
-    const int y = (int)((tIdx / tpr) % H);
-    const int b = (int)(tIdx / ((long long)tpr * H));
+    int b, z, y;
+    decode_row<D>(tIdx / tpr, H, b, z, y);
     const int x0 = tx * kTileP;
     __syncthreads();  // previous tile's readers are done (and ws is staged)
-    stage_rows(tile, in, b, H, y, x0, dil, sign);
+    stage_rows<D>(tile, in, b, H, z, y, x0, dil, sign, D == 3 ? 3 : 1, 1);
     __syncthreads();
     float acc[4][4];
 #pragma unroll
@@ -109,11 +139,11 @@ __global__ void __launch_bounds__(128) conv32_mma(int B, int H, const bf16* __re
     // A row address of this lane (ldmatrix x4: matrix q = lane/8, row lane%8)
     const int arow = warp * 16 + ((lane >> 3) & 1) * 8 + (lane & 7);
     const int acol = (lane >> 4) * 8;
-#pragma unroll
-    for (int t = 0; t < 9; t++) {
-      const int ty = t / 3, txx = t % 3;
+#pragma unroll 9
+    for (int t = 0; t < T; t++) {
+      const int r = t / 3, txx = t % 3;  // r = tz*3 + ty
       const int c = arow + dil + sign * dil * (txx - 1);
-      const bf16* abase = tile + (ty * kTileW + c) * kPix + acol;
+      const bf16* abase = tile + (r * kTileW + c) * kPix + acol;
 #pragma unroll
       for (int h = 0; h < 2; h++) {
         unsigned a[4];
@@ -138,7 +168,8 @@ __global__ void __launch_bounds__(128) conv32_mma(int B, int H, const bf16* __re
       const int p = warp * 16 + (lane >> 2) + half * 8;
       const int x = x0 + p;
       if (x >= H) continue;
-      const long long pix = ((long long)b * H + y) * H + x;
+      const long long pix = D == 3 ? (((long long)b * H + z) * H + y) * H + x
+                                   : ((long long)b * H + y) * H + x;
 #pragma unroll
       for (int nt = 0; nt < 4; nt++) {
         const int o = nt * 8 + 2 * (lane & 3);
@@ -169,12 +200,15 @@ __global__ void __launch_bounds__(128) conv32_mma(int B, int H, const bf16* __re
 }
 
 // Weight gradient: every CTA accumulates, over its tiles, the 32 x 288 product
-// g^T * im2col(in) in registers (warp w owns n-tiles 9w .. 9w+8 of the 36) and
-// the bias sums, then writes them as its partial (layout (tap*32 + k)*32 + o,
-// bias at 9216 + o).
+// g^T * im2col(in) of the 9 taps of plane tz (3D; all 9 taps in 2D) in
+// registers (warp w owns n-tiles 9w .. 9w+8 of the 36) and the bias sums, then
+// writes them as its partial (layout (tap*32 + k)*32 + o, tap = tz*9 + local
+// tap in 3D; bias at T*1024 + o, written by the tz = 0 launch).
+template <int D>
 __global__ void __launch_bounds__(128) wgrad_mma(int B, int H, const bf16* __restrict__ in,
-                                                 const bf16* __restrict__ g, int dil,
+                                                 const bf16* __restrict__ g, int dil, int tz,
                                                  float* __restrict__ part, int stride) {
+  constexpr int T = D == 3 ? 27 : 9;
   __shared__ __align__(16) bf16 tile[3 * kTileW * kPix];
   __shared__ __align__(16) bf16 gt[kTileP * kPix];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -187,19 +221,25 @@ __global__ void __launch_bounds__(128) wgrad_mma(int B, int H, const bf16* __res
       for (int e = 0; e < 4; e++) acc[mt][j][e] = 0.f;
   float bsum = 0.f;  // thread t < 32: bias sum of channel t
   const int tpr = (H + kTileP - 1) / kTileP;
-  const long long ntiles = (long long)B * H * tpr;
+  long long nrows = (long long)B * H;
+  if (D == 3) nrows *= H;
+  const long long ntiles = nrows * tpr;
   for (long long tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
     const int tx = (int)(tIdx % tpr);
-    const int y = (int)((tIdx / tpr) % H);
-    const int b = (int)(tIdx / ((long long)tpr * H));
+    int b, z, y;
+    decode_row<D>(tIdx / tpr, H, b, z, y);
     const int x0 = tx * kTileP;
     __syncthreads();
-    stage_rows(tile, in, b, H, y, x0, dil, 1);
+    stage_rows<D>(tile, in, b, H, z, y, x0, dil, 1, 1, tz);
     for (int idx = threadIdx.x; idx < kTileP * 4; idx += blockDim.x) {
       const int q = idx & 3, p = idx >> 2;
       const int x = x0 + p;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (x < H) v = *reinterpret_cast<const uint4*>(g + (((long long)b * H + y) * H + x) * kC + q * 8);
+      if (x < H) {
+        const long long pix = D == 3 ? (((long long)b * H + z) * H + y) * H + x
+                                     : ((long long)b * H + y) * H + x;
+        v = *reinterpret_cast<const uint4*>(g + pix * kC + q * 8);
+      }
       *reinterpret_cast<uint4*>(gt + p * kPix + q * 8) = v;
     }
     __syncthreads();
@@ -240,6 +280,7 @@ __global__ void __launch_bounds__(128) wgrad_mma(int B, int H, const bf16* __res
   }
   // write the partial: c0,c1 -> (o = row, n = col, col+1), c2,c3 -> o + 8
   float* dst = part + (long long)blockIdx.x * stride;
+  float* dw = dst + (D == 3 ? (long long)tz * 9 * kC * kC : 0);
 #pragma unroll
   for (int mt = 0; mt < 2; mt++) {
 #pragma unroll
@@ -249,43 +290,69 @@ __global__ void __launch_bounds__(128) wgrad_mma(int B, int H, const bf16* __res
       for (int e = 0; e < 4; e++) {
         const int o = mt * 16 + (lane >> 2) + (e >> 1) * 8;
         const int n = nt * 8 + 2 * (lane & 3) + (e & 1);
-        dst[(long long)n * kC + o] = acc[mt][j][e];
+        dw[(long long)n * kC + o] = acc[mt][j][e];
       }
     }
   }
-  if (threadIdx.x < kC) dst[9 * kC * kC + threadIdx.x] = bsum;
+  if (threadIdx.x < kC && (D == 2 || tz == 0)) dst[T * kC * kC + threadIdx.x] = bsum;
 }
 
 }  // namespace
 
-cudaError_t launch_conv32_mma(int mode, int B, int H, const __nv_bfloat16* in,
-                              const __nv_bfloat16* wop, const float* bias, int dil, int sign,
-                              __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
-                              float* fo, const float* addend, cudaStream_t s) {
-  if (dil < 1 || dil > kMaxDil) return cudaErrorInvalidValue;
+template <int D>
+static cudaError_t conv_launch(int mode, int B, int H, const __nv_bfloat16* in,
+                               const __nv_bfloat16* wop, const float* bias, int dil, int sign,
+                               __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
+                               float* fo, const float* addend, cudaStream_t s) {
+  constexpr int smem = conv_smem_bytes<D>();
+  static bool configured = false;  // the 3D variants need more than 48 KB
+  if (!configured) {
+    cudaFuncSetAttribute(conv32_mma<kRelu, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(conv32_mma<kResid, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(conv32_mma<kF32, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    configured = true;
+  }
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const long long ntiles = (long long)B * H * ((H + kTileP - 1) / kTileP);
+  long long ntiles = (long long)B * H * ((H + kTileP - 1) / kTileP);
+  if (D == 3) ntiles *= H;
   const int grid = (int)(ntiles < 8LL * nsm ? ntiles : 8LL * nsm);
   if (mode == kRelu)
-    conv32_mma<kRelu><<<grid, 128, 0, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
-                                            addend);
+    conv32_mma<kRelu, D><<<grid, 128, smem, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid,
+                                                  fo, addend);
   else if (mode == kResid)
-    conv32_mma<kResid><<<grid, 128, 0, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
-                                             addend);
+    conv32_mma<kResid, D><<<grid, 128, smem, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid,
+                                                   fo, addend);
   else
-    conv32_mma<kF32><<<grid, 128, 0, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
-                                           addend);
+    conv32_mma<kF32, D><<<grid, 128, smem, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid,
+                                                 fo, addend);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_wgrad_mma(int B, int H, const __nv_bfloat16* in, const __nv_bfloat16* g,
-                             int dil, float* part, int stride, int nparts, cudaStream_t s) {
-  if (dil < 1 || dil > kMaxDil) return cudaErrorInvalidValue;
-  wgrad_mma<<<nparts, 128, 0, s>>>(B, H, in, g, dil, part, stride);
-  note_launches(1);
+cudaError_t launch_conv32_mma(int dim, int mode, int B, int H, const __nv_bfloat16* in,
+                              const __nv_bfloat16* wop, const float* bias, int dil, int sign,
+                              __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
+                              float* fo, const float* addend, cudaStream_t s) {
+  if (dil < 1 || dil > kMaxDil || (dim != 2 && dim != 3)) return cudaErrorInvalidValue;
+  return dim == 3 ? conv_launch<3>(mode, B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
+                                   addend, s)
+                  : conv_launch<2>(mode, B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
+                                   addend, s);
+}
+
+cudaError_t launch_wgrad_mma(int dim, int B, int H, const __nv_bfloat16* in,
+                             const __nv_bfloat16* g, int dil, float* part, int stride, int nparts,
+                             cudaStream_t s) {
+  if (dil < 1 || dil > kMaxDil || (dim != 2 && dim != 3)) return cudaErrorInvalidValue;
+  if (dim == 2) {
+    wgrad_mma<2><<<nparts, 128, 0, s>>>(B, H, in, g, dil, 1, part, stride);
+    note_launches(1);
+  } else {
+    for (int tz = 0; tz < 3; tz++) wgrad_mma<3><<<nparts, 128, 0, s>>>(B, H, in, g, dil, tz, part, stride);
+    note_launches(3);
+  }
   return cudaGetLastError();
 }
 

@@ -72,3 +72,34 @@ def test_retraining_triggered_by_f_r_admitted_pairs():
     # the gate keeps only part of the post-warm-up pairs (the paper reports
     # about one in ten on its workload)
     assert 0 < admitted < T - tau0
+
+
+def test_learned_guess_3d_variable_kappa():
+    """The online loop on the 3D variable-coefficient operator with the 3D
+    network (3x3x3 kernels): after the warm-up the network's guess is formed,
+    smoothed with kappa-weighted Jacobi sweeps and scored against x0 = 0 by
+    one GMRES cycle; every step still reaches the tolerance and the oracle's
+    solution."""
+    from paper_2103_10975_gb300 import Solver
+    from oracle import native
+    from synthetic import MovingGaussians3D, lognormal_kappa
+    n, T, tau0 = 16, 10, 4
+    kap = lognormal_kappa(n, 5001, smooth_sigma=2.0).astype(np.float32)
+    gen = MovingGaussians3D(n, 5001, 40)
+    s = Solver(n, dim=3, kappa=kap, m=30, rtol=1e-10, precision="fp32_refine", guess="learned",
+               fallback="zero", warmup_steps=tau0, train_iters=8, batch=2, lr=2e-3,
+               deterministic_tos=1, max_iters=100000, seed=4)
+    formed = 0
+    for t in range(T):
+        b = gen.rhs(t)
+        x, r = s.solve(torch.as_tensor(b).cuda())
+        assert r["status"] == 0 and r["relres_true"] <= 1e-10, (t, r)
+        xr, _, _ = native.gmres(3, n, b, m=50, rtol=1e-13, kappa=kap.astype(np.float64))
+        assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-7 * np.linalg.norm(xr)
+        if t >= tau0:
+            assert np.isfinite(r["relres_learned"]) and r["relres_learned"] >= 0.0
+            assert r["guess_used"] in (0, 2)
+            formed += 1
+        if (t + 1) % 2 == 0:
+            s.train_step()
+    assert formed == T - tau0

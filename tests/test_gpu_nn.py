@@ -15,10 +15,10 @@ if torch.cuda.is_available():
     from paper_2103_10975_gb300 import Solver  # noqa: E402
 
 
-def unpack(flat, n, C=32):
+def unpack(flat, n, C=32, dim=2):
     out = {}
     o = 0
-    for name, shape in onn.param_shapes(n, C):
+    for name, shape in onn.param_shapes(n, C, dim=dim):
         k = int(np.prod(shape))
         out[name] = flat[o:o + k].astype(np.float64).reshape(shape)
         o += k
@@ -118,3 +118,58 @@ def test_adam_step_through_training():
     big = np.abs(g) > 1e-3 * np.abs(g).max()
     step = (p1 - p0)[big]
     assert np.allclose(step, -lr * np.sign(g[big]), rtol=1e-3, atol=1e-6)
+
+
+# ---------------------------------------------------------------- 3D network
+
+def sample_batch_3d(n, B, seed):
+    from synthetic import MovingGaussians3D
+    gen = MovingGaussians3D(n, seed, 50)
+    us, ts = [], []
+    for t in range(B):
+        b = gen.rhs(5 * t)
+        x = direct.dst_solve_3d(n, b)
+        s = onn.rms(b)
+        us.append(b / s)
+        ts.append(x / s)
+    return np.array(us), np.array(ts)
+
+
+def bf16_params_3d(s, n):
+    P = unpack(s.get_params(), n, dim=3)
+    for k in P:
+        if k.startswith("level") and k.endswith(".w") or k == "dil.w":
+            P[k] = bf16_round(P[k])
+    return P
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_forward_parity_3d(n):
+    """The 3D network (3x3x3 kernels, 2x2x2 pooling, trilinear upsampling)
+    against the FP64 oracle at the same weights."""
+    s = Solver(n, dim=3, m=10, batch=2)
+    assert s.param_count() == sum(int(np.prod(sh)) for _, sh in onn.param_shapes(n, dim=3))
+    P = bf16_params_3d(s, n)
+    u, _ = sample_batch_3d(n, 2, 3)
+    y = s.nn_forward(torch.as_tensor(u, dtype=torch.float32).cuda()).cpu().numpy()
+    for b in range(2):
+        yr = onn.forward(P, u[b], n, dim=3)
+        assert np.linalg.norm(y[b] - yr) <= 3e-2 * np.linalg.norm(yr), b
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_gradient_parity_3d(n):
+    s = Solver(n, dim=3, m=10, batch=2)
+    P = bf16_params_3d(s, n)
+    u, t = sample_batch_3d(n, 2, 5)
+    loss, g = s.nn_loss_grad(torch.as_tensor(u, dtype=torch.float32).cuda(),
+                             torch.as_tensor(t, dtype=torch.float32).cuda())
+    lr, gr = onn.loss_and_grads(P, u, t, n, dim=3)
+    assert abs(loss - lr) <= 2e-2 * lr
+    G = unpack(g, n, dim=3)
+    for name in gr:
+        ref = gr[name]
+        nrm = np.linalg.norm(ref)
+        if nrm == 0.0:
+            continue
+        assert np.linalg.norm(G[name] - ref) <= 5e-2 * nrm, (name, np.linalg.norm(G[name] - ref) / nrm)
