@@ -240,6 +240,14 @@ mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u_dev,
                                     const float* t_dev, float* loss_host, float* grad_host,
                                     void* stream);
 
+/* The network's initial guess for b alone (the x0 = N(b) step of Sec. 2.2,
+ * as mlgmres_solve forms it in guess mode LEARNED): x_dev = c s N(b/s) with
+ * s = rms(b) and c the target scale of the last training phase, after
+ * opt.guess_smooth damped-Jacobi sweeps.  Runs no GMRES and records nothing.
+ * b_dev, x_dev: N doubles each, distinct.  An untrained network gives its
+ * initial output. */
+mlgmres_status mlgmres_guess(mlgmres_t h, const double* b_dev, double* x_dev, void* stream);
+
 /* Pairs currently in the replay ring. */
 mlgmres_status mlgmres_replay_size(mlgmres_t h, int* count);
 

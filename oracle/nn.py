@@ -14,6 +14,8 @@ sum is the kind the paper stacks before the output layer, Fig. "Resblocks"):
     z_l = relu(conv3x3(p_l, W_l) + b_l)                    C -> C, one per level
     s   = sum_l upsample_bilinear(z_l -> n x n)
     t   = s + relu(conv3x3_dilation2(s, W_d) + b_d)        C -> C, residual
+    (adaptive growth: t <- t + relu(conv3x3_dilation2(t, W_r) + b_r) for the
+     extra blocks r = 1, 2, ... appended before the output layer)
     y   = conv3x3(t, W_out) + b_out                        C -> 1
 
 conv3x3 with dilation d is the cross-correlation
@@ -51,14 +53,28 @@ def level_sizes(n, min_size=8):
     return sizes
 
 
-def param_shapes(n, C=32, dim=2):
-    """Ordered (name, shape) list of the network's parameters."""
+def param_shapes(n, C=32, dim=2, extra_blocks=0):
+    """Ordered (name, shape) list of the network's parameters.  extra_blocks
+    residual blocks res1, res2, ... (the adaptive growth of Sec. 2.1) come
+    after out.b, so the base layout does not depend on them."""
     k = (3,) * dim
     shapes = [("in.w", (C, 1) + k), ("in.b", (C,))]
     for l in range(len(level_sizes(n))):
         shapes += [("level%d.w" % l, (C, C) + k), ("level%d.b" % l, (C,))]
     shapes += [("dil.w", (C, C) + k), ("dil.b", (C,)), ("out.w", (1, C) + k), ("out.b", (1,))]
+    for r in range(1, extra_blocks + 1):
+        shapes += [("res%d.w" % r, (C, C) + k), ("res%d.b" % r, (C,))]
     return shapes
+
+
+def _blocks(params):
+    """Residual blocks before the output layer, in order: dil, res1, res2, ..."""
+    out = [("dil.w", "dil.b")]
+    r = 1
+    while ("res%d.w" % r) in params:
+        out.append(("res%d.w" % r, "res%d.b" % r))
+        r += 1
+    return out
 
 
 def _taps(dim):
@@ -178,11 +194,18 @@ def forward(params, u, n, keep=False, dim=2):
         pres.append(pre)
         z = relu(pre)
         s = s + (z if l == 0 else upsample(z, n))
-    pred = conv_fwd(s, params["dil.w"], params["dil.b"], 2)
-    t = s + relu(pred)
+    # residual blocks t_{r+1} = t_r + relu(conv_dil2(t_r)), the first on t_0 = s
+    t = s
+    tins, preds = [], []
+    for wn, bn in _blocks(params):
+        pred = conv_fwd(t, params[wn], params[bn], 2)
+        tins.append(t)
+        preds.append(pred)
+        t = t + relu(pred)
     y = conv_fwd(t, params["out.w"], params["out.b"], 1)
     if keep:
-        return y.reshape(-1), dict(x=x, pre0=pre0, pools=pools, pres=pres, s=s, pred=pred, t=t)
+        return y.reshape(-1), dict(x=x, pre0=pre0, pools=pools, pres=pres, s=s, tins=tins,
+                                   preds=preds, t=t)
     return y.reshape(-1)
 
 
@@ -192,9 +215,13 @@ def backward(params, cache, gy, n, dim=2):
     g = {}
     gy = np.asarray(gy, dtype=np.float64).reshape((1,) + (n,) * dim)
     gt, g["out.w"], g["out.b"] = conv_bwd(cache["t"], params["out.w"], 1, gy)
-    gpred = gt * (cache["pred"] > 0)
-    gs_d, g["dil.w"], g["dil.b"] = conv_bwd(cache["s"], params["dil.w"], 2, gpred)
-    gs = gt + gs_d
+    blocks = _blocks(params)
+    for r in range(len(blocks) - 1, -1, -1):
+        wn, bn = blocks[r]
+        gpred = gt * (cache["preds"][r] > 0)
+        gin, g[wn], g[bn] = conv_bwd(cache["tins"][r], params[wn], 2, gpred)
+        gt = gt + gin
+    gs = gt
     gpools = [None] * len(sizes)
     for l in range(len(sizes)):
         gz = gs if l == 0 else upsample_bwd(gs, sizes[l])

@@ -133,6 +133,7 @@ _SIGS = {
     "mlgmres_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                             ctypes.c_longlong, _vp, _vp, _vp,
                                             ctypes.POINTER(Result)]),
+    "mlgmres_guess": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mlgmres_autotune": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                         ctypes.POINTER(Tuning)]),
     "mlgmres_batch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -377,6 +378,14 @@ class Solver:
             g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream_handle(stream)),
             "nn_loss_grad")
         return loss.value, g
+
+    def guess(self, b, stream=None):
+        """mlgmres_guess: the network's x0 for b (no solve)."""
+        import torch
+        x = torch.empty_like(b)
+        self._check(self.lib.mlgmres_guess(self.h, _ptr(b), _ptr(x), _stream_handle(stream)),
+                    "guess")
+        return x
 
     def replay_size(self):
         c = ctypes.c_int(0)

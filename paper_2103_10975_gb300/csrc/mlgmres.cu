@@ -126,6 +126,25 @@ void ensure_net(mlgmres* h) {
   CK(net_create(h->net, h->grid.n, opt->batch, opt->seed, h->grid.dim));
 }
 
+// The learned guess x0 = c s N(b/s) (s = rms(b), c the target scale of the
+// last training phase), then opt.guess_smooth damped-Jacobi sweeps; returns
+// the buffer (x_alt or x_tmp) that holds it.
+double* learned_guess(mlgmres* h, const double* b, cudaStream_t s) {
+  const int N = h->N;
+  CK(launch_sumsq(b, N, h->scal, s));
+  CK(launch_normalise(b, N, h->scal, h->u_in, s));
+  CK(net_forward(h->net, 1, h->u_in, h->y_out, s));
+  double* cur = h->x_alt;
+  double* oth = h->x_tmp;
+  CK(launch_denormalise(h->y_out, N, h->scal, h->c_train, cur, s));
+  for (int k = 0; k < h->opt.guess_smooth; k++) {
+    CK(launch_jacobi(h->grid.dim, h->grid.n, h->grid.kappa_dev, b, cur, oth,
+                     (double)h->opt.guess_omega, s));
+    std::swap(cur, oth);
+  }
+  return cur;
+}
+
 // Shared-memory bytes of a single solve's V slice at `blocks` CTAs (0 if the
 // slice does not fit).
 int single_vsmem(const mlgmres* h, int blocks) {
@@ -493,19 +512,7 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
         h->train_pending = false;
       }
       CK(cudaEventRecord(h->ev2, s));
-      CK(launch_sumsq(b, N, h->scal, s));
-      CK(launch_normalise(b, N, h->scal, h->u_in, s));
-      CK(net_forward(h->net, 1, h->u_in, h->y_out, s));
-      // guess = c s N(b/s), then optional damped-Jacobi smoothing
-      double* cur = h->x_alt;
-      double* oth = h->x_tmp;
-      CK(launch_denormalise(h->y_out, N, h->scal, h->c_train, cur, s));
-      for (int k = 0; k < h->opt.guess_smooth; k++) {
-        CK(launch_jacobi(h->grid.dim, h->grid.n, h->grid.kappa_dev, b, cur, oth,
-                         (double)h->opt.guess_omega, s));
-        std::swap(cur, oth);
-      }
-      x_alt = cur;
+      x_alt = learned_guess(h, b, s);
     }
     // one persistent launch from the guess in xs (optionally competing with
     // alt by initial residual), capped at maxit Arnoldi steps
@@ -974,6 +981,23 @@ mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u, cons
     CK(cudaMemcpyAsync(grad_host, h->net.grad, sizeof(float) * h->net.nparams,
                        cudaMemcpyDeviceToHost, s));
     CK(cudaFreeAsync(y, s));
+    CK(cudaStreamSynchronize(s));
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_guess(mlgmres_t h, const double* b, double* x, void* stream) {
+  if (!h) return MLGMRES_ERR_ARG;
+  h->last_error.clear();
+  try {
+    ARG(b && x && b != x, "b and x must be distinct device pointers");
+    ensure_net(h);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->train_pending) CK(cudaStreamWaitEvent(s, h->train_done, 0));
+    const double* g = learned_guess(h, b, s);
+    CK(cudaMemcpyAsync(x, g, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
     return MLGMRES_OK;
   } catch (const Fail& f) {

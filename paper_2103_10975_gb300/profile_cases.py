@@ -5,6 +5,8 @@
     python -m paper_2103_10975_gb300.profile_cases batch --count 512 --nmax 512
     python -m paper_2103_10975_gb300.profile_cases cube --n 192 --max-iters 500
 
+    python -m paper_2103_10975_gb300.profile_cases dipole --n 64 --T 200
+
 --stages selects the bulk-copy depth for an FP32 basis in HBM (0 = direct
 loads, -1 = automatic); --autotune runs mlgmres_autotune first.
 
@@ -45,13 +47,13 @@ def solve_case(n, blocks, max_iters, m, precision, source, stages=-1, autotune=F
              1e3 * r["tos_ms"] / r["iters"]))
 
 
-def nn_case(n, batch):
+def nn_case(n, batch, dim=2):
     import torch
     from paper_2103_10975_gb300 import Solver
-    s = Solver(n, m=10, batch=batch)
+    s = Solver(n, dim=dim, m=10, batch=batch)
     g = torch.Generator(device="cuda").manual_seed(0)
-    u = torch.randn(batch, n * n, device="cuda", dtype=torch.float32, generator=g)
-    t = torch.randn(batch, n * n, device="cuda", dtype=torch.float32, generator=g)
+    u = torch.randn(batch, n ** dim, device="cuda", dtype=torch.float32, generator=g)
+    t = torch.randn(batch, n ** dim, device="cuda", dtype=torch.float32, generator=g)
     times = []
     for _ in range(7):
         torch.cuda.synchronize()
@@ -59,7 +61,7 @@ def nn_case(n, batch):
         s.nn_loss_grad(u, t)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
-    print("network forward+backward %dx%d batch %d: %.2f ms" % (n, n, batch,
+    print("network forward+backward %d^%d batch %d: %.2f ms" % (n, dim, batch,
                                                                1e3 * sum(times[2:]) / 5))
 
 
@@ -102,6 +104,50 @@ def cube_case(n, m, max_iters, stages=-1, autotune=False):
           % (n, m, r["iters"], r["tos_ms"], 1e3 * r["tos_ms"] / r["iters"], r["relres_true"]))
 
 
+def dipole_case(n, T, tau0, train_iters, lr, k):
+    """The two-scale dipole workload (a fresh asymmetric dipole with a random
+    overall scale every step): the online loop (learned guess with x0 = 0 as
+    fallback, training every 10 steps) against GMRES from x0 = 0, reporting
+    after the warm-up the true residual after k GMRES(30) iterations from the
+    network's guess and from x0 = 0 (the paper's fifth-iteration error), and
+    the iterations to rtol 1e-10 of both."""
+    import math
+    import torch
+    from paper_2103_10975_gb300 import Solver
+    from synthetic import Dipoles2D
+    gen = Dipoles2D(n, 6001)
+    learned = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", guess="learned",
+                     fallback="zero", warmup_steps=tau0, train_iters=train_iters, lr=lr,
+                     batch=8, guess_smooth=32, max_iters=10 ** 6, seed=5)
+    plain = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", max_iters=10 ** 6)
+    cap_user = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", guess="user", max_iters=k)
+    cap_zero = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", max_iters=k)
+    ratios, it_l, it_z, used = [], [], [], []
+    for t in range(T):
+        b = torch.as_tensor(gen.rhs(t)).cuda()
+        if t >= tau0:
+            x0 = learned.guess(b)
+            _, ru = cap_user.solve(b, x=x0)
+            _, rz = cap_zero.solve(b)
+            ratios.append(rz["relres_true"] / ru["relres_true"])
+        _, rl = learned.solve(b)
+        _, rp = plain.solve(b)
+        if t >= tau0:
+            it_l.append(rl["iters"])
+            it_z.append(rp["iters"])
+            used.append(rl["guess_used"] == 2)
+        if (t + 1) % 10 == 0:
+            learned.train_step()
+    lr_ = [math.log(r) for r in ratios]
+    gm = math.exp(sum(lr_) / len(lr_))
+    last = ratios[-20:]
+    gm_last = math.exp(sum(math.log(r) for r in last) / len(last))
+    print("dipoles %d^2, T=%d, tau0=%d: E_%d(x0=0)/E_%d(learned) geometric mean %.2f "
+          "(last 20 steps %.2f); iterations learned %.0f vs x0=0 %.0f; learned used %.2f"
+          % (n, T, tau0, k, k, gm, gm_last, sum(it_l) / len(it_l), sum(it_z) / len(it_z),
+             sum(used) / len(used)))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="case", required=True)
@@ -117,6 +163,7 @@ def main(argv=None):
     b = sub.add_parser("nn")
     b.add_argument("--n", type=int, default=256)
     b.add_argument("--batch", type=int, default=8)
+    b.add_argument("--dim", type=int, default=2)
     c = sub.add_parser("batch")
     c.add_argument("--count", type=int, default=512)
     c.add_argument("--nmin", type=int, default=64)
@@ -130,14 +177,23 @@ def main(argv=None):
     d.add_argument("--max-iters", type=int, default=500)
     d.add_argument("--stages", type=int, default=-1)
     d.add_argument("--autotune", action="store_true")
+    e = sub.add_parser("dipole")
+    e.add_argument("--n", type=int, default=64)
+    e.add_argument("--T", type=int, default=200)
+    e.add_argument("--tau0", type=int, default=50)
+    e.add_argument("--train-iters", type=int, default=64)
+    e.add_argument("--lr", type=float, default=2e-3)
+    e.add_argument("--k", type=int, default=5)
     args = ap.parse_args(argv)
     if args.case == "solve":
         solve_case(args.n, args.blocks, args.max_iters, args.m, args.precision, args.source,
                    args.stages, args.autotune)
     elif args.case == "nn":
-        nn_case(args.n, args.batch)
+        nn_case(args.n, args.batch, args.dim)
     elif args.case == "batch":
         batch_case(args.count, args.nmin, args.nmax, args.rtol, args.m, args.stages)
+    elif args.case == "dipole":
+        dipole_case(args.n, args.T, args.tau0, args.train_iters, args.lr, args.k)
     else:
         cube_case(args.n, args.m, args.max_iters, args.stages, args.autotune)
 

@@ -16,6 +16,7 @@ from .sources import (
     grid_coords,
     MovingGaussians2D,
     RandomWalkSources2D,
+    Dipoles2D,
     MovingGaussians3D,
     batched_instances,
     batched_sides,
@@ -25,6 +26,6 @@ from .sources import (
 
 __all__ = [
     "SplitMix64", "splitmix64_stream", "uniform_stream", "normal_stream",
-    "grid_coords", "MovingGaussians2D", "RandomWalkSources2D", "MovingGaussians3D",
+    "grid_coords", "MovingGaussians2D", "RandomWalkSources2D", "Dipoles2D", "MovingGaussians3D",
     "batched_instances", "batched_sides", "lognormal_kappa", "mode_rhs_2d",
 ]

@@ -75,6 +75,61 @@ class MovingGaussians2D:
         return b.reshape(-1)
 
 
+class Dipoles2D:
+    """Asymmetric two-scale dipoles, drawn afresh at every step (the
+    multi-scale workload of the network-architecture section: each pole is
+    made of two scales, the poles are shifted on the domain and relative to
+    each other, and every right-hand side has its own random overall scale).
+
+    Step t draws from SplitMix64(seed + 7919 t), in this order:
+    centre c ~ U[-0.5,0.5]^2 (x then y); separation r ~ U[0.15,0.5] at angle
+    phi ~ U[0,2pi) (poles at c -+ r/2 (cos phi, sin phi)); then per pole (the
+    positive one first): narrow width s1 ~ U[0.03,0.06], wide width
+    s2 ~ U[0.1,0.2], weights w1, w2 ~ U[0.5,1.5], and the offset of the wide
+    part from the narrow one, (dx, dy) ~ U[-0.1,0.1]^2; the negative pole's
+    strength a ~ U[0.5,1.5] (so the dipole is not symmetric); finally the
+    overall scale S = 10^u, u ~ U[-1,1].
+
+    b_t = S (pole_+ - a pole_-), pole = w1 G(s1) + w2 G(s2, shifted).
+    """
+
+    def __init__(self, n, seed):
+        self.n = int(n)
+        self.seed = int(seed)
+        self.coords = grid_coords(self.n)
+
+    def params(self, t):
+        g = SplitMix64(self.seed + 7919 * int(t))
+        cx = g.uniform(-0.5, 0.5)
+        cy = g.uniform(-0.5, 0.5)
+        r = g.uniform(0.15, 0.5)
+        phi = g.uniform(0.0, TWO_PI)
+        poles = []
+        for sgn in (1.0, -1.0):
+            px = cx - sgn * 0.5 * r * math.cos(phi)
+            py = cy - sgn * 0.5 * r * math.sin(phi)
+            s1 = g.uniform(0.03, 0.06)
+            s2 = g.uniform(0.1, 0.2)
+            w1 = g.uniform(0.5, 1.5)
+            w2 = g.uniform(0.5, 1.5)
+            dx = g.uniform(-0.1, 0.1)
+            dy = g.uniform(-0.1, 0.1)
+            poles.append((px, py, s1, s2, w1, w2, dx, dy))
+        a = g.uniform(0.5, 1.5)
+        S = 10.0 ** g.uniform(-1.0, 1.0)
+        return poles, a, S
+
+    def rhs(self, t):
+        x = self.coords
+        poles, a, S = self.params(t)
+        b = np.zeros((self.n, self.n), dtype=np.float64)
+        for k, (px, py, s1, s2, w1, w2, dx, dy) in enumerate(poles):
+            amp = 1.0 if k == 0 else -a
+            b += amp * w1 * np.outer(_gauss1d(x, py, s1), _gauss1d(x, px, s1))
+            b += amp * w2 * np.outer(_gauss1d(x, py + dy, s2), _gauss1d(x, px + dx, s2))
+        return (S * b).reshape(-1)
+
+
 class RandomWalkSources2D:
     """Sixteen signed Gaussians on a random walk plus one exact Laplacian
     eigenmode (the 2048^2 refinement workload).

@@ -103,3 +103,35 @@ def test_learned_guess_3d_variable_kappa():
         if (t + 1) % 2 == 0:
             s.train_step()
     assert formed == T - tau0
+
+
+def test_dipole_workload_fifth_iteration_error():
+    """The two-scale dipole workload (a fresh asymmetric dipole with a random
+    overall scale every step, so x_{t-1} carries no information): after the
+    warm-up, five GMRES(30) iterations from the network's guess (mlgmres_guess)
+    leave a smaller true residual than five from x0 = 0 (geometric mean over
+    the last 40 steps; about 4x at 64^2 over 200 steps)."""
+    import math
+    from paper_2103_10975_gb300 import Solver
+    from synthetic import Dipoles2D
+    n, T, tau0 = 64, 120, 40
+    gen = Dipoles2D(n, 6001)
+    learned = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", guess="learned",
+                     fallback="zero", warmup_steps=tau0, train_iters=64, lr=2e-3, batch=8,
+                     guess_smooth=32, deterministic_tos=1, max_iters=10 ** 6, seed=5)
+    cap_user = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", guess="user", max_iters=5)
+    cap_zero = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", max_iters=5)
+    logs = []
+    for t in range(T):
+        b = torch.as_tensor(gen.rhs(t)).cuda()
+        if t >= T - 40:
+            _, ru = cap_user.solve(b, x=learned.guess(b))
+            _, rz = cap_zero.solve(b)
+            assert ru["iters"] == 5 and rz["iters"] == 5
+            logs.append(math.log(rz["relres_true"] / ru["relres_true"]))
+        _, r = learned.solve(b)
+        assert r["status"] == 0 and r["relres_true"] <= 1e-10
+        if (t + 1) % 10 == 0:
+            learned.train_step()
+    gm = math.exp(sum(logs) / len(logs))
+    assert gm > 1.5, gm

@@ -216,3 +216,37 @@ def test_3d_gradients_vs_central_differences():
             fd = (lp - lm) / (2 * eps)
             an = grads[name].reshape(-1)[i]
             assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-3), (name, i, fd, an)
+
+
+def test_grown_network_gradients_and_identity_start():
+    """Adaptive growth (Sec. 2.1, residual blocks appended before the output
+    layer): with zero weights an extra block is the identity, so the grown
+    network computes the same output; gradients of the grown network match
+    central differences."""
+    n, C = 16, 3
+    rng = np.random.default_rng(21)
+    base = {k: rng.standard_normal(s) * (0.4 if k.endswith(".w") else 0.1)
+            for k, s in nn.param_shapes(n, C)}
+    grown = dict(base)
+    for k, s in nn.param_shapes(n, C, extra_blocks=2)[len(base):]:
+        grown[k] = np.zeros(s)
+    u = rng.standard_normal(n * n)
+    assert np.allclose(nn.forward(base, u, n), nn.forward(grown, u, n), atol=1e-14)
+    for k, s in nn.param_shapes(n, C, extra_blocks=2)[len(base):]:
+        grown[k] = rng.standard_normal(s) * (0.3 if k.endswith(".w") else 0.1)
+    inputs = rng.standard_normal((1, n * n))
+    targets = rng.standard_normal((1, n * n))
+    _, grads = nn.loss_and_grads(grown, inputs, targets, n)
+    eps = 1e-6
+    for name in ("res1.w", "res2.b", "dil.w", "level0.w", "in.w"):
+        flat = grown[name].reshape(-1)
+        for i in rng.choice(flat.size, size=3, replace=False):
+            old = flat[i]
+            flat[i] = old + eps
+            lp, _ = nn.loss_and_grads(grown, inputs, targets, n)
+            flat[i] = old - eps
+            lm, _ = nn.loss_and_grads(grown, inputs, targets, n)
+            flat[i] = old
+            fd = (lp - lm) / (2 * eps)
+            an = grads[name].reshape(-1)[i]
+            assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-3), (name, i, fd, an)

@@ -1,5 +1,7 @@
 """Input generators: splitmix64 against its published test vector, the
 vectorised stream against the scalar generator, and workload shapes."""
+import math
+
 import numpy as np
 
 from synthetic import (SplitMix64, splitmix64_stream, uniform_stream, normal_stream,
@@ -46,3 +48,21 @@ def test_other_generators_shapes():
     assert k.shape == (4096,) and np.all(k > 0)
     assert abs(np.log(k).std() - 1.0) < 1e-12
     assert mode_rhs_2d(8, 1, 2).shape == (64,)
+
+
+def test_dipoles_structure_and_determinism():
+    from synthetic import Dipoles2D
+    g = Dipoles2D(48, 6001)
+    b1, b2 = g.rhs(3), Dipoles2D(48, 6001).rhs(3)
+    assert np.array_equal(b1, b2)                       # random access by step
+    assert not np.allclose(g.rhs(3), g.rhs(4))           # fresh draw every step
+    scales = []
+    for t in range(40):
+        poles, a, S = g.params(t)
+        assert 0.5 <= a <= 1.5 and 0.1 <= S <= 10.0
+        (px, py, *_), (qx, qy, *_) = poles
+        assert 0.15 - 1e-12 <= math.hypot(px - qx, py - qy) <= 0.5 + 1e-12
+        b = g.rhs(t).reshape(48, 48)
+        assert b.max() > 0 > b.min()                       # one pole of each sign
+        scales.append(S)
+    assert max(scales) / min(scales) > 10                  # overall scale varies
