@@ -126,6 +126,12 @@ typedef struct {
                                 of the handle) once f_r pairs have been admitted since the
                                 previous phase, and from tau0 on; 0 = the caller decides
                                 when to call mlgmres_train_step (fixed cadence) */
+  int grow_blocks;           /* adaptive depth (Sec. 2.1): up to this many residual blocks
+                                (0..4) are appended before the output layer, one at a
+                                training phase whose M_p(E_k) has stagnated (0 = fixed
+                                depth) */
+  double grow_tol;           /* stagnation: M_p(E_k) at a training phase is above
+                                (1 - grow_tol) times its value at the previous phase */
 } mlgmres_options;
 
 typedef struct {
@@ -149,7 +155,8 @@ typedef struct {
  * guess ZERO, fallback ZERO, replay_cap 64, warmup 50, p = 10, theta = 0.9,
  * deterministic_tos 0, train_iters 32, batch 8, lr 1e-3, seed 1,
  * grid_blocks 0, batch_slots 0, barrier_timeout_s 2, guess_smooth 8, guess_omega 0.8,
- * guess_select 0, fault_inject 0, v_stages -1, retrain_after 0. */
+ * guess_select 0, fault_inject 0, v_stages -1, retrain_after 0, grow_blocks 0,
+ * grow_tol 0.02. */
 void mlgmres_default_options(mlgmres_options* opt);
 
 /* Creates a solver for one grid and allocates all workspace on the current
@@ -222,7 +229,8 @@ mlgmres_status mlgmres_arnoldi(mlgmres_t h, const double* v0_dev, int steps, dou
 mlgmres_status mlgmres_nn_param_count(mlgmres_t h, long long* count);
 
 /* Copies the FP32 master parameters out / in, in the order
- * in.w, in.b, level[0].w, level[0].b, ..., dil.w, dil.b, out.w, out.b
+ * in.w, in.b, level[0].w, level[0].b, ..., dil.w, dil.b, out.w, out.b (then
+ * res1.w, res1.b, ... when opt.grow_blocks > 0)
  * (weights as [out][in][ky][kx], 3D [out][in][kz][ky][kx]).  Setting them also
  * resets Adam's moments. */
 mlgmres_status mlgmres_nn_get_params(mlgmres_t h, float* params_host, long long count);
@@ -247,6 +255,13 @@ mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u_dev,
  * b_dev, x_dev: N doubles each, distinct.  An untrained network gives its
  * initial output. */
 mlgmres_status mlgmres_guess(mlgmres_t h, const double* b_dev, double* x_dev, void* stream);
+
+/* Residual blocks appended so far by the adaptive growth (opt.grow_blocks).
+ * set_to >= 0 sets the count (clamped to opt.grow_blocks; for tests and for
+ * callers that choose the depth themselves), -1 only queries.  *active
+ * receives the count after the call.  Parameters of every possible block are
+ * always part of the parameter array (after out.b: res1.w, res1.b, ...). */
+mlgmres_status mlgmres_nn_blocks(mlgmres_t h, int set_to, int* active);
 
 /* Pairs currently in the replay ring. */
 mlgmres_status mlgmres_replay_size(mlgmres_t h, int* count);

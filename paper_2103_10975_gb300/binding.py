@@ -58,6 +58,8 @@ class Options(ctypes.Structure):
         ("fault_inject", ctypes.c_int),
         ("v_stages", ctypes.c_int),
         ("retrain_after", ctypes.c_int),
+        ("grow_blocks", ctypes.c_int),
+        ("grow_tol", ctypes.c_double),
     ]
 
 
@@ -134,6 +136,7 @@ _SIGS = {
                                             ctypes.c_longlong, _vp, _vp, _vp,
                                             ctypes.POINTER(Result)]),
     "mlgmres_guess": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "mlgmres_nn_blocks": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mlgmres_autotune": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                         ctypes.POINTER(Tuning)]),
     "mlgmres_batch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -386,6 +389,13 @@ class Solver:
         self._check(self.lib.mlgmres_guess(self.h, _ptr(b), _ptr(x), _stream_handle(stream)),
                     "guess")
         return x
+
+    def nn_blocks(self, set_to=-1):
+        """mlgmres_nn_blocks: residual blocks appended so far (optionally set)."""
+        c = ctypes.c_int(0)
+        self._check(self.lib.mlgmres_nn_blocks(self.h, int(set_to), ctypes.byref(c)),
+                    "nn_blocks")
+        return c.value
 
     def replay_size(self):
         c = ctypes.c_int(0)

@@ -67,6 +67,7 @@ struct mlgmres {
   std::vector<double> E_hist, T_hist;
   std::vector<double> ring_c;         // rms(x)/rms(b) of each stored pair
   double c_train = 1.0;               // target scale used by the last training phase
+  double mp_last_phase = 0.0;         // M_p(E_k) at the previous training phase (growth)
   double* x_tmp = nullptr;            // smoothing ping-pong buffer
   long long solves = 0;
   double* ddots = nullptr;            // device dots for the spread check

@@ -100,6 +100,8 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
           gmres_bulk_cap(o->precision == MLGMRES_FP32_REFINE, o->m, o->v_stages) > 0,
       "v_stages: no stage of m rows fits in shared memory");
   ARG(o->retrain_after >= 0, "retrain_after must be >= 0");
+  ARG(o->grow_blocks >= 0 && o->grow_blocks <= kMaxExtra, "grow_blocks must be in 0..4");
+  ARG(o->grow_tol >= 0.0 && o->grow_tol <= 1.0, "grow_tol must be in [0, 1]");
 }
 
 // Bulk-copy stages the passes use for an FP32 basis in HBM.
@@ -123,7 +125,7 @@ void ensure_net(mlgmres* h) {
   CK(cudaMalloc(&h->ddots, sizeof(double) * (2 * opt->replay_cap + 1)));
   CK(cudaMallocHost(&h->hdots, sizeof(double) * (2 * opt->replay_cap + 1)));
   CK(cudaMalloc(&h->loss_dev, sizeof(float) * 4));
-  CK(net_create(h->net, h->grid.n, opt->batch, opt->seed, h->grid.dim));
+  CK(net_create(h->net, h->grid.n, opt->batch, opt->seed, h->grid.dim, opt->grow_blocks));
 }
 
 // The learned guess x0 = c s N(b/s) (s = rms(b), c the target scale of the
@@ -305,6 +307,18 @@ void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
   if (h->ring_count == 0 || h->solves < h->opt.warmup_steps || h->opt.train_iters == 0) return;
   // the ring was written on the solve streams; the handle's solves synchronise
   // before returning, so everything they enqueued is complete here.
+  // adaptive depth (Sec. 2.1): append a residual block when M_p(E_k) has not
+  // improved by grow_tol since the previous training phase
+  if (h->net.extra_max > 0 && !h->E_hist.empty()) {
+    const size_t k = std::min<size_t>((size_t)h->opt.window_p, h->E_hist.size());
+    double mp = 0.0;
+    for (size_t i = h->E_hist.size() - k; i < h->E_hist.size(); i++) mp += h->E_hist[i];
+    mp /= (double)k;
+    if (h->mp_last_phase > 0.0 && mp >= (1.0 - h->opt.grow_tol) * h->mp_last_phase &&
+        h->net.extra_active < h->net.extra_max)
+      h->net.extra_active++;
+    h->mp_last_phase = mp;
+  }
   const int B = std::min(h->opt.batch, std::max(1, h->ring_count));
   std::vector<int> pick(B);
   // unit-scale targets: t / c with c the mean rms(x)/rms(b) over the ring
@@ -364,6 +378,8 @@ void mlgmres_default_options(mlgmres_options* o) {
   o->fault_inject = 0;
   o->v_stages = -1;
   o->retrain_after = 0;
+  o->grow_blocks = 0;
+  o->grow_tol = 0.02;
 }
 
 mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* opt,
@@ -999,6 +1015,23 @@ mlgmres_status mlgmres_guess(mlgmres_t h, const double* b, double* x, void* stre
     const double* g = learned_guess(h, b, s);
     CK(cudaMemcpyAsync(x, g, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_nn_blocks(mlgmres_t h, int set_to, int* active) {
+  if (!h || !active) return MLGMRES_ERR_ARG;
+  h->last_error.clear();
+  try {
+    ARG(set_to >= -1, "set_to must be >= -1");
+    ensure_net(h);
+    if (set_to >= 0) {
+      CK(cudaDeviceSynchronize());  // no training phase may be using the old depth
+      h->net.extra_active = std::min(set_to, h->net.extra_max);
+    }
+    *active = h->net.extra_active;
     return MLGMRES_OK;
   } catch (const Fail& f) {
     return f.st;

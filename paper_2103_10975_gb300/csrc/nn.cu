@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -456,8 +457,12 @@ unsigned long long sm64(unsigned long long& st) {
     if (e_ != cudaSuccess) return e_;     \
   } while (0)
 
-cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int dim) {
+cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int dim,
+                       int extra_max) {
   if (dim != 2 && dim != 3) return cudaErrorInvalidValue;
+  if (extra_max < 0 || extra_max > kMaxExtra) return cudaErrorInvalidValue;
+  net.extra_max = extra_max;
+  net.extra_active = 0;
   net.n = n;
   net.dim = dim;
   net.taps = dim == 3 ? 27 : 9;
@@ -483,6 +488,10 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
   net.off_b[L + 1] = off; off += kC;
   net.off_w[L + 2] = off; off += kC * T;
   net.off_b[L + 2] = off; off += 1;
+  for (int r = 0; r < extra_max; r++) {
+    net.off_rw[r] = off; off += per;
+    net.off_rb[r] = off; off += kC;
+  }
   net.nparams = off;
 
   // He-uniform initialisation from splitmix64: U[-a, a], a = sqrt(6 / fan_in);
@@ -500,6 +509,9 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
   for (int l = 0; l < L; l++) fill(net.off_w[1 + l], per, T * kC, 6.f);
   fill(net.off_w[L + 1], per, T * kC, 6.f);
   fill(net.off_w[L + 2], kC * T, T * kC, 3.f);
+  // a grown block starts close to the identity (small weights, zero bias) so
+  // the guess changes little when it is appended, yet its gradient is not zero
+  for (int r = 0; r < extra_max; r++) fill(net.off_rw[r], per, T * kC, 0.06f);
 
   const long long np = net.nparams;
   NN_CK(cudaMalloc(&net.master, sizeof(float) * np));
@@ -510,12 +522,14 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
   NN_CK(cudaMemset(net.grad, 0, sizeof(float) * np));
   NN_CK(cudaMemset(net.adam_m, 0, sizeof(float) * np));
   NN_CK(cudaMemset(net.adam_v, 0, sizeof(float) * np));
-  NN_CK(cudaMalloc(&net.wq, sizeof(bf16) * per * (L + 1)));
-  NN_CK(cudaMalloc(&net.wqT, sizeof(bf16) * per * (L + 1)));
-  long long offs[kMaxLevels + 1];
+  const int nconv = L + 1 + extra_max;  // the 32 -> 32 convolutions
+  NN_CK(cudaMalloc(&net.wq, sizeof(bf16) * per * nconv));
+  NN_CK(cudaMalloc(&net.wqT, sizeof(bf16) * per * nconv));
+  long long offs[kMaxLevels + 1 + kMaxExtra];
   for (int c = 0; c < L + 1; c++) offs[c] = net.off_w[1 + c];
+  for (int r = 0; r < extra_max; r++) offs[L + 1 + r] = net.off_rw[r];
   NN_CK(cudaMalloc(&net.offs_dev, sizeof(offs)));
-  NN_CK(cudaMemcpy(net.offs_dev, offs, sizeof(long long) * (L + 1), cudaMemcpyHostToDevice));
+  NN_CK(cudaMemcpy(net.offs_dev, offs, sizeof(long long) * nconv, cudaMemcpyHostToDevice));
 
   auto pts = [dim](int side) {
     return dim == 3 ? (long long)side * side * side : (long long)side * side;
@@ -533,6 +547,10 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
   NN_CK(cudaMalloc(&net.s, sizeof(bf16) * full));
   NN_CK(cudaMalloc(&net.e, sizeof(bf16) * full));
   NN_CK(cudaMalloc(&net.t, sizeof(bf16) * full));
+  for (int r = 0; r < extra_max; r++) {
+    NN_CK(cudaMalloc(&net.te[r], sizeof(bf16) * full));
+    NN_CK(cudaMalloc(&net.tt[r], sizeof(bf16) * full));
+  }
   NN_CK(cudaMalloc(&net.g_t, sizeof(float) * full));
   NN_CK(cudaMalloc(&net.g_s, sizeof(float) * full));
   NN_CK(cudaMalloc(&net.g_lvl, sizeof(float) * full));
@@ -569,6 +587,10 @@ void net_destroy(Net& net) {
   cudaFree(net.s);
   cudaFree(net.e);
   cudaFree(net.t);
+  for (int r = 0; r < kMaxExtra; r++) {
+    cudaFree(net.te[r]);
+    cudaFree(net.tt[r]);
+  }
   cudaFree(net.g_t);
   cudaFree(net.g_s);
   cudaFree(net.g_lvl);
@@ -584,7 +606,7 @@ void net_destroy(Net& net) {
 }
 
 cudaError_t net_sync_weights(Net& net, cudaStream_t s) {
-  const int nconv = net.L + 1;
+  const int nconv = net.L + 1 + net.extra_max;
   const long long tot = (long long)nconv * net.taps * kC * kC;
   sync_weights_kernel<<<nblk(tot, 256), 256, 0, s>>>(nconv, net.taps, net.master, net.offs_dev,
                                                     net.wq, net.wqT);
@@ -624,7 +646,14 @@ cudaError_t forward_t(Net& net, int B, const float* u, float* y, cudaStream_t s)
   note_launches(1);
   NN_CK(launch_conv32_mma(D, 1, B, n, net.s, net.wqT + per * L, net.master + net.off_b[L + 1], 2,
                           1, net.e, net.t, net.s, nullptr, nullptr, s));
-  conv_out_fwd<D><<<nblk(pix, 256), 256, 0, s>>>(B, n, net.t, net.master + net.off_w[L + 2],
+  const bf16* cur = net.t;
+  for (int r = 0; r < net.extra_active; r++) {  // grown residual blocks
+    NN_CK(launch_conv32_mma(D, 1, B, n, cur, net.wqT + per * (L + 1 + r),
+                            net.master + net.off_rb[r], 2, 1, net.te[r], net.tt[r], cur, nullptr,
+                            nullptr, s));
+    cur = net.tt[r];
+  }
+  conv_out_fwd<D><<<nblk(pix, 256), 256, 0, s>>>(B, n, cur, net.master + net.off_w[L + 2],
                                                   net.master + net.off_b[L + 2], y);
   note_launches(1);
   return cudaGetLastError();
@@ -648,7 +677,8 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   loss_finish<<<1, 32, 0, s>>>(net.loss_part, lparts, 1.f / (float)pix, loss_dev);
   note_launches(1);
   // output conv
-  conv1_wgrad<0, D><<<P, 256, 0, s>>>(B, n, net.gy, net.t, nullptr, nullptr, net.wgrad_part,
+  const bf16* tfin = net.extra_active > 0 ? net.tt[net.extra_active - 1] : net.t;
+  conv1_wgrad<0, D><<<P, 256, 0, s>>>(B, n, net.gy, tfin, nullptr, nullptr, net.wgrad_part,
                                       stride);
   note_launches(1);
   reduce_wgrad<<<nblk(T * kC + 1, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 2, T,
@@ -658,6 +688,29 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   conv_out_bwd_data<D><<<nblk(pix, 256), 256, 0, s>>>(B, n, net.gy,
                                                       net.master + net.off_w[L + 2], net.g_t);
   note_launches(1);
+  // grown residual blocks, last first: t_out = t_in + relu(conv_d2(t_in));
+  // blocks not appended yet get a zero gradient (Adam then leaves them as they are)
+  for (int r = net.extra_active; r < net.extra_max; r++)
+    NN_CK(cudaMemsetAsync(net.grad + net.off_rw[r], 0, sizeof(float) * (per + kC), s));
+  {
+    float* gcur = net.g_t;
+    float* gnext = net.g_s;
+    for (int r = net.extra_active - 1; r >= 0; r--) {
+      const bf16* tin = r == 0 ? net.t : net.tt[r - 1];
+      mask_to_bf16<<<nblk(full, 256), 256, 0, s>>>(full, gcur, net.te[r], net.g_bf);
+      note_launches(1);
+      NN_CK(launch_wgrad_mma(D, B, n, tin, net.g_bf, 2, net.wgrad_part, stride, P, s));
+      reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
+                                                       net.grad + net.off_rw[r],
+                                                       net.grad + net.off_rb[r]);
+      note_launches(1);
+      NN_CK(launch_conv32_mma(D, 2, B, n, net.g_bf, net.wq + per * (L + 1 + r), nullptr, 2, -1,
+                              nullptr, nullptr, nullptr, gnext, gcur, s));
+      std::swap(gcur, gnext);
+    }
+    if (gcur != net.g_t)
+      NN_CK(cudaMemcpyAsync(net.g_t, gcur, sizeof(float) * full, cudaMemcpyDeviceToDevice, s));
+  }
   // dilated residual block: t = s + e, e = relu(conv_d2(s))
   mask_to_bf16<<<nblk(full, 256), 256, 0, s>>>(full, net.g_t, net.e, net.g_bf);
   note_launches(1);

@@ -25,6 +25,7 @@ namespace mlg {
 
 constexpr int kC = 32;      // channels
 constexpr int kMaxLevels = 12;
+constexpr int kMaxExtra = 4;  // residual blocks the network may grow (Sec. 2.1)
 
 struct Net {
   int n = 0;                // grid side
@@ -36,6 +37,14 @@ struct Net {
   long long nparams = 0;
   long long off_w[kMaxLevels + 3];  // offsets of each conv's weights (0 in, 1..L levels, L+1 dil, L+2 out)
   long long off_b[kMaxLevels + 3];
+  // adaptive growth: residual blocks appended before the output layer,
+  // t <- t + relu(conv_dil2(t) + b); parameters after out.b (res1, res2, ...)
+  int extra_max = 0;
+  int extra_active = 0;
+  long long off_rw[kMaxExtra] = {};
+  long long off_rb[kMaxExtra] = {};
+  __nv_bfloat16* te[kMaxExtra] = {};         // relu part of extra block r
+  __nv_bfloat16* tt[kMaxExtra] = {};         // output of extra block r
   float* master = nullptr;  // FP32 parameters
   float* grad = nullptr;
   float* adam_m = nullptr;
@@ -82,7 +91,8 @@ cudaError_t launch_wgrad_mma(int dim, int B, int H, const __nv_bfloat16* in,
                              const __nv_bfloat16* g, int dil, float* part, int stride, int nparts,
                              cudaStream_t s);
 
-cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int dim = 2);
+cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int dim = 2,
+                       int extra_max = 0);
 void net_destroy(Net& net);
 // Re-derive the BF16 operand copies from the FP32 master parameters.
 cudaError_t net_sync_weights(Net& net, cudaStream_t s);

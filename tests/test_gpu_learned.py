@@ -135,3 +135,22 @@ def test_dipole_workload_fifth_iteration_error():
             learned.train_step()
     gm = math.exp(sum(logs) / len(logs))
     assert gm > 1.5, gm
+
+
+def test_adaptive_growth_appends_blocks_on_stagnation():
+    """grow_tol = 1 counts every training phase after the first as stagnant,
+    so one residual block is appended per phase until grow_blocks; the solves
+    stay correct while the network deepens."""
+    from paper_2103_10975_gb300 import Solver
+    n = 32
+    gen = MovingGaussians2D(n, 1001, 50)
+    s = Solver(n, m=20, rtol=1e-8, guess="learned", fallback="zero", warmup_steps=5,
+               train_iters=2, batch=4, grow_blocks=2, grow_tol=1.0, deterministic_tos=1, seed=9)
+    depth = []
+    for t in range(30):
+        _, r = s.solve(torch.as_tensor(gen.rhs(t)).cuda())
+        assert r["status"] == 0 and r["relres_true"] <= 1e-8
+        if (t + 1) % 5 == 0:
+            s.train_step()
+            depth.append(s.nn_blocks())
+    assert depth[:4] == [0, 1, 2, 2], depth

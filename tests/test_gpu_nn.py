@@ -173,3 +173,49 @@ def test_gradient_parity_3d(n):
         if nrm == 0.0:
             continue
         assert np.linalg.norm(G[name] - ref) <= 5e-2 * nrm, (name, np.linalg.norm(G[name] - ref) / nrm)
+
+
+# ------------------------------------------------ adaptive depth (grown blocks)
+
+def test_grown_blocks_parity():
+    """Two residual blocks appended before the output layer (Sec. 2.1): the
+    forward pass and every gradient against the oracle with the same blocks."""
+    n = 16
+    s = Solver(n, m=10, batch=2, grow_blocks=2)
+    assert s.nn_blocks() == 0
+    assert s.nn_blocks(2) == 2
+    shapes = onn.param_shapes(n, extra_blocks=2)
+    assert s.param_count() == sum(int(np.prod(sh)) for _, sh in shapes)
+    flat = s.get_params()
+    P, o = {}, 0
+    for name, shape in shapes:
+        k = int(np.prod(shape))
+        P[name] = flat[o:o + k].astype(np.float64).reshape(shape)
+        o += k
+    for k in P:
+        if (k.startswith("level") or k.startswith("res") or k == "dil.w") and k.endswith(".w"):
+            P[k] = bf16_round(P[k])
+    u, t = sample_batch(n, 2, 7)
+    y = s.nn_forward(torch.as_tensor(u, dtype=torch.float32).cuda()).cpu().numpy()
+    for b in range(2):
+        yr = onn.forward(P, u[b], n)
+        assert np.linalg.norm(y[b] - yr) <= 3e-2 * np.linalg.norm(yr)
+    loss, g = s.nn_loss_grad(torch.as_tensor(u, dtype=torch.float32).cuda(),
+                             torch.as_tensor(t, dtype=torch.float32).cuda())
+    lr, gr = onn.loss_and_grads(P, u, t, n)
+    assert abs(loss - lr) <= 2e-2 * lr
+    o = 0
+    for name, shape in shapes:
+        k = int(np.prod(shape))
+        ref = gr[name]
+        nrm = np.linalg.norm(ref)
+        if nrm > 0:
+            got = g[o:o + k].reshape(shape)
+            assert np.linalg.norm(got - ref) <= 5e-2 * nrm, name
+        o += k
+    # back to one block: the extra blocks get no gradient
+    assert s.nn_blocks(0) == 0
+    _, g0 = s.nn_loss_grad(torch.as_tensor(u, dtype=torch.float32).cuda(),
+                           torch.as_tensor(t, dtype=torch.float32).cuda())
+    base = sum(int(np.prod(sh)) for _, sh in onn.param_shapes(n))
+    assert np.all(g0[base:] == 0)
