@@ -48,6 +48,12 @@ typedef enum {
   MLGMRES_ERR_NONFINITE = -5  /* a residual or norm became NaN/Inf */
 } mlgmres_status;
 
+/* Model of the learned guess. */
+enum {
+  MLGMRES_MODEL_CONV = 0,
+  MLGMRES_MODEL_LINEAR = 1
+};
+
 /* Arithmetic of the Arnoldi cycles. */
 enum {
   MLGMRES_FP64 = 0,        /* everything in FP64 */
@@ -132,6 +138,12 @@ typedef struct {
                                 depth) */
   double grow_tol;           /* stagnation: M_p(E_k) at a training phase is above
                                 (1 - grow_tol) times its value at the previous phase */
+  int model;                 /* MLGMRES_MODEL_CONV: the multi-scale network of Sec. 2.1;
+                                MLGMRES_MODEL_LINEAR: one dense layer x0 = c s T (b/s) =
+                                c T b (the simplified model of Sec. 3.1, for studying the
+                                spectrum of A T; N <= 4096, T starts at 0 and trains by
+                                plain gradient descent with step lr; the nn_* entry
+                                points then see T, row-major, as the parameters) */
 } mlgmres_options;
 
 typedef struct {
@@ -156,7 +168,7 @@ typedef struct {
  * deterministic_tos 0, train_iters 32, batch 8, lr 1e-3, seed 1,
  * grid_blocks 0, batch_slots 0, barrier_timeout_s 2, guess_smooth 8, guess_omega 0.8,
  * guess_select 0, fault_inject 0, v_stages -1, retrain_after 0, grow_blocks 0,
- * grow_tol 0.02. */
+ * grow_tol 0.02, model CONV. */
 void mlgmres_default_options(mlgmres_options* opt);
 
 /* Creates a solver for one grid and allocates all workspace on the current

@@ -60,6 +60,7 @@ class Options(ctypes.Structure):
         ("retrain_after", ctypes.c_int),
         ("grow_blocks", ctypes.c_int),
         ("grow_tol", ctypes.c_double),
+        ("model", ctypes.c_int),
     ]
 
 
@@ -217,6 +218,8 @@ def default_options(**kw):
             v = GUESS_NAMES[v]
         if k == "fallback" and isinstance(v, str):
             v = GUESS_NAMES[v]
+        if k == "model" and isinstance(v, str):
+            v = {"conv": 0, "linear": 1}[v]
         if k == "precision" and isinstance(v, str):
             v = {"fp64": FP64, "fp32_refine": FP32_REFINE}[v]
         setattr(o, k, v)

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/mlgmres.h"
+#include "linear.h"
 #include "nn.h"
 #include "solver.h"
 
@@ -56,6 +57,8 @@ struct mlgmres {
 
   // ---- learned guess / training ----
   mlg::Net net;
+  mlg::Lin lin;                       // the dense linear model (opt.model = LINEAR)
+  bool linear = false;
   bool net_ready = false;             // trained at least once
   int train_calls = 0;
   // replay ring: normalised (b/s, x/s) pairs, FP32, N each

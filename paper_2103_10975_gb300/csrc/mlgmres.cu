@@ -102,6 +102,9 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
   ARG(o->retrain_after >= 0, "retrain_after must be >= 0");
   ARG(o->grow_blocks >= 0 && o->grow_blocks <= kMaxExtra, "grow_blocks must be in 0..4");
   ARG(o->grow_tol >= 0.0 && o->grow_tol <= 1.0, "grow_tol must be in [0, 1]");
+  ARG(o->model == MLGMRES_MODEL_CONV || o->model == MLGMRES_MODEL_LINEAR, "bad model");
+  ARG(o->model == MLGMRES_MODEL_CONV || o->grow_blocks == 0,
+      "grow_blocks applies to the convolutional model only");
 }
 
 // Bulk-copy stages the passes use for an FP32 basis in HBM.
@@ -114,7 +117,7 @@ int effective_stages(const mlgmres* h) {
 // Allocates the network, its replay ring and the learned-guess buffers (2D
 // and 3D networks; once per handle).
 void ensure_net(mlgmres* h) {
-  if (h->net.master) return;
+  if (h->net.master || h->lin.T) return;
   const mlgmres_options* opt = &h->opt;
   CK(cudaMalloc(&h->x_alt, sizeof(double) * h->ldv));
   CK(cudaMalloc(&h->x_tmp, sizeof(double) * h->ldv));
@@ -125,8 +128,28 @@ void ensure_net(mlgmres* h) {
   CK(cudaMalloc(&h->ddots, sizeof(double) * (2 * opt->replay_cap + 1)));
   CK(cudaMallocHost(&h->hdots, sizeof(double) * (2 * opt->replay_cap + 1)));
   CK(cudaMalloc(&h->loss_dev, sizeof(float) * 4));
-  CK(net_create(h->net, h->grid.n, opt->batch, opt->seed, h->grid.dim, opt->grow_blocks));
+  if (opt->model == MLGMRES_MODEL_LINEAR) {
+    ARG(h->N <= 4096, "the linear model needs N <= 4096");
+    h->linear = true;
+    CK(lin_create(h->lin, h->N, opt->batch));
+  } else {
+    CK(net_create(h->net, h->grid.n, opt->batch, opt->seed, h->grid.dim, opt->grow_blocks));
+  }
 }
+
+// Forward pass of the handle's model on `batch` normalised inputs.
+void model_forward(mlgmres* h, int batch, const float* u, float* y, cudaStream_t s) {
+  if (h->linear)
+    CK(lin_forward(h->lin, batch, u, y, s));
+  else
+    CK(net_forward(h->net, batch, u, y, s));
+}
+
+long long model_params(const mlgmres* h) {
+  return h->linear ? (long long)h->lin.N * h->lin.N : h->net.nparams;
+}
+float* model_master(mlgmres* h) { return h->linear ? h->lin.T : h->net.master; }
+float* model_grad(mlgmres* h) { return h->linear ? h->lin.grad : h->net.grad; }
 
 // The learned guess x0 = c s N(b/s) (s = rms(b), c the target scale of the
 // last training phase), then opt.guess_smooth damped-Jacobi sweeps; returns
@@ -135,7 +158,7 @@ double* learned_guess(mlgmres* h, const double* b, cudaStream_t s) {
   const int N = h->N;
   CK(launch_sumsq(b, N, h->scal, s));
   CK(launch_normalise(b, N, h->scal, h->u_in, s));
-  CK(net_forward(h->net, 1, h->u_in, h->y_out, s));
+  model_forward(h, 1, h->u_in, h->y_out, s);
   double* cur = h->x_alt;
   double* oth = h->x_tmp;
   CK(launch_denormalise(h->y_out, N, h->scal, h->c_train, cur, s));
@@ -333,8 +356,12 @@ void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
       pick[k++] = f;
     }
     while (k < B) pick[k++] = (int)(splitmix_next(h->rng_state) % (unsigned long long)h->ring_count);
-    CK(net_train_batch(h->net, B, h->ring_u, h->ring_t, h->ldv, pick.data(), tscale, h->opt.lr,
-                       h->loss_dev, s));
+    if (h->linear)
+      CK(lin_train_batch(h->lin, B, h->ring_u, h->ring_t, h->ldv, pick.data(), tscale,
+                         h->opt.lr, h->loss_dev, s));
+    else
+      CK(net_train_batch(h->net, B, h->ring_u, h->ring_t, h->ldv, pick.data(), tscale,
+                         h->opt.lr, h->loss_dev, s));
   }
   CK(cudaEventRecord(h->train_done, s));
   h->train_pending = true;
@@ -380,6 +407,7 @@ void mlgmres_default_options(mlgmres_options* o) {
   o->retrain_after = 0;
   o->grow_blocks = 0;
   o->grow_tol = 0.02;
+  o->model = MLGMRES_MODEL_CONV;
 }
 
 mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* opt,
@@ -487,6 +515,7 @@ void mlgmres_destroy(mlgmres_t h) {
   cudaFreeHost(h->hdots);
   cudaFree(h->loss_dev);
   net_destroy(h->net);
+  lin_destroy(h->lin);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev2) cudaEventDestroy(h->ev2);
@@ -726,7 +755,7 @@ mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_ho
   if (!h) return MLGMRES_ERR_ARG;
   h->last_error.clear();
   try {
-    if (!h->net.master) {  // no learned guess on this handle: nothing to train
+    if (!h->net.master && !h->lin.T) {  // no learned guess on this handle: nothing to train
       if (loss_host) *loss_host = -1.0f;
       return MLGMRES_OK;
     }
@@ -930,7 +959,7 @@ mlgmres_status mlgmres_nn_param_count(mlgmres_t h, long long* count) {
   } catch (const Fail& f) {
     return f.st;
   }
-  *count = h->net.nparams;
+  *count = model_params(h);
   return MLGMRES_OK;
 }
 
@@ -938,9 +967,9 @@ mlgmres_status mlgmres_nn_get_params(mlgmres_t h, float* p, long long count) {
   if (!h) return MLGMRES_ERR_ARG;
   try {
     ensure_net(h);
-    ARG(p && count == h->net.nparams, "bad parameter buffer");
+    ARG(p && count == model_params(h), "bad parameter buffer");
     CK(cudaDeviceSynchronize());
-    CK(cudaMemcpy(p, h->net.master, sizeof(float) * count, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(p, model_master(h), sizeof(float) * count, cudaMemcpyDeviceToHost));
     return MLGMRES_OK;
   } catch (const Fail& f) {
     return f.st;
@@ -951,13 +980,15 @@ mlgmres_status mlgmres_nn_set_params(mlgmres_t h, const float* p, long long coun
   if (!h) return MLGMRES_ERR_ARG;
   try {
     ensure_net(h);
-    ARG(p && count == h->net.nparams, "bad parameter buffer");
+    ARG(p && count == model_params(h), "bad parameter buffer");
     CK(cudaDeviceSynchronize());
-    CK(cudaMemcpy(h->net.master, p, sizeof(float) * count, cudaMemcpyHostToDevice));
-    CK(cudaMemset(h->net.adam_m, 0, sizeof(float) * count));
-    CK(cudaMemset(h->net.adam_v, 0, sizeof(float) * count));
-    h->net.adam_t = 0;
-    CK(net_sync_weights(h->net, 0));
+    CK(cudaMemcpy(model_master(h), p, sizeof(float) * count, cudaMemcpyHostToDevice));
+    if (!h->linear) {
+      CK(cudaMemset(h->net.adam_m, 0, sizeof(float) * count));
+      CK(cudaMemset(h->net.adam_v, 0, sizeof(float) * count));
+      h->net.adam_t = 0;
+      CK(net_sync_weights(h->net, 0));
+    }
     CK(cudaDeviceSynchronize());
     return MLGMRES_OK;
   } catch (const Fail& f) {
@@ -973,7 +1004,7 @@ mlgmres_status mlgmres_nn_forward(mlgmres_t h, int batch, const float* u, float*
     ARG(u && y, "bad arguments");
     ARG(batch >= 1 && batch <= h->opt.batch, "batch must be in 1..opt.batch");
     cudaStream_t s = (cudaStream_t)stream;
-    CK(net_forward(h->net, batch, u, y, s));
+    model_forward(h, batch, u, y, s);
     CK(cudaStreamSynchronize(s));
     return MLGMRES_OK;
   } catch (const Fail& f) {
@@ -991,10 +1022,13 @@ mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u, cons
     cudaStream_t s = (cudaStream_t)stream;
     float* y = nullptr;
     CK(cudaMallocAsync(&y, sizeof(float) * (size_t)batch * h->N, s));
-    CK(net_forward(h->net, batch, u, y, s));
-    CK(net_backward(h->net, batch, u, y, t, 1.0f, h->loss_dev, s));
+    model_forward(h, batch, u, y, s);
+    if (h->linear)
+      CK(lin_backward(h->lin, batch, u, y, t, 1.0f, h->loss_dev, s));
+    else
+      CK(net_backward(h->net, batch, u, y, t, 1.0f, h->loss_dev, s));
     CK(cudaMemcpyAsync(loss_host, h->loss_dev, sizeof(float), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(grad_host, h->net.grad, sizeof(float) * h->net.nparams,
+    CK(cudaMemcpyAsync(grad_host, model_grad(h), sizeof(float) * model_params(h),
                        cudaMemcpyDeviceToHost, s));
     CK(cudaFreeAsync(y, s));
     CK(cudaStreamSynchronize(s));

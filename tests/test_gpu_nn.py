@@ -1,5 +1,7 @@
 """GPU parity of the initial-guess network (Sec. 2.1) and its training step
 (Sec. 2.3) against the FP64 oracle at the same weights, through the C ABI."""
+import math
+
 import numpy as np
 import pytest
 
@@ -219,3 +221,28 @@ def test_grown_blocks_parity():
                            torch.as_tensor(t, dtype=torch.float32).cuda())
     base = sum(int(np.prod(sh)) for _, sh in onn.param_shapes(n))
     assert np.all(g0[base:] == 0)
+
+
+# --------------------------------------------- the dense linear model (Sec. 3.1)
+
+def test_linear_model_parity():
+    """model = linear: y = T u with the N x N matrix T as the parameters;
+    forward and the MSE gradient against their definitions."""
+    n = 16
+    N = n * n
+    s = Solver(n, m=10, batch=3, model="linear")
+    assert s.param_count() == N * N
+    assert np.all(s.get_params() == 0)             # T starts at 0
+    rng = np.random.default_rng(4)
+    T = (rng.standard_normal((N, N)) / math.sqrt(N)).astype(np.float32)
+    s.set_params(T.reshape(-1))
+    u = rng.standard_normal((3, N)).astype(np.float32)
+    t = rng.standard_normal((3, N)).astype(np.float32)
+    y = s.nn_forward(torch.as_tensor(u).cuda()).cpu().numpy()
+    yr = u.astype(np.float64) @ T.T.astype(np.float64)
+    assert np.abs(y - yr).max() <= 1e-4 * np.abs(yr).max()
+    loss, g = s.nn_loss_grad(torch.as_tensor(u).cuda(), torch.as_tensor(t).cuda())
+    d = yr - t
+    assert abs(loss - (d * d).mean()) <= 1e-4 * (d * d).mean()
+    gr = 2.0 / (3 * N) * d.T @ u.astype(np.float64)
+    assert np.abs(g.reshape(N, N) - gr).max() <= 1e-4 * np.abs(gr).max()
