@@ -60,6 +60,7 @@ class Options(ctypes.Structure):
         ("retrain_after", ctypes.c_int),
         ("grow_blocks", ctypes.c_int),
         ("grow_tol", ctypes.c_double),
+        ("compact", ctypes.c_int),
         ("model", ctypes.c_int),
     ]
 
@@ -74,14 +75,18 @@ class Tuning(ctypes.Structure):
         ("cand_stages", ctypes.c_int * 32),
         ("cand_us_per_step", ctypes.c_float * 32),
         ("from_cache", ctypes.c_int),
+        ("compact", ctypes.c_int),
+        ("cand_compact", ctypes.c_int * 32),
     ]
 
     def as_dict(self):
         k = self.candidates
         return {"grid_blocks": self.grid_blocks, "v_stages": self.v_stages,
                 "us_per_step": self.us_per_step, "from_cache": self.from_cache,
+                "compact": self.compact,
                 "candidates": [(self.cand_blocks[i], self.cand_stages[i],
-                                self.cand_us_per_step[i]) for i in range(k)]}
+                                self.cand_us_per_step[i], self.cand_compact[i])
+                               for i in range(k)]}
 
 
 class Result(ctypes.Structure):

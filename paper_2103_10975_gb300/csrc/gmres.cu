@@ -23,9 +23,36 @@ MLG_VARIANT(d2b)
 MLG_VARIANT(d3d)
 MLG_VARIANT(d3b)
 #undef MLG_VARIANT
+cudaError_t launch_gmres_f2c(const KParams& kp, int grid, cudaStream_t s);
+int max_blocks_f2c(int* bs, int extra);
+int own_bytes_f2c();
+
+bool gmres_compact_ok(bool fp32, int dim, int m) { return fp32 && dim == 2 && m < kCompactM; }
+
+int gmres_compact_cap(int m, int P) {
+  if (P <= 0) return 0;
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const long long budget = (long long)per_sm / 2 - 1024 - own_bytes_f2c();  // per CTA
+  const long long row = 32LL * 4;
+  const long long share = budget / 8 / 128 * 128;
+  const long long want = (long long)P * m * row;
+  const long long cap = want < share ? want : share;
+  return cap >= (long long)m * row ? (int)cap : 0;
+}
+
+int gmres_compact_max_blocks(int m) {
+  int bs = 0;
+  return max_blocks_f2c(&bs, 8 * gmres_compact_cap(m, kMaxStages));
+}
 
 cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid, cudaStream_t s) {
   if (dim == 3 && kp.vmode == kVShared) return cudaErrorInvalidValue;
+  if (kp.compact) {
+    if (!gmres_compact_ok(fp32, dim, kp.m) || kp.vmode != kVBulk) return cudaErrorInvalidValue;
+    return launch_gmres_f2c(kp, grid, s);
+  }
   if (fp32) {
     if (dim == 2) {
       if (kp.vmode == kVShared) return launch_gmres_f2s(kp, grid, s);

@@ -801,16 +801,16 @@ __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
 }
 
 // Bucket dispatch: the pass instantiated for the smallest multiple of 8 above j.
-#define MLG_BUCKETS(CALL)                   \
-  switch (j >> 3) {                         \
-    case 0: CALL(8); break;                 \
-    case 1: CALL(16); break;                \
-    case 2: CALL(24); break;                \
-    case 3: CALL(32); break;                \
-    case 4: CALL(40); break;                \
-    case 5: CALL(48); break;                \
-    case 6: CALL(56); break;                \
-    default: CALL(64); break;               \
+#define MLG_BUCKETS(CALL)                           \
+  switch (j >> 3) {                                 \
+    case 0: CALL(8); break;                         \
+    case 1: CALL(16); break;                        \
+    case 2: CALL(24); break;                        \
+    case 3: CALL(32); break;                        \
+    case 4: CALL(40); break;                        \
+    case 5: if constexpr (MAXM >= 48) { CALL(48); } break; \
+    case 6: if constexpr (MAXM >= 56) { CALL(56); } break; \
+    default: if constexpr (MAXM >= 64) { CALL(64); } break; \
   }
 
 // --------------------------------------------------------------- one solve --
@@ -1176,8 +1176,8 @@ finish:
   }
 }
 
-template <typename T, int DIM, int MAXM, int BS, int VM>
-__global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
+template <typename T, int DIM, int MAXM, int BS, int VM, int MINB = 1>
+__global__ void __launch_bounds__(BS, MINB) gmres_persistent(KParams kp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<T, MAXM, BS>& sm = *reinterpret_cast<Smem<T, MAXM, BS>*>(smem_raw);
   int g = 0;
@@ -1206,35 +1206,38 @@ __global__ void __launch_bounds__(BS, 1) gmres_persistent(KParams kp) {
 // The shared state lives in dynamic shared memory (about 90 KB for m <= 64),
 // followed by the CTA's slice of V (VM = kVShared) or the warps' bulk-copy
 // stages (VM = kVBulk).
-template <typename T, int DIM, int MAXM, int BS, int VM>
+template <typename T, int DIM, int MAXM, int BS, int VM, int MINB = 1>
 cudaError_t prepare_t(int extra = 0) {
-  return cudaFuncSetAttribute(gmres_persistent<T, DIM, MAXM, BS, VM>,
+  return cudaFuncSetAttribute(gmres_persistent<T, DIM, MAXM, BS, VM, MINB>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_own_bytes<T, MAXM, BS>() + extra);
 }
 
-template <typename T, int DIM, int MAXM, int BS, int VM>
+template <typename T, int DIM, int MAXM, int BS, int VM, int MINB = 1>
 cudaError_t launch_t(const KParams& kp, int grid, cudaStream_t s) {
+  if (kp.m > MAXM) return cudaErrorInvalidValue;
   int extra = 0;
   if (VM == kVShared) extra = kp.vsmem;
   if (VM == kVBulk) extra = (BS / 32) * kp.bulk_cap;
-  cudaError_t e = prepare_t<T, DIM, MAXM, BS, VM>(extra);
+  cudaError_t e = prepare_t<T, DIM, MAXM, BS, VM, MINB>(extra);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&kp};
   note_launches(1);
-  return cudaLaunchCooperativeKernel((const void*)gmres_persistent<T, DIM, MAXM, BS, VM>,
+  return cudaLaunchCooperativeKernel((const void*)gmres_persistent<T, DIM, MAXM, BS, VM, MINB>,
                                      dim3(grid), dim3(BS), args,
                                      smem_own_bytes<T, MAXM, BS>() + extra, s);
 }
 
-template <typename T, int DIM, int MAXM, int BS, int VM>
-int max_blocks_t(int* bs) {
+// Co-resident CTAs of the variant with `extra` bytes of dynamic shared memory
+// beyond its own state.
+template <typename T, int DIM, int MAXM, int BS, int VM, int MINB = 1>
+int max_blocks_t(int* bs, int extra = 0) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (prepare_t<T, DIM, MAXM, BS, VM>() != cudaSuccess) return 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gmres_persistent<T, DIM, MAXM, BS, VM>, BS,
-                                                smem_own_bytes<T, MAXM, BS>());
+  if (prepare_t<T, DIM, MAXM, BS, VM, MINB>(extra) != cudaSuccess) return 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gmres_persistent<T, DIM, MAXM, BS, VM, MINB>,
+                                                BS, smem_own_bytes<T, MAXM, BS>() + extra);
   *bs = BS;
   return per * nsm;
 }

@@ -22,6 +22,7 @@ struct mlgmres {
   int bs = 0;
   int vsmem = 0;        // shared-memory bytes for the V slice of a single solve
   int tuned_stages = -1;  // bulk-copy stages chosen by mlgmres_autotune (-1 = none)
+  int tuned_compact = 0;  // 1: the autotuner chose the two-CTAs-per-SM bulk variant
 
   // ---- solver workspace (one group for single solves) ----
   long long ldv = 0;

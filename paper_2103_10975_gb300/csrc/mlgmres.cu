@@ -103,6 +103,7 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
   ARG(o->grow_blocks >= 0 && o->grow_blocks <= kMaxExtra, "grow_blocks must be in 0..4");
   ARG(o->grow_tol >= 0.0 && o->grow_tol <= 1.0, "grow_tol must be in [0, 1]");
   ARG(o->model == MLGMRES_MODEL_CONV || o->model == MLGMRES_MODEL_LINEAR, "bad model");
+  ARG(o->compact >= -1 && o->compact <= 1, "compact must be -1, 0 or 1");
   ARG(o->model == MLGMRES_MODEL_CONV || o->grow_blocks == 0,
       "grow_blocks applies to the convolutional model only");
 }
@@ -170,6 +171,13 @@ double* learned_guess(mlgmres* h, const double* b, cudaStream_t s) {
   return cur;
 }
 
+// Whether single solves launch the compact bulk-copy variant.
+int use_compact(const mlgmres* h) {
+  if (h->opt.compact == 0) return 0;
+  if (h->opt.compact == 1) return 1;
+  return h->tuned_compact;
+}
+
 // Shared-memory bytes of a single solve's V slice at `blocks` CTAs (0 if the
 // slice does not fit).
 int single_vsmem(const mlgmres* h, int blocks) {
@@ -182,7 +190,8 @@ int single_vsmem(const mlgmres* h, int blocks) {
 // Run the persistent kernel for `count` tasks already staged in h->htasks,
 // with the group layout staged in h->hcfg / h->hwork.
 void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps,
-                cudaStream_t s, int vsmem = 0, long long max_iters = -1, int stages = -1) {
+                cudaStream_t s, int vsmem = 0, long long max_iters = -1, int stages = -1,
+                int compact = 0) {
   const size_t cfg_bytes = sizeof(int) * (size_t)(2 * (ngroups + 1) + ntasks);
   CK(cudaMemcpyAsync(h->dcfg, h->hcfg, cfg_bytes, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(h->dtasks, h->htasks, sizeof(SolveTask) * ntasks, cudaMemcpyHostToDevice,
@@ -205,6 +214,15 @@ void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps
   kp.vmode = kVDirect;
   if (kp.vsmem > 0 && h->grid.dim == 2) kp.vmode = kVShared;
   else if (kp.bulk_stages > 0) kp.vmode = kVBulk;
+  // the compact (two CTAs per SM) bulk variant, when chosen
+  kp.compact = 0;
+  if (compact && kp.vmode == kVBulk && gmres_compact_ok(h->fp32, h->grid.dim, h->opt.m)) {
+    const int cap = gmres_compact_cap(h->opt.m, kp.bulk_stages);
+    if (cap > 0) {
+      kp.compact = 1;
+      kp.bulk_cap = cap;
+    }
+  }
   kp.ngroups = ngroups;
   kp.group_first = h->dcfg;
   kp.task_first = h->dcfg + (ngroups + 1);
@@ -407,6 +425,7 @@ void mlgmres_default_options(mlgmres_options* o) {
   o->retrain_after = 0;
   o->grow_blocks = 0;
   o->grow_tol = 0.02;
+  o->compact = -1;
   o->model = MLGMRES_MODEL_CONV;
 }
 
@@ -431,11 +450,15 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     h->max_blocks = gmres_max_blocks(h->fp32, grid->dim, opt->m, &h->bs);
     CK(cudaGetLastError());
     ARG(h->max_blocks >= 1, "solver kernel cannot be resident");
-    h->blocks = opt->grid_blocks > 0 ? std::min(opt->grid_blocks, h->max_blocks)
-                                     : auto_blocks(h, h->N);
+    const bool force_compact =
+        opt->compact == 1 && gmres_compact_ok(h->fp32, grid->dim, opt->m);
+    const int maxb = force_compact ? std::max(h->max_blocks, gmres_compact_max_blocks(opt->m))
+                                   : h->max_blocks;
+    h->blocks = opt->grid_blocks > 0 ? std::min(opt->grid_blocks, maxb) : auto_blocks(h, h->N);
     h->blocks = std::min(h->blocks, kPartStride);
     h->ldv = ((long long)h->N + 63) / 64 * 64;
-    h->vsmem = single_vsmem(h, h->blocks);  // V slice in shared memory when it fits
+    // V slice in shared memory when it fits (the compact variant streams V)
+    h->vsmem = force_compact ? 0 : single_vsmem(h, h->blocks);
     const size_t es = h->fp32 ? sizeof(float) : sizeof(double);
     CK(cudaMalloc(&h->V, es * (size_t)(opt->m + 1) * h->ldv));
     CK(cudaMalloc(&h->W0, es * (size_t)h->ldv));
@@ -574,7 +597,7 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
       t.hist_cap = 0;
       t.zero_x = 0;
       stage_single(h, t, h->blocks);
-      run_solver(h, 1, 1, h->blocks, 0, s, h->vsmem, maxit);
+      run_solver(h, 1, 1, h->blocks, 0, s, h->vsmem, maxit, -1, use_compact(h));
       CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       return h->hres[0];
@@ -774,7 +797,7 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int blocks, stages;
+  int blocks, stages, compact;
   float us;
 };
 std::mutex g_tune_mu;
@@ -794,18 +817,20 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
     const TuneKey key{h->dev, h->grid.dim, h->grid.n, h->opt.m, h->fp32 ? 1 : 0};
     mlgmres_tuning t;
     memset(&t, 0, sizeof(t));
-    auto apply = [&](int blocks, int stages) {
+    auto apply = [&](int blocks, int stages, int compact) {
       if (h->opt.grid_blocks == 0) {
         h->blocks = blocks;
-        h->vsmem = single_vsmem(h, blocks);
+        h->vsmem = compact ? 0 : single_vsmem(h, blocks);
       }
       h->tuned_stages = stages;
+      h->tuned_compact = compact && h->opt.grid_blocks == 0 ? 1 : 0;
     };
     if (!retune) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune_cache.find(key);
       if (it != g_tune_cache.end()) {
-        apply(it->second.blocks, it->second.stages);
+        apply(it->second.blocks, it->second.stages, it->second.compact);
+        t.compact = h->tuned_compact;
         t.grid_blocks = h->blocks;
         t.v_stages = it->second.stages;
         t.us_per_step = it->second.us;
@@ -828,15 +853,30 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
         if (std::find(blocks.begin(), blocks.end(), c) == blocks.end()) blocks.push_back(c);
       }
     }
-    int best_b = h->blocks, best_p = -1;
+    int best_b = h->blocks, best_p = -1, best_c = 0;
     float best_us = INFINITY;
-    for (int nb : blocks) {
+    // the compact variant (two CTAs per SM) as well, where it applies
+    std::vector<std::pair<int, int>> shapes;  // (CTAs, compact)
+    for (int nb : blocks) shapes.push_back({nb, 0});
+    if (h->opt.compact == 1) shapes.clear();
+    if (h->opt.grid_blocks == 0 && h->opt.v_stages != 0 && h->opt.compact != 0 &&
+        gmres_compact_ok(h->fp32, h->grid.dim, h->opt.m)) {
+      const int cmax = std::min(gmres_compact_max_blocks(h->opt.m), kPartStride);
+      for (int c : {cap, std::min(2 * cap, cmax)})
+        if (c > 0 && single_vsmem(h, c) == 0) shapes.push_back({c, 1});
+    }
+    for (auto [nb, compact] : shapes) {
       const int vs = single_vsmem(h, nb);
       // 2D passes keep V in shared memory when the slice fits
       const bool shared = h->grid.dim == 2 && vs > 0;
       std::vector<int> stages;
       if (shared) {
+        if (compact) continue;
         stages.push_back(-1);
+      } else if (compact) {
+        for (int P : {2, 4, 8, 16})
+          if (gmres_compact_cap(h->opt.m, P) > 0 && (h->opt.v_stages < 0 || P == h->opt.v_stages))
+            stages.push_back(P);
       } else if (h->opt.v_stages >= 0) {
         stages.push_back(h->opt.v_stages);
       } else {
@@ -860,7 +900,7 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
         for (int rep = 0; rep < 2; rep++) {  // the first run warms up
           stage_single(h, tk, nb);
           CK(cudaEventRecord(h->ev0, s));
-          run_solver(h, 1, 1, nb, 0, s, vs, steps, P < 0 ? 0 : P);
+          run_solver(h, 1, 1, nb, 0, s, compact ? 0 : vs, steps, P < 0 ? 0 : P, compact);
           CK(cudaEventRecord(h->ev1, s));
           CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));
           CK(cudaStreamSynchronize(s));
@@ -872,24 +912,27 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
         t.cand_blocks[t.candidates] = nb;
         t.cand_stages[t.candidates] = P;
         t.cand_us_per_step[t.candidates] = us;
+        t.cand_compact[t.candidates] = compact;
         t.candidates++;
         if (us < best_us) {
           best_us = us;
           best_b = nb;
           best_p = P;
+          best_c = compact;
         }
       }
     }
     CK(cudaFree(xs));
     xs = nullptr;
-    apply(best_b, best_p);
+    apply(best_b, best_p, best_c);
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
-      g_tune_cache[key] = TuneVal{best_b, best_p, best_us};
+      g_tune_cache[key] = TuneVal{best_b, best_p, best_c, best_us};
     }
     t.grid_blocks = h->blocks;
     t.v_stages = best_p;
     t.us_per_step = best_us;
+    t.compact = h->tuned_compact;
     if (out) *out = t;
     return MLGMRES_OK;
   } catch (const Fail& f) {

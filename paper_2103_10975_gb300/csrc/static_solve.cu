@@ -129,6 +129,7 @@ extern "C" mlgmres_status mlgmres_solve_static(int n, int m, double rtol, long l
   kp.bulk_stages = 0;
   kp.bulk_cap = 0;
   kp.vmode = kVDirect;
+  kp.compact = 0;
   kp.ngroups = 1;
   kp.group_first = cfg;
   kp.task_first = cfg + 2;

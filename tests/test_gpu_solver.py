@@ -146,6 +146,20 @@ def test_fp32_basis_stage_counts(stages):
     assert abs(r["iters"] - r0["iters"]) <= max(3, r0["iters"] // 100)
 
 
+@pytest.mark.parametrize("n,blocks", [(256, 304), (250, 300)])
+def test_compact_variant(n, blocks):
+    """The two-CTAs-per-SM bulk-copy variant (128 registers, m <= 47): same
+    certificate, solution and iteration count as the standard variant."""
+    b = MovingGaussians2D(n, 2001, 500).rhs(11)
+    s = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", grid_blocks=blocks, compact=1)
+    x, r = s.solve(dev(b))
+    assert r["status"] == 0 and r["relres_true"] <= 1e-10
+    assert rel(x.cpu().numpy(), direct.dst_solve_2d(n, b)) <= 1e-7
+    ref = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", compact=0)
+    _, r0 = ref.solve(dev(b))
+    assert abs(r["iters"] - r0["iters"]) <= max(3, r0["iters"] // 100), (r["iters"], r0["iters"])
+
+
 def test_autotune_picks_the_fastest_candidate_and_caches():
     n = 512
     b = MovingGaussians2D(n, 2001, 500).rhs(2)
