@@ -149,15 +149,28 @@ struct Levels {
   int L;
 };
 
-// s[p][c] = sum_l upsample(z_l)[p][c]  (bilinear in 2D, trilinear in 3D)
+// s[p][c] = sum_l upsample(z_l)[p][c]  (bilinear in 2D, trilinear in 3D);
+// four threads per point, eight channels (16 bytes) each, so the
+// interpolation weights are computed once per 8 channels
 template <int D>
 __global__ void upsum_fwd(int B, int n, Levels lv, bf16* __restrict__ s) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= B * Geo<D>::pts(n) * kC) return;
-  const int c = (int)(i % kC);
+  if (i >= B * Geo<D>::pts(n) * 4) return;
+  const int cg = (int)(i & 3);
+  const long long p = i >> 2;
   int b, z, y, x;
-  Geo<D>::decode(i / kC, n, b, z, y, x);
-  float acc = __bfloat162float(lv.z[0][i]);
+  Geo<D>::decode(p, n, b, z, y, x);
+  float acc[8];
+  {
+    const uint4 v = *reinterpret_cast<const uint4*>(lv.z[0] + p * kC + cg * 8);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const float2 f = __bfloat1622float2(h[q]);
+      acc[2 * q] = f.x;
+      acc[2 * q + 1] = f.y;
+    }
+  }
   for (int l = 1; l < lv.L; l++) {
     const int m = lv.side[l];
     int z0 = 0, z1 = 0, y0, y1, x0, x1;
@@ -165,19 +178,27 @@ __global__ void upsum_fwd(int B, int n, Levels lv, bf16* __restrict__ s) {
     if (D == 3) bilin(z, m, n, z0, z1, lz);
     bilin(y, m, n, y0, y1, ly);
     bilin(x, m, n, x0, x1, lx);
-    const bf16* zl = lv.z[l] + c;
-    float v = 0.f;
 #pragma unroll
     for (int k = 0; k < (1 << D); k++) {
       const int zz = (k >> 2) & 1 ? z1 : z0, yy = (k >> 1) & 1 ? y1 : y0, xx = k & 1 ? x1 : x0;
       const float wz = D == 3 ? ((k >> 2) & 1 ? lz : 1.f - lz) : 1.f;
-      const float wy = (k >> 1) & 1 ? ly : 1.f - ly, wx = k & 1 ? lx : 1.f - lx;
+      const float w = wz * ((k >> 1) & 1 ? ly : 1.f - ly) * (k & 1 ? lx : 1.f - lx);
       const long long q = Geo<D>::nb(b, zz, yy, xx, 0, 0, 0, m);
-      v += wz * wy * wx * __bfloat162float(zl[q * kC]);
+      const uint4 v = *reinterpret_cast<const uint4*>(lv.z[l] + q * kC + cg * 8);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+      for (int qq = 0; qq < 4; qq++) {
+        const float2 f = __bfloat1622float2(h[qq]);
+        acc[2 * qq] += w * f.x;
+        acc[2 * qq + 1] += w * f.y;
+      }
     }
-    acc += v;
   }
-  s[i] = __float2bfloat16(acc);
+  uint4 o;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+  for (int q = 0; q < 4; q++) h[q] = __floats2bfloat162_rn(acc[2 * q], acc[2 * q + 1]);
+  *reinterpret_cast<uint4*>(s + p * kC + cg * 8) = o;
 }
 
 // y[p] = b + sum_tap sum_c w[c][tap] t[p + off_tap][c]
@@ -293,19 +314,36 @@ __global__ void __launch_bounds__(256) conv1_wgrad(int B, int n, const float* __
 #pragma unroll
   for (int t = 0; t < T; t++) acc[t] = 0.f;
   float accb = 0.f;
-  for (long long p = p0 + w; p < p1; p += 8) {
-    int b, z, y, x;
-    Geo<D>::decode(p, n, b, z, y, x);
-    const float gp = MODE == 0 ? g1[p] : g32[p * kC + c];
-    accb += gp;
+  // four consecutive points per warp and trip: their loads of each tap are
+  // issued together (the loop is latency-bound otherwise)
+  constexpr int U = 4;
+  for (long long p = p0 + (long long)w * U; p < p1; p += 8 * U) {
+    int b[U], z[U], y[U], x[U];
+    float gp[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      const long long pk = p + k;
+      if (pk < p1) {
+        Geo<D>::decode(pk, n, b[k], z[k], y[k], x[k]);
+        gp[k] = MODE == 0 ? g1[pk] : g32[pk * kC + c];
+      } else {
+        b[k] = z[k] = y[k] = x[k] = 0;
+        gp[k] = 0.f;
+      }
+      accb += gp[k];
+    }
 #pragma unroll
     for (int t = 0; t < T; t++) {
       int dz, dy, dx;
       Geo<D>::tap(t, dz, dy, dx);
-      const long long q = Geo<D>::nb(b, z, y, x, dz, dy, dx, n);
-      if (q < 0) continue;
-      const float v = MODE == 0 ? __bfloat162float(x32[q * kC + c]) : u[q];
-      acc[t] += gp * v;
+      float v[U];
+#pragma unroll
+      for (int k = 0; k < U; k++) {
+        const long long q = p + k < p1 ? Geo<D>::nb(b[k], z[k], y[k], x[k], dz, dy, dx, n) : -1;
+        v[k] = q < 0 ? 0.f : (MODE == 0 ? __bfloat162float(x32[q * kC + c]) : u[q]);
+      }
+#pragma unroll
+      for (int k = 0; k < U; k++) acc[t] += gp[k] * v[k];
     }
   }
 #pragma unroll
@@ -343,54 +381,58 @@ __global__ void mask_f32(long long count, const float* __restrict__ g,
 // here so the parameters keep the documented order (T taps).
 //   kind 0 (32->32): part index (tap*32 + k)*32 + o  -> param (o*32 + k)*T + tap; bias 1024 T + o
 //   kind 1/2 (1-ch): part index c*T + tap (+ 32 T + c bias) -> same order
-__global__ void reduce_wgrad(const float* __restrict__ part, int nparts, int stride, int kind,
-                             int T, float* __restrict__ gw, float* __restrict__ gb) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) reduce_wgrad(const float* __restrict__ part, int nparts,
+                                                    int stride, int kind, int T,
+                                                    float* __restrict__ gw,
+                                                    float* __restrict__ gb) {
+  // 32 outputs per CTA (lane = output), the CTA partials split over the 8 warps
+  // (coalesced rows), the 8 warp sums added in a fixed order
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   const int nw = kind == 0 ? T * kC * kC : T * kC;
   const int nb = kind == 0 ? kC : (kind == 1 ? kC : 1);
-  if (i >= nw + nb) return;
   double s = 0.0;
-  for (int c = 0; c < nparts; c++) s += part[(long long)c * stride + i];
+  if (i < nw + nb)
+    for (int c = w; c < nparts; c += 8) s += part[(long long)c * stride + i];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w != 0 || i >= nw + nb) return;
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) t += red[k][lane];
   if (i < nw) {
     if (kind == 0) {
       const int tp = i / (kC * kC), k = (i / kC) % kC, o = i % kC;
-      gw[(o * kC + k) * T + tp] = (float)s;
+      gw[(o * kC + k) * T + tp] = (float)t;
     } else {
-      gw[i] = (float)s;
+      gw[i] = (float)t;
     }
   } else {
-    gb[i - nw] = (float)s;
+    gb[i - nw] = (float)t;
   }
 }
 
 // Transpose of the linear upsampling from m to n along one axis of a tensor
 // viewed as (outer, n, inner) -> (outer, m, inner):
 //   out[o][j][c] = sum_x U[x][j] in[o][x][c],  U[x][j] = the weight of coarse j
-// in fine x's half-pixel interpolation.  The D-dimensional transpose is D such
-// passes, one per axis.
-__device__ __forceinline__ float up_weight(int f_idx, int m, int n, int j) {
-  int i0, i1;
-  float l;
-  bilin(f_idx, m, n, i0, i1, l);
-  return (i0 == j ? 1.f - l : 0.f) + (i1 == j ? l : 0.f);
-}
+// in fine x's half-pixel interpolation, read from the level's sparse rows
+// (built once on the host with the same arithmetic as bilin).  The
+// D-dimensional transpose is D such passes, one per axis.
 
 __global__ void upsample_bwd_axis(long long outer, int n, int m, long long inner,
-                                  const float* __restrict__ in, float* __restrict__ out) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= outer * m * inner) return;
-  const long long c = idx % inner;
-  const long long p = idx / inner;
+                                  const int* __restrict__ ptr, const int* __restrict__ idx,
+                                  const float* __restrict__ wt, const float* __restrict__ in,
+                                  float* __restrict__ out) {
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= outer * m * inner) return;
+  const long long c = id % inner;
+  const long long p = id / inner;
   const int j = (int)(p % m);
   const long long o = p / m;
-  const float f = (float)n / (float)m;
-  const int xlo = max(0, (int)floorf((j - 1.5f) * f)), xhi = min(n - 1, (int)ceilf((j + 2.5f) * f));
   float acc = 0.f;
-  for (int x = xlo; x <= xhi; x++) {
-    const float wx = up_weight(x, m, n, j);
-    if (wx != 0.f) acc += wx * in[(o * n + x) * inner + c];
-  }
-  out[idx] = acc;
+  for (int k = ptr[j]; k < ptr[j + 1]; k++) acc += wt[k] * in[(o * n + idx[k]) * inner + c];
+  out[id] = acc;
 }
 
 // fine[p][c] += coarse[p / 2][c] / 2^D (fine side s, coarse side s/2)
@@ -544,6 +586,39 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
     net.lvl_off[l] = net.pyr;
     net.pyr += sz;
   }
+  for (int l = 1; l < L; l++) {
+    const int m = net.side[l];
+    std::vector<std::vector<std::pair<int, float>>> rows(m);
+    for (int x = 0; x < n; x++) {
+      float src = ((float)x + 0.5f) * (float)m / (float)n - 0.5f;  // as bilin
+      if (src < 0.f) src = 0.f;
+      int i0 = (int)floorf(src);
+      if (i0 > m - 1) i0 = m - 1;
+      const int i1 = i0 + 1 < m - 1 ? i0 + 1 : m - 1;
+      const float lam = src - (float)i0;
+      if (i0 == i1) {
+        rows[i0].push_back({x, (1.f - lam) + lam});
+      } else {
+        rows[i0].push_back({x, 1.f - lam});
+        rows[i1].push_back({x, lam});
+      }
+    }
+    std::vector<int> ptr(m + 1, 0), idx;
+    std::vector<float> wt;
+    for (int j = 0; j < m; j++) {
+      for (auto& e : rows[j]) {
+        idx.push_back(e.first);
+        wt.push_back(e.second);
+      }
+      ptr[j + 1] = (int)idx.size();
+    }
+    NN_CK(cudaMalloc(&net.up_ptr[l], sizeof(int) * (m + 1)));
+    NN_CK(cudaMalloc(&net.up_idx[l], sizeof(int) * idx.size()));
+    NN_CK(cudaMalloc(&net.up_w[l], sizeof(float) * wt.size()));
+    NN_CK(cudaMemcpy(net.up_ptr[l], ptr.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice));
+    NN_CK(cudaMemcpy(net.up_idx[l], idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice));
+    NN_CK(cudaMemcpy(net.up_w[l], wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice));
+  }
   NN_CK(cudaMalloc(&net.s, sizeof(bf16) * full));
   NN_CK(cudaMalloc(&net.e, sizeof(bf16) * full));
   NN_CK(cudaMalloc(&net.t, sizeof(bf16) * full));
@@ -583,6 +658,9 @@ void net_destroy(Net& net) {
   for (int l = 0; l < kMaxLevels; l++) {
     cudaFree(net.pool[l]);
     cudaFree(net.z[l]);
+    cudaFree(net.up_ptr[l]);
+    cudaFree(net.up_idx[l]);
+    cudaFree(net.up_w[l]);
   }
   cudaFree(net.s);
   cudaFree(net.e);
@@ -642,7 +720,7 @@ cudaError_t forward_t(Net& net, int B, const float* u, float* y, cudaStream_t s)
     lv.z[l] = net.z[l];
     lv.side[l] = net.side[l];
   }
-  upsum_fwd<D><<<nblk(pix * kC, 256), 256, 0, s>>>(B, n, lv, net.s);
+  upsum_fwd<D><<<nblk(pix * 4, 256), 256, 0, s>>>(B, n, lv, net.s);
   note_launches(1);
   NN_CK(launch_conv32_mma(D, 1, B, n, net.s, net.wqT + per * L, net.master + net.off_b[L + 1], 2,
                           1, net.e, net.t, net.s, nullptr, nullptr, s));
@@ -681,7 +759,7 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   conv1_wgrad<0, D><<<P, 256, 0, s>>>(B, n, net.gy, tfin, nullptr, nullptr, net.wgrad_part,
                                       stride);
   note_launches(1);
-  reduce_wgrad<<<nblk(T * kC + 1, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 2, T,
+  reduce_wgrad<<<nblk(T * kC + 1, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 2, T,
                                                      net.grad + net.off_w[L + 2],
                                                      net.grad + net.off_b[L + 2]);
   note_launches(1);
@@ -700,7 +778,7 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
       mask_to_bf16<<<nblk(full, 256), 256, 0, s>>>(full, gcur, net.te[r], net.g_bf);
       note_launches(1);
       NN_CK(launch_wgrad_mma(D, B, n, tin, net.g_bf, 2, net.wgrad_part, stride, P, s));
-      reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
+      reduce_wgrad<<<nblk(per + kC, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
                                                        net.grad + net.off_rw[r],
                                                        net.grad + net.off_rb[r]);
       note_launches(1);
@@ -715,7 +793,7 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   mask_to_bf16<<<nblk(full, 256), 256, 0, s>>>(full, net.g_t, net.e, net.g_bf);
   note_launches(1);
   NN_CK(launch_wgrad_mma(D, B, n, net.s, net.g_bf, 2, net.wgrad_part, stride, P, s));
-  reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
+  reduce_wgrad<<<nblk(per + kC, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
                                                    net.grad + net.off_w[L + 1],
                                                    net.grad + net.off_b[L + 1]);
   note_launches(1);
@@ -730,20 +808,23 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
       // transposed upsampling, one axis at a time (x, y, then z); g_t and
       // g_lvl are free here (the residual block's gradient is already in g_s)
       const long long nn = n, m = sd;
+      const int* up = net.up_ptr[l];
+      const int* ui = net.up_idx[l];
+      const float* uw = net.up_w[l];
       if (D == 2) {
-        upsample_bwd_axis<<<nblk(B * nn * m * kC, 256), 256, 0, s>>>(B * nn, n, sd, kC, net.g_s,
-                                                                     net.g_t);
-        upsample_bwd_axis<<<nblk(B * m * m * kC, 256), 256, 0, s>>>(B, n, sd, m * kC, net.g_t,
-                                                                    net.g_lvl);
+        upsample_bwd_axis<<<nblk(B * nn * m * kC, 256), 256, 0, s>>>(B * nn, n, sd, kC, up, ui,
+                                                                     uw, net.g_s, net.g_t);
+        upsample_bwd_axis<<<nblk(B * m * m * kC, 256), 256, 0, s>>>(B, n, sd, m * kC, up, ui, uw,
+                                                                    net.g_t, net.g_lvl);
         note_launches(2);
         gz = net.g_lvl;
       } else {
-        upsample_bwd_axis<<<nblk(B * nn * nn * m * kC, 256), 256, 0, s>>>(B * nn * nn, n, sd, kC,
-                                                                          net.g_s, net.g_t);
-        upsample_bwd_axis<<<nblk(B * nn * m * m * kC, 256), 256, 0, s>>>(B * nn, n, sd, m * kC,
-                                                                         net.g_t, net.g_lvl);
-        upsample_bwd_axis<<<nblk(B * m * m * m * kC, 256), 256, 0, s>>>(B, n, sd, m * m * kC,
-                                                                        net.g_lvl, net.g_t);
+        upsample_bwd_axis<<<nblk(B * nn * nn * m * kC, 256), 256, 0, s>>>(
+            B * nn * nn, n, sd, kC, up, ui, uw, net.g_s, net.g_t);
+        upsample_bwd_axis<<<nblk(B * nn * m * m * kC, 256), 256, 0, s>>>(
+            B * nn, n, sd, m * kC, up, ui, uw, net.g_t, net.g_lvl);
+        upsample_bwd_axis<<<nblk(B * m * m * m * kC, 256), 256, 0, s>>>(
+            B, n, sd, m * m * kC, up, ui, uw, net.g_lvl, net.g_t);
         note_launches(3);
         gz = net.g_t;
       }
@@ -752,7 +833,7 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
     note_launches(1);
     const bf16* in = l == 0 ? net.a0 : net.pool[l];
     NN_CK(launch_wgrad_mma(D, B, sd, in, net.g_bf, 1, net.wgrad_part, stride, P, s));
-    reduce_wgrad<<<nblk(per + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
+    reduce_wgrad<<<nblk(per + kC, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
                                                      net.grad + net.off_w[1 + l],
                                                      net.grad + net.off_b[1 + l]);
     note_launches(1);
@@ -773,7 +854,7 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   conv1_wgrad<1, D><<<P, 256, 0, s>>>(B, n, nullptr, nullptr, net.g_lvl, u, net.wgrad_part,
                                       stride);
   note_launches(1);
-  reduce_wgrad<<<nblk(T * kC + kC, 256), 256, 0, s>>>(net.wgrad_part, P, stride, 1, T,
+  reduce_wgrad<<<nblk(T * kC + kC, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 1, T,
                                                       net.grad + net.off_w[0],
                                                       net.grad + net.off_b[0]);
   note_launches(1);

@@ -75,6 +75,11 @@ struct Net {
   float* bt = nullptr;                       // gathered minibatch targets
   float* by = nullptr;                       // minibatch outputs
   long long lvl_off[kMaxLevels];             // offsets of level l inside g_pool (per sample)
+  // transposed linear upsampling n -> side[l], per axis, as sparse rows:
+  // coarse j takes sum over k in [up_ptr[j], up_ptr[j+1]) of up_w[k] * fine[up_idx[k]]
+  int* up_ptr[kMaxLevels] = {};
+  int* up_idx[kMaxLevels] = {};
+  float* up_w[kMaxLevels] = {};
   long long pyr = 0;                         // sum of level sizes (pixels) per sample
   int wparts = 0;                            // CTAs of the weight-gradient kernels
 };

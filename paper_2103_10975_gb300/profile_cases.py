@@ -7,8 +7,9 @@
 
     python -m paper_2103_10975_gb300.profile_cases dipole --n 64 --T 200
 
---stages selects the bulk-copy depth for an FP32 basis in HBM (0 = direct
-loads, -1 = automatic); --autotune runs mlgmres_autotune first.
+--stages selects the bulk-copy depth for a basis in HBM (0 = direct loads,
+-1 = automatic); --compact 1 forces the two-CTAs-per-SM variant; --autotune
+runs mlgmres_autotune first.
 
 `solve` runs the same capped solve twice on one moving-Gaussian right-hand
 side (the second launch is the one to capture) and prints the device time
@@ -26,7 +27,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def solve_case(n, blocks, max_iters, m, precision, source, stages=-1, autotune=False):
+def solve_case(n, blocks, max_iters, m, precision, source, stages=-1, autotune=False,
+               compact=-1):
     import torch
     from paper_2103_10975_gb300 import Solver
     from synthetic import MovingGaussians2D, RandomWalkSources2D
@@ -36,7 +38,7 @@ def solve_case(n, blocks, max_iters, m, precision, source, stages=-1, autotune=F
         b = MovingGaussians2D(n, 2001, 500).rhs(0)
     bd = torch.as_tensor(b).cuda()
     s = Solver(n, m=m, rtol=1e-10, precision=precision, grid_blocks=blocks, max_iters=max_iters,
-               v_stages=stages)
+               v_stages=stages, compact=compact)
     if autotune:
         t = s.autotune(bd, retune=True)
         print("autotune:", t)
@@ -160,6 +162,7 @@ def main(argv=None):
     a.add_argument("--source", default="moving", choices=["moving", "walk"])
     a.add_argument("--stages", type=int, default=-1)
     a.add_argument("--autotune", action="store_true")
+    a.add_argument("--compact", type=int, default=-1)
     b = sub.add_parser("nn")
     b.add_argument("--n", type=int, default=256)
     b.add_argument("--batch", type=int, default=8)
@@ -187,7 +190,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.case == "solve":
         solve_case(args.n, args.blocks, args.max_iters, args.m, args.precision, args.source,
-                   args.stages, args.autotune)
+                   args.stages, args.autotune, args.compact)
     elif args.case == "nn":
         nn_case(args.n, args.batch, args.dim)
     elif args.case == "batch":
