@@ -44,6 +44,7 @@ struct mlgmres {
   int group_cap = 0;                  // capacity (groups) of the group buffers
   // batched solves: one-CTA groups with their own bases
   int batch_groups = 0;
+  bool batch_compact = false;         // batches may launch the compact variant
   void* Vb = nullptr;
   void* Wb = nullptr;                 // 2 work vectors per group
   double* partb = nullptr;

@@ -467,7 +467,13 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     h->group_cap = 1;
     h->cfg_cap = 1;
     if (opt->batch_slots > 0) {
-      h->batch_groups = std::min(opt->batch_slots, h->max_blocks);
+      // batches may run the compact variant (two CTAs per SM) when V streams
+      // from HBM: reserve workspaces for that many groups
+      h->batch_compact = opt->compact != 0 && gmres_compact_ok(h->fp32, grid->dim, opt->m);
+      const int bmax = h->batch_compact
+                           ? std::max(h->max_blocks, gmres_compact_max_blocks(opt->m))
+                           : h->max_blocks;
+      h->batch_groups = std::min(opt->batch_slots, bmax);
       h->group_cap = std::max(h->group_cap, h->batch_groups);
       h->cfg_cap = kBatchCap;
       const size_t G = (size_t)h->batch_groups;
@@ -691,7 +697,25 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
     // CTA groups in proportion to the systems' cost (see schedule.cu)
     std::vector<int> sides(count), gctas, gof, order;
     for (int i = 0; i < count; i++) sides[i] = grids[i].n;
-    const int G = plan_batch(dim, count, sides.data(), h->batch_groups, gctas, gof, order);
+    const size_t es0 = h->fp32 ? sizeof(float) : sizeof(double);
+    // shared-memory bytes of the largest CTA slice of V under a plan (0: does not fit)
+    auto slice_need = [&](const std::vector<int>& gc, const std::vector<int>& go) {
+      long long need = 0;
+      for (int i = 0; i < count; i++) {
+        const long long N = grid_points(dim, grids[i].n);
+        const long long k = gc[go[i]];
+        const long long chunk = ((N + k - 1) / k + 31) / 32 * 32;
+        need = std::max(need, chunk * (h->opt.m + 1) * (long long)es0);
+      }
+      return need <= gmres_vsmem_budget(h->fp32) ? (int)need : 0;
+    };
+    // one CTA per SM first; if the basis streams from HBM anyway, the compact
+    // variant (two CTAs per SM) gets all the reserved CTAs
+    int G = plan_batch(dim, count, sides.data(), std::min(h->batch_groups, h->max_blocks), gctas,
+                       gof, order);
+    const int vsmem = slice_need(gctas, gof);
+    const bool compact = vsmem == 0 && h->batch_compact && h->batch_groups > h->max_blocks;
+    if (compact) G = plan_batch(dim, count, sides.data(), h->batch_groups, gctas, gof, order);
     ARG(G >= 1 && G <= h->batch_groups, "batch schedule failed");
     int* gf = h->hcfg;
     int* tf = h->hcfg + (G + 1);
@@ -738,20 +762,9 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
       w.bar.timeout_ns = (unsigned long long)(h->opt.barrier_timeout_s * 1e9);
       h->hwork[g] = w;
     }
-    int vsmem = 0;
-    {
-      long long need = 0;
-      for (int i = 0; i < count; i++) {
-        const long long N = grid_points(dim, grids[i].n);
-        const long long k = gctas[gof[i]];
-        const long long chunk = ((N + k - 1) / k + 31) / 32 * 32;
-        need = std::max(need, chunk * (h->opt.m + 1) * (long long)es);
-      }
-      const int budget = gmres_vsmem_budget(h->fp32);
-      vsmem = need <= budget ? (int)need : 0;
-    }
     CK(cudaEventRecord(h->ev0, s));
-    run_solver(h, G, count, grid_ctas, 0, s, vsmem);
+    run_solver(h, G, count, grid_ctas, 0, s, vsmem, -1, -1,
+               (compact || (vsmem == 0 && h->batch_compact)) ? 1 : 0);
     CK(cudaEventRecord(h->ev1, s));
     CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult) * count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

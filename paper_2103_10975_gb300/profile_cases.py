@@ -67,7 +67,7 @@ def nn_case(n, batch, dim=2):
                                                                1e3 * sum(times[2:]) / 5))
 
 
-def batch_case(count, nmin, nmax, rtol, m, stages=-1):
+def batch_case(count, nmin, nmax, rtol, m, stages=-1, compact=-1):
     """Independent systems with sides drawn from U{nmin..nmax} (seed 4001 + i),
     FP32-refined GMRES(m), all in one persistent launch."""
     import torch
@@ -77,7 +77,7 @@ def batch_case(count, nmin, nmax, rtol, m, stages=-1):
     ns = [n for n, _ in inst]
     bs = [torch.as_tensor(b).cuda() for _, b in inst]
     s = Solver(max(ns), m=m, rtol=rtol, precision="fp32_refine", batch_slots=4096,
-               max_iters=10 ** 7, v_stages=stages)
+               max_iters=10 ** 7, v_stages=stages, compact=compact)
     xs, res = s.solve_batch(ns, bs)
     worst = max(r["relres_true"] for r in res)
     iters = sum(r["iters"] for r in res)
@@ -174,6 +174,7 @@ def main(argv=None):
     c.add_argument("--rtol", type=float, default=1e-8)
     c.add_argument("--m", type=int, default=30)
     c.add_argument("--stages", type=int, default=-1)
+    c.add_argument("--compact", type=int, default=-1)
     d = sub.add_parser("cube")
     d.add_argument("--n", type=int, default=192)
     d.add_argument("--m", type=int, default=50)
@@ -194,7 +195,7 @@ def main(argv=None):
     elif args.case == "nn":
         nn_case(args.n, args.batch, args.dim)
     elif args.case == "batch":
-        batch_case(args.count, args.nmin, args.nmax, args.rtol, args.m, args.stages)
+        batch_case(args.count, args.nmin, args.nmax, args.rtol, args.m, args.stages, args.compact)
     elif args.case == "dipole":
         dipole_case(args.n, args.T, args.tau0, args.train_iters, args.lr, args.k)
     else:
