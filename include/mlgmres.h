@@ -138,9 +138,11 @@ typedef struct {
                                 depth) */
   double grow_tol;           /* stagnation: M_p(E_k) at a training phase is above
                                 (1 - grow_tol) times its value at the previous phase */
-  int compact;               /* the two-CTAs-per-SM bulk-copy variant for FP32 2D grids with
-                                m <= 47 and V in HBM: -1 = if the autotuner chose it, 0 =
-                                never, 1 = always (where it applies) */
+  int compact;               /* the two-CTAs-per-SM variants (at most 128 registers, smaller
+                                shared state) for FP32 grids: 2D with m <= 47 (V slices in
+                                shared memory when they fit, else streamed), 3D with m <= 44
+                                (streamed): -1 = if the autotuner chose it, 0 = never, 1 =
+                                always (where it applies) */
   int model;                 /* MLGMRES_MODEL_CONV: the multi-scale network of Sec. 2.1;
                                 MLGMRES_MODEL_LINEAR: one dense layer x0 = c s T (b/s) =
                                 c T b (the simplified model of Sec. 3.1, for studying the
@@ -324,8 +326,8 @@ typedef struct {
   int cand_stages[32];
   float cand_us_per_step[32];
   int from_cache;         /* 1: taken from the process-wide cache, nothing was timed */
-  int compact;            /* 1: the chosen shape is the compact variant (FP32 2D bulk-copy,
-                             m <= 47, two CTAs of at most 128 registers per SM) */
+  int compact;            /* 1: the chosen shape is a compact variant (two CTAs of at most
+                             128 registers per SM; see mlgmres_options.compact) */
   int cand_compact[32];
 } mlgmres_tuning;
 
@@ -333,8 +335,8 @@ typedef struct {
  * Arnoldi steps (0 = 2m) of A x = b_dev from x0 = 0, with the handle's
  * precision and m, for candidate launch shapes -- CTA counts around one per
  * 512 grid points (x1/2, x1, x2, and the co-resident maximum) and, for an FP32
- * basis held in HBM, 0/2/4/8/16 bulk-copy stages, and for FP32 2D grids with
- * m <= 47 the compact variant at one and two CTAs per SM -- and keeps the fastest per
+ * basis held in HBM, 0/2/4/8/16 bulk-copy stages, and for FP32 grids the compact
+ * variants at one and two CTAs per SM -- and keeps the fastest per
  * step for this handle's later solves (options grid_blocks and v_stages set
  * explicitly at create still win).  Results are cached per process by
  * (device, dim, n, m, precision); a cached shape is reused without timing

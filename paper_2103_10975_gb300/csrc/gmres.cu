@@ -26,15 +26,20 @@ MLG_VARIANT(d3b)
 cudaError_t launch_gmres_f2c(const KParams& kp, int grid, cudaStream_t s);
 int max_blocks_f2c(int* bs, int extra);
 int own_bytes_f2c();
+cudaError_t launch_gmres_f3c(const KParams& kp, int grid, cudaStream_t s);
+cudaError_t launch_gmres_f2cs(const KParams& kp, int grid, cudaStream_t s);
+int max_blocks_f3c(int* bs, int extra);
+int own_bytes_f3c();
 
-bool gmres_compact_ok(bool fp32, int dim, int m) { return fp32 && dim == 2 && m < kCompactM; }
 
-int gmres_compact_cap(int m, int P) {
+
+int gmres_compact_cap(int dim, int m, int P) {
   if (P <= 0) return 0;
   int dev = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  const long long budget = (long long)per_sm / 2 - 1024 - own_bytes_f2c();  // per CTA
+  const int own = dim == 2 ? own_bytes_f2c() : own_bytes_f3c();
+  const long long budget = (long long)per_sm / 2 - 1024 - own;  // per CTA
   const long long row = 32LL * 4;
   const long long share = budget / 8 / 128 * 128;
   const long long want = (long long)P * m * row;
@@ -42,16 +47,33 @@ int gmres_compact_cap(int m, int P) {
   return cap >= (long long)m * row ? (int)cap : 0;
 }
 
-int gmres_compact_max_blocks(int m) {
+bool gmres_compact_ok(bool fp32, int dim, int m) {
+  // and one stage of m rows must fit in a warp's share (3D: m <= 44 on GB300)
+  return fp32 && (dim == 2 ? m < kCompactM2 : m < kCompactM3) && gmres_compact_cap(dim, m, 1) > 0;
+}
+
+int gmres_compact_vsmem_budget() {
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int left = per_sm / 2 - 1024 - own_bytes_f2c();
+  return left > 0 ? left : 0;
+}
+
+int gmres_compact_max_blocks(int dim, int m) {
   int bs = 0;
-  return max_blocks_f2c(&bs, 8 * gmres_compact_cap(m, kMaxStages));
+  const int extra = 8 * gmres_compact_cap(dim, m, kMaxStages);
+  return dim == 2 ? max_blocks_f2c(&bs, extra) : max_blocks_f3c(&bs, extra);
 }
 
 cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid, cudaStream_t s) {
   if (dim == 3 && kp.vmode == kVShared) return cudaErrorInvalidValue;
   if (kp.compact) {
-    if (!gmres_compact_ok(fp32, dim, kp.m) || kp.vmode != kVBulk) return cudaErrorInvalidValue;
-    return launch_gmres_f2c(kp, grid, s);
+    if (!gmres_compact_ok(fp32, dim, kp.m) || kp.vmode == kVDirect ||
+        (dim == 3 && kp.vmode == kVShared))
+      return cudaErrorInvalidValue;
+    if (dim == 2 && kp.vmode == kVShared) return launch_gmres_f2cs(kp, grid, s);
+    return dim == 2 ? launch_gmres_f2c(kp, grid, s) : launch_gmres_f3c(kp, grid, s);
   }
   if (fp32) {
     if (dim == 2) {

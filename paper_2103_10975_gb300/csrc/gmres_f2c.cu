@@ -9,13 +9,13 @@
 namespace mlg {
 
 cudaError_t launch_gmres_f2c(const KParams& kp, int grid, cudaStream_t s) {
-  return launch_t<float, 2, kCompactM, 256, kVBulk, 2>(kp, grid, s);
+  return launch_t<float, 2, kCompactM2, 256, kVBulk, 2>(kp, grid, s);
 }
 
 int max_blocks_f2c(int* bs, int extra) {
-  return max_blocks_t<float, 2, kCompactM, 256, kVBulk, 2>(bs, extra);
+  return max_blocks_t<float, 2, kCompactM2, 256, kVBulk, 2>(bs, extra);
 }
 
-int own_bytes_f2c() { return (int)smem_own_bytes<float, kCompactM, 256>(); }
+int own_bytes_f2c() { return (int)smem_own_bytes<float, kCompactM2, 256>(); }
 
 }  // namespace mlg

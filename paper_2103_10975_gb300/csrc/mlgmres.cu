@@ -180,10 +180,11 @@ int use_compact(const mlgmres* h) {
 
 // Shared-memory bytes of a single solve's V slice at `blocks` CTAs (0 if the
 // slice does not fit).
-int single_vsmem(const mlgmres* h, int blocks) {
+int single_vsmem(const mlgmres* h, int blocks, bool compact = false) {
   const long long chunk = (((long long)h->N + blocks - 1) / blocks + 31) / 32 * 32;
   const long long need = chunk * (h->opt.m + 1) * (h->fp32 ? 4 : 8);
-  const int budget = gmres_vsmem_budget(h->fp32);
+  const int budget = compact ? (h->grid.dim == 2 ? gmres_compact_vsmem_budget() : 0)
+                             : gmres_vsmem_budget(h->fp32);
   return need <= budget ? (int)need : 0;
 }
 
@@ -216,11 +217,15 @@ void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps
   else if (kp.bulk_stages > 0) kp.vmode = kVBulk;
   // the compact (two CTAs per SM) bulk variant, when chosen
   kp.compact = 0;
-  if (compact && kp.vmode == kVBulk && gmres_compact_ok(h->fp32, h->grid.dim, h->opt.m)) {
-    const int cap = gmres_compact_cap(h->opt.m, kp.bulk_stages);
-    if (cap > 0) {
-      kp.compact = 1;
-      kp.bulk_cap = cap;
+  if (compact && gmres_compact_ok(h->fp32, h->grid.dim, h->opt.m)) {
+    if (kp.vmode == kVBulk) {
+      const int cap = gmres_compact_cap(h->grid.dim, h->opt.m, kp.bulk_stages);
+      if (cap > 0) {
+        kp.compact = 1;
+        kp.bulk_cap = cap;
+      }
+    } else if (kp.vmode == kVShared && kp.vsmem <= gmres_compact_vsmem_budget()) {
+      kp.compact = 1;  // V slices in shared memory, two CTAs per SM
     }
   }
   kp.ngroups = ngroups;
@@ -452,13 +457,13 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     ARG(h->max_blocks >= 1, "solver kernel cannot be resident");
     const bool force_compact =
         opt->compact == 1 && gmres_compact_ok(h->fp32, grid->dim, opt->m);
-    const int maxb = force_compact ? std::max(h->max_blocks, gmres_compact_max_blocks(opt->m))
+    const int maxb = force_compact ? std::max(h->max_blocks, gmres_compact_max_blocks(grid->dim, opt->m))
                                    : h->max_blocks;
     h->blocks = opt->grid_blocks > 0 ? std::min(opt->grid_blocks, maxb) : auto_blocks(h, h->N);
     h->blocks = std::min(h->blocks, kPartStride);
     h->ldv = ((long long)h->N + 63) / 64 * 64;
     // V slice in shared memory when it fits (the compact variant streams V)
-    h->vsmem = force_compact ? 0 : single_vsmem(h, h->blocks);
+    h->vsmem = single_vsmem(h, h->blocks, force_compact);
     const size_t es = h->fp32 ? sizeof(float) : sizeof(double);
     CK(cudaMalloc(&h->V, es * (size_t)(opt->m + 1) * h->ldv));
     CK(cudaMalloc(&h->W0, es * (size_t)h->ldv));
@@ -471,7 +476,7 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
       // from HBM: reserve workspaces for that many groups
       h->batch_compact = opt->compact != 0 && gmres_compact_ok(h->fp32, grid->dim, opt->m);
       const int bmax = h->batch_compact
-                           ? std::max(h->max_blocks, gmres_compact_max_blocks(opt->m))
+                           ? std::max(h->max_blocks, gmres_compact_max_blocks(grid->dim, opt->m))
                            : h->max_blocks;
       h->batch_groups = std::min(opt->batch_slots, bmax);
       h->group_cap = std::max(h->group_cap, h->batch_groups);
@@ -833,7 +838,7 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
     auto apply = [&](int blocks, int stages, int compact) {
       if (h->opt.grid_blocks == 0) {
         h->blocks = blocks;
-        h->vsmem = compact ? 0 : single_vsmem(h, blocks);
+        h->vsmem = single_vsmem(h, blocks, compact != 0);
       }
       h->tuned_stages = stages;
       h->tuned_compact = compact && h->opt.grid_blocks == 0 ? 1 : 0;
@@ -874,21 +879,23 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
     if (h->opt.compact == 1) shapes.clear();
     if (h->opt.grid_blocks == 0 && h->opt.v_stages != 0 && h->opt.compact != 0 &&
         gmres_compact_ok(h->fp32, h->grid.dim, h->opt.m)) {
-      const int cmax = std::min(gmres_compact_max_blocks(h->opt.m), kPartStride);
-      for (int c : {cap, std::min(2 * cap, cmax)})
-        if (c > 0 && single_vsmem(h, c) == 0) shapes.push_back({c, 1});
+      const int cmax = std::min(gmres_compact_max_blocks(h->grid.dim, h->opt.m), kPartStride);
+      std::vector<int> cs = {cap, std::min(2 * cap, cmax)};
+      const int two = std::min(2 * auto_blocks(h, h->N), cmax);
+      if (std::find(cs.begin(), cs.end(), two) == cs.end()) cs.push_back(two);
+      for (int c : cs)
+        if (c > 0) shapes.push_back({c, 1});
     }
     for (auto [nb, compact] : shapes) {
-      const int vs = single_vsmem(h, nb);
+      const int vs = single_vsmem(h, nb, compact != 0);
       // 2D passes keep V in shared memory when the slice fits
       const bool shared = h->grid.dim == 2 && vs > 0;
       std::vector<int> stages;
       if (shared) {
-        if (compact) continue;
         stages.push_back(-1);
       } else if (compact) {
         for (int P : {2, 4, 8, 16})
-          if (gmres_compact_cap(h->opt.m, P) > 0 && (h->opt.v_stages < 0 || P == h->opt.v_stages))
+          if (gmres_compact_cap(h->grid.dim, h->opt.m, P) > 0 && (h->opt.v_stages < 0 || P == h->opt.v_stages))
             stages.push_back(P);
       } else if (h->opt.v_stages >= 0) {
         stages.push_back(h->opt.v_stages);
@@ -913,7 +920,7 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
         for (int rep = 0; rep < 2; rep++) {  // the first run warms up
           stage_single(h, tk, nb);
           CK(cudaEventRecord(h->ev0, s));
-          run_solver(h, 1, 1, nb, 0, s, compact ? 0 : vs, steps, P < 0 ? 0 : P, compact);
+          run_solver(h, 1, 1, nb, 0, s, vs, steps, P < 0 ? 0 : P, compact);
           CK(cudaEventRecord(h->ev1, s));
           CK(cudaMemcpyAsync(h->hres, h->dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s));
           CK(cudaStreamSynchronize(s));

@@ -8,7 +8,9 @@
 namespace mlg {
 
 constexpr int kMaxM = 64;          // largest supported restart length
-constexpr int kCompactM = 48;      // bucket limit of the compact (2 CTAs per SM) variant: m <= 47
+// bucket limits of the compact (2 CTAs per SM) variants: m <= 47 (2D), m <= 55 (3D)
+constexpr int kCompactM2 = 48;
+constexpr int kCompactM3 = 56;
 // Where a launch keeps the basis V (one kernel variant each):
 constexpr int kVDirect = 0;  // HBM, loaded into registers by the passes
 constexpr int kVShared = 1;  // each CTA's slice in shared memory (2D)
@@ -65,7 +67,7 @@ struct KParams {
   int bulk_stages;          // most bulk-copy stages per warp when V is in HBM (0 = off)
   int bulk_cap;             // bytes of staging area per warp (>= m 32-point rows)
   int vmode;                // kVDirect | kVShared | kVBulk (the kernel variant launched)
-  int compact;              // 1: the two-CTAs-per-SM bulk variant (FP32 2D, m < kCompactM)
+  int compact;              // 1: the two-CTAs-per-SM bulk variant (FP32, m below its limit)
   int ngroups;
   const int* group_first;   // ngroups+1 CTA ranges
   const int* task_first;    // ngroups+1 ranges into task_order
@@ -94,12 +96,14 @@ int gmres_bulk_stages(bool fp32, int m);
 // at P m rows; 0 if not even one stage of m rows fits.
 int gmres_bulk_cap(bool fp32, int m, int P);
 
-// The compact variant (FP32 2D bulk-copy, m < kCompactM, two CTAs per SM):
-// whether it applies, its co-resident CTA count, and its staging bytes per
-// warp for at most P stages (0 if none fits).
+// The compact variants (FP32 bulk-copy, two CTAs per SM; m < kCompactM2 in
+// 2D, m < kCompactM3 in 3D): whether one applies, its co-resident CTA count,
+// and its staging bytes per warp for at most P stages (0 if none fits).
 bool gmres_compact_ok(bool fp32, int dim, int m);
-int gmres_compact_max_blocks(int m);
-int gmres_compact_cap(int m, int P);
+int gmres_compact_max_blocks(int dim, int m);
+int gmres_compact_cap(int dim, int m, int P);
+// Shared-memory bytes a compact 2D CTA may use for its slice of V.
+int gmres_compact_vsmem_budget();
 
 // FP64 operator application out = A u (2D or 3D) on one grid.
 cudaError_t launch_apply(int dim, int n, const float* kappa, const double* u, double* out,

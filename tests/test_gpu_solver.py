@@ -146,10 +146,12 @@ def test_fp32_basis_stage_counts(stages):
     assert abs(r["iters"] - r0["iters"]) <= max(3, r0["iters"] // 100)
 
 
-@pytest.mark.parametrize("n,blocks", [(256, 304), (250, 300)])
+@pytest.mark.parametrize("n,blocks", [(256, 256), (250, 300), (512, 200)])
 def test_compact_variant(n, blocks):
-    """The two-CTAs-per-SM bulk-copy variant (128 registers, m <= 47): same
-    certificate, solution and iteration count as the standard variant."""
+    """The two-CTAs-per-SM variants (128 registers, m <= 47), with V slices in
+    shared memory (256^2, 250^2: slices fit next to the smaller state) and
+    streamed by bulk copies (512^2): same certificate, solution and iteration
+    count as the standard variant."""
     b = MovingGaussians2D(n, 2001, 500).rhs(11)
     s = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", grid_blocks=blocks, compact=1)
     x, r = s.solve(dev(b))
@@ -158,6 +160,21 @@ def test_compact_variant(n, blocks):
     ref = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", compact=0)
     _, r0 = ref.solve(dev(b))
     assert abs(r["iters"] - r0["iters"]) <= max(3, r0["iters"] // 100), (r["iters"], r0["iters"])
+
+
+def test_compact_variant_3d():
+    """The 3D compact variant (two CTAs per SM; m = 40 so that a stage of m
+    rows fits next to the 3D shared state) on variable kappa against the
+    oracle's solution."""
+    n = 24
+    kap = lognormal_kappa(n, 5001, smooth_sigma=2.0).astype(np.float32)
+    b = MovingGaussians3D(n, 5001, 200).rhs(7)
+    xr, _, _ = native.gmres(3, n, b, m=50, rtol=1e-13, kappa=kap.astype(np.float64))
+    s = Solver(n, dim=3, kappa=kap, m=40, rtol=1e-10, precision="fp32_refine", grid_blocks=60,
+               compact=1)
+    x, r = s.solve(dev(b))
+    assert r["status"] == 0 and r["relres_true"] <= 1e-10
+    assert rel(x.cpu().numpy(), xr) <= 1e-7
 
 
 def test_autotune_picks_the_fastest_candidate_and_caches():
