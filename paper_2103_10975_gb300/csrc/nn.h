@@ -91,6 +91,15 @@ cudaError_t launch_conv32_mma(int dim, int mode, int B, int H, const __nv_bfloat
                               const __nv_bfloat16* wop, const float* bias, int dil, int sign,
                               __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                               float* fo, const float* addend, cudaStream_t s);
+// The same convolution on the fifth-generation tensor cores (tcgen05.mma into
+// tensor memory), for 2D grids with at least 128 points per row.
+bool conv32_tc_applies(int dim, int H);
+cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
+                             const __nv_bfloat16* wop, const float* bias, int dil, int sign,
+                             __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
+                             float* fo, const float* addend, cudaStream_t s);
+// 1 if a tcgen05 convolution tile timed out waiting for its MMAs (0 otherwise).
+int conv32_tc_error();
 // Tensor-core weight gradient partials of a 32 -> 32 convolution (nparts CTAs).
 cudaError_t launch_wgrad_mma(int dim, int B, int H, const __nv_bfloat16* in,
                              const __nv_bfloat16* g, int dil, float* part, int stride, int nparts,

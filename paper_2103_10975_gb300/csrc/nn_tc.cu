@@ -1,0 +1,279 @@
+// 32 -> 32 channel 3x3 convolutions of the 2D network on the fifth-generation
+// tensor cores (tcgen05): the same implicit GEMM as conv32_mma
+//   out[p][n] = sum_{tap,k} in[p + sign*dil*off(tap)][k] * Wop[tap][n][k],
+// M = 128 pixels of one grid row per tile, N = 32 output channels,
+// K = 9 taps x 32 input channels (18 MMAs of K = 16), accumulated in tensor
+// memory (32 columns) by one thread's tcgen05.mma, completion signalled to an
+// mbarrier by tcgen05.commit, and read back by every warp with tcgen05.ld
+// (warp w owns TMEM lanes 32w..32w+31, i.e. pixels 32w..32w+31 of the tile).
+// Operands sit in shared memory in the no-swizzle K-major layout (core
+// matrices of 8 rows x 16 bytes).  The A operand is not materialised per tap:
+// the three input rows a tile needs are staged once, each as 4 column blocks
+// (8 channels each) of 132 pixel rows 16 bytes apart (so 8-row groups are 128
+// bytes apart, the stride offset, and column blocks 2112 bytes apart, the
+// leading-dimension offset); a tap's operand is then the same rows shifted by
+// its x offset, i.e. a descriptor whose start address moves by 16 bytes per
+// pixel.  The weights use 128 / 512-byte offsets.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "nn.h"
+
+namespace mlg {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTcM = 128;                    // pixels per tile (TMEM lanes)
+constexpr int kRows = kTcM + 4;              // staged pixels per input row (dilation <= 2)
+constexpr int kLboA = kRows * 16;            // bytes between 8-channel column blocks
+constexpr int kRowBytes = 4 * kLboA;         // one staged input row
+constexpr int kWBytes = kC * kC * 2;         // one tap's B operand: 2 KB
+constexpr int kTcSmem = 3 * kRowBytes + 9 * kWBytes + 64;
+
+__device__ __forceinline__ unsigned saddr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor (no swizzle): start address, leading-
+// dimension byte offset (between 8-element K blocks) and stride byte offset
+// (between 8-row groups)
+__device__ __forceinline__ unsigned long long mdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr >> 4) & 0x3FFFu) |
+         ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor: D F32, A and B BF16, both K-major, N = 32, M = 128
+constexpr unsigned kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(unsigned tmem, unsigned long long a, unsigned long long b,
+                                       unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_tc(unsigned bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+  return ok != 0;
+}
+
+enum { kRelu = 0, kResid = 1, kF32 = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(128) conv32_tc(int B, int H, const bf16* __restrict__ in,
+                                                 const bf16* __restrict__ wop,
+                                                 const float* __restrict__ bias, int dil,
+                                                 int sign, bf16* __restrict__ zo,
+                                                 bf16* __restrict__ to,
+                                                 const bf16* __restrict__ resid,
+                                                 float* __restrict__ fo,
+                                                 const float* __restrict__ addend,
+                                                 int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* As = tc_smem;                         // 3 staged input rows
+  unsigned char* Ws = tc_smem + 3 * kRowBytes;         // 9 x 2 KB
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(Ws + 9 * kWBytes);
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(mbar + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // B operand (weights) of all 9 taps: (n, k) at (n/8)*512 + (k/8)*128 + (n%8)*16 + (k%8)*2
+  for (int idx = threadIdx.x; idx < 9 * kC * 4; idx += blockDim.x) {
+    const int kc = idx & 3, n = (idx >> 2) & 31, t = idx >> 7;
+    const uint4 v = *reinterpret_cast<const uint4*>(wop + (t * kC + n) * kC + kc * 8);
+    *reinterpret_cast<uint4*>(Ws + t * kWBytes + (n >> 3) * 512 + kc * 128 + (n & 7) * 16) = v;
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+                     saddr(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+
+  float bv[kC];
+#pragma unroll
+  for (int o = 0; o < kC; o++) bv[o] = (MODE != kF32 && bias) ? bias[o] : 0.f;
+
+  const int tpr = (H + kTcM - 1) / kTcM;
+  const long long ntiles = (long long)B * H * tpr;
+  unsigned phase = 0;
+  bool ok = true;
+  for (long long tIdx = blockIdx.x; tIdx < ntiles && ok; tIdx += gridDim.x) {
+    const int tx = (int)(tIdx % tpr);
+    const int y = (int)((tIdx / tpr) % H);
+    const int b = (int)(tIdx / ((long long)tpr * H));
+    const int x0 = tx * kTcM;
+    // input rows y + sign*dil*(ty-1), pixels x0 - dil + r (r < kRows), channels
+    // 8kc..8kc+7 at ty*kRowBytes + kc*kLboA + r*16 (zero outside the grid)
+    for (int idx = threadIdx.x; idx < 3 * kRows * 4; idx += blockDim.x) {
+      const int kc = idx & 3, r = (idx >> 2) % kRows, ty = (idx >> 2) / kRows;
+      const int yy = y + sign * dil * (ty - 1);
+      const int xx = x0 - dil + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (yy >= 0 && yy < H && xx >= 0 && xx < H && r < kTcM + 2 * dil)
+        v = *reinterpret_cast<const uint4*>(in + (((long long)b * H + yy) * H + xx) * kC + kc * 8);
+      *reinterpret_cast<uint4*>(As + ty * kRowBytes + kc * kLboA + r * 16) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x == 0) {
+      for (int t = 0; t < 9; t++) {
+        // tap (ty, tx): pixel p reads staged row ty, pixel p + dil + sign*dil*(tx-1)
+        const int row0 = dil + sign * dil * (t % 3 - 1);
+        for (int h = 0; h < 2; h++)
+          tc_mma(tmem,
+                 mdesc(saddr(As + (t / 3) * kRowBytes + row0 * 16 + h * 2 * kLboA), kLboA, 128),
+                 mdesc(saddr(Ws + t * kWBytes + h * 256), 128, 512), (t | h) ? 1u : 0u);
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              saddr(mbar))
+          : "memory");
+    }
+    // bounded wait for the MMAs of this tile
+    if (!mbar_test_tc(saddr(mbar), phase)) {
+      const unsigned long long t0 = globaltimer_ns();
+      while (!mbar_test_tc(saddr(mbar), phase)) {
+        if (globaltimer_ns() - t0 > 2000000000ull) {
+          atomicExch(err, 1);
+          ok = false;
+          break;
+        }
+      }
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      unsigned r[32];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+          "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+            "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+            "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+            "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+            "=r"(r[31])
+          : "r"(tmem + ((unsigned)(warp * 32) << 16)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int p = warp * 32 + lane;
+      const int x = x0 + p;
+      if (x < H) {
+        const long long pix = ((long long)b * H + y) * H + x;
+        float v[kC];
+#pragma unroll
+        for (int o = 0; o < kC; o++) v[o] = __uint_as_float(r[o]) + bv[o];
+        if (MODE == kF32) {
+          float4* dst = reinterpret_cast<float4*>(fo + pix * kC);
+          const float4* add = addend ? reinterpret_cast<const float4*>(addend + pix * kC) : nullptr;
+#pragma unroll
+          for (int q = 0; q < 8; q++) {
+            float4 w = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            if (add) {
+              const float4 a = add[q];
+              w.x += a.x; w.y += a.y; w.z += a.z; w.w += a.w;
+            }
+            dst[q] = w;
+          }
+        } else {
+#pragma unroll
+          for (int o = 0; o < kC; o++) v[o] = fmaxf(v[o], 0.f);
+          uint4* zd = reinterpret_cast<uint4*>(zo + pix * kC);
+          const uint4* rs = MODE == kResid ? reinterpret_cast<const uint4*>(resid + pix * kC)
+                                           : nullptr;
+          uint4* td = MODE == kResid ? reinterpret_cast<uint4*>(to + pix * kC) : nullptr;
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            uint4 pz, pt;
+            __nv_bfloat162* hz = reinterpret_cast<__nv_bfloat162*>(&pz);
+            __nv_bfloat162* ht = reinterpret_cast<__nv_bfloat162*>(&pt);
+            uint4 rv = make_uint4(0u, 0u, 0u, 0u);
+            if (MODE == kResid) rv = rs[q];
+            const __nv_bfloat162* hr = reinterpret_cast<const __nv_bfloat162*>(&rv);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const float a0 = v[8 * q + 2 * e], a1 = v[8 * q + 2 * e + 1];
+              hz[e] = __floats2bfloat162_rn(a0, a1);
+              if (MODE == kResid) {
+                const float2 sr = __bfloat1622float2(hr[e]);
+                ht[e] = __floats2bfloat162_rn(sr.x + a0, sr.y + a1);
+              }
+            }
+            zd[q] = pz;
+            if (MODE == kResid) td[q] = pt;
+          }
+        }
+      }
+    }
+    // every warp's TMEM reads are done before the next tile's MMAs overwrite it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
+int* g_tc_err = nullptr;  // set by a tile whose MMAs did not complete in time
+
+}  // namespace
+
+bool conv32_tc_applies(int dim, int H) { return dim == 2 && H >= kTcM; }
+
+cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
+                             const __nv_bfloat16* wop, const float* bias, int dil, int sign,
+                             __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
+                             float* fo, const float* addend, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(conv32_tc<kRelu>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(conv32_tc<kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(conv32_tc<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaError_t e = cudaMalloc(&g_tc_err, sizeof(int));
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(g_tc_err, 0, sizeof(int));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (long long)B * H * ((H + kTcM - 1) / kTcM);
+  const int grid = (int)(ntiles < 4LL * nsm ? ntiles : 4LL * nsm);
+  if (mode == kRelu)
+    conv32_tc<kRelu><<<grid, 128, kTcSmem, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
+                                                addend, g_tc_err);
+  else if (mode == kResid)
+    conv32_tc<kResid><<<grid, 128, kTcSmem, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid,
+                                                 fo, addend, g_tc_err);
+  else
+    conv32_tc<kF32><<<grid, 128, kTcSmem, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
+                                               addend, g_tc_err);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+int conv32_tc_error() {
+  int v = 0;
+  if (g_tc_err) cudaMemcpy(&v, g_tc_err, sizeof(int), cudaMemcpyDeviceToHost);
+  return v;
+}
+
+}  // namespace mlg

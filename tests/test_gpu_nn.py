@@ -1,5 +1,7 @@
 """GPU parity of the initial-guess network (Sec. 2.1) and its training step
-(Sec. 2.3) against the FP64 oracle at the same weights, through the C ABI."""
+(Sec. 2.3) against the FP64 oracle at the same weights, through the C ABI.
+Grids with rows of 128 points or more run their 32 -> 32 convolutions on the
+tcgen05 kernel (n = 128, 256 here), smaller ones on the mma.sync kernel."""
 import math
 
 import numpy as np
@@ -58,7 +60,7 @@ def test_param_layout(n):
     assert np.array_equal(s.get_params(), (p * 0.5).astype(np.float32))
 
 
-@pytest.mark.parametrize("n", [16, 32, 40])
+@pytest.mark.parametrize("n", [16, 32, 40, 128, 256])
 def test_forward_parity(n):
     s = Solver(n, m=10, batch=2)
     flat = s.get_params()
@@ -74,7 +76,7 @@ def test_forward_parity(n):
         assert np.linalg.norm(y[b] - yr) <= 3e-2 * np.linalg.norm(yr), b
 
 
-@pytest.mark.parametrize("n", [16, 32])
+@pytest.mark.parametrize("n", [16, 32, 128])
 def test_gradient_parity(n):
     s = Solver(n, m=10, batch=2)
     flat = s.get_params()
