@@ -756,10 +756,14 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   note_launches(1);
   // output conv
   const bf16* tfin = net.extra_active > 0 ? net.tt[net.extra_active - 1] : net.t;
-  conv1_wgrad<0, D><<<P, 256, 0, s>>>(B, n, net.gy, tfin, nullptr, nullptr, net.wgrad_part,
-                                      stride);
+  // the 1-channel weight gradients have only 32 (T + 1) outputs per CTA: four
+  // times the CTAs of the 32 -> 32 ones, with a short partial stride, so the
+  // long pixel reduction has enough warps in flight
+  const int P1 = 4 * P, stride1 = kC * (T + 1);
+  conv1_wgrad<0, D><<<P1, 256, 0, s>>>(B, n, net.gy, tfin, nullptr, nullptr, net.wgrad_part,
+                                       stride1);
   note_launches(1);
-  reduce_wgrad<<<nblk(T * kC + 1, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 2, T,
+  reduce_wgrad<<<nblk(T * kC + 1, 32), 256, 0, s>>>(net.wgrad_part, P1, stride1, 2, T,
                                                      net.grad + net.off_w[L + 2],
                                                      net.grad + net.off_b[L + 2]);
   note_launches(1);
@@ -851,10 +855,10 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   // input conv
   mask_f32<<<nblk(full, 256), 256, 0, s>>>(full, net.g_pool + net.lvl_off[0], net.a0, net.g_lvl);
   note_launches(1);
-  conv1_wgrad<1, D><<<P, 256, 0, s>>>(B, n, nullptr, nullptr, net.g_lvl, u, net.wgrad_part,
-                                      stride);
+  conv1_wgrad<1, D><<<P1, 256, 0, s>>>(B, n, nullptr, nullptr, net.g_lvl, u, net.wgrad_part,
+                                       stride1);
   note_launches(1);
-  reduce_wgrad<<<nblk(T * kC + kC, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 1, T,
+  reduce_wgrad<<<nblk(T * kC + kC, 32), 256, 0, s>>>(net.wgrad_part, P1, stride1, 1, T,
                                                       net.grad + net.off_w[0],
                                                       net.grad + net.off_b[0]);
   note_launches(1);
