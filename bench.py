@@ -42,9 +42,9 @@ LEARN = dict(train_iters=64, lr=2e-3, batch=8, guess_smooth=32)
 METRIC = "time-to-solution per time step (ms) and GMRES iters, learned vs plain GMRES, rel res 1e-10"
 # DRAM bytes per Arnoldi step of gmres_persistent<float, 2, 64, 256, shared V>
 # on this workload, from one ncu capture of a 300-step solve of the kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum = 1.228 MB + 0.027 MB); scaled
+# (dram__bytes_read.sum + dram__bytes_write.sum = 1.227 MB + 0.026 MB); scaled
 # to a launch by its steps.
-DRAM_BYTES_PER_STEP = 1.255e6 / 300
+DRAM_BYTES_PER_STEP = 1.253e6 / 300
 WORKLOAD = ("2D Poisson -Lap u = f, 256x256 interior (N=65,536), zero Dirichlet, 5-point; "
             "3 moving signed Gaussians (sigma 0.1), 500-step series seed 2001; GMRES(30) "
             "rel tol 1e-10 (true FP64 residual)")
