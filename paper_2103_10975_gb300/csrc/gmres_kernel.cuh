@@ -102,7 +102,6 @@ struct Smem {
   T red[BS / 32][MAXM + 2];      // per-warp partials in the working precision
   double redd[BS / 32][4];       // per-warp partials of the FP64 residual norms
   double tot[MAXM + 2];
-  double cr[MAXM], sr[MAXM];     // Givens products with the unrotated column
   double Hu[(MAXM + 1) * MAXM];  // Hessenberg as built (Arnoldi relation), ld MAXM+1
   double R[(MAXM + 1) * MAXM];   // the same columns after the Givens rotations
   double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
@@ -273,29 +272,53 @@ __device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot
 
 // Givens update of Hessenberg column c (Hu -> R): apply rotations 0..c-1, form
 // rotation c, update g, and return the stop code (0 go on, 1 end the cycle,
-// 2 non-finite).  Warp 0 only: the lanes form the products of the rotations
-// with the column's untouched entries in parallel, so lane 0's dependent chain
-// is one FMA per rotation.
+// 2 non-finite).  One warp.  Applying rotation i to the running entry ri_i and
+// the untouched h_{i+1} gives R(i,c) = cs_i ri_i + sn_i h_{i+1} and
+// ri_{i+1} = -sn_i ri_i + cs_i h_{i+1}: an affine recurrence in ri, so the maps
+// x -> a_i x + b_i are composed by an inclusive warp scan (composition is
+// associative), 32 rotations per round.  The dependent FP64 chain is five scan
+// steps per round instead of one FMA per rotation (an FP64 operation has a
+// latency of about 70 cycles on this GPU).
 template <typename T, int MAXM, int BS>
 __device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, long long it,
                              long long max_iters, int m, double* hist, long long hist_cap,
                              double bnorm) {
   constexpr int LD = MAXM + 1;
+  constexpr unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const double* hc = sm.Hu + c * LD;
   double* rc = sm.R + c * LD;
-  for (int i = lane; i < c; i += 32) {
-    sm.cr[i] = sm.cs[i] * hc[i + 1];
-    sm.sr[i] = sm.sn[i] * hc[i + 1];
+  const double h0 = hc[0];
+  double ca = 1.0, cb = 0.0;  // composition of the maps of the earlier rounds
+  double ri = h0;             // ri_base entering a round, ri_c after the last
+  for (int base = 0; base < c; base += 32) {
+    const int i = base + lane;
+    const bool in = i < c;
+    const double csi = in ? sm.cs[i] : 0.0, sni = in ? sm.sn[i] : 0.0;
+    const double hi = in ? hc[i + 1] : 0.0;
+    double a = in ? -sni : 1.0;  // identity past the last rotation
+    double b = csi * hi;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double pa = __shfl_up_sync(kAll, a, off);
+      const double pb = __shfl_up_sync(kAll, b, off);
+      if (lane >= off) {  // this lane's map after the earlier lane's
+        b = fma(a, pb, b);
+        a *= pa;
+      }
+    }
+    const double fa = a * ca, fb = fma(a, cb, b);  // after the earlier rounds
+    const double next = fma(fa, h0, fb);           // ri_{i+1}
+    double prev = __shfl_up_sync(kAll, next, 1);   // ri_i
+    if (lane == 0) prev = ri;
+    if (in) rc[i] = fma(csi, prev, sni * hi);
+    ca = __shfl_sync(kAll, fa, 31);
+    cb = __shfl_sync(kAll, fb, 31);
+    ri = __shfl_sync(kAll, next, min(c - 1 - base, 31));
   }
   __syncwarp();
   int stop = 0;
   if (lane == 0) {
-    double ri = hc[0];
-    for (int i = 0; i < c; i++) {
-      rc[i] = fma(sm.cs[i], ri, sm.sr[i]);
-      ri = fma(-sm.sn[i], ri, sm.cr[i]);
-    }
     const double hsub = hc[c + 1];
     const double r2 = fma(ri, ri, hsub * hsub);
     double rho;
@@ -529,11 +552,42 @@ __device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
 // memory twice (update, then dots) instead of being held in registers, so
 // registers only carry the accumulators; U points per trip keep the
 // stencil's global loads in flight together.
+// What a thread carries between the passes of the shared-slice 2D variant for
+// its first U = 2 points: w' at each point and its four neighbours, loaded
+// right after the Y barrier so that the loads are in flight while the CTA
+// gathers h2 and runs the scalar recurrences; and z from the X pass, which the
+// Y pass of the same step needs at the same points (no reload through L2).
+template <typename T>
+struct XCarry {
+  T c[2], l[2], r[2], d[2], t[2];
+  T z[2];
+  bool pre;  // the w' values are those the next X pass needs
+};
+
+template <typename T, int BS>
+__device__ __forceinline__ void prefetch_x2d(XCarry<T>& cy, const T* __restrict__ WP, int lo,
+                                             int hi, int n) {
+#pragma unroll
+  for (int u = 0; u < 2; u++) {
+    const int i = lo + (int)threadIdx.x + u * BS;
+    const bool ok = i < hi;
+    const int ix = i % n, iy = i / n;
+    cy.c[u] = ok ? ldcg(WP + i) : T(0);
+    cy.l[u] = ok && ix > 0 ? ldcg(WP + i - 1) : T(0);
+    cy.r[u] = ok && ix < n - 1 ? ldcg(WP + i + 1) : T(0);
+    cy.d[u] = ok && iy > 0 ? ldcg(WP + i - n) : T(0);
+    cy.t[u] = ok && iy < n - 1 ? ldcg(WP + i + n) : T(0);
+  }
+  cy.pre = true;
+}
+
 template <typename T, int DIM, int MAXM, int BS, int K>
 __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi, int j, int n,
                                           const T* __restrict__ WP, T* __restrict__ Z,
                                           T* __restrict__ Vs, int rows,
-                                          const float* __restrict__ kappa, T s2t) {
+                                          const float* __restrict__ kappa, T s2t,
+                                          XCarry<T>& cy) {
+  static_assert(DIM == 2, "shared-memory slices are a 2D variant");
   constexpr int LMAX = MAXM + 2;
   constexpr int U = 2;
   const int tid = threadIdx.x;
@@ -544,6 +598,7 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
   const T inv = sm.invT;
   const T cj = sm.cc[j];
   for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
+    const bool first = i0 == lo + tid;
     int ii[U];
     bool ok_[U];
     T wp[U], znum[U];
@@ -551,11 +606,24 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
     for (int u = 0; u < U; u++) {
       ii[u] = i0 + u * BS;
       ok_[u] = ii[u] < hi;
-      wp[u] = ok_[u] ? ldcg(WP + ii[u]) : T(0);
     }
+    if (first && cy.pre) {
+      // the same differences, in the same order, as stencil2d
 #pragma unroll
-    for (int u = 0; u < U; u++)
-      znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
+      for (int u = 0; u < U; u++) {
+        const T uc = cy.c[u];
+        wp[u] = uc;
+        znum[u] = ok_[u] ? s2t * (((uc - cy.l[u]) + (uc - cy.r[u])) +
+                                  ((uc - cy.d[u]) + (uc - cy.t[u])))
+                         : T(0);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; u++) wp[u] = ok_[u] ? ldcg(WP + ii[u]) : T(0);
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
+    }
 #pragma unroll
     for (int u = 0; u < U; u++) {
       if (!ok_[u]) continue;
@@ -573,6 +641,7 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
       const T z = (zn - cj * vj) * inv;
       Vs[vbase(ii[u] - lo, rows) + (j << 5)] = vj;
       Z[ii[u]] = z;
+      if (first) cy.z[u] = z;
       accZ += z * z;
 #pragma unroll
       for (int k = 0; k < K; k++) {
@@ -590,15 +659,17 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
 template <typename T, int MAXM, int BS, int K>
 __device__ __forceinline__ void y_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi, int j,
                                           T* __restrict__ WP, const T* __restrict__ Z,
-                                          const T* __restrict__ Vs, int rows) {
+                                          const T* __restrict__ Vs, int rows,
+                                          const XCarry<T>& cy) {
   constexpr int LMAX = MAXM + 2;
-  constexpr int U = 2;
+  constexpr int U = 2;  // the X pass's points per trip (its first trip's z is in cy)
   const int tid = threadIdx.x;
   T acc[K];
 #pragma unroll
   for (int k = 0; k < K; k++) acc[k] = T(0);
   T accN = T(0);
   for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
+    const bool first = i0 == lo + tid;
     int ii[U];
     bool ok_[U];
     T q[U];
@@ -606,7 +677,7 @@ __device__ __forceinline__ void y_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
     for (int u = 0; u < U; u++) {
       ii[u] = i0 + u * BS;
       ok_[u] = ii[u] < hi;
-      q[u] = ok_[u] ? Z[ii[u]] : T(0);
+      q[u] = ok_[u] ? (first ? cy.z[u] : Z[ii[u]]) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < U; u++) {
@@ -989,12 +1060,14 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
     double* hist = (lb == 0) ? tk.hist : nullptr;
     int kcols = 0;
     const int jmax = arnoldi ? kp.arnoldi_steps : m;
+    XCarry<T> cy;  // shared-slice variant: values carried between its passes
+    cy.pre = false;
     for (int j = 0;; j++) {
       // ---- X: v_j and z = A v_j, h1 = V^T z; warp 1 rotates column j-1
       // while thread 0 waits at the group barrier
       {
 #define MLG_X(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vg, rows, 0, kappa, s2t)
-#define MLG_XS(KK) x_pass_sm<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vs, rows, kappa, s2t)
+#define MLG_XS(KK) x_pass_sm<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vs, rows, kappa, s2t, cy)
 #define MLG_XB(KK) \
   x_pass_bulk<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vg, rows, kappa, s2t, pipe, bphase)
         if constexpr (VM == kVShared) {
@@ -1027,7 +1100,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       // ---- Y: w'_{j+1} = z - V h1, h2 = V^T w'_{j+1}, ||w'_{j+1}||^2
       {
 #define MLG_Y(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vg, rows, 0)
-#define MLG_YS(KK) y_pass_sm<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vs, rows)
+#define MLG_YS(KK) y_pass_sm<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vs, rows, cy)
 #define MLG_YB(KK) y_pass_bulk<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vg, rows, pipe, bphase)
         if constexpr (VM == kVShared) {
           MLG_BUCKETS(MLG_YS)
@@ -1042,6 +1115,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         ok = finish_and_sync<LMAX, BS, T>(j + 2, (T*)part(), lb, sm.red, ps, w.bar, epoch,
                                           &sm.flag, NoSide());
         if (!ok) goto abort;
+        // w' is final everywhere: the next X pass's loads go out before the gather
+        if constexpr (VM == kVShared) prefetch_x2d<T, BS>(cy, WP, lo, hi, n);
         gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef, ps);
         red++;
       }
@@ -1054,6 +1129,16 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         sm.HuT[tid + j * LD] = (T)hv;
         sm.h2c[tid] = sm.coef[tid];
       }
+      // hn_{j+1} from hn2T: 1/hn for the next X pass and the subdiagonal of Hu
+      auto set_norm = [&]() {
+        const T h2v = sm.hn2T > T(0) ? sm.hn2T : T(0);
+        const T hnT = sqrt(h2v);
+        sm.invT = T(1) / hnT;
+        const double hnext = (double)hnT;
+        sm.hn = hnext;
+        sm.Hu[j + 1 + j * LD] = hnext;
+        sm.HuT[j + 1 + j * LD] = hnT;
+      };
       if (tid < 32) {
         T q = T(0);
         for (int k = lane; k <= j; k += 32) q += sm.coef[k] * sm.coef[k];
@@ -1061,8 +1146,10 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         if (lane == 0) {
           const T wn2 = sm.coef[j + 1];
           const T hn2 = wn2 - q;
-          sm.fallback = !(hn2 > T(0.5) * wn2);
+          const bool fb = !(hn2 > T(0.5) * wn2);
+          sm.fallback = fb;
           sm.hn2T = hn2;
+          if (!fb) set_norm();
         }
       }
       __syncthreads();
@@ -1083,27 +1170,20 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         if (!ok) goto abort;
         gather<BS, T, T>((const T*)part(), 1, nb, sm.tot, sm.coef, ps);
         red++;
-        if (tid == 0) sm.hn2T = sm.coef[0];
+        if (tid == 0) {
+          sm.hn2T = sm.coef[0];
+          set_norm();
+        }
         if (tid <= j) sm.h2c[tid] = T(0);
+        cy.pre = false;  // w' changed at this CTA's points
         __syncthreads();
       }
-      if (tid < 32) {
-        if (lane == 0) {
-          const T h2v = sm.hn2T > T(0) ? sm.hn2T : T(0);
-          const T hnT = sqrt(h2v);
-          sm.invT = T(1) / hnT;
-          const double hnext = (double)hnT;
-          sm.hn = hnext;
-          sm.Hu[j + 1 + j * LD] = hnext;
-          sm.HuT[j + 1 + j * LD] = hnT;
-          if (arnoldi) {
-            if (hist)
-              for (int k = 0; k <= j + 1; k++) hist[(long long)j * (jmax + 1) + k] = sm.Hu[k + j * LD];
-            sm.stop = !(hnext * hnext > 1e-28 * sm.anorm2) ? 1 : 0;
-          }
-        }
+      if (arnoldi && tid == 0) {
+        // column j is complete (the CTA barrier above ordered its entries)
+        if (hist)
+          for (int k = 0; k <= j + 1; k++) hist[(long long)j * (jmax + 1) + k] = sm.Hu[k + j * LD];
+        sm.stop = !(sm.hn * sm.hn > 1e-28 * sm.anorm2) ? 1 : 0;
       }
-      __syncthreads();
       // c_i = sum_{k >= i-1} Hu(i,k) h2_k for the next X pass: eight lanes per
       // row, each a strided part of the sum, added in a fixed order
       for (int i0 = 0; i0 <= j + 1; i0 += BS / 8) {
