@@ -228,15 +228,50 @@ __device__ __forceinline__ bool finish_and_sync(int L, R* part, int lb, R (*red)
   return *s_flag != 0;
 }
 
+// finish_and_sync for an exchange whose `side` work may outlast the group
+// barrier: warp 1 runs `side` and skips the barrier that releases the other
+// warps once thread 0 has passed the group barrier (a named barrier over the
+// other BS - 32 threads), so that `side` also overlaps the gather that follows
+// (gather with SKIP1, whose closing CTA barrier warp 1 joins when `side` is
+// done).  *s_flag is valid for every thread after that gather.
+template <int LW, int BS, typename R, typename Side>
+__device__ __forceinline__ void finish_and_sync_side(int L, R* part, int lb, R (*red)[LW], int ps,
+                                                     const GroupBarrier& gb,
+                                                     unsigned long long& epoch, int* s_flag,
+                                                     Side side) {
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 1) {
+    side();
+    return;
+  }
+  if (warp == 0) {
+    for (int k = lane; k < L; k += 32) {
+      R s = R(0);
+#pragma unroll
+      for (int w = 0; w < BS / 32; w++) s += red[w][k];
+      part[(long long)k * ps + lb] = s;
+    }
+    __syncwarp();
+    if (lane == 0)
+      *s_flag = gb.nblocks == 1 ? (*(volatile int*)gb.err == kErrNone)
+                                : group_arrive_wait(gb, epoch);
+  }
+  asm volatile("bar.sync 1, %0;" ::"r"(BS - 32) : "memory");
+}
+
 // Sum of the group's partials for k < L, identical in every CTA (same order);
 // tot gets the sums in FP64, coef the same values in the working precision.
 // Each warp takes up to four slots at a time, four partials per lane each, so
-// that sixteen loads per lane are in flight together.
-template <int BS, typename R, typename T>
+// that sixteen loads per lane are in flight together.  SKIP1: warp 1 takes no
+// slots (it is still on finish_and_sync_side's `side` work).
+template <int BS, typename R, typename T, bool SKIP1 = false>
 __device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot, T* coef,
                                        int ps) {
-  constexpr int NW = BS / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = BS / 32 - (SKIP1 ? 1 : 0);
+  const int lane = threadIdx.x & 31, warp0 = threadIdx.x >> 5;
+  // (warp 1 under SKIP1 starts past every slot)
+  const int warp = SKIP1 ? (warp0 == 1 ? (1 << 20) : (warp0 == 0 ? 0 : warp0 - 1)) : warp0;
   for (int k0 = warp; k0 < L; k0 += 4 * NW) {
     R s[4] = {R(0), R(0), R(0), R(0)};
     // 128 partials per round, all 16 loads of a lane issued before any is used
@@ -1086,13 +1121,15 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
             givens_column<T, MAXM, BS>(sm, j - 1, rtol_bnorm, iters, kp.max_iters, m, hist,
                                        tk.hist_cap, bnorm);
         };
-        ok = finish_and_sync<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red, ps, w.bar,
+        // the Givens rotation of column j-1 (warp 1) overlaps the barrier and
+        // the gather; its stop code is read after the gather
+        finish_and_sync_side<LMAX, BS, T>(min(j + 2, LMAX), (T*)part(), lb, sm.red, ps, w.bar,
                                           epoch, &sm.flag, givens_prev);
-        if (!ok) goto abort;
+        gather<BS, T, T, true>((const T*)part(), j + 2, nb, sm.tot, sm.coef, ps);
+        if (!sm.flag) goto abort;
         const int stop = sm.stop;
         if (stop == 2) { status = kErrNonfinite; goto finish; }
         if (stop == 1) { kcols = j; break; }
-        gather<BS, T, T>((const T*)part(), j + 2, nb, sm.tot, sm.coef, ps);
         red++;
         if (tid <= j) sm.Hu[tid + j * LD] = sm.tot[tid];
         if (tid == 0) sm.anorm2 = sm.tot[j + 1];
