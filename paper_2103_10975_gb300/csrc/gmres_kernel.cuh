@@ -102,14 +102,17 @@ struct Smem {
   T red[BS / 32][MAXM + 2];      // per-warp partials in the working precision
   double redd[BS / 32][4];       // per-warp partials of the FP64 residual norms
   double tot[MAXM + 2];
-  double Hu[(MAXM + 1) * MAXM];  // Hessenberg as built (Arnoldi relation), ld MAXM+1
+  double hcol[MAXM + 2];         // the column being rotated, in FP64 (Givens warp)
   double R[(MAXM + 1) * MAXM];   // the same columns after the Givens rotations
   double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
-  T HuT[(MAXM + 1) * MAXM];      // Hu in the working precision
+  T HuT[(MAXM + 1) * MAXM];      // Hessenberg as built (Arnoldi relation), ld MAXM+1
   T coef[MAXM + 2];              // h1 in the working precision (gather output)
   T h2c[MAXM + 2];               // pending second-pass coefficients of w'
   T cc[MAXM + 2];                // A w' -> A v_j correction coefficients
-  double hn, anorm2, h2sq;
+  // the latest column's two projections, from which the Givens warp forms
+  // the FP64 column (FP64 work kept off the step's critical path)
+  T h1c[MAXM + 2], h2h[MAXM + 2];
+  T anorm2T;                     // ||z||^2 of the latest column
   T invT;                        // 1 / hn in the working precision
   T hn2T;                        // ||w'||^2 - ||h2||^2 in the working precision
   int ctl, stop, flag, fallback;
@@ -296,7 +299,9 @@ __device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot
       for (int q = 0; q < 4; q++) {
         const int k = k0 + q * NW;
         if (k < L) {
-          tot[k] = (double)s[q];
+          // FP32 partials: coef only (an FP64 conversion is a long-latency
+          // operation on this GPU; consumers convert where they need FP64)
+          if constexpr (sizeof(R) == 8) tot[k] = (double)s[q];
           coef[k] = (T)s[q];
         }
       }
@@ -321,8 +326,12 @@ __device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, lo
   constexpr int LD = MAXM + 1;
   constexpr unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const double* hc = sm.Hu + c * LD;
+  double* hc = sm.hcol;
   double* rc = sm.R + c * LD;
+  // column c in FP64: h1 + h2 (exact sum of two FP32 values) and hn below
+  for (int i = lane; i <= c + 1; i += 32)
+    hc[i] = i <= c ? (double)sm.h1c[i] + (double)sm.h2h[i] : (double)sm.HuT[c + 1 + c * LD];
+  __syncwarp();
   const double h0 = hc[0];
   double ca = 1.0, cb = 0.0;  // composition of the maps of the earlier rounds
   double ri = h0;             // ri_base entering a round, ri_c after the last
@@ -378,7 +387,7 @@ __device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, lo
     if (hist && it <= hist_cap) hist[it - 1] = res / bnorm;
     if (!isfinite(res) || !isfinite(hsub))
       stop = 2;
-    else if (res <= rtol_bnorm || !(hsub * hsub > 1e-28 * sm.anorm2) || it >= max_iters ||
+    else if (res <= rtol_bnorm || !(hsub * hsub > 1e-28 * (double)sm.anorm2T) || it >= max_iters ||
              c + 1 >= m)
       stop = 1;
     sm.stop = stop;
@@ -1086,7 +1095,6 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
     if (tid == 0) {
       for (int k = 0; k <= MAXM; k++) sm.g[k] = 0.0;
       sm.g[0] = beta;
-      sm.hn = beta;
       sm.invT = (T)(1.0 / beta);
       sm.stop = 0;
     }
@@ -1131,8 +1139,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         if (stop == 2) { status = kErrNonfinite; goto finish; }
         if (stop == 1) { kcols = j; break; }
         red++;
-        if (tid <= j) sm.Hu[tid + j * LD] = sm.tot[tid];
-        if (tid == 0) sm.anorm2 = sm.tot[j + 1];
+        if (tid <= j) sm.h1c[tid] = sm.coef[tid];
+        if (tid == 0) sm.anorm2T = sm.coef[j + 1];
       }
       // ---- Y: w'_{j+1} = z - V h1, h2 = V^T w'_{j+1}, ||w'_{j+1}||^2
       {
@@ -1161,20 +1169,17 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       // ---- column j of Hu; hn_{j+1} = sqrt(||w'||^2 - ||h2||^2), in the working
       // precision (both terms come from reductions in that precision)
       if (tid <= j) {
-        const double hv = sm.Hu[tid + j * LD] + sm.tot[tid];
-        sm.Hu[tid + j * LD] = hv;
-        sm.HuT[tid + j * LD] = (T)hv;
-        sm.h2c[tid] = sm.coef[tid];
+        const T h2 = sm.coef[tid];
+        sm.HuT[tid + j * LD] = sm.h1c[tid] + h2;  // correctly rounded sum
+        sm.h2c[tid] = h2;
+        sm.h2h[tid] = h2;
       }
       // hn_{j+1} from hn2T: 1/hn for the next X pass and the subdiagonal of Hu
       auto set_norm = [&]() {
         const T h2v = sm.hn2T > T(0) ? sm.hn2T : T(0);
         const T hnT = sqrt(h2v);
         sm.invT = T(1) / hnT;
-        const double hnext = (double)hnT;
-        sm.hn = hnext;
-        sm.Hu[j + 1 + j * LD] = hnext;
-        sm.HuT[j + 1 + j * LD] = hnT;
+        sm.HuT[j + 1 + j * LD] = hnT;  // (the Givens warp reads it in FP64)
       };
       if (tid < 32) {
         T q = T(0);
@@ -1217,18 +1222,29 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       }
       if (arnoldi && tid == 0) {
         // column j is complete (the CTA barrier above ordered its entries)
+        const double hnext = (double)sm.HuT[j + 1 + j * LD];
         if (hist)
-          for (int k = 0; k <= j + 1; k++) hist[(long long)j * (jmax + 1) + k] = sm.Hu[k + j * LD];
-        sm.stop = !(sm.hn * sm.hn > 1e-28 * sm.anorm2) ? 1 : 0;
+          for (int k = 0; k <= j + 1; k++)
+            hist[(long long)j * (jmax + 1) + k] =
+                k <= j ? (double)sm.h1c[k] + (double)sm.h2h[k] : hnext;
+        sm.stop = !(hnext * hnext > 1e-28 * (double)sm.anorm2T) ? 1 : 0;
       }
       // c_i = sum_{k >= i-1} Hu(i,k) h2_k for the next X pass: eight lanes per
       // row, each a strided part of the sum, added in a fixed order
       for (int i0 = 0; i0 <= j + 1; i0 += BS / 8) {
         const int i = i0 + (tid >> 3);
         const int sub = tid & 7;
+        const int ir = min(i, j + 1);
+        const int k0 = (ir > 0 ? ir - 1 : 0) + sub;
         T c = T(0);
-        if (i <= j + 1)
-          for (int k = (i > 0 ? i - 1 : 0) + sub; k <= j; k += 8) c += sm.HuT[i + k * LD] * sm.h2c[k];
+        // all loads of a lane issued together (indices clamped into the column range)
+#pragma unroll
+        for (int t = 0; t < (MAXM + 7) / 8; t++) {
+          const int k = k0 + 8 * t;
+          const int kk = min(k, j);
+          const T prod = sm.HuT[ir + kk * LD] * sm.h2c[kk];
+          if (i <= j + 1 && k <= j) c += prod;
+        }
         c += __shfl_xor_sync(0xffffffffu, c, 4);
         c += __shfl_xor_sync(0xffffffffu, c, 2);
         c += __shfl_xor_sync(0xffffffffu, c, 1);
