@@ -97,7 +97,9 @@ typedef struct {
                                 x_c in C_t (Sec. 2.2 spread check) */
   int deterministic_tos;     /* 1: the gate uses iteration counts in place of wall-clock TOS */
   int train_iters;           /* Adam steps per mlgmres_train_step */
-  int batch;                 /* minibatch size */
+  int batch;                 /* minibatch size; the network's activations index points in
+                                32 bits, so 32 * batch * n^dim must stay below 2^31 (else
+                                MLGMRES_ERR_ARG when the network is created) */
   float lr;                  /* Adam learning rate */
   unsigned long long seed;   /* network initialisation and minibatch sampling */
   int grid_blocks;           /* solver CTAs; 0 = pick from the problem size */

@@ -97,6 +97,18 @@ __host__ __device__ __forceinline__ long long vix(int k, int i, int rows) {
 // ----------------------------------------------------------- shared state --
 constexpr int kMaxStages = 16;  // bulk-copy stages per warp (upper bound)
 
+// Two coefficients of one basis vector side by side (one shared-memory load).
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
 template <typename T, int MAXM, int BS>
 struct Smem {
   T red[BS / 32][MAXM + 2];      // per-warp partials in the working precision
@@ -107,8 +119,9 @@ struct Smem {
   double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
   T HuT[(MAXM + 1) * MAXM];      // Hessenberg as built (Arnoldi relation), ld MAXM+1
   T coef[MAXM + 2];              // h1 in the working precision (gather output)
-  T h2c[MAXM + 2];               // pending second-pass coefficients of w'
-  T cc[MAXM + 2];                // A w' -> A v_j correction coefficients
+  // per basis vector k: .x = h2_k, the pending second-pass coefficient of w';
+  // .y = c_k, the coefficient turning A w' into A v_j
+  typename Vec2<T>::type hcc[MAXM + 2];
   // the latest column's two projections, from which the Givens warp forms
   // the FP64 column (FP64 work kept off the step's critical path)
   T h1c[MAXM + 2], h2h[MAXM + 2];
@@ -476,7 +489,7 @@ __device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
   for (int k = 0; k < K; k++) acc[k] = T(0);
   T accZ = T(0);
   const T inv = sm.invT;
-  const T cj = sm.cc[j];
+  const T cj = sm.hcc[j].y;
   for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
     int ii[U];
     bool ok_[U];
@@ -506,7 +519,7 @@ __device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
 #pragma unroll
     for (int k = 0; k < K; k++) {
       if (k < j) {
-        const T h2k = sm.h2c[k], ck = sm.cc[k];
+        const T h2k = sm.hcc[k].x, ck = sm.hcc[k].y;
 #pragma unroll
         for (int u = 0; u < U; u++) {
           vnum[u] -= h2k * col[u][k];
@@ -640,7 +653,7 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
   for (int k = 0; k < K; k++) acc[k] = T(0);
   T accZ = T(0);
   const T inv = sm.invT;
-  const T cj = sm.cc[j];
+  const T cj = sm.hcc[j].y;
   for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
     const bool first = i0 == lo + tid;
     int ii[U];
@@ -677,8 +690,9 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
       for (int k = 0; k < K; k++) {
         if (k < j) {
           const T v = vc[k << 5];
-          vnum -= sm.h2c[k] * v;
-          zn -= sm.cc[k] * v;
+          const auto hc = sm.hcc[k];  // (h2_k, c_k) in one load
+          vnum -= hc.x * v;
+          zn -= hc.y * v;
         }
       }
       const T vj = vnum * inv;
@@ -807,7 +821,7 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
   for (int k = 0; k < K; k++) acc[k] = T(0);
   T accZ = T(0);
   const T inv = sm.invT;
-  const T cj = sm.cc[j];
+  const T cj = sm.hcc[j].y;
   const int ntile = (hi - lo + 31) >> 5;
   const int nq = ntile > warp ? (ntile - warp + NW - 1) / NW : 0;
   const BulkRing<T> r = bulk_ring<T>(pp, j);
@@ -835,8 +849,9 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
         for (int k = 0; k < K; k++) {
           if (k < j) {
             const T v = sc[k << 5];
-            vnum -= sm.h2c[k] * v;
-            znum -= sm.cc[k] * v;
+            const auto hc = sm.hcc[k];
+            vnum -= hc.x * v;
+            znum -= hc.y * v;
           }
         }
       }
@@ -1070,8 +1085,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         v0 += ri * ri;
       }
       for (int k = tid; k < LMAX; k += BS) {
-        sm.h2c[k] = T(0);
-        sm.cc[k] = T(0);
+        sm.hcc[k].x = T(0);
+        sm.hcc[k].y = T(0);
       }
       warp_slot<4>(sm.redd, 0, v0);
       block_finish<4, BS, double>(1, part(), lb, sm.redd, ps);
@@ -1171,7 +1186,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       if (tid <= j) {
         const T h2 = sm.coef[tid];
         sm.HuT[tid + j * LD] = sm.h1c[tid] + h2;  // correctly rounded sum
-        sm.h2c[tid] = h2;
+        sm.hcc[tid].x = h2;
         sm.h2h[tid] = h2;
       }
       // hn_{j+1} from hn2T: 1/hn for the next X pass and the subdiagonal of Hu
@@ -1202,7 +1217,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
           T q = WP[i];
 #pragma unroll
           for (int k = 0; k < MAXM; k++)
-            if (k <= j) q -= sm.h2c[k] * V[vix(k, i - voff, rows)];
+            if (k <= j) q -= sm.hcc[k].x * V[vix(k, i - voff, rows)];
           WP[i] = q;
           accN += q * q;
         }
@@ -1216,7 +1231,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
           sm.hn2T = sm.coef[0];
           set_norm();
         }
-        if (tid <= j) sm.h2c[tid] = T(0);
+        if (tid <= j) sm.hcc[tid].x = T(0);
         cy.pre = false;  // w' changed at this CTA's points
         __syncthreads();
       }
@@ -1242,13 +1257,13 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         for (int t = 0; t < (MAXM + 7) / 8; t++) {
           const int k = k0 + 8 * t;
           const int kk = min(k, j);
-          const T prod = sm.HuT[ir + kk * LD] * sm.h2c[kk];
+          const T prod = sm.HuT[ir + kk * LD] * sm.hcc[kk].x;
           if (i <= j + 1 && k <= j) c += prod;
         }
         c += __shfl_xor_sync(0xffffffffu, c, 4);
         c += __shfl_xor_sync(0xffffffffu, c, 2);
         c += __shfl_xor_sync(0xffffffffu, c, 1);
-        if (sub == 0 && i <= j + 1) sm.cc[i] = c;
+        if (sub == 0 && i <= j + 1) sm.hcc[i].y = c;
       }
       __syncthreads();
       if (!arnoldi && j + 1 >= m) {

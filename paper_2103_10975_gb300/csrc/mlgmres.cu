@@ -134,6 +134,8 @@ void ensure_net(mlgmres* h) {
     h->linear = true;
     CK(lin_create(h->lin, h->N, opt->batch));
   } else {
+    ARG(32LL * opt->batch * h->N < (1LL << 31),
+        "the network indexes its activations in 32 bits: 32 * batch * n^dim must be < 2^31");
     CK(net_create(h->net, h->grid.n, opt->batch, opt->seed, h->grid.dim, opt->grow_blocks));
   }
 }

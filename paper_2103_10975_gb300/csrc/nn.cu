@@ -50,14 +50,18 @@ __device__ __forceinline__ void store32(bf16* p, const float* v) {
 template <int D>
 struct Geo {
   static constexpr int T = D == 3 ? 27 : 9;
+  // Point indices stay below 2^31 (net_create checks 32 B_max n^D), so the
+  // arithmetic is 32-bit: a 64-bit division is a long software sequence.
   __device__ static void decode(long long p, int n, int& b, int& z, int& y, int& x) {
-    x = (int)(p % n);
-    long long r = p / n;
-    y = (int)(r % n);
-    r /= n;
+    const unsigned un = (unsigned)n;
+    unsigned r = (unsigned)p;
+    x = (int)(r % un);
+    r /= un;
+    y = (int)(r % un);
+    r /= un;
     if (D == 3) {
-      z = (int)(r % n);
-      r /= n;
+      z = (int)(r % un);
+      r /= un;
     } else {
       z = 0;
     }
@@ -68,7 +72,7 @@ struct Geo {
     const int zz = z + dz, yy = y + dy, xx = x + dx;
     if (yy < 0 || yy >= n || xx < 0 || xx >= n) return -1;
     if (D == 3 && (zz < 0 || zz >= n)) return -1;
-    return D == 3 ? (((long long)b * n + zz) * n + yy) * n + xx : ((long long)b * n + yy) * n + xx;
+    return D == 3 ? (long long)(((b * n + zz) * n + yy) * n + xx) : (long long)((b * n + yy) * n + xx);
   }
   __device__ static void tap(int t, int& dz, int& dy, int& dx) {
     dz = D == 3 ? t / 9 - 1 : 0;
@@ -426,12 +430,15 @@ __global__ void upsample_bwd_axis(long long outer, int n, int m, long long inner
                                   float* __restrict__ out) {
   const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= outer * m * inner) return;
-  const long long c = id % inner;
-  const long long p = id / inner;
-  const int j = (int)(p % m);
-  const long long o = p / m;
+  // element indices stay below 2^31 (network size check): 32-bit division
+  const unsigned ui = (unsigned)id, uin = (unsigned)inner;
+  const unsigned c = ui % uin;
+  const unsigned p = ui / uin;
+  const int j = (int)(p % (unsigned)m);
+  const unsigned o = p / (unsigned)m;
   float acc = 0.f;
-  for (int k = ptr[j]; k < ptr[j + 1]; k++) acc += wt[k] * in[(o * n + idx[k]) * inner + c];
+  for (int k = ptr[j]; k < ptr[j + 1]; k++)
+    acc += wt[k] * in[((long long)o * n + idx[k]) * inner + c];
   out[id] = acc;
 }
 
@@ -473,8 +480,8 @@ __global__ void sync_weights_kernel(int nconv, int T, const float* __restrict__ 
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long per = (long long)T * kC * kC;
   if (i >= nconv * per) return;
-  const int cv = (int)(i / per);
-  const int r = (int)(i % per);
+  const int cv = (int)((unsigned)i / (unsigned)per);
+  const int r = (int)((unsigned)i % (unsigned)per);
   const int o = r / (kC * T), k = (r / T) % kC, tp = r % T;
   const bf16 v = __float2bfloat16(master[offs[cv] + r]);
   wq[(long long)cv * per + (tp * kC + k) * kC + o] = v;
@@ -503,6 +510,10 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
                        int extra_max) {
   if (dim != 2 && dim != 3) return cudaErrorInvalidValue;
   if (extra_max < 0 || extra_max > kMaxExtra) return cudaErrorInvalidValue;
+  // the kernels index points and point-channel elements in 32 bits
+  if (n < 1 || bmax < 1 ||
+      (long long)bmax * (dim == 3 ? (long long)n * n * n : (long long)n * n) * kC >= (1LL << 31))
+    return cudaErrorInvalidValue;
   net.extra_max = extra_max;
   net.extra_active = 0;
   net.n = n;

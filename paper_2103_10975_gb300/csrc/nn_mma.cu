@@ -80,10 +80,12 @@ __device__ __forceinline__ void stage_rows(bf16* tile, const bf16* __restrict__ 
 // row index (b, z, y) of a grid with rows = B n^(D-1)
 template <int D>
 __device__ __forceinline__ void decode_row(long long row, int n, int& b, int& z, int& y) {
-  y = (int)(row % n);
-  const long long r2 = row / n;
-  z = D == 3 ? (int)(r2 % n) : 0;
-  b = D == 3 ? (int)(r2 / n) : (int)r2;
+  // row indices stay below 2^31 (the network's size check): 32-bit division
+  const unsigned un = (unsigned)n, r = (unsigned)row;
+  y = (int)(r % un);
+  const unsigned r2 = r / un;
+  z = D == 3 ? (int)(r2 % un) : 0;
+  b = D == 3 ? (int)(r2 / un) : (int)r2;
 }
 
 enum { kRelu = 0, kResid = 1, kF32 = 2 };
