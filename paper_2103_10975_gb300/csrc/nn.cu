@@ -266,118 +266,225 @@ __global__ void loss_finish(const float* __restrict__ part, int nparts, float sc
 }
 
 // g_t[p][c] = sum_tap w[c][tap] gy[p - off_tap]
+// Segments of the 1-channel <-> 32-channel kernels: R rows x W points of one
+// (b, z) plane (W = min(n, 256), R = max(1, 256 / n)), with the 1-channel field
+// of the segment and its one-point halo staged in shared memory, zero outside
+// the grid, so each tap is one shared-memory read at a fixed offset.
+constexpr int kSeg = 256;
+constexpr int kW1Threads = 512;
+
 template <int D>
-__global__ void conv_out_bwd_data(int B, int n, const float* __restrict__ gy,
-                                  const float* __restrict__ w, float* __restrict__ gt) {
-  constexpr int T = Geo<D>::T;
-  __shared__ float ws[kC * T];
-  for (int i = threadIdx.x; i < kC * T; i += blockDim.x) ws[i] = w[i];
-  __syncthreads();
-  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= B * Geo<D>::pts(n)) return;
-  int b, z, y, x;
-  Geo<D>::decode(p, n, b, z, y, x);
-  float g[T];
-#pragma unroll
-  for (int tp = 0; tp < T; tp++) {
-    int dz, dy, dx;
-    Geo<D>::tap(tp, dz, dy, dx);
-    const long long q = Geo<D>::nb(b, z, y, x, -dz, -dy, -dx, n);
-    g[tp] = q >= 0 ? gy[q] : 0.f;
+__host__ __device__ constexpr int w1_planes() { return D == 3 ? 3 : 1; }
+
+__host__ __device__ inline int w1_w(int n) { return n < kSeg ? n : kSeg; }
+__host__ __device__ inline int w1_r(int n) { return n < kSeg ? kSeg / n : 1; }
+
+template <int D>
+int w1_stage_floats(int n) { return w1_planes<D>() * (w1_r(n) + 2) * (w1_w(n) + 2); }
+
+// sf[pz][r][cx] = f at (plane pl + pz - 1 (3D), row y0 + r - 1, column x0 + cx - 1)
+template <int D, int NT>
+__device__ __forceinline__ void w1_stage(float* sf, const float* __restrict__ f, int n, int pl,
+                                         int y0, int x0, int W, int R) {
+  const int TW = W + 2, TP = (R + 2) * TW;
+  for (int i = threadIdx.x; i < w1_planes<D>() * TP; i += NT) {
+    const int pz = D == 3 ? i / TP : 1, r = (i % TP) / TW, cx = (i % TP) % TW;
+    const int gy = y0 + r - 1, gx = x0 + cx - 1;
+    bool ok = gy >= 0 && gy < n && gx >= 0 && gx < n;
+    int gpl = pl;
+    if (D == 3) {
+      const int gz = pl % n + pz - 1;
+      ok = ok && gz >= 0 && gz < n;
+      gpl = pl + pz - 1;
+    }
+    sf[i] = ok ? f[((long long)gpl * n + gy) * n + gx] : 0.f;
   }
-  float* dst = gt + p * kC;
+}
+
+// gt[p][c] = sum_tap w[c][tap] gy[p - off_tap] (transpose of the 32 -> 1 output
+// conv) and, when gbf is given, gbf[p][c] = bf16(mask[p][c] > 0 ? gt : 0) for
+// the masked consumer that follows.  Segments as above (gy staged); lane =
+// channel (coalesced 128-byte rows), each warp U points of the segment.
+template <int D>
+__global__ void __launch_bounds__(kW1Threads) conv_out_bwd_data(int B, int n,
+                                                               const float* __restrict__ gy,
+                                                               const float* __restrict__ w,
+                                                               float* __restrict__ gt,
+                                                               const bf16* __restrict__ mask,
+                                                               bf16* __restrict__ gbf) {
+  constexpr int T = Geo<D>::T;
+  constexpr int NW = kW1Threads / 32;
+  constexpr int U = kSeg / NW;
+  extern __shared__ float sf[];
+  const int W = w1_w(n), R = w1_r(n);
+  const int TW = W + 2, TP = (R + 2) * TW;
+  const int xsegs = (n + W - 1) / W, ysegs = (n + R - 1) / R;
+  const int nseg = B * (D == 3 ? n : 1) * ysegs * xsegs;
+  const int c = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  float wc[T];
 #pragma unroll
-  for (int c = 0; c < kC; c++) {
-    float acc = 0.f;
+  for (int tp = 0; tp < T; tp++) wc[tp] = w[c * T + tp];
+  const int ry0 = (wp * U) / W, xl0 = (wp * U) % W;
+  const int center = D == 3 ? TP : 0;
+  for (int sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    const int xs = sg % xsegs, t2 = sg / xsegs;
+    const int ys = t2 % ysegs, pl = t2 / ysegs;
+    const int x0 = xs * W, y0 = ys * R;
+    __syncthreads();
+    w1_stage<D, kW1Threads>(sf, gy, n, pl, y0, x0, W, R);
+    __syncthreads();
+    int ry = ry0, xl = xl0;
+#pragma unroll 4
+    for (int k = 0; k < U; k++) {
+      const int y = y0 + ry, x = x0 + xl;
+      if (ry < R && y < n && x < n) {
+        const int base = center + (ry + 1) * TW + xl + 1;
+        float acc = 0.f;
 #pragma unroll
-    for (int tp = 0; tp < T; tp++) acc += ws[c * T + tp] * g[tp];
-    dst[c] = acc;
+        for (int tp = 0; tp < T; tp++) {
+          int dz, dy, dx;
+          Geo<D>::tap(tp, dz, dy, dx);
+          acc += wc[tp] * sf[base - (dz * TP + dy * TW + dx)];
+        }
+        const long long p = ((long long)pl * n + y) * n + x;
+        gt[p * kC + c] = acc;
+        if (gbf)
+          gbf[p * kC + c] = __float2bfloat16(__bfloat162float(mask[p * kC + c]) > 0.f ? acc : 0.f);
+      }
+      if (++xl == W) {
+        xl = 0;
+        ++ry;
+      }
+    }
   }
 }
 
 // Per-CTA partial weight gradients of a 1-channel <-> 32-channel 3^D conv:
 //   part[cta][c*T + tap] and the biases at part[cta][32 T + c].
-// MODE 0 (output conv):  dW[c][tap] = sum_p gy[p] t[p + off][c], db = sum_p gy[p]
-// MODE 1 (input conv):   dW[c][tap] = sum_p g32[p][c] u[p + off], db[c] = sum_p g32[p][c]
-// Lane = channel (coalesced 32-channel rows), warp = one of 8 interleaved pixel
-// streams of the CTA's range; the 8 warp sums are added in a fixed order.
-template <int MODE, int D>
-__global__ void __launch_bounds__(256) conv1_wgrad(int B, int n, const float* __restrict__ g1,
-                                                   const bf16* __restrict__ x32,
-                                                   const float* __restrict__ g32,
-                                                   const float* __restrict__ u,
-                                                   float* __restrict__ part, int stride) {
+// MODE 0 (output conv):  dW[c][tap] = sum_p gy[p] t[p + off][c]
+//                                   = sum_q t[q][c] gy[q - off],  db = sum_q gy[q]
+// MODE 1 (input conv):   dW[c][tap] = sum_p g32[p][c] u[p + off], db[c] = sum_p g32[p][c],
+//                        with g32 taken as 0 where m32 <= 0 (the ReLU of a0)
+// The grid is cut into segments of R rows x W points of one (b, z) plane
+// (W = min(n, 256), R = max(1, 256 / n)).  Lane = channel: every 32-channel row
+// is read once, coalesced, U rows per warp in flight; the 1-channel field (gy
+// or u) of the segment and its halo is staged in shared memory, zero outside
+// the grid, so each tap is one shared-memory read at a fixed offset.  The 16
+// warp sums are added in a fixed order.
+template <int D>
+int conv1_wgrad_smem(int n) {
   constexpr int T = Geo<D>::T;
-  __shared__ float red[8][kC * (T + 1)];
-  const long long total = B * Geo<D>::pts(n);
-  const long long per = (total + gridDim.x - 1) / gridDim.x;
-  const long long p0 = blockIdx.x * per;
-  const long long p1 = min(total, p0 + per);
+  const int stage = w1_stage_floats<D>(n);
+  const int red = (kW1Threads / 32) * 32 * (T + 1);
+  return (int)sizeof(float) * (stage > red ? stage : red);
+}
+
+template <int MODE, int D>
+__global__ void __launch_bounds__(kW1Threads, D == 3 ? 1 : 2) conv1_wgrad(
+    int B, int n, const float* __restrict__ g1, const bf16* __restrict__ x32,
+    const float* __restrict__ g32, const bf16* __restrict__ m32, const float* __restrict__ u,
+    float* __restrict__ part, int stride) {
+  constexpr int T = Geo<D>::T;
+  constexpr int NW = kW1Threads / 32;
+  constexpr int U = kSeg / NW;             // points per warp and segment
+  constexpr int sgn = MODE == 0 ? -1 : 1;  // MODE 0 reads gy at q - off, MODE 1 u at p + off
+  extern __shared__ float sf[];
+  const int W = w1_w(n), R = w1_r(n);
+  const int TW = W + 2, TP = (R + 2) * TW;
+  const int xsegs = (n + W - 1) / W, ysegs = (n + R - 1) / R;
+  const int nplanes = B * (D == 3 ? n : 1);  // (b, z) planes
+  const int nseg = nplanes * ysegs * xsegs;
   const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float* __restrict__ f = MODE == 0 ? g1 : u;
   float acc[T];
 #pragma unroll
   for (int t = 0; t < T; t++) acc[t] = 0.f;
   float accb = 0.f;
-  // four consecutive points per warp and trip: their loads of each tap are
-  // issued together (the loop is latency-bound otherwise)
-  constexpr int U = 4;
-  for (long long p = p0 + (long long)w * U; p < p1; p += 8 * U) {
-    int b[U], z[U], y[U], x[U];
-    float gp[U];
-#pragma unroll
-    for (int k = 0; k < U; k++) {
-      const long long pk = p + k;
-      if (pk < p1) {
-        Geo<D>::decode(pk, n, b[k], z[k], y[k], x[k]);
-        gp[k] = MODE == 0 ? g1[pk] : g32[pk * kC + c];
-      } else {
-        b[k] = z[k] = y[k] = x[k] = 0;
-        gp[k] = 0.f;
-      }
-      accb += gp[k];
-    }
-#pragma unroll
-    for (int t = 0; t < T; t++) {
-      int dz, dy, dx;
-      Geo<D>::tap(t, dz, dy, dx);
-      float v[U];
+  for (int sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    const int xs = sg % xsegs, t2 = sg / xsegs;
+    const int ys = t2 % ysegs, pl = t2 / ysegs;  // pl = b (2D) or b n + z (3D)
+    const int x0 = xs * W, y0 = ys * R;
+    // this warp's rows first (their loads overlap the staging below)
+    // (the warp's U points run along x from (ry0, xl0), wrapping to the next row)
+    const int ry0 = (w * U) / W, xl0 = (w * U) % W;
+    float val[U];
+    {
+      int ry = ry0, xl = xl0;
 #pragma unroll
       for (int k = 0; k < U; k++) {
-        const long long q = p + k < p1 ? Geo<D>::nb(b[k], z[k], y[k], x[k], dz, dy, dx, n) : -1;
-        v[k] = q < 0 ? 0.f : (MODE == 0 ? __bfloat162float(x32[q * kC + c]) : u[q]);
+        const int x = x0 + xl, y = y0 + ry;
+        float v = 0.f;
+        if (ry < R && y < n && x < n) {
+          const long long p = ((long long)pl * n + y) * n + x;
+          if (MODE == 0)
+            v = __bfloat162float(x32[p * kC + c]);
+          else
+            v = __bfloat162float(m32[p * kC + c]) > 0.f ? g32[p * kC + c] : 0.f;
+        }
+        val[k] = v;
+        if (++xl == W) {
+          xl = 0;
+          ++ry;
+        }
       }
+    }
+    __syncthreads();  // the previous segment's readers are done with sf
+    w1_stage<D, kW1Threads>(sf, f, n, pl, y0, x0, W, R);
+    __syncthreads();
+    const int center = D == 3 ? TP : 0;
+    int ry = ry0, xl = xl0;
 #pragma unroll
-      for (int k = 0; k < U; k++) acc[t] += gp[k] * v[k];
+    for (int k = 0; k < U; k++) {
+      if (ry < R && y0 + ry < n && x0 + xl < n) {
+        const int base = center + (ry + 1) * TW + xl + 1;
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+          int dz, dy, dx;
+          Geo<D>::tap(t, dz, dy, dx);
+          acc[t] += val[k] * sf[base + sgn * (dz * TP + dy * TW + dx)];
+        }
+        accb += MODE == 0 ? sf[base] : val[k];
+      }
+      if (++xl == W) {
+        xl = 0;
+        ++ry;
+      }
     }
   }
-#pragma unroll
-  for (int t = 0; t < T; t++) red[w][c * (T + 1) + t] = acc[t];
-  red[w][c * (T + 1) + T] = accb;
+  // fixed-order sum of the 16 warps' partials
   __syncthreads();
-  for (int t = threadIdx.x; t < kC * T + kC; t += blockDim.x) {
+  float* red = sf;  // [NW][32 (T + 1)]
+#pragma unroll
+  for (int t = 0; t < T; t++) red[w * 32 * (T + 1) + c * (T + 1) + t] = acc[t];
+  red[w * 32 * (T + 1) + c * (T + 1) + T] = accb;
+  __syncthreads();
+  for (int t = threadIdx.x; t < kC * T + kC; t += kW1Threads) {
     // t < 32 T: weight c*T + tap; t >= 32 T: bias of channel t - 32 T (MODE 0: one bias)
     const int cc = t < kC * T ? t / T : t - kC * T;
     const int k = t < kC * T ? t % T : T;
     float v = 0.f;
     if (!(MODE == 0 && k == T && cc != 0))
-      for (int ww = 0; ww < 8; ww++) v += red[ww][cc * (T + 1) + k];
+      for (int ww = 0; ww < NW; ww++) v += red[ww * 32 * (T + 1) + cc * (T + 1) + k];
     part[(long long)blockIdx.x * stride + t] = v;
   }
 }
 
-// out = bf16(g * (mask > 0))
+// out = bf16(g * (mask > 0)), eight elements per thread (count is a multiple
+// of 32: whole channel rows; the buffers are 32-byte aligned)
 __global__ void mask_to_bf16(long long count, const float* __restrict__ g,
                              const bf16* __restrict__ mask, bf16* __restrict__ out) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 8;
   if (i >= count) return;
-  out[i] = __float2bfloat16(__bfloat162float(mask[i]) > 0.f ? g[i] : 0.f);
-}
-
-__global__ void mask_f32(long long count, const float* __restrict__ g,
-                         const bf16* __restrict__ mask, float* __restrict__ out) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  out[i] = __bfloat162float(mask[i]) > 0.f ? g[i] : 0.f;
+  const float4 a = *reinterpret_cast<const float4*>(g + i);
+  const float4 b = *reinterpret_cast<const float4*>(g + i + 4);
+  const uint4 mv = *reinterpret_cast<const uint4*>(mask + i);
+  const bf16* m = reinterpret_cast<const bf16*>(&mv);
+  const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint4 o;
+  bf16* ob = reinterpret_cast<bf16*>(&o);
+#pragma unroll
+  for (int k = 0; k < 8; k++) ob[k] = __float2bfloat16(__bfloat162float(m[k]) > 0.f ? v[k] : 0.f);
+  *reinterpret_cast<uint4*>(out + i) = o;
 }
 
 // grad[dst_w[i]] = sum over CTAs of part[cta][i] for the weight layout used by
@@ -390,19 +497,28 @@ __global__ void __launch_bounds__(256) reduce_wgrad(const float* __restrict__ pa
                                                     float* __restrict__ gw,
                                                     float* __restrict__ gb) {
   // 32 outputs per CTA (lane = output), the CTA partials split over the 8 warps
-  // (coalesced rows), the 8 warp sums added in a fixed order
-  __shared__ double red[8][32];
+  // (coalesced rows), four independent sums per lane so that four loads are in
+  // flight, all added in a fixed order (FP32: the FP64 pipe of this GPU is slow)
+  __shared__ float red[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
   const int nw = kind == 0 ? T * kC * kC : T * kC;
   const int nb = kind == 0 ? kC : (kind == 1 ? kC : 1);
-  double s = 0.0;
-  if (i < nw + nb)
-    for (int c = w; c < nparts; c += 8) s += part[(long long)c * stride + i];
-  red[w][lane] = s;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  if (i < nw + nb) {
+    int c = w;
+    for (; c + 24 < nparts; c += 32) {
+      s0 += part[(long long)c * stride + i];
+      s1 += part[(long long)(c + 8) * stride + i];
+      s2 += part[(long long)(c + 16) * stride + i];
+      s3 += part[(long long)(c + 24) * stride + i];
+    }
+    for (; c < nparts; c += 8) s0 += part[(long long)c * stride + i];
+  }
+  red[w][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   if (w != 0 || i >= nw + nb) return;
-  double t = 0.0;
+  float t = 0.f;
 #pragma unroll
   for (int k = 0; k < 8; k++) t += red[k][lane];
   if (i < nw) {
@@ -424,10 +540,12 @@ __global__ void __launch_bounds__(256) reduce_wgrad(const float* __restrict__ pa
 // (built once on the host with the same arithmetic as bilin).  The
 // D-dimensional transpose is D such passes, one per axis.
 
+// With outbf (the last axis): outbf = bf16(mask > 0 ? out : 0) instead of out.
 __global__ void upsample_bwd_axis(long long outer, int n, int m, long long inner,
                                   const int* __restrict__ ptr, const int* __restrict__ idx,
                                   const float* __restrict__ wt, const float* __restrict__ in,
-                                  float* __restrict__ out) {
+                                  float* __restrict__ out, const bf16* __restrict__ mask,
+                                  bf16* __restrict__ outbf) {
   const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= outer * m * inner) return;
   // element indices stay below 2^31 (network size check): 32-bit division
@@ -439,7 +557,53 @@ __global__ void upsample_bwd_axis(long long outer, int n, int m, long long inner
   float acc = 0.f;
   for (int k = ptr[j]; k < ptr[j + 1]; k++)
     acc += wt[k] * in[((long long)o * n + idx[k]) * inner + c];
-  out[id] = acc;
+  if (outbf)
+    outbf[id] = __float2bfloat16(__bfloat162float(mask[id]) > 0.f ? acc : 0.f);
+  else
+    out[id] = acc;
+}
+
+// The x-axis pass of every coarse level's transposed upsampling at once:
+//   out_l[r][j][c] = sum_x U_l[x][j] in[r][x][c]   (levels l = 1 .. L-1)
+// for each row r of the fine grid (x is the innermost axis in 2D and 3D).  One
+// CTA per row: its n x 32 values are read from HBM once and from L1 for the
+// other levels (the per-level pass reads the whole fine gradient per level).
+// Same sums, in the same order, as upsample_bwd_axis.
+struct UpXLevels {
+  int nlev;
+  int m[kMaxLevels];
+  const int* ptr[kMaxLevels];
+  const int* idx[kMaxLevels];
+  const float* wt[kMaxLevels];
+  long long off[kMaxLevels];  // out_l = out + off[l], rows of m_l x 32
+};
+
+constexpr int kXLevelsMaxN = 384;  // the staged row (n x 32 floats) stays within 48 KB
+
+__global__ void __launch_bounds__(256) upsample_bwd_x_levels(int n, UpXLevels lv,
+                                                             const float* __restrict__ in,
+                                                             float* __restrict__ out) {
+  extern __shared__ float row[];  // the fine row, n x 32
+  const long long r = blockIdx.x;
+  const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
+  {
+    const float4* src = reinterpret_cast<const float4*>(in + r * n * kC);
+    float4* dst = reinterpret_cast<float4*>(row);
+    for (int i = threadIdx.x; i < n * kC / 4; i += 256) dst[i] = src[i];
+  }
+  __syncthreads();
+  for (int l = 1; l < lv.nlev; l++) {
+    const int m = lv.m[l];
+    const int* __restrict__ ptr = lv.ptr[l];
+    const int* __restrict__ idx = lv.idx[l];
+    const float* __restrict__ wt = lv.wt[l];
+    float* __restrict__ o = out + lv.off[l] + r * m * kC;
+    for (int j = w; j < m; j += 8) {
+      float acc = 0.f;
+      for (int k = ptr[j]; k < ptr[j + 1]; k++) acc += wt[k] * row[idx[k] * kC + c];
+      o[j * kC + c] = acc;
+    }
+  }
 }
 
 // fine[p][c] += coarse[p / 2][c] / 2^D (fine side s, coarse side s/2)
@@ -646,6 +810,19 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
   NN_CK(cudaGetDevice(&dev));
   NN_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   net.wparts = 2 * nsm;
+  // the 1-channel weight gradients take more than the default 48 KB of
+  // dynamic shared memory in 3D (their fixed-order reduction buffer)
+  if (dim == 3) {
+    NN_CK(cudaFuncSetAttribute(conv1_wgrad<0, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               conv1_wgrad_smem<3>(n)));
+    NN_CK(cudaFuncSetAttribute(conv1_wgrad<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               conv1_wgrad_smem<3>(n)));
+  } else {
+    NN_CK(cudaFuncSetAttribute(conv1_wgrad<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               conv1_wgrad_smem<2>(n)));
+    NN_CK(cudaFuncSetAttribute(conv1_wgrad<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               conv1_wgrad_smem<2>(n)));
+  }
   NN_CK(cudaMalloc(&net.wgrad_part, sizeof(float) * (long long)net.wparts * (per + kC)));
   const long long pix = (long long)bmax * pts(n);
   NN_CK(cudaMalloc(&net.gy, sizeof(float) * pix));
@@ -767,19 +944,21 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   note_launches(1);
   // output conv
   const bf16* tfin = net.extra_active > 0 ? net.tt[net.extra_active - 1] : net.t;
-  // the 1-channel weight gradients have only 32 (T + 1) outputs per CTA: four
-  // times the CTAs of the 32 -> 32 ones, with a short partial stride, so the
-  // long pixel reduction has enough warps in flight
-  const int P1 = 4 * P, stride1 = kC * (T + 1);
-  conv1_wgrad<0, D><<<P1, 256, 0, s>>>(B, n, net.gy, tfin, nullptr, nullptr, net.wgrad_part,
-                                       stride1);
+  // the 1-channel weight gradients: 32 (T + 1) outputs per CTA (short stride)
+  const int P1 = P, stride1 = kC * (T + 1);
+  const int smem1 = conv1_wgrad_smem<D>(n);
+  conv1_wgrad<0, D><<<P1, kW1Threads, smem1, s>>>(B, n, net.gy, tfin, nullptr, nullptr, nullptr,
+                                                  net.wgrad_part, stride1);
   note_launches(1);
   reduce_wgrad<<<nblk(T * kC + 1, 32), 256, 0, s>>>(net.wgrad_part, P1, stride1, 2, T,
                                                      net.grad + net.off_w[L + 2],
                                                      net.grad + net.off_b[L + 2]);
   note_launches(1);
-  conv_out_bwd_data<D><<<nblk(pix, 256), 256, 0, s>>>(B, n, net.gy,
-                                                      net.master + net.off_w[L + 2], net.g_t);
+  // the first masked use of g_t (the last grown block's, else the residual
+  // block's) is written by the same kernel
+  const bf16* mask0 = net.extra_active > 0 ? net.te[net.extra_active - 1] : net.e;
+  conv_out_bwd_data<D><<<2 * P, kW1Threads, sizeof(float) * w1_stage_floats<D>(n), s>>>(
+      B, n, net.gy, net.master + net.off_w[L + 2], net.g_t, mask0, net.g_bf);
   note_launches(1);
   // grown residual blocks, last first: t_out = t_in + relu(conv_d2(t_in));
   // blocks not appended yet get a zero gradient (Adam then leaves them as they are)
@@ -790,8 +969,10 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
     float* gnext = net.g_s;
     for (int r = net.extra_active - 1; r >= 0; r--) {
       const bf16* tin = r == 0 ? net.t : net.tt[r - 1];
-      mask_to_bf16<<<nblk(full, 256), 256, 0, s>>>(full, gcur, net.te[r], net.g_bf);
-      note_launches(1);
+      if (r != net.extra_active - 1) {  // (the first one came with g_t)
+        mask_to_bf16<<<nblk((full) / 8, 256), 256, 0, s>>>(full, gcur, net.te[r], net.g_bf);
+        note_launches(1);
+      }
       NN_CK(launch_wgrad_mma(D, B, n, tin, net.g_bf, 2, net.wgrad_part, stride, P, s));
       reduce_wgrad<<<nblk(per + kC, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
                                                        net.grad + net.off_rw[r],
@@ -805,8 +986,10 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
       NN_CK(cudaMemcpyAsync(net.g_t, gcur, sizeof(float) * full, cudaMemcpyDeviceToDevice, s));
   }
   // dilated residual block: t = s + e, e = relu(conv_d2(s))
-  mask_to_bf16<<<nblk(full, 256), 256, 0, s>>>(full, net.g_t, net.e, net.g_bf);
-  note_launches(1);
+  if (net.extra_active > 0) {
+    mask_to_bf16<<<nblk((full) / 8, 256), 256, 0, s>>>(full, net.g_t, net.e, net.g_bf);
+    note_launches(1);
+  }
   NN_CK(launch_wgrad_mma(D, B, n, net.s, net.g_bf, 2, net.wgrad_part, stride, P, s));
   reduce_wgrad<<<nblk(per + kC, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
                                                    net.grad + net.off_w[L + 1],
@@ -814,7 +997,28 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   note_launches(1);
   NN_CK(launch_conv32_mma(D, 2, B, n, net.g_bf, net.wq + per * L, nullptr, 2, -1, nullptr,
                           nullptr, nullptr, net.g_s, net.g_t, s));
-  // pyramid levels
+  // pyramid levels; first the x-axis pass of every coarse level's transposed
+  // upsampling, from one read of the fine gradient (g_s) into g_t (free here:
+  // the residual block's gradient is already in g_s)
+  long long xoff[kMaxLevels] = {};
+  const bool fused_x = L > 1 && n <= kXLevelsMaxN;
+  if (fused_x) {
+    UpXLevels lv;
+    lv.nlev = L;
+    const long long rows = B * Geo<D>::pts(n) / n;
+    long long off = 0;
+    for (int l = 1; l < L; l++) {
+      lv.m[l] = net.side[l];
+      lv.ptr[l] = net.up_ptr[l];
+      lv.idx[l] = net.up_idx[l];
+      lv.wt[l] = net.up_w[l];
+      lv.off[l] = xoff[l] = off;
+      off += rows * net.side[l] * kC;
+    }
+    upsample_bwd_x_levels<<<(unsigned)rows, 256, sizeof(float) * n * kC, s>>>(n, lv, net.g_s,
+                                                                               net.g_t);
+    note_launches(1);
+  }
   for (int l = 0; l < L; l++) {
     const int sd = net.side[l];
     const long long lp = B * Geo<D>::pts(sd);
@@ -826,26 +1030,31 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
       const int* up = net.up_ptr[l];
       const int* ui = net.up_idx[l];
       const float* uw = net.up_w[l];
+      const float* gx = net.g_t + xoff[l];  // this level's x-axis pass (above)
+      if (!fused_x) {  // (rows too long to stage: the level's own x-axis pass)
+        upsample_bwd_axis<<<nblk(B * Geo<D>::pts(n) / n * m * kC, 256), 256, 0, s>>>(
+            B * Geo<D>::pts(n) / n, n, sd, kC, up, ui, uw, net.g_s, net.g_t, nullptr, nullptr);
+        note_launches(1);
+        gx = net.g_t;
+      }
       if (D == 2) {
-        upsample_bwd_axis<<<nblk(B * nn * m * kC, 256), 256, 0, s>>>(B * nn, n, sd, kC, up, ui,
-                                                                     uw, net.g_s, net.g_t);
-        upsample_bwd_axis<<<nblk(B * m * m * kC, 256), 256, 0, s>>>(B, n, sd, m * kC, up, ui, uw,
-                                                                    net.g_t, net.g_lvl);
-        note_launches(2);
-        gz = net.g_lvl;
+        upsample_bwd_axis<<<nblk(B * m * m * kC, 256), 256, 0, s>>>(
+            B, n, sd, m * kC, up, ui, uw, gx, nullptr, net.z[l], net.g_bf);
+        note_launches(1);
+        gz = nullptr;  // masked BF16 gradient already in g_bf
       } else {
-        upsample_bwd_axis<<<nblk(B * nn * nn * m * kC, 256), 256, 0, s>>>(
-            B * nn * nn, n, sd, kC, up, ui, uw, net.g_s, net.g_t);
         upsample_bwd_axis<<<nblk(B * nn * m * m * kC, 256), 256, 0, s>>>(
-            B * nn, n, sd, m * kC, up, ui, uw, net.g_t, net.g_lvl);
+            B * nn, n, sd, m * kC, up, ui, uw, gx, net.g_lvl, nullptr, nullptr);
         upsample_bwd_axis<<<nblk(B * m * m * m * kC, 256), 256, 0, s>>>(
-            B, n, sd, m * m * kC, up, ui, uw, net.g_lvl, net.g_t);
-        note_launches(3);
-        gz = net.g_t;
+            B, n, sd, m * m * kC, up, ui, uw, net.g_lvl, nullptr, net.z[l], net.g_bf);
+        note_launches(2);
+        gz = nullptr;
       }
     }
-    mask_to_bf16<<<nblk(lp * kC, 256), 256, 0, s>>>(lp * kC, gz, net.z[l], net.g_bf);
-    note_launches(1);
+    if (gz) {
+      mask_to_bf16<<<nblk((lp * kC) / 8, 256), 256, 0, s>>>(lp * kC, gz, net.z[l], net.g_bf);
+      note_launches(1);
+    }
     const bf16* in = l == 0 ? net.a0 : net.pool[l];
     NN_CK(launch_wgrad_mma(D, B, sd, in, net.g_bf, 1, net.wgrad_part, stride, P, s));
     reduce_wgrad<<<nblk(per + kC, 32), 256, 0, s>>>(net.wgrad_part, P, stride, 0, T,
@@ -864,10 +1073,10 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
     note_launches(1);
   }
   // input conv
-  mask_f32<<<nblk(full, 256), 256, 0, s>>>(full, net.g_pool + net.lvl_off[0], net.a0, net.g_lvl);
-  note_launches(1);
-  conv1_wgrad<1, D><<<P1, 256, 0, s>>>(B, n, nullptr, nullptr, net.g_lvl, u, net.wgrad_part,
-                                       stride1);
+  // (the ReLU mask of a0 is applied inside the weight-gradient kernel)
+  conv1_wgrad<1, D><<<P1, kW1Threads, smem1, s>>>(B, n, nullptr, nullptr,
+                                                  net.g_pool + net.lvl_off[0], net.a0, u,
+                                                  net.wgrad_part, stride1);
   note_launches(1);
   reduce_wgrad<<<nblk(T * kC + kC, 32), 256, 0, s>>>(net.wgrad_part, P1, stride1, 1, T,
                                                       net.grad + net.off_w[0],
