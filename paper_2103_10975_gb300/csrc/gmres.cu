@@ -42,9 +42,12 @@ int gmres_compact_cap(int dim, int m, int P) {
   const long long budget = (long long)per_sm / 2 - 1024 - own;  // per CTA
   const long long row = 32LL * 4;
   const long long share = budget / 8 / 128 * 128;
-  const long long want = (long long)P * m * row;
+  // a stage: m rows of V and the X pass's w'/kappa windows
+  const long long stage = (long long)m * row + (dim == 2 ? Aux<float, 2>::kXBytes
+                                                          : Aux<float, 3>::kXBytes);
+  const long long want = (long long)P * stage;
   const long long cap = want < share ? want : share;
-  return cap >= (long long)m * row ? (int)cap : 0;
+  return cap >= stage ? (int)cap : 0;
 }
 
 bool gmres_compact_ok(bool fp32, int dim, int m) {
@@ -105,9 +108,13 @@ int gmres_bulk_cap(bool fp32, int m, int P) {
   if (P <= 0) return 0;
   const long long row = 32LL * (fp32 ? 4 : 8);                                  // bytes
   const long long share = (long long)gmres_vsmem_budget(fp32) / 8 / 128 * 128;  // per warp
-  const long long want = (long long)P * m * row;
+  // a stage: m rows of V and the X pass's w'/kappa windows (the 3D size, the
+  // larger of the two dimensions)
+  const long long stage =
+      (long long)m * row + (fp32 ? Aux<float, 3>::kXBytes : Aux<double, 3>::kXBytes);
+  const long long want = (long long)P * stage;
   const long long cap = want < share ? want : share;
-  return cap >= (long long)m * row ? (int)cap : 0;
+  return cap >= stage ? (int)cap : 0;
 }
 
 int gmres_bulk_stages(bool fp32, int m) {

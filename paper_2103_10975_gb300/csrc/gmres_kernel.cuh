@@ -756,46 +756,132 @@ __device__ __forceinline__ void y_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
   warp_slot<LMAX>(sm.red, j + 1, accN);
 }
 
-// Per-warp ring of bulk-copy stages for one pass that needs `rows` rows of V
-// per tile: as many stages as fit in the warp's share of the staging buffer
-// (up to pp.P), so that small j keep more tiles in flight.
-template <typename T>
+// Besides the tile's V rows, every stage carries the other values the pass
+// needs, so that no load of a pass waits outside the bulk-copy pipeline:
+//   X pass: w' over [i0 - 4, i0 + 36) (the tile and its +-1 neighbours) and
+//           the rows of the tile's neighbours across the grid (+-n; in 3D also
+//           +-n^2), 36 values each from a 16-byte aligned start; in 3D with
+//           kappa (when kappa is 16-byte aligned and N a multiple of 4) the
+//           same windows of kappa;
+//   Y pass: z over the tile.
+// Copies are clipped to the arrays (w' and z to ldv, kappa to N); the clipped
+// parts are never read (the stencil's boundary tests exclude them).
+template <typename T, int DIM>
+struct Aux {
+  static constexpr int kRows = DIM == 3 ? 4 : 2;  // -n, +n (, -n^2, +n^2)
+  static constexpr int kCen = 40, kRow = 36;
+  static constexpr int kW = kCen + kRows * kRow;  // elements of T (w')
+  static constexpr int kK = DIM == 3 ? kW : 0;    // floats (kappa)
+  static constexpr int kXBytes = kW * (int)sizeof(T) + kK * 4;
+  static constexpr int kYBytes = 32 * (int)sizeof(T);
+};
+
+// Per-warp ring of bulk-copy stages for one pass: `vrows` rows of V per tile
+// plus `abytes` of auxiliary values; as many stages as fit in the warp's share
+// of the staging buffer (up to pp.P), so that small j keep more tiles in flight.
 struct BulkRing {
-  T* st;                      // the warp's staging area
+  unsigned char* st;          // the warp's staging area
   unsigned long long* bars;   // the warp's stage barriers
-  unsigned bytes;             // bytes per stage (rows * 32 * sizeof(T))
+  unsigned vbytes;            // V part of a stage (rows * 32 * sizeof(T))
+  unsigned bytes;             // bytes per stage (V part + auxiliary part)
   int P;                      // stages in use for this pass
 };
 
 template <typename T>
-__device__ __forceinline__ BulkRing<T> bulk_ring(const BulkPipe& pp, int rows) {
-  BulkRing<T> r;
+__device__ __forceinline__ BulkRing bulk_ring(const BulkPipe& pp, int vrows, int abytes) {
+  BulkRing r;
   const int warp = threadIdx.x >> 5;
-  r.st = reinterpret_cast<T*>(pp.stage + (size_t)warp * pp.cap);
+  r.st = pp.stage + (size_t)warp * pp.cap;
   r.bars = pp.bar + warp * kMaxStages;
-  r.bytes = (unsigned)rows * 32u * (unsigned)sizeof(T);
-  const int fit = rows > 0 ? pp.cap / (int)r.bytes : pp.P;
+  r.vbytes = (unsigned)vrows * 32u * (unsigned)sizeof(T);
+  r.bytes = r.vbytes + (unsigned)abytes;
+  const int fit = pp.cap / (int)r.bytes;
   r.P = max(1, min(pp.P, fit));
   return r;
 }
 
-// Lane 0 issues the copy of tile q (rows 0..rows-1 of tile lo/32 + warp + NW q)
-// into stage q mod P.  The stage's previous contents were consumed by this
-// warp's shared loads before the __syncwarp that precedes every re-issue.
-template <int NW, typename T>
-__device__ __forceinline__ void bulk_issue(const BulkRing<T>& r, const T* V, int lo, int rows,
-                                           int q) {
+// a multiple of a (a power of two) at or below v, for negative v as well
+__device__ __forceinline__ int floor_to(int v, int a) { return v & ~(a - 1); }
+
+// Adds `bytes` to the stage's expected transaction count (no arrival).
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Copies the part of the run src[want, want + cnt) that lies in [0, limit) to
+// dst + (its start - want) elements, registering its bytes on the stage's
+// barrier first.  want, cnt and limit are multiples of 16 / sizeof(E).
+template <typename E>
+__device__ __forceinline__ void stage_run(E* dst, const E* src, int want, int cnt,
+                                          long long limit, unsigned long long* bar) {
+  const long long lo = want < 0 ? 0 : want;
+  const long long hi = (long long)want + cnt < limit ? (long long)want + cnt : limit;
+  if (hi <= lo) return;
+  const unsigned bytes = (unsigned)(hi - lo) * (unsigned)sizeof(E);
+  mbar_expect(bar, bytes);
+  bulk_g2s(dst + (lo - want), src + lo, bytes, bar);
+}
+
+struct AuxSrc {  // what the X pass's stages copy besides V
+  const void* wp;       // w' (elements of T)
+  const float* kap;     // kappa (3D), or null when it is not staged
+  int n;
+  long long N, ldv;
+};
+
+// Lane 0 issues stage q: tile lo/32 + warp + NW q.  X pass (aux != null):
+// V rows 0..r.vbytes/128-1 of the tile (layout of `rows` rows per tile) and the
+// w'/kappa windows; Y pass: V rows and z.  Each
+// copy registers its bytes before it is issued; the single arrival comes last,
+// so the stage's phase cannot complete early.
+template <int NW, typename T, int DIM>
+__device__ __forceinline__ void bulk_issue_stage(const BulkRing& r, const T* V, int lo, int rows,
+                                                 int q, const AuxSrc* aux, const T* Zsrc,
+                                                 long long ldv) {
+  using A = Aux<T, DIM>;
+  constexpr int ALN = 16 / (int)sizeof(T);
   const int sidx = q % r.P;
   const int i0 = lo + (int)((threadIdx.x >> 5) + NW * q) * 32;
-  mbar_expect_tx(&r.bars[sidx], r.bytes);
-  bulk_g2s(r.st + (size_t)sidx * (r.bytes / sizeof(T)), V + vbase(i0, rows), r.bytes,
-           &r.bars[sidx]);
+  unsigned char* st = r.st + (size_t)sidx * r.bytes;
+  T* at = reinterpret_cast<T*>(st + r.vbytes);
+  unsigned long long* bar = &r.bars[sidx];
+  if (r.vbytes) {
+    mbar_expect(bar, r.vbytes);
+    bulk_g2s(st, V + vbase(i0, rows), r.vbytes, bar);
+  }
+  if (aux) {
+    const T* wp = reinterpret_cast<const T*>(aux->wp);
+    const int n = aux->n, nn = n * n;
+    stage_run<T>(at, wp, i0 - 4, A::kCen, ldv, bar);
+#pragma unroll
+    for (int k = 0; k < A::kRows; k++) {
+      const int d = k == 0 ? -n : (k == 1 ? n : (k == 2 ? -nn : nn));
+      stage_run<T>(at + A::kCen + k * A::kRow, wp, floor_to(i0 + d, ALN), A::kRow, ldv, bar);
+    }
+    if (A::kK > 0 && aux->kap) {
+      float* ak = reinterpret_cast<float*>(at + A::kW);
+      stage_run<float>(ak, aux->kap, i0 - 4, A::kCen, aux->N, bar);
+#pragma unroll
+      for (int k = 0; k < A::kRows; k++) {
+        const int d = k == 0 ? -n : (k == 1 ? n : (k == 2 ? -nn : nn));
+        stage_run<float>(ak + A::kCen + k * A::kRow, aux->kap, floor_to(i0 + d, 4), A::kRow,
+                         aux->N, bar);
+      }
+    }
+  } else {
+    stage_run<T>(at, Zsrc, i0, 32, ldv, bar);
+  }
+  mbar_arrive(bar);
 }
 
 // Waits (bounded) for the copies this warp issued for trips q+1 .. last, so
 // that none is left in flight when a pass is abandoned.
-template <typename T>
-__device__ __forceinline__ void bulk_drain(const BulkRing<T>& r, const BulkPipe& pp, int q, int nq,
+__device__ __forceinline__ void bulk_drain(const BulkRing& r, const BulkPipe& pp, int q, int nq,
                                            unsigned& phase) {
   for (int t = q + 1; t < nq && t < q + r.P; t++) {
     const int sidx = t % r.P;
@@ -804,15 +890,78 @@ __device__ __forceinline__ void bulk_drain(const BulkRing<T>& r, const BulkPipe&
   }
 }
 
-// X pass with V in HBM, staged per warp through the bulk-copy ring.
-// The V column of a point is read from the stage twice (update, then dots)
-// instead of being held in registers.
+// The stencil of stencil<T, DIM> at point i = i0 + lane from a stage's w'
+// windows (and kappa windows when staged; else kappa from global memory):
+// the same differences, faces and order.
+template <typename T, int DIM>
+__device__ __forceinline__ T stencil_staged(const T* aw, const float* ak,
+                                            const float* __restrict__ kappa, int i, int i0,
+                                            int lane, int n) {
+  using A = Aux<T, DIM>;
+  constexpr int ALN = 16 / (int)sizeof(T);
+  const T uc = aw[4 + lane];
+  // neighbour f (-1, +1, -n, +n, -n^2, +n^2): its w' in the stage, and its kappa
+  auto wnb = [&](int f) -> T {
+    if (f < 2) return aw[4 + lane + (f == 0 ? -1 : 1)];
+    const int k = f - 2, nn = n * n;
+    const int d = k == 0 ? -n : (k == 1 ? n : (k == 2 ? -nn : nn));
+    return aw[A::kCen + k * A::kRow + (i0 + d - floor_to(i0 + d, ALN)) + lane];
+  };
+  if constexpr (DIM == 2) {
+    const int ix = i % n, iy = i / n;
+    const T l = ix > 0 ? wnb(0) : T(0);
+    const T r = ix < n - 1 ? wnb(1) : T(0);
+    const T d = iy > 0 ? wnb(2) : T(0);
+    const T t = iy < n - 1 ? wnb(3) : T(0);
+    return ((uc - l) + (uc - r)) + ((uc - d) + (uc - t));
+  } else {
+    const int ix = i % n;
+    const int tq = i / n;
+    const int iy = tq % n;
+    const int iz = tq / n;
+    const int nn = n * n;
+    T acc = T(0);
+    if (kappa) {
+      auto knbf = [&](int f) -> T {
+        const int off = f == 0 ? -1 : (f == 1 ? 1 : (f == 2 ? -n : (f == 3 ? n : (f == 4 ? -nn : nn))));
+        if (!ak) return (T)__ldg(kappa + i + off);
+        if (f < 2) return (T)ak[4 + lane + off];
+        const int k = f - 2;
+        return (T)ak[A::kCen + k * A::kRow + (i0 + off - floor_to(i0 + off, 4)) + lane];
+      };
+      const T kc = ak ? (T)ak[4 + lane] : (T)__ldg(kappa + i);
+#pragma unroll
+      for (int f = 0; f < 6; f++) {
+        const bool has = f == 0 ? ix > 0 : f == 1 ? ix < n - 1 : f == 2 ? iy > 0
+                       : f == 3 ? iy < n - 1 : f == 4 ? iz > 0 : iz < n - 1;
+        if (has)
+          acc += face(kc, knbf(f)) * (uc - wnb(f));
+        else
+          acc += kc * uc;
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < 6; f++) {
+        const bool has = f == 0 ? ix > 0 : f == 1 ? ix < n - 1 : f == 2 ? iy > 0
+                       : f == 3 ? iy < n - 1 : f == 4 ? iz > 0 : iz < n - 1;
+        acc += has ? (uc - wnb(f)) : uc;
+      }
+    }
+    return acc;
+  }
+}
+
+// X pass with V in HBM, staged per warp through the bulk-copy ring together
+// with the w' (and kappa) windows.  The V column of a point is read from the
+// stage twice (update, then dots) instead of being held in registers.
 template <typename T, int DIM, int MAXM, int BS, int K>
 __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int hi, int j,
                                             int n, const T* __restrict__ WP,
                                             T* __restrict__ Z, T* __restrict__ V,
                                             int rows, const float* __restrict__ kappa,
-                                            T s2t, const BulkPipe& pp, unsigned& phase) {
+                                            T s2t, const BulkPipe& pp, unsigned& phase,
+                                            const AuxSrc& aux) {
+  using A = Aux<T, DIM>;
   constexpr int LMAX = MAXM + 2;
   constexpr int NW = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -824,35 +973,40 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
   const T cj = sm.hcc[j].y;
   const int ntile = (hi - lo + 31) >> 5;
   const int nq = ntile > warp ? (ntile - warp + NW - 1) / NW : 0;
-  const BulkRing<T> r = bulk_ring<T>(pp, j);
-  if (j > 0 && lane == 0)
-    for (int q = 0; q < r.P && q < nq; q++) bulk_issue<NW>(r, V, lo, rows, q);
+  const BulkRing r = bulk_ring<T>(pp, j, A::kXBytes);
+  // w' (and z, V) were written through the generic proxy; the copies read
+  // through the async proxy
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  if (lane == 0)
+    for (int q = 0; q < r.P && q < nq; q++)
+      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q, &aux, nullptr, aux.ldv);
   bool good = true;
   int q = 0;
   for (; q < nq; q++) {
     const int sidx = q % r.P;
-    const int i = lo + (warp + NW * q) * 32 + lane;
+    const int i0 = lo + (warp + NW * q) * 32;
+    const int i = i0 + lane;
     const bool ok = i < hi;
-    // the operator part first: its loads overlap the wait for the stage
-    const T wp = ok ? ldcg(WP + i) : T(0);
-    T znum = ok ? s2t * stencil<T, DIM>(WP, i, n, kappa, wp) : T(0);
+    if (!mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
+      good = false;
+      break;
+    }
+    phase ^= 1u << sidx;
+    const unsigned char* stb = r.st + (size_t)sidx * r.bytes;
+    const T* sc = reinterpret_cast<const T*>(stb) + lane;
+    const T* aw = reinterpret_cast<const T*>(stb + r.vbytes);
+    const float* ak = (A::kK > 0 && aux.kap) ? reinterpret_cast<const float*>(aw + A::kW) : nullptr;
+    const T wp = ok ? aw[4 + lane] : T(0);
+    T znum = ok ? s2t * stencil_staged<T, DIM>(aw, ak, kappa, i, i0, lane, n) : T(0);
     T vnum = wp;
-    const T* sc = r.st + (size_t)sidx * (r.bytes / sizeof(T)) + lane;
-    if (j > 0) {
-      if (!mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
-        good = false;
-        break;
-      }
-      phase ^= 1u << sidx;
-      if (ok) {
+    if (ok) {
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-          if (k < j) {
-            const T v = sc[k << 5];
-            const auto hc = sm.hcc[k];
-            vnum -= hc.x * v;
-            znum -= hc.y * v;
-          }
+      for (int k = 0; k < K; k++) {
+        if (k < j) {
+          const T v = sc[k << 5];
+          const auto hc = sm.hcc[k];
+          vnum -= hc.x * v;
+          znum -= hc.y * v;
         }
       }
     }
@@ -872,21 +1026,23 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
       accZ += z * z;
     }
     __syncwarp();
-    if (j > 0 && lane == 0 && q + r.P < nq) bulk_issue<NW>(r, V, lo, rows, q + r.P);
+    if (lane == 0 && q + r.P < nq)
+      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q + r.P, &aux, nullptr, aux.ldv);
   }
-  if (!good && j > 0) bulk_drain(r, pp, q, nq, phase);
-  // the V_j stores above are read by later bulk copies (async proxy)
+  if (!good) bulk_drain(r, pp, q, nq, phase);
+  // the V_j and z stores above are read by later bulk copies (async proxy)
   asm volatile("fence.proxy.async.global;" ::: "memory");
   warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accZ);
 }
 
-// Y pass with V in HBM through the bulk-copy ring.
-template <typename T, int MAXM, int BS, int K>
+// Y pass with V in HBM through the bulk-copy ring (V rows and z per stage).
+template <typename T, int DIM, int MAXM, int BS, int K>
 __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int hi, int j,
                                             T* __restrict__ WP, const T* __restrict__ Z,
                                             const T* __restrict__ V, int rows,
-                                            const BulkPipe& pp, unsigned& phase) {
+                                            const BulkPipe& pp, unsigned& phase, long long ldv) {
+  using A = Aux<T, DIM>;
   constexpr int LMAX = MAXM + 2;
   constexpr int NW = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -896,22 +1052,24 @@ __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
   T accN = T(0);
   const int ntile = (hi - lo + 31) >> 5;
   const int nq = ntile > warp ? (ntile - warp + NW - 1) / NW : 0;
-  const BulkRing<T> r = bulk_ring<T>(pp, j + 1);
+  const BulkRing r = bulk_ring<T>(pp, j + 1, A::kYBytes);
   if (lane == 0)
-    for (int q = 0; q < r.P && q < nq; q++) bulk_issue<NW>(r, V, lo, rows, q);
+    for (int q = 0; q < r.P && q < nq; q++)
+      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q, nullptr, Z, ldv);
   bool good = true;
   int q = 0;
   for (; q < nq; q++) {
     const int sidx = q % r.P;
     const int i = lo + (warp + NW * q) * 32 + lane;
     const bool ok = i < hi;
-    T qv = ok ? Z[i] : T(0);
     if (!mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
       good = false;
       break;
     }
     phase ^= 1u << sidx;
-    const T* sc = r.st + (size_t)sidx * (r.bytes / sizeof(T)) + lane;
+    const unsigned char* stb = r.st + (size_t)sidx * r.bytes;
+    const T* sc = reinterpret_cast<const T*>(stb) + lane;
+    T qv = ok ? reinterpret_cast<const T*>(stb + r.vbytes)[lane] : T(0);
     if (ok) {
 #pragma unroll
       for (int k = 0; k < K; k++)
@@ -923,7 +1081,8 @@ __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
         if (k <= j) acc[k] += sc[k << 5] * qv;
     }
     __syncwarp();
-    if (lane == 0 && q + r.P < nq) bulk_issue<NW>(r, V, lo, rows, q + r.P);
+    if (lane == 0 && q + r.P < nq)
+      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q + r.P, nullptr, Z, ldv);
   }
   if (!good) bulk_drain(r, pp, q, nq, phase);
   warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
@@ -998,6 +1157,17 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   pipe.timeout_ns = w.bar.timeout_ns;
   T* __restrict__ WP = (T*)w.W0;  // w' (read by neighbours in X, rewritten in Y)
   T* __restrict__ Z = (T*)w.W1;   // z = A v_j, own rows only
+  // what the bulk-copy stages carry besides V (kappa only when its copies can
+  // be 16-byte aligned: aligned base, N a multiple of 4)
+  AuxSrc auxs;
+  auxs.wp = WP;
+  auxs.kap = (tk.kappa && ((unsigned long long)tk.kappa & 15ull) == 0 && (N & 3) == 0)
+                 ? tk.kappa
+                 : nullptr;
+  auxs.n = n;
+  auxs.N = N;
+  auxs.ldv = w.ldv;
+  (void)auxs;
   const double h = 2.0 / (n + 1);
   const double s2 = 1.0 / (h * h);
   const T s2t = (T)s2;
@@ -1017,6 +1187,12 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
 
   if (VM == kVShared && (long long)chunk * rows * (long long)sizeof(T) > kp.vsmem) {
     status = kErrConfig;  // the slice would overrun the shared-memory reservation
+    goto finish;
+  }
+  // a warp's staging area must hold one stage of m rows and the X pass's windows
+  if (VM == kVBulk &&
+      kp.bulk_cap < m * 32 * (int)sizeof(T) + Aux<T, DIM>::kXBytes) {
+    status = kErrConfig;
     goto finish;
   }
 
@@ -1126,8 +1302,9 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       {
 #define MLG_X(KK) x_pass<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vg, rows, 0, kappa, s2t)
 #define MLG_XS(KK) x_pass_sm<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vs, rows, kappa, s2t, cy)
-#define MLG_XB(KK) \
-  x_pass_bulk<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vg, rows, kappa, s2t, pipe, bphase)
+#define MLG_XB(KK)                                                                       \
+  x_pass_bulk<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, n, WP, Z, Vg, rows, kappa, s2t, pipe, bphase, \
+                                    auxs)
         if constexpr (VM == kVShared) {
           MLG_BUCKETS(MLG_XS)
         } else if constexpr (VM == kVBulk) {
@@ -1161,7 +1338,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       {
 #define MLG_Y(KK) y_pass<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vg, rows, 0)
 #define MLG_YS(KK) y_pass_sm<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vs, rows, cy)
-#define MLG_YB(KK) y_pass_bulk<T, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vg, rows, pipe, bphase)
+#define MLG_YB(KK) \
+  y_pass_bulk<T, DIM, MAXM, BS, KK>(sm, lo, hi, j, WP, Z, Vg, rows, pipe, bphase, w.ldv)
         if constexpr (VM == kVShared) {
           MLG_BUCKETS(MLG_YS)
         } else if constexpr (VM == kVBulk) {
