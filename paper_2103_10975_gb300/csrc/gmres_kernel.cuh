@@ -43,6 +43,14 @@ __device__ __forceinline__ T stencil2d(const T* __restrict__ u, int i, int n, T 
 
 template <typename T>
 __device__ __forceinline__ T face(T kc, T knb) { return T(2) * kc * knb / (kc + knb); }
+// The FP32 inner operator takes the fast reciprocal-based division (about 2 ulp,
+// two instructions) instead of the IEEE division sequence: six per point in 3D
+// were a third of the X pass's instructions.  Its rounding is of the order of
+// the FP32 arithmetic around it; the FP64 restart residual keeps the exact face.
+template <>
+__device__ __forceinline__ float face<float>(float kc, float knb) {
+  return __fdividef(2.f * kc * knb, kc + knb);
+}
 
 template <typename T>
 __device__ __forceinline__ T stencil3d(const T* __restrict__ u, int i, int n,
@@ -896,7 +904,7 @@ __device__ __forceinline__ void bulk_drain(const BulkRing& r, const BulkPipe& pp
 template <typename T, int DIM>
 __device__ __forceinline__ T stencil_staged(const T* aw, const float* ak,
                                             const float* __restrict__ kappa, int i, int i0,
-                                            int lane, int n) {
+                                            int lane, int n, int ix, int iy, int iz) {
   using A = Aux<T, DIM>;
   constexpr int ALN = 16 / (int)sizeof(T);
   const T uc = aw[4 + lane];
@@ -908,17 +916,12 @@ __device__ __forceinline__ T stencil_staged(const T* aw, const float* ak,
     return aw[A::kCen + k * A::kRow + (i0 + d - floor_to(i0 + d, ALN)) + lane];
   };
   if constexpr (DIM == 2) {
-    const int ix = i % n, iy = i / n;
     const T l = ix > 0 ? wnb(0) : T(0);
     const T r = ix < n - 1 ? wnb(1) : T(0);
     const T d = iy > 0 ? wnb(2) : T(0);
     const T t = iy < n - 1 ? wnb(3) : T(0);
     return ((uc - l) + (uc - r)) + ((uc - d) + (uc - t));
   } else {
-    const int ix = i % n;
-    const int tq = i / n;
-    const int iy = tq % n;
-    const int iz = tq / n;
     const int nn = n * n;
     T acc = T(0);
     if (kappa) {
@@ -981,6 +984,16 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
     for (int q = 0; q < r.P && q < nq; q++)
       bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q, &aux, nullptr, aux.ldv);
   bool good = true;
+  // grid coordinates of this lane's point, advanced by NW * 32 points per trip
+  // (integer divisions once per pass instead of once per point)
+  int px = 0, py = 0, pz = 0;
+  {
+    const int i = lo + warp * 32 + lane;
+    px = i % n;
+    const int t = i / n;
+    py = DIM == 3 ? t % n : t;
+    pz = DIM == 3 ? t / n : 0;
+  }
   int q = 0;
   for (; q < nq; q++) {
     const int sidx = q % r.P;
@@ -997,7 +1010,22 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
     const T* aw = reinterpret_cast<const T*>(stb + r.vbytes);
     const float* ak = (A::kK > 0 && aux.kap) ? reinterpret_cast<const float*>(aw + A::kW) : nullptr;
     const T wp = ok ? aw[4 + lane] : T(0);
-    T znum = ok ? s2t * stencil_staged<T, DIM>(aw, ak, kappa, i, i0, lane, n) : T(0);
+    // (2D: the division per point measured faster than the incremental form)
+    if constexpr (DIM == 2) {
+      px = i % n;
+      py = i / n;
+    }
+    T znum = ok ? s2t * stencil_staged<T, DIM>(aw, ak, kappa, i, i0, lane, n, px, py, pz) : T(0);
+    if constexpr (DIM == 3) {
+      px += NW * 32;  // the next trip's point
+      while (px >= n) {
+        px -= n;
+        if (++py == n) {
+          py = 0;
+          ++pz;
+        }
+      }
+    }
     T vnum = wp;
     if (ok) {
 #pragma unroll
