@@ -131,8 +131,10 @@ typedef struct {
                                 else 16) */
   int retrain_after;         /* f_r of Algorithm 1 (Sec. 2.2): when > 0, mlgmres_solve itself
                                 starts a training phase (as mlgmres_train_step, on a stream
-                                of the handle) once f_r pairs have been admitted since the
-                                previous phase, and from tau0 on; 0 = the caller decides
+                                of the handle) at tau0 and then once f_r under-performing
+                                steps (steps that fail the M_p test, whether or not their
+                                pair passes the spread check: Algorithm 1's counter N) have
+                                been seen since the previous phase; 0 = the caller decides
                                 when to call mlgmres_train_step (fixed cadence) */
   int grow_blocks;           /* adaptive depth (Sec. 2.1): up to this many residual blocks
                                 (0..4) are appended before the output layer, one at a
@@ -151,6 +153,14 @@ typedef struct {
                                 spectrum of A T; N <= 4096, T starts at 0 and trains by
                                 plain gradient descent with step lr; the nn_* entry
                                 points then see T, row-major, as the parameters) */
+  int overlap_train;         /* 1: training phases run beside the solves (Sec. 2.3 trains in
+                                real time while the simulation goes on): the guess is formed
+                                by an inference copy of the network, and a solve takes the
+                                parameters of the latest phase only once that phase has
+                                completed -- it never waits for one that is still running
+                                (unless the phase runs on the solve's own stream); 0: every
+                                solve waits for the latest phase first (deterministic, the
+                                linear model always does) */
 } mlgmres_options;
 
 typedef struct {
@@ -175,7 +185,7 @@ typedef struct {
  * deterministic_tos 0, train_iters 32, batch 8, lr 1e-3, seed 1,
  * grid_blocks 0, batch_slots 0, barrier_timeout_s 2, guess_smooth 8, guess_omega 0.8,
  * guess_select 0, fault_inject 0, v_stages -1, retrain_after 0, grow_blocks 0,
- * grow_tol 0.02, compact -1, model CONV. */
+ * grow_tol 0.02, compact -1, model CONV, overlap_train 1. */
 void mlgmres_default_options(mlgmres_options* opt);
 
 /* Creates a solver for one grid and allocates all workspace on the current
@@ -214,11 +224,18 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
  * ||N(b/s) - x/(c s)||^2 over minibatches drawn from the replay ring (c is the
  * mean of rms(x)/rms(b) over the ring, so the targets have unit scale; the
  * guess is then x0 = c s N(b/s)), each batch
- * holding every pair admitted since the previous call (up to opt.batch) and
- * uniform samples of the rest.  Runs on side_stream and returns once enqueued;
- * the next solve waits for it.  loss_host (may be NULL) receives the mean loss
- * of the last minibatch after the phase completes (this synchronises). Does
- * nothing and returns OK while the ring is empty. */
+ * holding every candidate pair admitted since the previous call (C_t of
+ * Algorithm 1, up to opt.batch) and uniform samples of the rest.  The phase
+ * trains on a copy of the ring taken at its start, so solves issued while it
+ * runs may store new pairs.  Runs on side_stream and returns once enqueued.
+ * With opt.overlap_train = 1 the solves do not wait for it: each takes the
+ * phase's parameters once the phase has completed (solves issued on another
+ * stream while it runs keep the previous ones); with 0 the next solve waits
+ * for it.  If the previous phase is still running, this call first waits for
+ * it on the host (one phase at a time).  loss_host (may be NULL) receives the
+ * mean loss of the last minibatch after the phase completes (this
+ * synchronises). Does nothing and returns OK while the ring is empty or
+ * before tau0 solves. */
 mlgmres_status mlgmres_train_step(mlgmres_t h, void* side_stream, float* loss_host);
 
 /* Text of the last error on this handle ("" if none); valid until the next call. */
@@ -274,6 +291,16 @@ mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u_dev,
  * b_dev, x_dev: N doubles each, distinct.  An untrained network gives its
  * initial output. */
 mlgmres_status mlgmres_guess(mlgmres_t h, const double* b_dev, double* x_dev, void* stream);
+
+/* The damped-Jacobi sweeps that follow the network in the learned guess:
+ * `sweeps` times x <- x + omega D^-1 (b - A x), D the diagonal of A (4/h^2 in
+ * 2D; the sum of the face coefficients over h^2 in 3D) and omega the handle's
+ * guess_omega, on x_dev in place (input: the starting x; output: the result).
+ * b_dev, x_dev: N doubles each, distinct.  sweeps in 0..1000.  Not a step of
+ * the paper: it is how the library removes the BF16 rounding noise of the
+ * network's output, exposed so that its effect can be measured on its own. */
+mlgmres_status mlgmres_smooth(mlgmres_t h, const double* b_dev, double* x_dev, int sweeps,
+                              void* stream);
 
 /* Residual blocks appended so far by the adaptive growth (opt.grow_blocks).
  * set_to >= 0 sets the count (clamped to opt.grow_blocks; for tests and for

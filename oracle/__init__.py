@@ -12,9 +12,12 @@ Modules:
 * ``direct``  - dense assembly, DST-I fast Poisson solves, closed-form
                 eigenpairs, brute-force Krylov least squares (the pins).
 * ``nn``      - FP64 forward / backward / Adam of the initial-guess network.
-* ``gate``    - Algorithm 1's moving-average gate and spread check.
+* ``gate``    - Algorithm 1's moving-average gate, spread check and
+                retraining counter.
+* ``guess``   - the learned guess as a whole: c s N(b/s), then damped-Jacobi
+                sweeps.
 
-Parity status: the GMRES oracle, operators, network and gate are each pinned
+Parity status: the GMRES oracle, operators, network, guess and gate are each pinned
 by tests under ``tests/`` against closed forms, dense LU, finite differences
 or hand-worked sequences.  The online training trajectory as a whole is
 parity unpinned (it depends on stochastic minibatch sampling); only its

@@ -12,7 +12,12 @@ Readings of the paper used here (it leaves these open or prints them garbled):
   |cos angle(x_n, x_c)| <= theta for every x_c already in C_t (the candidates
   gathered since the last training call).  theta = 0.9.
 * During warm-up (steps before tau0) every pair is admitted; the gate only
-  runs from step tau0 on.
+  runs from step tau0 on.  Warm-up pairs go to the training set X_t, not to
+  C_t: Algorithm 1 starts from an empty C_t right after the warm-up training.
+* The retraining counter N of Algorithm 1 counts every step after warm-up that
+  fails the M_p test, whether or not its pair passes the spread check (the
+  algorithm increments N after the spread test, outside it).  Retraining is
+  due once N >= f_r; training resets N and empties C_t.
 """
 
 import math
@@ -52,7 +57,9 @@ class GateRef:
     """Step-by-step decisions of the collection policy.
 
     ``step(E, TOS, x)`` returns True when the pair is admitted to the replay
-    buffer.  ``trained()`` empties C_t, as after a training call.
+    buffer.  ``trained()`` empties C_t and resets N, as after a training call.
+    ``N`` is Algorithm 1's count of under-performing steps since then;
+    ``due(f_r)`` says whether retraining is due.
     """
 
     def __init__(self, p=10, theta=0.9, warmup=50):
@@ -62,6 +69,7 @@ class GateRef:
         self.E = []
         self.T = []
         self.C = []
+        self.N = 0
         self.steps = 0
 
     def step(self, E, TOS, x):
@@ -72,6 +80,7 @@ class GateRef:
             return True
         if is_good(self.E, self.T, self.p):
             return False
+        self.N += 1
         if spread_ok(x, self.C, self.theta):
             self.C.append(np.asarray(x, dtype=np.float64))
             return True
@@ -79,3 +88,7 @@ class GateRef:
 
     def trained(self):
         self.C = []
+        self.N = 0
+
+    def due(self, f_r):
+        return self.N >= f_r

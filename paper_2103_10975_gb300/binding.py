@@ -62,6 +62,7 @@ class Options(ctypes.Structure):
         ("grow_tol", ctypes.c_double),
         ("compact", ctypes.c_int),
         ("model", ctypes.c_int),
+        ("overlap_train", ctypes.c_int),
     ]
 
 
@@ -143,6 +144,7 @@ _SIGS = {
                                             ctypes.POINTER(Result)]),
     "mlgmres_guess": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mlgmres_nn_blocks": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "mlgmres_smooth": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "mlgmres_autotune": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                         ctypes.POINTER(Tuning)]),
     "mlgmres_batch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -396,6 +398,12 @@ class Solver:
         x = torch.empty_like(b)
         self._check(self.lib.mlgmres_guess(self.h, _ptr(b), _ptr(x), _stream_handle(stream)),
                     "guess")
+        return x
+
+    def smooth(self, b, x, sweeps, stream=None):
+        """mlgmres_smooth: `sweeps` damped-Jacobi sweeps of A x = b on x, in place."""
+        self._check(self.lib.mlgmres_smooth(self.h, _ptr(b), _ptr(x), int(sweeps),
+                                            _stream_handle(stream)), "smooth")
         return x
 
     def nn_blocks(self, set_to=-1):

@@ -61,14 +61,17 @@ struct mlgmres {
   mlg::Net net;
   mlg::Lin lin;                       // the dense linear model (opt.model = LINEAR)
   bool linear = false;
-  bool net_ready = false;             // trained at least once
+  bool net_ready = false;             // the guess holds trained parameters
   int train_calls = 0;
   // replay ring: normalised (b/s, x/s) pairs, FP32, N each
   float* ring_u = nullptr;
   float* ring_t = nullptr;
   int ring_count = 0;
   int ring_head = 0;                  // next slot to write
-  std::vector<int> fresh;             // slots admitted since the last train call (C_t)
+  std::vector<int> fresh;             // C_t: slots of the candidates admitted since the last
+                                      // training phase (warm-up pairs are not candidates)
+  int cand_n = 0;                     // Algorithm 1's N: under-performing steps since the
+                                      // last training phase (admitted or not)
   std::vector<double> E_hist, T_hist;
   std::vector<double> ring_c;         // rms(x)/rms(b) of each stored pair
   double c_train = 1.0;               // target scale used by the last training phase
@@ -78,9 +81,25 @@ struct mlgmres {
   double* ddots = nullptr;            // device dots for the spread check
   double* hdots = nullptr;            // pinned
   unsigned long long rng_state = 0;
-  cudaEvent_t train_done = nullptr;
+  // training phases run beside the solves (Sec. 2.3, training in real time):
+  // the guess reads only `inf`, an inference copy of the network with its own
+  // activations; a phase reads a snapshot of the ring taken at its start and
+  // ends by copying its parameters to `snap`, which a later solve copies into
+  // `inf` once the phase has completed
+  mlg::Net inf;
+  float* snap = nullptr;
+  float* ring_u_snap = nullptr;
+  float* ring_t_snap = nullptr;
+  cudaEvent_t train_done = nullptr;   // the latest phase (and its parameter snapshot) completed
+  cudaEvent_t ring_copied = nullptr;  // the latest phase's ring snapshot completed
+  cudaStream_t phase_stream = nullptr;  // stream of the latest phase
+  bool phase_enqueued = false;        // some phase was enqueued (the events are meaningful)
+  bool snap_pending = false;          // the latest phase's parameters are not in `inf` yet
+  double snap_c = 1.0;                // target scale c of that phase
+  int snap_extra = 0;                 // residual blocks of that phase
+  double c_guess = 1.0;               // c of the parameters `inf` holds
+  int phase_waits = 0;                // phases that had to wait for the previous one
   cudaStream_t train_stream = nullptr;  // training phases started by solve (retrain_after)
-  bool train_pending = false;
   float* loss_dev = nullptr;
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;

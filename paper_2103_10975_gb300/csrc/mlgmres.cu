@@ -106,6 +106,7 @@ void check_options(mlgmres* h, const mlgmres_options* o) {
   ARG(o->compact >= -1 && o->compact <= 1, "compact must be -1, 0 or 1");
   ARG(o->model == MLGMRES_MODEL_CONV || o->grow_blocks == 0,
       "grow_blocks applies to the convolutional model only");
+  ARG(o->overlap_train == 0 || o->overlap_train == 1, "overlap_train must be 0 or 1");
 }
 
 // Bulk-copy stages the passes use for an FP32 basis in HBM.
@@ -120,14 +121,14 @@ int effective_stages(const mlgmres* h) {
 void ensure_net(mlgmres* h) {
   if (h->net.master || h->lin.T) return;
   const mlgmres_options* opt = &h->opt;
-  CK(cudaMalloc(&h->x_alt, sizeof(double) * h->ldv));
-  CK(cudaMalloc(&h->x_tmp, sizeof(double) * h->ldv));
   CK(cudaMalloc(&h->u_in, sizeof(float) * h->ldv));
   CK(cudaMalloc(&h->y_out, sizeof(float) * h->ldv));
   CK(cudaMalloc(&h->ring_u, sizeof(float) * h->ldv * opt->replay_cap));
   CK(cudaMalloc(&h->ring_t, sizeof(float) * h->ldv * opt->replay_cap));
   CK(cudaMalloc(&h->ddots, sizeof(double) * (2 * opt->replay_cap + 1)));
   CK(cudaMallocHost(&h->hdots, sizeof(double) * (2 * opt->replay_cap + 1)));
+  CK(cudaMalloc(&h->ring_u_snap, sizeof(float) * h->ldv * opt->replay_cap));
+  CK(cudaMalloc(&h->ring_t_snap, sizeof(float) * h->ldv * opt->replay_cap));
   CK(cudaMalloc(&h->loss_dev, sizeof(float) * 4));
   if (opt->model == MLGMRES_MODEL_LINEAR) {
     ARG(h->N <= 4096, "the linear model needs N <= 4096");
@@ -137,15 +138,64 @@ void ensure_net(mlgmres* h) {
     ARG(32LL * opt->batch * h->N < (1LL << 31),
         "the network indexes its activations in 32 bits: 32 * batch * n^dim must be < 2^31");
     CK(net_create(h->net, h->grid.n, opt->batch, opt->seed, h->grid.dim, opt->grow_blocks));
+    // the inference copy starts from the same initial parameters (same seed)
+    CK(net_create(h->inf, h->grid.n, 1, opt->seed, h->grid.dim, opt->grow_blocks, true));
+    CK(cudaMalloc(&h->snap, sizeof(float) * h->net.nparams));
   }
 }
 
-// Forward pass of the handle's model on `batch` normalised inputs.
+// cudaEventQuery's "not ready" is a state, not a failure: keep it out of the
+// error that the next launch check reads
+cudaError_t query_event(cudaEvent_t e) {
+  const cudaError_t q = cudaEventQuery(e);
+  if (q == cudaErrorNotReady && cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+  return q;
+}
+
+// Moves the parameters of the latest training phase into the guess's network,
+// on stream s.  With overlap_train (and for another stream than the phase's)
+// only once the phase has completed: a solve issued while it runs keeps the
+// previous parameters and never waits.  Otherwise s waits for the phase.
+void take_snapshot(mlgmres* h, cudaStream_t s) {
+  if (!h->snap_pending) return;
+  const bool same = s == h->phase_stream;
+  if (h->linear || h->opt.overlap_train == 0 || same) {
+    if (!same) CK(cudaStreamWaitEvent(s, h->train_done, 0));
+  } else {
+    const cudaError_t q = query_event(h->train_done);
+    if (q == cudaErrorNotReady) return;
+    CK(q);
+  }
+  if (!h->linear) {
+    CK(net_copy_params(h->inf, h->snap, s));
+    h->inf.extra_active = h->snap_extra;
+  }
+  h->c_guess = h->snap_c;
+  h->snap_pending = false;
+  h->net_ready = true;
+}
+
+// Forward pass of the handle's model on `batch` normalised inputs (the
+// training copy of the network).
 void model_forward(mlgmres* h, int batch, const float* u, float* y, cudaStream_t s) {
   if (h->linear)
     CK(lin_forward(h->lin, batch, u, y, s));
   else
     CK(net_forward(h->net, batch, u, y, s));
+}
+
+// Forward pass of the guess: the inference copy of the network (one sample).
+void guess_forward(mlgmres* h, const float* u, float* y, cudaStream_t s) {
+  if (h->linear)
+    CK(lin_forward(h->lin, 1, u, y, s));
+  else
+    CK(net_forward(h->inf, 1, u, y, s));
+}
+
+// Streams that touch the training copy of the network (inspection entry
+// points) first wait for the latest phase.
+void wait_phase(mlgmres* h, cudaStream_t s) {
+  if (h->phase_enqueued && s != h->phase_stream) CK(cudaStreamWaitEvent(s, h->train_done, 0));
 }
 
 long long model_params(const mlgmres* h) {
@@ -155,16 +205,16 @@ float* model_master(mlgmres* h) { return h->linear ? h->lin.T : h->net.master; }
 float* model_grad(mlgmres* h) { return h->linear ? h->lin.grad : h->net.grad; }
 
 // The learned guess x0 = c s N(b/s) (s = rms(b), c the target scale of the
-// last training phase), then opt.guess_smooth damped-Jacobi sweeps; returns
-// the buffer (x_alt or x_tmp) that holds it.
+// training phase whose parameters the guess holds), then opt.guess_smooth
+// damped-Jacobi sweeps; returns the buffer (x_alt or x_tmp) that holds it.
 double* learned_guess(mlgmres* h, const double* b, cudaStream_t s) {
   const int N = h->N;
   CK(launch_sumsq(b, N, h->scal, s));
   CK(launch_normalise(b, N, h->scal, h->u_in, s));
-  model_forward(h, 1, h->u_in, h->y_out, s);
+  guess_forward(h, h->u_in, h->y_out, s);
   double* cur = h->x_alt;
   double* oth = h->x_tmp;
-  CK(launch_denormalise(h->y_out, N, h->scal, h->c_train, cur, s));
+  CK(launch_denormalise(h->y_out, N, h->scal, h->c_guess, cur, s));
   for (int k = 0; k < h->opt.guess_smooth; k++) {
     CK(launch_jacobi(h->grid.dim, h->grid.n, h->grid.kappa_dev, b, cur, oth,
                      (double)h->opt.guess_omega, s));
@@ -297,8 +347,9 @@ int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_r
   h->T_hist.push_back(T);
   h->solves++;
   bool admit = false;
-  if (h->solves <= h->opt.warmup_steps) {
-    admit = true;  // warm-up: every pair is kept (Sec. 2.3)
+  const bool warm = h->solves <= h->opt.warmup_steps;
+  if (warm) {
+    admit = true;  // warm-up: every pair joins the training set X_t directly (Sec. 2.3)
   } else {
     auto mean_last = [p](const std::vector<double>& v) {
       const size_t k = std::min<size_t>((size_t)p, v.size());
@@ -308,6 +359,9 @@ int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_r
     };
     const bool good = (E < mean_last(h->E_hist)) && (T < mean_last(h->T_hist));
     if (!good) {
+      // an under-performing step: Algorithm 1 counts it towards f_r (N = N + 1)
+      // whether or not it passes the spread check
+      h->cand_n++;
       admit = true;
       const int cnt = (int)h->fresh.size();
       if (cnt > 0) {  // spread check against C_t
@@ -333,6 +387,9 @@ int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_r
   h->ring_head = (h->ring_head + 1) % h->opt.replay_cap;
   if (h->ring_count < h->opt.replay_cap) h->ring_count++;
   h->fresh.erase(std::remove(h->fresh.begin(), h->fresh.end(), slot), h->fresh.end());
+  // a running phase reads its own copy of the ring; the store waits until that
+  // copy has been taken
+  if (h->phase_enqueued && s != h->phase_stream) CK(cudaStreamWaitEvent(s, h->ring_copied, 0));
   CK(launch_sumsq(b, h->N, h->scal + 1, s));
   CK(launch_sumsq(x, h->N, h->scal + 2, s));
   CK(launch_store_pair(b, x, h->N, h->scal + 1, h->ring_u + (long long)slot * h->ldv,
@@ -345,7 +402,9 @@ int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_r
     if ((int)h->ring_c.size() < h->opt.replay_cap) h->ring_c.resize(h->opt.replay_cap, 0.0);
     h->ring_c[slot] = (std::isfinite(ci) && ci > 0.0) ? ci : 1.0;
   }
-  h->fresh.push_back(slot);
+  // C_t holds the candidates admitted since the last training phase; the
+  // warm-up pairs are part of X_t, so C_t starts empty after them (Algorithm 1)
+  if (!warm) h->fresh.push_back(slot);
   return 1;
 }
 
@@ -353,8 +412,26 @@ int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_r
 void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
   if (loss_host) *loss_host = -1.0f;
   if (h->ring_count == 0 || h->solves < h->opt.warmup_steps || h->opt.train_iters == 0) return;
+  // one phase at a time: if the previous phase is still running, the caller
+  // waits for it here (its ring and parameter snapshots are reused below)
+  if (h->phase_enqueued) {
+    const cudaError_t q = query_event(h->train_done);
+    if (q == cudaErrorNotReady) {
+      h->phase_waits++;
+      CK(cudaEventSynchronize(h->train_done));
+    } else {
+      CK(q);
+    }
+  }
   // the ring was written on the solve streams; the handle's solves synchronise
-  // before returning, so everything they enqueued is complete here.
+  // before returning, so everything they enqueued is complete here.  The
+  // phase trains on a copy of it, so that solves issued while it runs can
+  // store new pairs.
+  CK(cudaMemcpyAsync(h->ring_u_snap, h->ring_u, sizeof(float) * h->ldv * h->ring_count,
+                     cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->ring_t_snap, h->ring_t, sizeof(float) * h->ldv * h->ring_count,
+                     cudaMemcpyDeviceToDevice, s));
+  CK(cudaEventRecord(h->ring_copied, s));
   // adaptive depth (Sec. 2.1): append a residual block when M_p(E_k) has not
   // improved by grow_tol since the previous training phase
   if (h->net.extra_max > 0 && !h->E_hist.empty()) {
@@ -382,17 +459,25 @@ void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
     }
     while (k < B) pick[k++] = (int)(splitmix_next(h->rng_state) % (unsigned long long)h->ring_count);
     if (h->linear)
-      CK(lin_train_batch(h->lin, B, h->ring_u, h->ring_t, h->ldv, pick.data(), tscale,
+      CK(lin_train_batch(h->lin, B, h->ring_u_snap, h->ring_t_snap, h->ldv, pick.data(), tscale,
                          h->opt.lr, h->loss_dev, s));
     else
-      CK(net_train_batch(h->net, B, h->ring_u, h->ring_t, h->ldv, pick.data(), tscale,
-                         h->opt.lr, h->loss_dev, s));
+      CK(net_train_batch(h->net, B, h->ring_u_snap, h->ring_t_snap, h->ldv, pick.data(),
+                         tscale, h->opt.lr, h->loss_dev, s));
   }
+  // the parameters the guess will take once the phase has completed
+  if (!h->linear)
+    CK(cudaMemcpyAsync(h->snap, h->net.master, sizeof(float) * h->net.nparams,
+                       cudaMemcpyDeviceToDevice, s));
   CK(cudaEventRecord(h->train_done, s));
-  h->train_pending = true;
-  h->net_ready = true;
+  h->phase_enqueued = true;
+  h->phase_stream = s;
+  h->snap_pending = true;
+  h->snap_c = h->c_train;
+  h->snap_extra = h->net.extra_active;
   h->train_calls++;
   h->fresh.clear();
+  h->cand_n = 0;
   if (loss_host) {
     CK(cudaStreamSynchronize(s));
     CK(cudaMemcpy(loss_host, h->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
@@ -434,6 +519,7 @@ void mlgmres_default_options(mlgmres_options* o) {
   o->grow_tol = 0.02;
   o->compact = -1;
   o->model = MLGMRES_MODEL_CONV;
+  o->overlap_train = 1;
 }
 
 mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* opt,
@@ -499,13 +585,21 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     CK(cudaMalloc(&h->dwork, sizeof(GroupWork) * h->group_cap));
     CK(cudaMallocHost(&h->hwork, sizeof(GroupWork) * h->group_cap));
     CK(cudaMalloc(&h->x_prev, sizeof(double) * h->ldv));
+    CK(cudaMalloc(&h->x_alt, sizeof(double) * h->ldv));
+    CK(cudaMalloc(&h->x_tmp, sizeof(double) * h->ldv));
     CK(cudaMalloc(&h->scal, sizeof(double) * (8 + 4096)));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
     CK(cudaEventCreate(&h->ev2));
     CK(cudaEventCreateWithFlags(&h->train_done, cudaEventDisableTiming));
-    if (opt->guess == MLGMRES_GUESS_LEARNED && opt->retrain_after > 0)
-      CK(cudaStreamCreateWithFlags(&h->train_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ring_copied, cudaEventDisableTiming));
+    if (opt->guess == MLGMRES_GUESS_LEARNED && opt->retrain_after > 0) {
+      // the phases the solves start run at the lowest stream priority, so that
+      // the solver's CTAs are dispatched first when both wait for SMs
+      int least = 0, greatest = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      CK(cudaStreamCreateWithPriority(&h->train_stream, cudaStreamNonBlocking, least));
+    }
     h->rng_state = opt->seed;
     // learned-guess machinery: at create for the LEARNED mode, else on the
     // first call of an nn_* inspection entry point
@@ -550,12 +644,17 @@ void mlgmres_destroy(mlgmres_t h) {
   cudaFree(h->ddots);
   cudaFreeHost(h->hdots);
   cudaFree(h->loss_dev);
+  cudaFree(h->ring_u_snap);
+  cudaFree(h->ring_t_snap);
+  cudaFree(h->snap);
+  net_destroy(h->inf);
   net_destroy(h->net);
   lin_destroy(h->lin);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev2) cudaEventDestroy(h->ev2);
   if (h->train_done) cudaEventDestroy(h->train_done);
+  if (h->ring_copied) cudaEventDestroy(h->ring_copied);
   if (h->train_stream) cudaStreamDestroy(h->train_stream);
   delete h;
 }
@@ -587,11 +686,8 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
     } else {
       r.guess_used = MLGMRES_GUESS_USER;
     }
+    if (mode == MLGMRES_GUESS_LEARNED) take_snapshot(h, s);
     if (mode == MLGMRES_GUESS_LEARNED && h->net_ready) {
-      if (h->train_pending) {
-        CK(cudaStreamWaitEvent(s, h->train_done, 0));
-        h->train_pending = false;
-      }
       CK(cudaEventRecord(h->ev2, s));
       x_alt = learned_guess(h, b, s);
     }
@@ -665,12 +761,12 @@ mlgmres_status mlgmres_solve(mlgmres_t h, const double* b, double* x, void* stre
     CK(cudaEventElapsedTime(&r.tos_ms, h->ev0, h->ev1));
     if (mode == MLGMRES_GUESS_LEARNED && r.status != MLGMRES_ERR_TIMEOUT)
       r.admitted = gate_and_store(h, b, x, r, s);
-    // Algorithm 1's trigger: retrain once f_r pairs were admitted since the
-    // previous phase (the first phase at tau0 takes the warm-up pairs)
+    // Algorithm 1's trigger: retrain once f_r under-performing steps were seen
+    // since the previous phase (the first phase at tau0 takes the warm-up pairs)
     r.trained = 0;
     if (h->opt.guess == MLGMRES_GUESS_LEARNED && h->opt.retrain_after > 0 &&
         h->solves >= h->opt.warmup_steps &&
-        ((int)h->fresh.size() >= h->opt.retrain_after || h->train_calls == 0)) {
+        (h->cand_n >= h->opt.retrain_after || h->train_calls == 0)) {
       const int before = h->train_calls;
       train_phase(h, h->train_stream, nullptr);
       r.trained = h->train_calls > before ? 1 : 0;
@@ -859,7 +955,7 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
         return MLGMRES_OK;
       }
     }
-    if (h->train_pending) CK(cudaStreamWaitEvent(s, h->train_done, 0));
+    if (h->phase_enqueued) CK(cudaStreamWaitEvent(s, h->train_done, 0));
     CK(cudaMalloc(&xs, sizeof(double) * (size_t)h->N));
     // candidate CTA counts around one per 512 points, and the co-resident limit
     std::vector<int> blocks;
@@ -1053,6 +1149,9 @@ mlgmres_status mlgmres_nn_set_params(mlgmres_t h, const float* p, long long coun
       CK(cudaMemset(h->net.adam_v, 0, sizeof(float) * count));
       h->net.adam_t = 0;
       CK(net_sync_weights(h->net, 0));
+      // the guess uses the parameters just set (they supersede a pending phase's)
+      CK(net_copy_params(h->inf, h->net.master, 0));
+      h->snap_pending = false;
     }
     CK(cudaDeviceSynchronize());
     return MLGMRES_OK;
@@ -1069,6 +1168,7 @@ mlgmres_status mlgmres_nn_forward(mlgmres_t h, int batch, const float* u, float*
     ARG(u && y, "bad arguments");
     ARG(batch >= 1 && batch <= h->opt.batch, "batch must be in 1..opt.batch");
     cudaStream_t s = (cudaStream_t)stream;
+    wait_phase(h, s);
     model_forward(h, batch, u, y, s);
     CK(cudaStreamSynchronize(s));
     return MLGMRES_OK;
@@ -1085,6 +1185,7 @@ mlgmres_status mlgmres_nn_loss_grad(mlgmres_t h, int batch, const float* u, cons
     ARG(u && t && loss_host && grad_host, "bad arguments");
     ARG(batch >= 1 && batch <= h->opt.batch, "batch must be in 1..opt.batch");
     cudaStream_t s = (cudaStream_t)stream;
+    wait_phase(h, s);
     float* y = nullptr;
     CK(cudaMallocAsync(&y, sizeof(float) * (size_t)batch * h->N, s));
     model_forward(h, batch, u, y, s);
@@ -1110,9 +1211,34 @@ mlgmres_status mlgmres_guess(mlgmres_t h, const double* b, double* x, void* stre
     ARG(b && x && b != x, "b and x must be distinct device pointers");
     ensure_net(h);
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->train_pending) CK(cudaStreamWaitEvent(s, h->train_done, 0));
+    // the guess of the latest phase: wait for it to complete
+    if (h->phase_enqueued) CK(cudaEventSynchronize(h->train_done));
+    take_snapshot(h, s);
     const double* g = learned_guess(h, b, s);
     CK(cudaMemcpyAsync(x, g, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return MLGMRES_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+mlgmres_status mlgmres_smooth(mlgmres_t h, const double* b, double* x, int sweeps,
+                              void* stream) {
+  if (!h) return MLGMRES_ERR_ARG;
+  h->last_error.clear();
+  try {
+    ARG(b && x && b != x, "b and x must be distinct device pointers");
+    ARG(sweeps >= 0 && sweeps <= 1000, "sweeps must be in 0..1000");
+    cudaStream_t s = (cudaStream_t)stream;
+    double* cur = x;
+    double* oth = h->x_tmp;
+    for (int k = 0; k < sweeps; k++) {
+      CK(launch_jacobi(h->grid.dim, h->grid.n, h->grid.kappa_dev, b, cur, oth,
+                       (double)h->opt.guess_omega, s));
+      std::swap(cur, oth);
+    }
+    if (cur != x) CK(cudaMemcpyAsync(x, cur, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
     return MLGMRES_OK;
   } catch (const Fail& f) {
@@ -1129,6 +1255,7 @@ mlgmres_status mlgmres_nn_blocks(mlgmres_t h, int set_to, int* active) {
     if (set_to >= 0) {
       CK(cudaDeviceSynchronize());  // no training phase may be using the old depth
       h->net.extra_active = std::min(set_to, h->net.extra_max);
+      h->inf.extra_active = h->net.extra_active;
     }
     *active = h->net.extra_active;
     return MLGMRES_OK;

@@ -671,13 +671,14 @@ unsigned long long sm64(unsigned long long& st) {
   } while (0)
 
 cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int dim,
-                       int extra_max) {
+                       int extra_max, bool infer_only) {
   if (dim != 2 && dim != 3) return cudaErrorInvalidValue;
   if (extra_max < 0 || extra_max > kMaxExtra) return cudaErrorInvalidValue;
   // the kernels index points and point-channel elements in 32 bits
   if (n < 1 || bmax < 1 ||
       (long long)bmax * (dim == 3 ? (long long)n * n * n : (long long)n * n) * kC >= (1LL << 31))
     return cudaErrorInvalidValue;
+  if (dim == 2) NN_CK(conv32_tc_setup());
   net.extra_max = extra_max;
   net.extra_active = 0;
   net.n = n;
@@ -732,13 +733,15 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
 
   const long long np = net.nparams;
   NN_CK(cudaMalloc(&net.master, sizeof(float) * np));
-  NN_CK(cudaMalloc(&net.grad, sizeof(float) * np));
-  NN_CK(cudaMalloc(&net.adam_m, sizeof(float) * np));
-  NN_CK(cudaMalloc(&net.adam_v, sizeof(float) * np));
   NN_CK(cudaMemcpy(net.master, p.data(), sizeof(float) * np, cudaMemcpyHostToDevice));
-  NN_CK(cudaMemset(net.grad, 0, sizeof(float) * np));
-  NN_CK(cudaMemset(net.adam_m, 0, sizeof(float) * np));
-  NN_CK(cudaMemset(net.adam_v, 0, sizeof(float) * np));
+  if (!infer_only) {
+    NN_CK(cudaMalloc(&net.grad, sizeof(float) * np));
+    NN_CK(cudaMalloc(&net.adam_m, sizeof(float) * np));
+    NN_CK(cudaMalloc(&net.adam_v, sizeof(float) * np));
+    NN_CK(cudaMemset(net.grad, 0, sizeof(float) * np));
+    NN_CK(cudaMemset(net.adam_m, 0, sizeof(float) * np));
+    NN_CK(cudaMemset(net.adam_v, 0, sizeof(float) * np));
+  }
   const int nconv = L + 1 + extra_max;  // the 32 -> 32 convolutions
   NN_CK(cudaMalloc(&net.wq, sizeof(bf16) * per * nconv));
   NN_CK(cudaMalloc(&net.wqT, sizeof(bf16) * per * nconv));
@@ -800,6 +803,10 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
   for (int r = 0; r < extra_max; r++) {
     NN_CK(cudaMalloc(&net.te[r], sizeof(bf16) * full));
     NN_CK(cudaMalloc(&net.tt[r], sizeof(bf16) * full));
+  }
+  if (infer_only) {  // forward passes only: no gradient, Adam or minibatch buffers
+    NN_CK(net_sync_weights(net, 0));
+    return cudaDeviceSynchronize();
   }
   NN_CK(cudaMalloc(&net.g_t, sizeof(float) * full));
   NN_CK(cudaMalloc(&net.g_s, sizeof(float) * full));
@@ -869,6 +876,12 @@ void net_destroy(Net& net) {
   cudaFree(net.bt);
   cudaFree(net.by);
   net = Net();
+}
+
+cudaError_t net_copy_params(Net& dst, const float* src, cudaStream_t s) {
+  NN_CK(cudaMemcpyAsync(dst.master, src, sizeof(float) * dst.nparams, cudaMemcpyDeviceToDevice,
+                        s));
+  return net_sync_weights(dst, s);
 }
 
 cudaError_t net_sync_weights(Net& net, cudaStream_t s) {

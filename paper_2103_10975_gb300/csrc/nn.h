@@ -98,6 +98,9 @@ cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
                              const __nv_bfloat16* wop, const float* bias, int dil, int sign,
                              __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                              float* fo, const float* addend, cudaStream_t s);
+// One-time set-up of the tcgen05 convolution (shared-memory limits, its error
+// flag); net_create calls it so that no forward pass allocates.
+cudaError_t conv32_tc_setup();
 // 1 if a tcgen05 convolution tile timed out waiting for its MMAs (0 otherwise).
 int conv32_tc_error();
 // Tensor-core weight gradient partials of a 32 -> 32 convolution (nparts CTAs).
@@ -105,8 +108,14 @@ cudaError_t launch_wgrad_mma(int dim, int B, int H, const __nv_bfloat16* in,
                              const __nv_bfloat16* g, int dil, float* part, int stride, int nparts,
                              cudaStream_t s);
 
+// infer_only: allocate what forward passes need (parameters, BF16 operand
+// copies, activations) and no gradient, Adam or minibatch buffers; such a
+// network takes its weights from another one (net_copy_params).
 cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int dim = 2,
-                       int extra_max = 0);
+                       int extra_max = 0, bool infer_only = false);
+// dst.master = src (FP32 parameters, dst.nparams of them) and dst's BF16
+// operand copies re-derived, on stream s.
+cudaError_t net_copy_params(Net& dst, const float* src, cudaStream_t s);
 void net_destroy(Net& net);
 // Re-derive the BF16 operand copies from the FP32 master parameters.
 cudaError_t net_sync_weights(Net& net, cudaStream_t s);

@@ -14,6 +14,7 @@
 // leading-dimension offset); a tap's operand is then the same rows shifted by
 // its x offset, i.e. a descriptor whose start address moves by 16 bytes per
 // pixel.  The weights use 128 / 512-byte offsets.
+#include <mutex>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -237,20 +238,29 @@ int* g_tc_err = nullptr;  // set by a tile whose MMAs did not complete in time
 
 bool conv32_tc_applies(int dim, int H) { return dim == 2 && H >= kTcM; }
 
+cudaError_t conv32_tc_setup() {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (g_tc_err) return cudaSuccess;
+  cudaFuncSetAttribute(conv32_tc<kRelu>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(conv32_tc<kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  cudaFuncSetAttribute(conv32_tc<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  int* flag = nullptr;
+  cudaError_t e = cudaMalloc(&flag, sizeof(int));
+  if (e != cudaSuccess) return e;
+  e = cudaMemset(flag, 0, sizeof(int));
+  if (e != cudaSuccess) return e;
+  g_tc_err = flag;
+  return cudaSuccess;
+}
+
 cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
                              const __nv_bfloat16* wop, const float* bias, int dil, int sign,
                              __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                              float* fo, const float* addend, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(conv32_tc<kRelu>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    cudaFuncSetAttribute(conv32_tc<kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    cudaFuncSetAttribute(conv32_tc<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    cudaError_t e = cudaMalloc(&g_tc_err, sizeof(int));
+  if (!g_tc_err) {
+    const cudaError_t e = conv32_tc_setup();
     if (e != cudaSuccess) return e;
-    e = cudaMemset(g_tc_err, 0, sizeof(int));
-    if (e != cudaSuccess) return e;
-    configured = true;
   }
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);

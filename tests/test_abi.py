@@ -42,7 +42,7 @@ def test_struct_layouts_match_header():
     assert o.m == 30 and o.rtol == 1e-10 and o.replay_cap == 64 and o.warmup_steps == 50
     assert o.window_p == 10 and abs(o.ortho_theta - 0.9) < 1e-15 and o.batch == 8
     assert o.fault_inject == 0 and o.v_stages == -1 and o.retrain_after == 0
-    assert o.grow_blocks == 0 and o.grow_tol == 0.02
+    assert o.grow_blocks == 0 and o.grow_tol == 0.02 and o.overlap_train == 1
 
 
 def test_create_without_gpu_fails_cleanly():

@@ -1,0 +1,99 @@
+"""GPU parity of the learned initial guess as a whole (row a1): the guess the
+library forms in a solve (mlgmres_guess: x0 = c s N(b/s), s = rms(b), then
+damped-Jacobi sweeps) against the same composition built on the oracle
+(oracle/guess.py) at the same weights, and the sweeps alone
+(mlgmres_smooth) against the oracle's."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import guess as og  # noqa: E402
+from oracle import nn as onn  # noqa: E402
+from synthetic import MovingGaussians2D, MovingGaussians3D, lognormal_kappa  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a):
+    t = torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float32)
+    return t.numpy().astype(np.float64)
+
+
+def oracle_params(s, n, dim):
+    """The handle's parameters as the GPU network uses them: FP32 master
+    values, the 32 -> 32 weights rounded to BF16."""
+    flat = s.get_params()
+    P, o = {}, 0
+    for name, shape in onn.param_shapes(n, dim=dim):
+        k = int(np.prod(shape))
+        P[name] = flat[o:o + k].astype(np.float64).reshape(shape)
+        o += k
+    for k in P:
+        if (k.startswith("level") or k == "dil.w") and k.endswith(".w"):
+            P[k] = bf16_round(P[k])
+    return P
+
+
+@pytest.mark.parametrize("dim,n", [(2, 37), (2, 64), (3, 12)])
+def test_smoothing_sweeps_match_the_oracle(dim, n):
+    from paper_2103_10975_gb300 import Solver
+    kap = lognormal_kappa(n, 5001, smooth_sigma=1.5).astype(np.float32) if dim == 3 else None
+    s = Solver(n, dim=dim, kappa=kap, m=10, guess_omega=0.7)
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal(n ** dim)
+    x0 = rng.standard_normal(n ** dim)
+    for sweeps in (0, 1, 5):
+        xd = torch.as_tensor(x0.copy()).cuda()
+        s.smooth(torch.as_tensor(b).cuda(), xd, sweeps)
+        ref = og.jacobi(dim, n, b, x0, sweeps, 0.7,
+                        None if kap is None else kap.astype(np.float64))
+        assert np.linalg.norm(xd.cpu().numpy() - ref) <= 1e-13 * np.linalg.norm(ref), sweeps
+
+
+@pytest.mark.parametrize("dim,n", [(2, 64), (2, 128), (3, 16)])
+def test_learned_guess_matches_the_oracle_composition(dim, n):
+    """After two training phases (so c is the ring's mean rms(x)/rms(b), not
+    1), the guess for a new right-hand side equals c s N(b/s) of the oracle's
+    network at the same weights followed by the oracle's sweeps.  Bound: the
+    network's BF16 forward parity (3e-2 of the unsmoothed guess).  The sweeps
+    are linear, x <- S x + omega D^-1 b with S = I - omega D^-1 A, and D^-1 A
+    has its spectrum in (0, 2), so |1 - omega lambda| < 1 for omega <= 1: in 2D
+    (D = 4/h^2 I) S is symmetric and shrinks a difference in the 2-norm, so
+    the bound carries over; in 3D S shrinks it in the D-norm, and D varies
+    with kappa, so the 2-norm bound gets a factor 2 of slack."""
+    from paper_2103_10975_gb300 import Solver
+    sweeps, omega = 8, 0.8
+    if dim == 3:
+        kap = lognormal_kappa(n, 5001, smooth_sigma=2.0)
+        gen = MovingGaussians3D(n, 5001, 40)
+        s = Solver(n, dim=3, kappa=kap.astype(np.float32), m=30, rtol=1e-10,
+                   precision="fp32_refine", guess="learned", fallback="zero", warmup_steps=6,
+                   train_iters=8, batch=2, lr=2e-3, guess_smooth=sweeps, guess_omega=omega,
+                   deterministic_tos=1, seed=13)
+        kap64 = kap.astype(np.float32).astype(np.float64)
+    else:
+        kap64 = None
+        gen = MovingGaussians2D(n, 2001, 60)
+        s = Solver(n, m=30, rtol=1e-10, precision="fp32_refine", guess="learned",
+                   fallback="zero", warmup_steps=6, train_iters=16, batch=4, lr=2e-3,
+                   guess_smooth=sweeps, guess_omega=omega, deterministic_tos=1, seed=13)
+    ratios = []
+    for t in range(12):
+        b = gen.rhs(t)
+        x, r = s.solve(torch.as_tensor(b).cuda())
+        assert r["status"] == 0
+        if r["admitted"]:
+            ratios.append(onn.rms(x.cpu().numpy()) / onn.rms(b))
+        if (t + 1) % 6 == 0:
+            s.train_step()
+    c = float(np.mean(ratios[-64:]))
+    assert abs(c - 1.0) > 1e-3
+    b = gen.rhs(13)
+    xg = s.guess(torch.as_tensor(b).cuda()).cpu().numpy()
+    P = oracle_params(s, n, dim)
+    x_raw = og.learned_guess(P, b, n, c, 0, omega, dim=dim, kappa=kap64)
+    x_ref = og.learned_guess(P, b, n, c, sweeps, omega, dim=dim, kappa=kap64)
+    err = np.linalg.norm(xg - x_ref) / np.linalg.norm(x_raw)
+    print("learned guess %dD n=%d: ||x_gpu - x_oracle|| / ||c s N(b/s)|| = %.3g" % (dim, n, err))
+    assert err <= (3e-2 if dim == 2 else 6e-2), err

@@ -18,6 +18,25 @@ pytestmark = pytest.mark.gpu
 if torch.cuda.is_available():
     from paper_2103_10975_gb300 import Solver  # noqa: E402
 
+# Per-tensor relative bound on the BF16 gradients against the FP64 oracle at
+# the same weights: ||g_gpu - g_ref|| <= GRAD_TOL ||g_ref||.
+GRAD_TOL = 5e-2
+
+
+def check_grads(G, gr, label):
+    """Every tensor's relative gradient error within GRAD_TOL; prints the worst."""
+    worst, which = 0.0, None
+    for name in gr:
+        nrm = np.linalg.norm(gr[name])
+        if nrm == 0.0:
+            continue
+        e = np.linalg.norm(G[name] - gr[name]) / nrm
+        if e > worst:
+            worst, which = e, name
+        assert e <= GRAD_TOL, (label, name, e)
+    print("gradient parity %s: worst per-tensor relative error %.3g (%s)" % (label, worst, which))
+    return worst
+
 
 def unpack(flat, n, C=32, dim=2):
     out = {}
@@ -89,39 +108,70 @@ def test_gradient_parity(n):
                              torch.as_tensor(t, dtype=torch.float32).cuda())
     lr, gr = onn.loss_and_grads(P, u, t, n)
     assert abs(loss - lr) <= 2e-2 * lr
-    G = unpack(g, n)
-    for name in gr:
-        ref = gr[name]
-        nrm = np.linalg.norm(ref)
-        if nrm == 0.0:
-            continue
-        assert np.linalg.norm(G[name] - ref) <= 5e-2 * nrm, (name, np.linalg.norm(G[name] - ref) / nrm)
+    check_grads(unpack(g, n), gr, "2D n=%d" % n)
 
 
-def test_adam_step_through_training():
-    """One training phase of one Adam step on one stored pair moves every
-    weight by -lr * sign(g) (first Adam step), g the oracle gradient."""
-    n = 16
-    lr = 1e-3
+def test_adam_steps_through_training():
+    """Four training phases of one Adam step each on one stored pair (batch 1,
+    so every minibatch is that pair).  Before each phase the GPU gradient at
+    the current weights is read (mlgmres_nn_loss_grad, the same kernels the
+    phase runs) and checked against the oracle's gradient at the same weights
+    (GRAD_TOL per tensor); the phase's update must then equal the oracle's
+    Adam (Kingma & Ba, step t = k, moments carried over) applied to that
+    gradient.  From t = 2 on the update is no longer -lr sign(g), so the
+    moment bookkeeping and the bias correction are pinned.  Elements whose
+    gradient is below 1e-3 of their tensor's largest at some step are left out
+    of the elementwise check: near g = 0 Adam's first step is a sign, and the
+    phase's inputs differ from the test's in the last bit (s = rms(b) is
+    summed in another order)."""
+    n, lr, K = 16, 1e-3, 4
     s = Solver(n, m=30, rtol=1e-10, guess="learned", warmup_steps=1, batch=1, train_iters=1,
                lr=lr)
     b = MovingGaussians2D(n, 9, 20).rhs(0)
-    bd = torch.as_tensor(b).cuda()
-    x, r = s.solve(bd)
+    x, r = s.solve(torch.as_tensor(b).cuda())
     assert r["admitted"] == 1 and s.replay_size() == 1
-    p0 = s.get_params()
     sc = onn.rms(b)
     u = (b / sc).astype(np.float32)
     t = x.cpu().numpy() / sc
     # the training phase scales targets to unit rms: t / (rms(x) / rms(b))
     t = (t / onn.rms(t)).astype(np.float32)
-    _, g = s.nn_loss_grad(torch.as_tensor(u[None]).cuda(), torch.as_tensor(t[None]).cuda())
-    s.train_step()
-    torch.cuda.synchronize()
-    p1 = s.get_params()
-    big = np.abs(g) > 1e-3 * np.abs(g).max()
-    step = (p1 - p0)[big]
-    assert np.allclose(step, -lr * np.sign(g[big]), rtol=1e-3, atol=1e-6)
+    ud = torch.as_tensor(u[None]).cuda()
+    td = torch.as_tensor(t[None]).cuda()
+    m = v = None
+    keep = None
+    worst_grad = 0.0
+    for k in range(1, K + 1):
+        p0 = s.get_params()
+        _, g = s.nn_loss_grad(ud, td)
+        # gradient parity at these weights (32->32 weights BF16-rounded as the GPU uses them)
+        P = unpack(p0, n)
+        for name in P:
+            if name.startswith("level") and name.endswith(".w") or name == "dil.w":
+                P[name] = bf16_round(P[name])
+        _, gr = onn.loss_and_grads(P, u[None].astype(np.float64), t[None].astype(np.float64), n)
+        G = unpack(g, n)
+        for name in gr:
+            nrm = np.linalg.norm(gr[name])
+            if nrm > 0.0:
+                e = np.linalg.norm(G[name] - gr[name]) / nrm
+                worst_grad = max(worst_grad, e)
+                assert e <= GRAD_TOL, (k, name, e)
+        s.train_step()
+        p1 = s.get_params().astype(np.float64)
+        g64 = g.astype(np.float64)
+        if m is None:
+            m = np.zeros_like(g64)
+            v = np.zeros_like(g64)
+        want, m, v = onn.adam_update(p0.astype(np.float64), m, v, g64, k, lr=lr)
+        big = np.abs(g64) > 1e-3 * np.abs(g64).max()
+        keep = big if keep is None else keep & big
+        assert keep.mean() > 0.9
+        step_gpu = (p1 - p0)[keep]
+        step_ref = (want - p0)[keep]
+        assert np.max(np.abs(step_gpu - step_ref)) <= 1e-3 * lr + 2e-7, k
+        if k >= 2:  # not a sign any more
+            assert np.std(np.abs(step_ref)) > 1e-2 * lr
+    print("worst per-tensor gradient error over %d Adam steps: %.3g" % (K, worst_grad))
 
 
 # ---------------------------------------------------------------- 3D network
@@ -170,13 +220,7 @@ def test_gradient_parity_3d(n):
                              torch.as_tensor(t, dtype=torch.float32).cuda())
     lr, gr = onn.loss_and_grads(P, u, t, n, dim=3)
     assert abs(loss - lr) <= 2e-2 * lr
-    G = unpack(g, n, dim=3)
-    for name in gr:
-        ref = gr[name]
-        nrm = np.linalg.norm(ref)
-        if nrm == 0.0:
-            continue
-        assert np.linalg.norm(G[name] - ref) <= 5e-2 * nrm, (name, np.linalg.norm(G[name] - ref) / nrm)
+    check_grads(unpack(g, n, dim=3), gr, "3D n=%d" % n)
 
 
 # ------------------------------------------------ adaptive depth (grown blocks)
@@ -208,15 +252,12 @@ def test_grown_blocks_parity():
                              torch.as_tensor(t, dtype=torch.float32).cuda())
     lr, gr = onn.loss_and_grads(P, u, t, n)
     assert abs(loss - lr) <= 2e-2 * lr
-    o = 0
+    G, o = {}, 0
     for name, shape in shapes:
         k = int(np.prod(shape))
-        ref = gr[name]
-        nrm = np.linalg.norm(ref)
-        if nrm > 0:
-            got = g[o:o + k].reshape(shape)
-            assert np.linalg.norm(got - ref) <= 5e-2 * nrm, name
+        G[name] = g[o:o + k].reshape(shape)
         o += k
+    check_grads(G, gr, "2D n=16, two grown blocks")
     # back to one block: the extra blocks get no gradient
     assert s.nn_blocks(0) == 0
     _, g0 = s.nn_loss_grad(torch.as_tensor(u, dtype=torch.float32).cuda(),
