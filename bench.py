@@ -403,6 +403,9 @@ def run_ours(args):
     tos = sum(r["tos_ms"] for r in res)
     achieved = byts / (tos * 1e-3) / 1e9
     traffic = DRAM_BYTES_PER_STEP * statistics.mean(r["iters"] for r in res)
+    us_step = 1e3 * tos / max(1, sum(r["iters"] for r in res))
+    # the step's latency floor: its two group exchanges alone at the same CTA count
+    floor_us = pkg.exchange_floor(tuning["grid_blocks"], M, 3000)
 
     # ---- end to end through the public API with host buffers
     Bh = torch.stack([torch.as_tensor(gen.rhs(t)) for t in range(TAU0 + W + K, TAU0 + W + 2 * K)])
@@ -552,7 +555,12 @@ def run_ours(args):
                                  "vectors in L2: the algorithmic bytes are served on chip and the "
                                  "kernel is latency-bound; roofline_hbm is the HBM-bound case",
                          "launch_shape": {"ctas": tuning["grid_blocks"],
-                                          "v_stages": tuning["v_stages"]}},
+                                          "v_stages": tuning["v_stages"]},
+                         "us_per_arnoldi_step": us_step,
+                         "latency_floor_us": floor_us,
+                         "floor_note": "latency_floor_us: the step's two group exchanges (CTA "
+                                       "partials, group barrier, gather) alone, same CTA count, "
+                                       "no passes"},
             "roofline_hbm": roof_hbm,
             "e2e": {"value": e2e_ms / (K * world), "unit": "ms",
                     "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},

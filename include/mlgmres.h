@@ -312,6 +312,19 @@ mlgmres_status mlgmres_nn_blocks(mlgmres_t h, int set_to, int* active);
 /* Pairs currently in the replay ring. */
 mlgmres_status mlgmres_replay_size(mlgmres_t h, int* count);
 
+/* Latency floor of the solver's Arnoldi step (the paper has no counterpart: a
+ * profiling probe).  One persistent cooperative launch of `ctas` CTAs (256
+ * threads, one per SM, like mlgmres_solve's kernel) runs `steps` steps with j
+ * cycling 0..m-1 and does in each only the step's two group exchanges -- the
+ * per-CTA partial sums of j+2 slots, the group barrier and the gather of the
+ * j+2 sums, with the solver's own code -- and no pass over a grid and no
+ * scalar recurrence.  *us_per_step receives the device time per step of the
+ * second of two launches (CUDA events on the legacy default stream).  Allocates
+ * and frees its own partial-sum and barrier buffers and synchronises.
+ * ERR_ARG for ctas outside 1..min(co-resident CTAs, 1024), m outside 1..64,
+ * steps < 1 or a NULL output; ERR_TIMEOUT if a barrier wait ran out (2 s). */
+mlgmres_status mlgmres_exchange_floor(int ctas, int m, int steps, float* us_per_step);
+
 /* Number of CUDA kernels this library has launched in this process so far (all
  * handles).  Used to count the kernels inside a timed region. */
 mlgmres_status mlgmres_kernel_launches(long long* count);

@@ -8,5 +8,5 @@ wrapper.  Importing this package does not load the library; the first use of
 """
 
 from .binding import (Solver, Result, Options, Grid, default_options, load_library,  # noqa: F401
-                      library_path, MLGMRESError, kernel_launches, batch_plan, FP64, FP32_REFINE, GUESS_ZERO, GUESS_PREV,
+                      library_path, MLGMRESError, kernel_launches, batch_plan, exchange_floor, FP64, FP32_REFINE, GUESS_ZERO, GUESS_PREV,
                       GUESS_LEARNED, GUESS_USER)

@@ -145,6 +145,8 @@ _SIGS = {
     "mlgmres_guess": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mlgmres_nn_blocks": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "mlgmres_smooth": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "mlgmres_exchange_floor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_float)]),
     "mlgmres_autotune": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                         ctypes.POINTER(Tuning)]),
     "mlgmres_batch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -185,6 +187,16 @@ def kernel_launches():
     c = ctypes.c_longlong(0)
     load_library().mlgmres_kernel_launches(ctypes.byref(c))
     return c.value
+
+
+def exchange_floor(ctas, m, steps=2000):
+    """mlgmres_exchange_floor: device microseconds per Arnoldi step of a
+    persistent launch that does only the step's two group exchanges."""
+    us = ctypes.c_float(0.0)
+    st = load_library().mlgmres_exchange_floor(int(ctas), int(m), int(steps), ctypes.byref(us))
+    if st != MLGMRES_OK:
+        raise MLGMRESError(st, "exchange_floor failed")
+    return us.value
 
 
 def solve_static(n, b, x, m=30, rtol=1e-10, max_iters=10 ** 7, stream=None):

@@ -2,7 +2,11 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <condition_variable>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/mlgmres.h"
@@ -99,6 +103,24 @@ struct mlgmres {
   int snap_extra = 0;                 // residual blocks of that phase
   double c_guess = 1.0;               // c of the parameters `inf` holds
   int phase_waits = 0;                // phases that had to wait for the previous one
+  // A phase is thousands of launches; enqueued from the caller's thread it
+  // would block once the launch queue is full.  With overlap_train the
+  // caller prepares the phase (growth, minibatch picks, ring snapshot) and a
+  // worker thread of the handle enqueues its Adam steps.
+  struct PhaseJob {
+    cudaStream_t s = nullptr;
+    std::vector<int> picks;             // train_iters x B ring slots
+    int B = 0, iters = 0;
+    float tscale = 1.f, lr = 0.f;
+  };
+  std::thread worker;
+  std::mutex wmu;
+  std::condition_variable wcv;
+  bool wstop = false;                 // (under wmu) the worker is to exit
+  bool wjob = false;                  // (under wmu) a job is waiting or being enqueued
+  PhaseJob job;                       // (under wmu) the job
+  std::atomic<bool> phase_busy{false};  // the worker has not yet enqueued the latest phase
+  cudaError_t werr = cudaSuccess;     // (under wmu) first CUDA error of the worker
   cudaStream_t train_stream = nullptr;  // training phases started by solve (retrain_after)
   float* loss_dev = nullptr;
 

@@ -152,6 +152,18 @@ cudaError_t query_event(cudaEvent_t e) {
   return q;
 }
 
+// Blocks until the training worker has enqueued its latest phase (its
+// train_done record is then the phase's end), and reports a CUDA error it met.
+void wait_worker(mlgmres* h) {
+  if (!h->worker.joinable()) return;
+  std::unique_lock<std::mutex> lk(h->wmu);
+  h->wcv.wait(lk, [h] { return !h->wjob; });
+  if (h->werr != cudaSuccess) {
+    h->last_error = fmt_cuda("training phase", h->werr);
+    throw Fail{MLGMRES_ERR_CUDA};
+  }
+}
+
 // Moves the parameters of the latest training phase into the guess's network,
 // on stream s.  With overlap_train (and for another stream than the phase's)
 // only once the phase has completed: a solve issued while it runs keeps the
@@ -160,8 +172,11 @@ void take_snapshot(mlgmres* h, cudaStream_t s) {
   if (!h->snap_pending) return;
   const bool same = s == h->phase_stream;
   if (h->linear || h->opt.overlap_train == 0 || same) {
+    wait_worker(h);  // the phase is fully enqueued (stream order then does the rest)
     if (!same) CK(cudaStreamWaitEvent(s, h->train_done, 0));
   } else {
+    // the worker records train_done only after the phase's last launch
+    if (h->phase_busy.load(std::memory_order_acquire)) return;
     const cudaError_t q = query_event(h->train_done);
     if (q == cudaErrorNotReady) return;
     CK(q);
@@ -195,6 +210,7 @@ void guess_forward(mlgmres* h, const float* u, float* y, cudaStream_t s) {
 // Streams that touch the training copy of the network (inspection entry
 // points) first wait for the latest phase.
 void wait_phase(mlgmres* h, cudaStream_t s) {
+  wait_worker(h);
   if (h->phase_enqueued && s != h->phase_stream) CK(cudaStreamWaitEvent(s, h->train_done, 0));
 }
 
@@ -408,12 +424,52 @@ int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_r
   return 1;
 }
 
+// The launches of one phase on stream s: its Adam steps on the ring
+// snapshot, then the copy of its parameters for the guess, then train_done.
+// Returns the first CUDA error (runs on the worker thread with overlap_train).
+cudaError_t phase_launches(mlgmres* h, cudaStream_t s, const std::vector<int>& picks, int B,
+                           int iters, float tscale, float lr) {
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < iters && e == cudaSuccess; it++) {
+    const int* pick = picks.data() + (size_t)it * B;
+    e = h->linear ? lin_train_batch(h->lin, B, h->ring_u_snap, h->ring_t_snap, h->ldv, pick,
+                                    tscale, lr, h->loss_dev, s)
+                  : net_train_batch(h->net, B, h->ring_u_snap, h->ring_t_snap, h->ldv, pick,
+                                    tscale, lr, h->loss_dev, s);
+  }
+  // the parameters the guess will take once the phase has completed
+  if (e == cudaSuccess && !h->linear)
+    e = cudaMemcpyAsync(h->snap, h->net.master, sizeof(float) * h->net.nparams,
+                        cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->train_done, s);
+  return e;
+}
+
+void worker_main(mlgmres* h) {
+  cudaSetDevice(h->dev);
+  for (;;) {
+    std::unique_lock<std::mutex> lk(h->wmu);
+    h->wcv.wait(lk, [h] { return h->wstop || h->wjob; });
+    if (!h->wjob) return;  // stop requested and nothing left to enqueue
+    mlgmres::PhaseJob j = std::move(h->job);
+    lk.unlock();
+    const cudaError_t e = phase_launches(h, j.s, j.picks, j.B, j.iters, j.tscale, j.lr);
+    lk.lock();
+    if (e != cudaSuccess && h->werr == cudaSuccess) h->werr = e;
+    h->phase_busy.store(false, std::memory_order_release);
+    h->wjob = false;
+    lk.unlock();
+    h->wcv.notify_all();
+  }
+}
+
 // One training phase (Sec. 2.3) on stream s; see mlgmres_train_step.
 void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
   if (loss_host) *loss_host = -1.0f;
   if (h->ring_count == 0 || h->solves < h->opt.warmup_steps || h->opt.train_iters == 0) return;
   // one phase at a time: if the previous phase is still running, the caller
   // waits for it here (its ring and parameter snapshots are reused below)
+  wait_worker(h);
   if (h->phase_enqueued) {
     const cudaError_t q = query_event(h->train_done);
     if (q == cudaErrorNotReady) {
@@ -445,31 +501,41 @@ void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
     h->mp_last_phase = mp;
   }
   const int B = std::min(h->opt.batch, std::max(1, h->ring_count));
-  std::vector<int> pick(B);
   // unit-scale targets: t / c with c the mean rms(x)/rms(b) over the ring
   double csum = 0.0;
   for (int i = 0; i < h->ring_count; i++) csum += h->ring_c[i];
   h->c_train = csum > 0.0 ? csum / h->ring_count : 1.0;
   const float tscale = (float)(1.0 / h->c_train);
-  for (int it = 0; it < h->opt.train_iters; it++) {
+  // every minibatch: the candidates admitted since the last phase (C_t, up
+  // to B), then uniform samples of the ring
+  const int iters = h->opt.train_iters;
+  std::vector<int> picks((size_t)iters * B);
+  for (int it = 0; it < iters; it++) {
+    int* pick = picks.data() + (size_t)it * B;
     int k = 0;
     for (int f : h->fresh) {
       if (k >= B) break;
       pick[k++] = f;
     }
     while (k < B) pick[k++] = (int)(splitmix_next(h->rng_state) % (unsigned long long)h->ring_count);
-    if (h->linear)
-      CK(lin_train_batch(h->lin, B, h->ring_u_snap, h->ring_t_snap, h->ldv, pick.data(), tscale,
-                         h->opt.lr, h->loss_dev, s));
-    else
-      CK(net_train_batch(h->net, B, h->ring_u_snap, h->ring_t_snap, h->ldv, pick.data(),
-                         tscale, h->opt.lr, h->loss_dev, s));
   }
-  // the parameters the guess will take once the phase has completed
-  if (!h->linear)
-    CK(cudaMemcpyAsync(h->snap, h->net.master, sizeof(float) * h->net.nparams,
-                       cudaMemcpyDeviceToDevice, s));
-  CK(cudaEventRecord(h->train_done, s));
+  if (!h->linear && h->opt.overlap_train) {
+    if (!h->worker.joinable()) h->worker = std::thread(worker_main, h);
+    {
+      std::lock_guard<std::mutex> lk(h->wmu);
+      h->job.s = s;
+      h->job.picks = std::move(picks);
+      h->job.B = B;
+      h->job.iters = iters;
+      h->job.tscale = tscale;
+      h->job.lr = h->opt.lr;
+      h->phase_busy.store(true, std::memory_order_release);
+      h->wjob = true;
+    }
+    h->wcv.notify_all();
+  } else {
+    CK(phase_launches(h, s, picks, B, iters, tscale, h->opt.lr));
+  }
   h->phase_enqueued = true;
   h->phase_stream = s;
   h->snap_pending = true;
@@ -479,6 +545,7 @@ void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
   h->fresh.clear();
   h->cand_n = 0;
   if (loss_host) {
+    wait_worker(h);
     CK(cudaStreamSynchronize(s));
     CK(cudaMemcpy(loss_host, h->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
   }
@@ -616,6 +683,15 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
 
 void mlgmres_destroy(mlgmres_t h) {
   if (!h) return;
+  if (h->worker.joinable()) {
+    {
+      std::lock_guard<std::mutex> lk(h->wmu);
+      h->wstop = true;
+    }
+    h->wcv.notify_all();
+    h->worker.join();  // after it has enqueued a phase it had started
+  }
+  cudaDeviceSynchronize();  // no phase may still use the workspace freed below
   cudaFree(h->Vb);
   cudaFree(h->Wb);
   cudaFree(h->partb);
@@ -955,7 +1031,7 @@ mlgmres_status mlgmres_autotune(mlgmres_t h, const double* b, int steps, int ret
         return MLGMRES_OK;
       }
     }
-    if (h->phase_enqueued) CK(cudaStreamWaitEvent(s, h->train_done, 0));
+    wait_phase(h, s);
     CK(cudaMalloc(&xs, sizeof(double) * (size_t)h->N));
     // candidate CTA counts around one per 512 points, and the co-resident limit
     std::vector<int> blocks;
@@ -1129,6 +1205,7 @@ mlgmres_status mlgmres_nn_get_params(mlgmres_t h, float* p, long long count) {
   try {
     ensure_net(h);
     ARG(p && count == model_params(h), "bad parameter buffer");
+    wait_worker(h);
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(p, model_master(h), sizeof(float) * count, cudaMemcpyDeviceToHost));
     return MLGMRES_OK;
@@ -1142,6 +1219,7 @@ mlgmres_status mlgmres_nn_set_params(mlgmres_t h, const float* p, long long coun
   try {
     ensure_net(h);
     ARG(p && count == model_params(h), "bad parameter buffer");
+    wait_worker(h);
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(model_master(h), p, sizeof(float) * count, cudaMemcpyHostToDevice));
     if (!h->linear) {
@@ -1212,6 +1290,7 @@ mlgmres_status mlgmres_guess(mlgmres_t h, const double* b, double* x, void* stre
     ensure_net(h);
     cudaStream_t s = (cudaStream_t)stream;
     // the guess of the latest phase: wait for it to complete
+    wait_worker(h);
     if (h->phase_enqueued) CK(cudaEventSynchronize(h->train_done));
     take_snapshot(h, s);
     const double* g = learned_guess(h, b, s);
@@ -1253,6 +1332,7 @@ mlgmres_status mlgmres_nn_blocks(mlgmres_t h, int set_to, int* active) {
     ARG(set_to >= -1, "set_to must be >= -1");
     ensure_net(h);
     if (set_to >= 0) {
+      wait_worker(h);
       CK(cudaDeviceSynchronize());  // no training phase may be using the old depth
       h->net.extra_active = std::min(set_to, h->net.extra_max);
       h->inf.extra_active = h->net.extra_active;

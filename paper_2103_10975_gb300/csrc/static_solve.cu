@@ -5,6 +5,7 @@
 // entered while it solves.  Its workspace is one fixed array compiled into the
 // library (kStaticBytes, held by every GPU that loads the library until the
 // process exits).
+#include <mutex>
 #include <string.h>
 
 #include "../../include/mlgmres.h"
@@ -31,6 +32,7 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;  // host threads calling for the first time on a device
 
 // Device address of the workspace on the current device (looked up once per
 // device, the first time that device calls mlgmres_solve_static).
@@ -39,6 +41,7 @@ cudaError_t scratch_address(unsigned char** out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);

@@ -6,6 +6,7 @@
     python -m paper_2103_10975_gb300.profile_cases cube --n 192 --max-iters 500
 
     python -m paper_2103_10975_gb300.profile_cases dipole --n 64 --T 200
+    python -m paper_2103_10975_gb300.profile_cases floor --ctas 128 --m 30
 
 --stages selects the bulk-copy depth for a basis in HBM (0 = direct loads,
 -1 = automatic); --compact 1 forces the two-CTAs-per-SM variant; --autotune
@@ -14,7 +15,9 @@ runs mlgmres_autotune first.
 `solve` runs the same capped solve twice on one moving-Gaussian right-hand
 side (the second launch is the one to capture) and prints the device time
 per Arnoldi step; `nn` runs the network's forward + backward seven times on
-random inputs and prints the mean time.
+random inputs and prints the mean time; `floor` times the solver's two group
+exchanges per Arnoldi step alone (mlgmres_exchange_floor), next to the full
+step of the same shape on the 256^2 moving-Gaussian right-hand side.
 """
 
 import argparse
@@ -150,6 +153,21 @@ def dipole_case(n, T, tau0, train_iters, lr, k):
              sum(used) / len(used)))
 
 
+def floor_case(ctas, m, steps, n):
+    import torch
+    from paper_2103_10975_gb300 import Solver, exchange_floor
+    from synthetic import MovingGaussians2D
+    fl = exchange_floor(ctas, m, steps)
+    b = torch.as_tensor(MovingGaussians2D(n, 2001, 500).rhs(0)).cuda()
+    s = Solver(n, m=m, rtol=1e-10, precision="fp32_refine", grid_blocks=ctas,
+               max_iters=10 * m)
+    s.solve(b)
+    _, r = s.solve(b)
+    full = 1e3 * r["tos_ms"] / r["iters"]
+    print("exchange floor at %d CTAs, m=%d: %.2f us/step; full step at n=%d: %.2f us/step "
+          "(%.2fx the floor)" % (ctas, m, fl, n, full, full / fl))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="case", required=True)
@@ -188,6 +206,11 @@ def main(argv=None):
     e.add_argument("--train-iters", type=int, default=64)
     e.add_argument("--lr", type=float, default=2e-3)
     e.add_argument("--k", type=int, default=5)
+    f = sub.add_parser("floor")
+    f.add_argument("--ctas", type=int, default=128)
+    f.add_argument("--m", type=int, default=30)
+    f.add_argument("--steps", type=int, default=3000)
+    f.add_argument("--n", type=int, default=256)
     args = ap.parse_args(argv)
     if args.case == "solve":
         solve_case(args.n, args.blocks, args.max_iters, args.m, args.precision, args.source,
@@ -196,6 +219,8 @@ def main(argv=None):
         nn_case(args.n, args.batch, args.dim)
     elif args.case == "batch":
         batch_case(args.count, args.nmin, args.nmax, args.rtol, args.m, args.stages, args.compact)
+    elif args.case == "floor":
+        floor_case(args.ctas, args.m, args.steps, args.n)
     elif args.case == "dipole":
         dipole_case(args.n, args.T, args.tau0, args.train_iters, args.lr, args.k)
     else:

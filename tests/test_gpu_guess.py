@@ -40,13 +40,14 @@ def test_smoothing_sweeps_match_the_oracle(dim, n):
     from paper_2103_10975_gb300 import Solver
     kap = lognormal_kappa(n, 5001, smooth_sigma=1.5).astype(np.float32) if dim == 3 else None
     s = Solver(n, dim=dim, kappa=kap, m=10, guess_omega=0.7)
+    om = float(np.float32(0.7))  # the ABI carries omega as a float
     rng = np.random.default_rng(11)
     b = rng.standard_normal(n ** dim)
     x0 = rng.standard_normal(n ** dim)
     for sweeps in (0, 1, 5):
         xd = torch.as_tensor(x0.copy()).cuda()
         s.smooth(torch.as_tensor(b).cuda(), xd, sweeps)
-        ref = og.jacobi(dim, n, b, x0, sweeps, 0.7,
+        ref = og.jacobi(dim, n, b, x0, sweeps, om,
                         None if kap is None else kap.astype(np.float64))
         assert np.linalg.norm(xd.cpu().numpy() - ref) <= 1e-13 * np.linalg.norm(ref), sweeps
 
@@ -55,15 +56,17 @@ def test_smoothing_sweeps_match_the_oracle(dim, n):
 def test_learned_guess_matches_the_oracle_composition(dim, n):
     """After two training phases (so c is the ring's mean rms(x)/rms(b), not
     1), the guess for a new right-hand side equals c s N(b/s) of the oracle's
-    network at the same weights followed by the oracle's sweeps.  Bound: the
-    network's BF16 forward parity (3e-2 of the unsmoothed guess).  The sweeps
+    network at the same weights followed by the oracle's sweeps, within 1e-2
+    of the unsmoothed guess's norm (measured: 5e-4 to 2e-3; the network's
+    forward pass, BF16 operands with a relative rounding of 2^-9 each, is the
+    only source of difference, and its own parity bound is 3e-2).  The sweeps
     are linear, x <- S x + omega D^-1 b with S = I - omega D^-1 A, and D^-1 A
     has its spectrum in (0, 2), so |1 - omega lambda| < 1 for omega <= 1: in 2D
     (D = 4/h^2 I) S is symmetric and shrinks a difference in the 2-norm, so
     the bound carries over; in 3D S shrinks it in the D-norm, and D varies
     with kappa, so the 2-norm bound gets a factor 2 of slack."""
     from paper_2103_10975_gb300 import Solver
-    sweeps, omega = 8, 0.8
+    sweeps, omega = 8, float(np.float32(0.8))
     if dim == 3:
         kap = lognormal_kappa(n, 5001, smooth_sigma=2.0)
         gen = MovingGaussians3D(n, 5001, 40)
@@ -96,4 +99,4 @@ def test_learned_guess_matches_the_oracle_composition(dim, n):
     x_ref = og.learned_guess(P, b, n, c, sweeps, omega, dim=dim, kappa=kap64)
     err = np.linalg.norm(xg - x_ref) / np.linalg.norm(x_raw)
     print("learned guess %dD n=%d: ||x_gpu - x_oracle|| / ||c s N(b/s)|| = %.3g" % (dim, n, err))
-    assert err <= (3e-2 if dim == 2 else 6e-2), err
+    assert err <= (1e-2 if dim == 2 else 2e-2), err

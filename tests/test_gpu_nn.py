@@ -19,8 +19,15 @@ if torch.cuda.is_available():
     from paper_2103_10975_gb300 import Solver  # noqa: E402
 
 # Per-tensor relative bound on the BF16 gradients against the FP64 oracle at
-# the same weights: ||g_gpu - g_ref|| <= GRAD_TOL ||g_ref||.
-GRAD_TOL = 5e-2
+# the same weights: ||g_gpu - g_ref|| <= GRAD_TOL ||g_ref||.  Every activation
+# and activation gradient that feeds a 32 -> 32 convolution is rounded to BF16
+# (relative 2^-9 = 2.0e-3); a gradient passes about four such roundings, and a
+# weight or bias gradient is a sum over pixels whose terms partly cancel, which
+# raises the relative error of the sum by the ratio sum|g_i| / |sum g_i|.
+# Measured maximum over all tensors and cases (2D 16^2/32^2/128^2, 3D 8^3/16^3,
+# two grown blocks, four Adam steps): 2.5e-2 (a coarse level's bias at 32^2),
+# most tensors below 1e-2.
+GRAD_TOL = 3e-2
 
 
 def check_grads(G, gr, label):
@@ -163,9 +170,16 @@ def test_adam_steps_through_training():
             m = np.zeros_like(g64)
             v = np.zeros_like(g64)
         want, m, v = onn.adam_update(p0.astype(np.float64), m, v, g64, k, lr=lr)
-        big = np.abs(g64) > 1e-3 * np.abs(g64).max()
+        # per tensor: elements above 1e-3 of the tensor's largest gradient
+        big = np.zeros(g64.shape, dtype=bool)
+        o = 0
+        for _, shape in onn.param_shapes(n):
+            c = int(np.prod(shape))
+            seg = np.abs(g64[o:o + c])
+            big[o:o + c] = seg > 1e-3 * seg.max()
+            o += c
         keep = big if keep is None else keep & big
-        assert keep.mean() > 0.9
+        assert keep.mean() > 0.8, keep.mean()
         step_gpu = (p1 - p0)[keep]
         step_ref = (want - p0)[keep]
         assert np.max(np.abs(step_gpu - step_ref)) <= 1e-3 * lr + 2e-7, k

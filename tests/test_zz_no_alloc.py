@@ -7,8 +7,6 @@ array compiled into the library.  This file is collected last so that a run
 stopping at its first failure has already run every other test; it passes on
 its own in a fresh process and after the other tests.
 """
-import ctypes
-
 import numpy as np
 import pytest
 
@@ -37,6 +35,26 @@ def test_static_solve_matches_handle_solve_twice():
         assert abs(r["iters"] - r_ref["iters"]) <= max(2, 0.01 * r_ref["iters"])
         xe = direct.dst_solve_2d(n, gen.rhs(t))
         assert np.linalg.norm(xs - xe) <= 1e-7 * np.linalg.norm(xe)
+
+
+def test_static_solve_leaves_free_device_memory_unchanged():
+    """The property the entry point exists for: a call takes no device memory.
+    After a first call (which loads the library's module with its fixed array),
+    the free device memory reported by the driver is the same before and after
+    a second call."""
+    from paper_2103_10975_gb300 import binding
+    n = 96
+    b = torch.as_tensor(MovingGaussians2D(n, 2001, 500).rhs(7)).cuda()
+    x = torch.zeros_like(b)
+    st, _ = binding.solve_static(n, b, x, m=20, rtol=1e-8, max_iters=100000)
+    assert st == binding.MLGMRES_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    st, r = binding.solve_static(n, b, x, m=20, rtol=1e-8, max_iters=100000)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert st == binding.MLGMRES_OK and r["relres_true"] <= 1e-8
+    assert free1 == free0, (free0, free1)
 
 
 def test_static_solve_rejects_sizes_beyond_the_fixed_array():
