@@ -2,11 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
-#include <atomic>
-#include <condition_variable>
-#include <mutex>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "../../include/mlgmres.h"
@@ -103,24 +99,21 @@ struct mlgmres {
   int snap_extra = 0;                 // residual blocks of that phase
   double c_guess = 1.0;               // c of the parameters `inf` holds
   int phase_waits = 0;                // phases that had to wait for the previous one
-  // A phase is thousands of launches; enqueued from the caller's thread it
-  // would block once the launch queue is full.  With overlap_train the
-  // caller prepares the phase (growth, minibatch picks, ring snapshot) and a
-  // worker thread of the handle enqueues its Adam steps.
-  struct PhaseJob {
-    cudaStream_t s = nullptr;
-    std::vector<int> picks;             // train_iters x B ring slots
-    int B = 0, iters = 0;
-    float tscale = 1.f, lr = 0.f;
+  // A phase is thousands of launches (train_iters Adam steps of ~60 kernels);
+  // enqueued one by one they fill the launch queue and block the caller.  One
+  // Adam step is captured once as a CUDA graph (its per-step inputs -- picks,
+  // step counter, target scale -- live in device memory) and a phase launches
+  // that graph train_iters times.
+  struct StepGraph {
+    int B = 0, extra = 0;               // minibatch size and grown blocks it was captured for
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;              // kernels per replay
   };
-  std::thread worker;
-  std::mutex wmu;
-  std::condition_variable wcv;
-  bool wstop = false;                 // (under wmu) the worker is to exit
-  bool wjob = false;                  // (under wmu) a job is waiting or being enqueued
-  PhaseJob job;                       // (under wmu) the job
-  std::atomic<bool> phase_busy{false};  // the worker has not yet enqueued the latest phase
-  cudaError_t werr = cudaSuccess;     // (under wmu) first CUDA error of the worker
+  std::vector<StepGraph> graphs;
+  cudaStream_t cap_stream = nullptr;  // capture stream (no work ever runs on it)
+  int* picks_dev = nullptr;           // the phase's minibatch picks, train_iters x batch
+  int* picks_host = nullptr;          // pinned staging of the picks
+  float* tscale_host = nullptr;       // pinned staging of the phase's target scale
   cudaStream_t train_stream = nullptr;  // training phases started by solve (retrain_after)
   float* loss_dev = nullptr;
 

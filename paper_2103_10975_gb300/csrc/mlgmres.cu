@@ -141,6 +141,11 @@ void ensure_net(mlgmres* h) {
     // the inference copy starts from the same initial parameters (same seed)
     CK(net_create(h->inf, h->grid.n, 1, opt->seed, h->grid.dim, opt->grow_blocks, true));
     CK(cudaMalloc(&h->snap, sizeof(float) * h->net.nparams));
+    const size_t np = (size_t)std::max(1, opt->train_iters) * opt->batch;
+    CK(cudaMalloc(&h->picks_dev, sizeof(int) * np));
+    CK(cudaMallocHost(&h->picks_host, sizeof(int) * np));
+    CK(cudaMallocHost(&h->tscale_host, sizeof(float)));
+    CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   }
 }
 
@@ -152,18 +157,6 @@ cudaError_t query_event(cudaEvent_t e) {
   return q;
 }
 
-// Blocks until the training worker has enqueued its latest phase (its
-// train_done record is then the phase's end), and reports a CUDA error it met.
-void wait_worker(mlgmres* h) {
-  if (!h->worker.joinable()) return;
-  std::unique_lock<std::mutex> lk(h->wmu);
-  h->wcv.wait(lk, [h] { return !h->wjob; });
-  if (h->werr != cudaSuccess) {
-    h->last_error = fmt_cuda("training phase", h->werr);
-    throw Fail{MLGMRES_ERR_CUDA};
-  }
-}
-
 // Moves the parameters of the latest training phase into the guess's network,
 // on stream s.  With overlap_train (and for another stream than the phase's)
 // only once the phase has completed: a solve issued while it runs keeps the
@@ -172,11 +165,8 @@ void take_snapshot(mlgmres* h, cudaStream_t s) {
   if (!h->snap_pending) return;
   const bool same = s == h->phase_stream;
   if (h->linear || h->opt.overlap_train == 0 || same) {
-    wait_worker(h);  // the phase is fully enqueued (stream order then does the rest)
     if (!same) CK(cudaStreamWaitEvent(s, h->train_done, 0));
   } else {
-    // the worker records train_done only after the phase's last launch
-    if (h->phase_busy.load(std::memory_order_acquire)) return;
     const cudaError_t q = query_event(h->train_done);
     if (q == cudaErrorNotReady) return;
     CK(q);
@@ -210,7 +200,6 @@ void guess_forward(mlgmres* h, const float* u, float* y, cudaStream_t s) {
 // Streams that touch the training copy of the network (inspection entry
 // points) first wait for the latest phase.
 void wait_phase(mlgmres* h, cudaStream_t s) {
-  wait_worker(h);
   if (h->phase_enqueued && s != h->phase_stream) CK(cudaStreamWaitEvent(s, h->train_done, 0));
 }
 
@@ -424,43 +413,32 @@ int gate_and_store(mlgmres* h, const double* b, const double* x, const mlgmres_r
   return 1;
 }
 
-// The launches of one phase on stream s: its Adam steps on the ring
-// snapshot, then the copy of its parameters for the guess, then train_done.
-// Returns the first CUDA error (runs on the worker thread with overlap_train).
-cudaError_t phase_launches(mlgmres* h, cudaStream_t s, const std::vector<int>& picks, int B,
-                           int iters, float tscale, float lr) {
-  cudaError_t e = cudaSuccess;
-  for (int it = 0; it < iters && e == cudaSuccess; it++) {
-    const int* pick = picks.data() + (size_t)it * B;
-    e = h->linear ? lin_train_batch(h->lin, B, h->ring_u_snap, h->ring_t_snap, h->ldv, pick,
-                                    tscale, lr, h->loss_dev, s)
-                  : net_train_batch(h->net, B, h->ring_u_snap, h->ring_t_snap, h->ldv, pick,
-                                    tscale, lr, h->loss_dev, s);
-  }
-  // the parameters the guess will take once the phase has completed
-  if (e == cudaSuccess && !h->linear)
-    e = cudaMemcpyAsync(h->snap, h->net.master, sizeof(float) * h->net.nparams,
-                        cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaEventRecord(h->train_done, s);
-  return e;
-}
-
-void worker_main(mlgmres* h) {
-  cudaSetDevice(h->dev);
-  for (;;) {
-    std::unique_lock<std::mutex> lk(h->wmu);
-    h->wcv.wait(lk, [h] { return h->wstop || h->wjob; });
-    if (!h->wjob) return;  // stop requested and nothing left to enqueue
-    mlgmres::PhaseJob j = std::move(h->job);
-    lk.unlock();
-    const cudaError_t e = phase_launches(h, j.s, j.picks, j.B, j.iters, j.tscale, j.lr);
-    lk.lock();
-    if (e != cudaSuccess && h->werr == cudaSuccess) h->werr = e;
-    h->phase_busy.store(false, std::memory_order_release);
-    h->wjob = false;
-    lk.unlock();
-    h->wcv.notify_all();
-  }
+// The graph of one Adam step of the network for minibatch size B at the
+// current depth, captured on first use (its launches, counted once at
+// capture, are counted again at every replay).
+const mlgmres::StepGraph& step_graph(mlgmres* h, int B) {
+  for (const auto& g : h->graphs)
+    if (g.B == B && g.extra == h->net.extra_active) return g;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+  const long long l0 = launches_so_far();
+  const cudaError_t e = net_train_step_dev(h->net, B, h->ring_u_snap, h->ring_t_snap, h->ldv,
+                                           h->picks_dev, h->net.ctr, h->opt.lr, h->loss_dev,
+                                           h->cap_stream);
+  const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+  const long long k = launches_so_far() - l0;
+  note_launches(-k);
+  CK(e);
+  CK(e2);
+  mlgmres::StepGraph g;
+  g.B = B;
+  g.extra = h->net.extra_active;
+  g.kernels = k;
+  const cudaError_t e3 = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e3);
+  h->graphs.push_back(g);
+  return h->graphs.back();
 }
 
 // One training phase (Sec. 2.3) on stream s; see mlgmres_train_step.
@@ -469,7 +447,6 @@ void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
   if (h->ring_count == 0 || h->solves < h->opt.warmup_steps || h->opt.train_iters == 0) return;
   // one phase at a time: if the previous phase is still running, the caller
   // waits for it here (its ring and parameter snapshots are reused below)
-  wait_worker(h);
   if (h->phase_enqueued) {
     const cudaError_t q = query_event(h->train_done);
     if (q == cudaErrorNotReady) {
@@ -519,23 +496,30 @@ void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
     }
     while (k < B) pick[k++] = (int)(splitmix_next(h->rng_state) % (unsigned long long)h->ring_count);
   }
-  if (!h->linear && h->opt.overlap_train) {
-    if (!h->worker.joinable()) h->worker = std::thread(worker_main, h);
-    {
-      std::lock_guard<std::mutex> lk(h->wmu);
-      h->job.s = s;
-      h->job.picks = std::move(picks);
-      h->job.B = B;
-      h->job.iters = iters;
-      h->job.tscale = tscale;
-      h->job.lr = h->opt.lr;
-      h->phase_busy.store(true, std::memory_order_release);
-      h->wjob = true;
-    }
-    h->wcv.notify_all();
+  if (h->linear) {
+    for (int it = 0; it < iters; it++)
+      CK(lin_train_batch(h->lin, B, h->ring_u_snap, h->ring_t_snap, h->ldv,
+                         picks.data() + (size_t)it * B, tscale, h->opt.lr, h->loss_dev, s));
   } else {
-    CK(phase_launches(h, s, picks, B, iters, tscale, h->opt.lr));
+    // the phase's inputs to device memory (the pinned staging is free: the
+    // previous phase has completed), then train_iters replays of the step
+    const mlgmres::StepGraph& g = step_graph(h, B);
+    memcpy(h->picks_host, picks.data(), sizeof(int) * picks.size());
+    *h->tscale_host = tscale;
+    CK(cudaMemcpyAsync(h->picks_dev, h->picks_host, sizeof(int) * picks.size(),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(&h->net.ctr->tscale, h->tscale_host, sizeof(float),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(&h->net.ctr->iter, 0, sizeof(int), s));
+    for (int it = 0; it < iters; it++) {
+      CK(cudaGraphLaunch(g.exec, s));
+      note_launches(g.kernels);
+    }
+    // the parameters the guess will take once the phase has completed
+    CK(cudaMemcpyAsync(h->snap, h->net.master, sizeof(float) * h->net.nparams,
+                       cudaMemcpyDeviceToDevice, s));
   }
+  CK(cudaEventRecord(h->train_done, s));
   h->phase_enqueued = true;
   h->phase_stream = s;
   h->snap_pending = true;
@@ -545,7 +529,6 @@ void train_phase(mlgmres* h, cudaStream_t s, float* loss_host) {
   h->fresh.clear();
   h->cand_n = 0;
   if (loss_host) {
-    wait_worker(h);
     CK(cudaStreamSynchronize(s));
     CK(cudaMemcpy(loss_host, h->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
   }
@@ -683,15 +666,12 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
 
 void mlgmres_destroy(mlgmres_t h) {
   if (!h) return;
-  if (h->worker.joinable()) {
-    {
-      std::lock_guard<std::mutex> lk(h->wmu);
-      h->wstop = true;
-    }
-    h->wcv.notify_all();
-    h->worker.join();  // after it has enqueued a phase it had started
-  }
   cudaDeviceSynchronize();  // no phase may still use the workspace freed below
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  cudaFree(h->picks_dev);
+  cudaFreeHost(h->picks_host);
+  cudaFreeHost(h->tscale_host);
   cudaFree(h->Vb);
   cudaFree(h->Wb);
   cudaFree(h->partb);
@@ -1205,7 +1185,6 @@ mlgmres_status mlgmres_nn_get_params(mlgmres_t h, float* p, long long count) {
   try {
     ensure_net(h);
     ARG(p && count == model_params(h), "bad parameter buffer");
-    wait_worker(h);
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(p, model_master(h), sizeof(float) * count, cudaMemcpyDeviceToHost));
     return MLGMRES_OK;
@@ -1219,13 +1198,10 @@ mlgmres_status mlgmres_nn_set_params(mlgmres_t h, const float* p, long long coun
   try {
     ensure_net(h);
     ARG(p && count == model_params(h), "bad parameter buffer");
-    wait_worker(h);
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(model_master(h), p, sizeof(float) * count, cudaMemcpyHostToDevice));
     if (!h->linear) {
-      CK(cudaMemset(h->net.adam_m, 0, sizeof(float) * count));
-      CK(cudaMemset(h->net.adam_v, 0, sizeof(float) * count));
-      h->net.adam_t = 0;
+      CK(net_adam_reset(h->net, 0));
       CK(net_sync_weights(h->net, 0));
       // the guess uses the parameters just set (they supersede a pending phase's)
       CK(net_copy_params(h->inf, h->net.master, 0));
@@ -1290,7 +1266,6 @@ mlgmres_status mlgmres_guess(mlgmres_t h, const double* b, double* x, void* stre
     ensure_net(h);
     cudaStream_t s = (cudaStream_t)stream;
     // the guess of the latest phase: wait for it to complete
-    wait_worker(h);
     if (h->phase_enqueued) CK(cudaEventSynchronize(h->train_done));
     take_snapshot(h, s);
     const double* g = learned_guess(h, b, s);
@@ -1332,7 +1307,6 @@ mlgmres_status mlgmres_nn_blocks(mlgmres_t h, int set_to, int* active) {
     ARG(set_to >= -1, "set_to must be >= -1");
     ensure_net(h);
     if (set_to >= 0) {
-      wait_worker(h);
       CK(cudaDeviceSynchronize());  // no training phase may be using the old depth
       h->net.extra_active = std::min(set_to, h->net.extra_max);
       h->inf.extra_active = h->net.extra_active;

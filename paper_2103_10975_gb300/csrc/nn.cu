@@ -234,11 +234,13 @@ __global__ void conv_out_fwd(int B, int n, const bf16* __restrict__ t,
 
 // --------------------------------------------------------------- backward --
 
-// gy = 2 (y - ts t) / (B N); per-CTA partial sums of (y - ts t)^2
-__global__ void mse_grad(long long total, float scale, float ts, const float* __restrict__ y,
-                         const float* __restrict__ t, float* __restrict__ gy,
-                         float* __restrict__ part) {
+// gy = 2 (y - ts t) / (B N); per-CTA partial sums of (y - ts t)^2 (ts from
+// tsp when given: the target scale of a training phase, in device memory)
+__global__ void mse_grad(long long total, float scale, float ts, const float* __restrict__ tsp,
+                         const float* __restrict__ y, const float* __restrict__ t,
+                         float* __restrict__ gy, float* __restrict__ part) {
   __shared__ float red[32];
+  if (tsp) ts = *tsp;
   float acc = 0.f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -623,11 +625,13 @@ __global__ void pool2_bwd_add(int B, int s, const float* __restrict__ coarse,
 
 // Adam (Kingma & Ba): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
 // theta -= lr * (m / c1) / (sqrt(v / c2) + eps), c1 = 1 - b1^t, c2 = 1 - b2^t
+// (c1, c2 of the step in progress, from the phase's device state)
 __global__ void adam_kernel(long long count, float* __restrict__ theta,
                             const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, float lr, float c1, float c2) {
+                            float* __restrict__ v, float lr, const TrainCtr* __restrict__ ctr) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= count) return;
+  const float c1 = ctr->c1, c2 = ctr->c2;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -635,6 +639,34 @@ __global__ void adam_kernel(long long count, float* __restrict__ theta,
   m[i] = mi;
   v[i] = vi;
   theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Start of one Adam step of a phase: t = adam_t + 1 with its bias corrections,
+// and the offset of this step's minibatch in the phase's picks.
+__global__ void step_begin(TrainCtr* ctr, int B) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const long long t = ctr->adam_t + 1;
+    ctr->adam_t = t;
+    ctr->c1 = 1.f - powf(0.9f, (float)t);
+    ctr->c2 = 1.f - powf(0.999f, (float)t);
+    ctr->pick_off = ctr->iter * B;
+    ctr->iter = ctr->iter + 1;
+  }
+}
+
+// bu[b] = ring_u[picks[pick_off + b]], bt[b] = ring_t[...] for b < B (N each,
+// ring slots `stride` floats apart)
+__global__ void gather_pairs(int B, long long N, const float* __restrict__ ring_u,
+                             const float* __restrict__ ring_t, long long stride,
+                             const int* __restrict__ picks, const TrainCtr* __restrict__ ctr,
+                             float* __restrict__ bu, float* __restrict__ bt) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)B * N) return;
+  const int b = (int)(i / N);
+  const long long p = i - (long long)b * N;
+  const long long src = (long long)picks[ctr->pick_off + b] * stride + p;
+  bu[i] = ring_u[src];
+  bt[i] = ring_t[src];
 }
 
 // wq[conv][tap][k][o] = W[o][k][tap], wqT[conv][tap][o][k] = W[o][k][tap] (BF16)
@@ -679,6 +711,7 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
       (long long)bmax * (dim == 3 ? (long long)n * n * n : (long long)n * n) * kC >= (1LL << 31))
     return cudaErrorInvalidValue;
   if (dim == 2) NN_CK(conv32_tc_setup());
+  NN_CK(conv32_mma_setup());
   net.extra_max = extra_max;
   net.extra_active = 0;
   net.n = n;
@@ -837,6 +870,12 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
   NN_CK(cudaMalloc(&net.bu, sizeof(float) * pix));
   NN_CK(cudaMalloc(&net.bt, sizeof(float) * pix));
   NN_CK(cudaMalloc(&net.by, sizeof(float) * pix));
+  NN_CK(cudaMalloc(&net.ctr, sizeof(TrainCtr)));
+  {
+    TrainCtr c0{};
+    c0.tscale = 1.f;
+    NN_CK(cudaMemcpy(net.ctr, &c0, sizeof(c0), cudaMemcpyHostToDevice));
+  }
   NN_CK(net_sync_weights(net, 0));
   return cudaDeviceSynchronize();
 }
@@ -875,6 +914,7 @@ void net_destroy(Net& net) {
   cudaFree(net.bu);
   cudaFree(net.bt);
   cudaFree(net.by);
+  cudaFree(net.ctr);
   net = Net();
 }
 
@@ -940,7 +980,7 @@ cudaError_t forward_t(Net& net, int B, const float* u, float* y, cudaStream_t s)
 
 template <int D>
 cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const float* target,
-                       float tscale, float* loss_dev, cudaStream_t s) {
+                       float tscale, const float* tscale_dev, float* loss_dev, cudaStream_t s) {
   constexpr int T = Geo<D>::T;
   const int n = net.n, L = net.L;
   const long long pix = B * Geo<D>::pts(n);
@@ -950,7 +990,7 @@ cudaError_t backward_t(Net& net, int B, const float* u, const float* y, const fl
   const int stride = (int)(per + kC);
   // loss and dL/dy
   const int lparts = 256;
-  mse_grad<<<lparts, 256, 0, s>>>(pix, 1.f / (float)pix, tscale, y, target, net.gy,
+  mse_grad<<<lparts, 256, 0, s>>>(pix, 1.f / (float)pix, tscale, tscale_dev, y, target, net.gy,
                                   net.loss_part);
   note_launches(1);
   loss_finish<<<1, 32, 0, s>>>(net.loss_part, lparts, 1.f / (float)pix, loss_dev);
@@ -1106,34 +1146,34 @@ cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t 
 
 cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const float* target,
                          float tscale, float* loss_dev, cudaStream_t s) {
-  return net.dim == 3 ? backward_t<3>(net, B, u, y, target, tscale, loss_dev, s)
-                      : backward_t<2>(net, B, u, y, target, tscale, loss_dev, s);
+  return net.dim == 3 ? backward_t<3>(net, B, u, y, target, tscale, nullptr, loss_dev, s)
+                      : backward_t<2>(net, B, u, y, target, tscale, nullptr, loss_dev, s);
 }
 
-cudaError_t net_adam(Net& net, float lr, cudaStream_t s) {
-  net.adam_t += 1;
-  const float c1 = 1.f - powf(0.9f, (float)net.adam_t);
-  const float c2 = 1.f - powf(0.999f, (float)net.adam_t);
+cudaError_t net_adam_reset(Net& net, cudaStream_t s) {
+  NN_CK(cudaMemsetAsync(net.adam_m, 0, sizeof(float) * net.nparams, s));
+  NN_CK(cudaMemsetAsync(net.adam_v, 0, sizeof(float) * net.nparams, s));
+  return cudaMemsetAsync(&net.ctr->adam_t, 0, sizeof(long long), s);
+}
+
+cudaError_t net_train_step_dev(Net& net, int B, const float* ring_u, const float* ring_t,
+                               long long stride, const int* picks, TrainCtr* ctr, float lr,
+                               float* loss_dev, cudaStream_t s) {
+  const long long N = net.dim == 3 ? (long long)net.n * net.n * net.n : (long long)net.n * net.n;
+  step_begin<<<1, 32, 0, s>>>(ctr, B);
+  gather_pairs<<<nblk((long long)B * N, 256), 256, 0, s>>>(B, N, ring_u, ring_t, stride, picks,
+                                                           ctr, net.bu, net.bt);
+  note_launches(2);
+  NN_CK(cudaGetLastError());
+  NN_CK(net_forward(net, B, net.bu, net.by, s));
+  NN_CK(net.dim == 3
+            ? backward_t<3>(net, B, net.bu, net.by, net.bt, 1.f, &ctr->tscale, loss_dev, s)
+            : backward_t<2>(net, B, net.bu, net.by, net.bt, 1.f, &ctr->tscale, loss_dev, s));
   adam_kernel<<<nblk(net.nparams, 256), 256, 0, s>>>(net.nparams, net.master, net.grad,
-                                                     net.adam_m, net.adam_v, lr, c1, c2);
+                                                     net.adam_m, net.adam_v, lr, ctr);
   note_launches(1);
   NN_CK(cudaGetLastError());
   return net_sync_weights(net, s);
-}
-
-cudaError_t net_train_batch(Net& net, int B, const float* ring_u, const float* ring_t,
-                            long long stride, const int* pick, float tscale, float lr,
-                            float* loss_dev, cudaStream_t s) {
-  const long long N = net.dim == 3 ? (long long)net.n * net.n * net.n : (long long)net.n * net.n;
-  for (int i = 0; i < B; i++) {
-    NN_CK(cudaMemcpyAsync(net.bu + i * N, ring_u + (long long)pick[i] * stride,
-                          sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
-    NN_CK(cudaMemcpyAsync(net.bt + i * N, ring_t + (long long)pick[i] * stride,
-                          sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
-  }
-  NN_CK(net_forward(net, B, net.bu, net.by, s));
-  NN_CK(net_backward(net, B, net.bu, net.by, net.bt, tscale, loss_dev, s));
-  return net_adam(net, lr, s);
 }
 
 }  // namespace mlg

@@ -27,6 +27,18 @@ constexpr int kC = 32;      // channels
 constexpr int kMaxLevels = 12;
 constexpr int kMaxExtra = 4;  // residual blocks the network may grow (Sec. 2.1)
 
+// Device-side state of a training phase, so that one Adam step is the same
+// sequence of launches every time (a CUDA graph replays it): the step counter
+// and bias corrections of Adam, the minibatch's offset into the phase's picks,
+// and the target scale.
+struct TrainCtr {
+  long long adam_t;   // Adam steps taken (t of the next step is adam_t + 1)
+  int iter;           // Adam steps taken in the current phase
+  int pick_off;       // iter * B for the step in progress
+  float c1, c2;       // 1 - b1^t, 1 - b2^t of the step in progress
+  float tscale;       // 1 / c: targets of the phase are t / c
+};
+
 struct Net {
   int n = 0;                // grid side
   int dim = 2;              // 2: 3x3 kernels, 2x2 pooling; 3: 3x3x3, 2x2x2
@@ -49,7 +61,6 @@ struct Net {
   float* grad = nullptr;
   float* adam_m = nullptr;
   float* adam_v = nullptr;
-  long long adam_t = 0;
   __nv_bfloat16* wq = nullptr;  // BF16 copies of the 32->32 weights, [conv][tap][ci][co]
                                 // (B operand of the data gradient)
   __nv_bfloat16* wqT = nullptr; // [conv][tap][co][ci] (B operand of the forward pass)
@@ -82,6 +93,7 @@ struct Net {
   float* up_w[kMaxLevels] = {};
   long long pyr = 0;                         // sum of level sizes (pixels) per sample
   int wparts = 0;                            // CTAs of the weight-gradient kernels
+  TrainCtr* ctr = nullptr;                   // device state of the training phase
 };
 
 // Tensor-core 32 -> 32 convolution (dim 2: 3x3, dim 3: 3x3x3; mode 0:
@@ -99,8 +111,11 @@ cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
                              __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                              float* fo, const float* addend, cudaStream_t s);
 // One-time set-up of the tcgen05 convolution (shared-memory limits, its error
-// flag); net_create calls it so that no forward pass allocates.
+// flag) and of the mma.sync convolution (shared-memory limits); net_create
+// calls them so that no forward pass allocates or sets attributes (which a
+// graph capture of a training step could not contain).
 cudaError_t conv32_tc_setup();
+cudaError_t conv32_mma_setup();
 // 1 if a tcgen05 convolution tile timed out waiting for its MMAs (0 otherwise).
 int conv32_tc_error();
 // Tensor-core weight gradient partials of a 32 -> 32 convolution (nparts CTAs).
@@ -125,12 +140,15 @@ cudaError_t net_forward(Net& net, int B, const float* u, float* y, cudaStream_t 
 // into *loss_dev and all parameter gradients into net.grad.
 cudaError_t net_backward(Net& net, int B, const float* u, const float* y, const float* target,
                          float tscale, float* loss_dev, cudaStream_t s);
-// One Adam step on net.master from net.grad; refreshes the BF16 copies.
-cudaError_t net_adam(Net& net, float lr, cudaStream_t s);
-// One minibatch step: gather ring slots `pick[0..B)` (stride floats apart) of
-// inputs u and targets t, forward, backward, Adam.  *loss_dev gets the loss.
-cudaError_t net_train_batch(Net& net, int B, const float* ring_u, const float* ring_t,
-                            long long stride, const int* pick, float tscale, float lr,
-                            float* loss_dev, cudaStream_t s);
+// Resets Adam (moments and the step counter), on stream s.
+cudaError_t net_adam_reset(Net& net, cudaStream_t s);
+// One minibatch step with every per-step input in device memory: advances
+// ctr (t, iter), gathers ring slots picks[pick_off .. pick_off + B) (stride
+// floats apart) of inputs u and targets t, runs forward, backward (targets
+// scaled by ctr->tscale) and Adam with lr.  *loss_dev gets the loss.  The
+// launches do not depend on the step, so a graph capture replays it.
+cudaError_t net_train_step_dev(Net& net, int B, const float* ring_u, const float* ring_t,
+                               long long stride, const int* picks, TrainCtr* ctr, float lr,
+                               float* loss_dev, cudaStream_t s);
 
 }  // namespace mlg

@@ -11,6 +11,7 @@
 // (3D) input rows it needs (with a dil-wide halo, zero outside the grid) are
 // staged in shared memory with an 80-byte pixel stride, which keeps ldmatrix
 // conflict-free.
+#include <mutex>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -307,13 +308,6 @@ static cudaError_t conv_launch(int mode, int B, int H, const __nv_bfloat16* in,
                                __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                                float* fo, const float* addend, cudaStream_t s) {
   constexpr int smem = conv_smem_bytes<D>();
-  static bool configured = false;  // the 3D variants need more than 48 KB
-  if (!configured) {
-    cudaFuncSetAttribute(conv32_mma<kRelu, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(conv32_mma<kResid, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(conv32_mma<kF32, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    configured = true;
-  }
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -331,6 +325,25 @@ static cudaError_t conv_launch(int mode, int B, int H, const __nv_bfloat16* in,
                                                  fo, addend);
   note_launches(1);
   return cudaGetLastError();
+}
+
+// The 3D variants need more than the default 48 KB of dynamic shared memory;
+// net_create calls this once, before any launch (and before a graph capture).
+cudaError_t conv32_mma_setup() {
+  static std::mutex mu;
+  static bool done = false;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done) return cudaSuccess;
+  constexpr int s2 = conv_smem_bytes<2>(), s3 = conv_smem_bytes<3>();
+  cudaError_t e = cudaSuccess;
+  for (const void* f : {(const void*)conv32_mma<kRelu, 2>, (const void*)conv32_mma<kResid, 2>,
+                        (const void*)conv32_mma<kF32, 2>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
+  for (const void* f : {(const void*)conv32_mma<kRelu, 3>, (const void*)conv32_mma<kResid, 3>,
+                        (const void*)conv32_mma<kF32, 3>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, s3);
+  done = e == cudaSuccess;
+  return e;
 }
 
 cudaError_t launch_conv32_mma(int dim, int mode, int B, int H, const __nv_bfloat16* in,
