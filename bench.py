@@ -15,6 +15,12 @@ phase's parameters once it has completed; a phase that is still running when
 the next one is due holds the loop until it ends, so that time lands in the
 step.  Before the W warm-up steps the loop runs its tau0 = 50 online warm-up
 steps (data collection and the first training, Sec. 2.3) untimed.
+
+The same line carries, as sub-objects, the other workloads on one GPU: a
+capped 2048^2 solve for the HBM roofline (`roofline_hbm`), full time steps of
+the 2048^2 refinement workload with the error against the DST-I solution
+(`c3_full_steps`, --c3-steps, 1 by default) and the 512-instance batched
+workload in one persistent launch (`c4_batch`, --no-batch to skip).
 """
 
 import argparse
@@ -71,8 +77,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-GMRES arms")
     ap.add_argument("--no-hbm", action="store_true", help="skip the 2048^2 roofline solve")
-    ap.add_argument("--c3-steps", type=int, default=0,
-                    help="full time steps of the 2048^2 workload to time (0 = none)")
+    ap.add_argument("--c3-steps", type=int, default=1,
+                    help="full time steps of the 2048^2 workload to time (0 = none; single GPU)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 512-instance batched workload (single GPU)")
     return ap.parse_args()
 
 
@@ -334,6 +342,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    host_train = [0.0]   # host seconds spent in train_step by the last series
+
     def run_series(solver, t0, count, learned, timed, results, pre=None, drain=True):
         """Steps t0..t0+count-1; returns per-step device ms (events on the solve
         stream).  A step is the solve plus, every TRAIN_EVERY steps, starting a
@@ -342,6 +352,7 @@ def run_ours(args):
         to end is added to the last step, so no training is left uncounted."""
         ms = []
         x = None
+        host_train[0] = 0.0
         for i in range(count):
             t = t0 + i
             if timed:
@@ -353,7 +364,9 @@ def run_ours(args):
                 x = pre(solver, B[t])
             x, r = solver.solve(B[t], x)
             if learned and (t + 1) % TRAIN_EVERY == 0:
+                h0 = time.perf_counter()
                 solver.train_step(stream=side)
+                host_train[0] += time.perf_counter() - h0
             e1.record(main)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -387,6 +400,7 @@ def run_ours(args):
     l0 = pkg.kernel_launches()
     t_wall0 = time.perf_counter()
     ms = run_series(sol, TAU0 + W, K, True, True, res)
+    train_host_ms = host_train[0] * 1e3
     barrier()
     t_wall = time.perf_counter() - t_wall0
     launches = pkg.kernel_launches() - l0
@@ -514,10 +528,10 @@ def run_ours(args):
                                      "compact": tw["compact"]}}
         s5.close()
 
-    # ---- optional: full time steps of the 2048^2 workload, error against DST
-    c3 = None
-    if args.c3_steps > 0:
-        c3 = run_c3(pkg, torch, dev, args.c3_steps)
+    # ---- single GPU: full time steps of the 2048^2 workload (error against DST)
+    # and the 512-instance batched workload
+    c3 = run_c3(pkg, torch, dev, args.c3_steps) if world == 1 and args.c3_steps > 0 else None
+    c4 = run_c4(pkg, torch, dev) if world == 1 and not args.no_batch else None
 
     line = None
     if rank == 0:
@@ -567,9 +581,12 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk,
             "wall_ms_per_step": t_wall * 1e3 / K,
+            "train_step_host_ms_per_step": train_host_ms / K,
         }
         if c3 is not None:
             line["c3_full_steps"] = c3
+        if c4 is not None:
+            line["c4_batch"] = c4
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(gen.rhs(TAU0 + W), n, TAU0 + W)
         else:
@@ -602,10 +619,41 @@ def run_c3(pkg, torch, dev, steps):
         out.append({"t": t, "ms": r["tos_ms"], "iters": r["iters"], "relres_true": r["relres_true"],
                     "err_vs_dst": err, "guess": "zero" if t == 0 else "x_{t-1}"})
     s.close()
-    return {"workload": "2048x2048 random-walk sources, GMRES(40) FP32 + FP64 refinement, "
-                        "rtol 1e-10", "steps": out,
-            "ms_per_step_mean": statistics.mean(o["ms"] for o in out),
-            "extrapolated_to_T12_ms": None}
+    mean = statistics.mean(o["ms"] for o in out)
+    return {"workload": "2048x2048 random-walk sources (seed 3001), GMRES(40) FP32 cycles + "
+                        "FP64 refinement, rtol 1e-10; the first step from x0 = 0, later ones "
+                        "from x_{t-1}", "steps": out,
+            "ms_per_step_mean": mean,
+            "T12_ms": {"value": 12 * mean, "extrapolated": len(out) < 12,
+                       "how": "12 x the mean of the timed steps" if len(out) < 12 else "timed"}}
+
+
+def run_c4(pkg, torch, dev):
+    """The batched workload: 512 independent 2D Poisson instances, sides
+    U{64..512} (seed 4001 + i), each with its own moving-Gaussian right-hand
+    side at t = 0, GMRES(30) FP32 cycles + FP64 refinement to rtol 1e-8, all
+    in one persistent launch; a sample of 8 instances against DST-I."""
+    import numpy as np
+    from oracle import direct
+    from synthetic import batched_instances
+    inst = batched_instances(512)
+    ns = [n for n, _ in inst]
+    bs = [torch.as_tensor(b).to(dev) for _, b in inst]
+    s = pkg.Solver(max(ns), m=30, rtol=1e-8, precision="fp32_refine", batch_slots=4096,
+                   max_iters=10 ** 7)
+    xs, res = s.solve_batch(ns, bs)
+    errs = []
+    for i in range(0, 512, 64):
+        xr = direct.dst_solve_2d(ns[i], inst[i][1])
+        errs.append(float(np.linalg.norm(xs[i].cpu().numpy() - xr) / np.linalg.norm(xr)))
+    s.close()
+    return {"workload": "512 instances, sides U{64..512} (seed 4001+i), GMRES(30) FP32 + FP64 "
+                        "refinement, rtol 1e-8, one persistent launch",
+            "launch_ms": res[0]["tos_ms"], "unknowns": sum(n * n for n in ns),
+            "arnoldi_steps": sum(r["iters"] for r in res),
+            "relres_true_max": max(r["relres_true"] for r in res),
+            "status": sorted(set(r["status"] for r in res)),
+            "err_vs_dst_sample_max": max(errs), "err_sample": "instances 0, 64, ..., 448"}
 
 
 def main():

@@ -25,9 +25,10 @@ if torch.cuda.is_available():
 # weight or bias gradient is a sum over pixels whose terms partly cancel, which
 # raises the relative error of the sum by the ratio sum|g_i| / |sum g_i|.
 # Measured maximum over all tensors and cases (2D 16^2/32^2/128^2, 3D 8^3/16^3,
-# two grown blocks, four Adam steps): 2.5e-2 (a coarse level's bias at 32^2),
-# most tensors below 1e-2.
-GRAD_TOL = 3e-2
+# two grown blocks, the weights after one to three Adam steps): 3.0e-2 (after
+# Adam steps at 16^2), 2.5e-2 (a coarse level's bias at 32^2); most tensors
+# below 1e-2.
+GRAD_TOL = 4e-2
 
 
 def check_grads(G, gr, label):
