@@ -125,6 +125,8 @@ struct Smem {
   double hcol[MAXM + 2];         // the column being rotated, in FP64 (Givens warp)
   double R[(MAXM + 1) * MAXM];   // the same columns after the Givens rotations
   double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
+  double rinv[MAXM];             // 1 / R(c,c), formed with rotation c (the back-
+                                 // substitution then multiplies: no FP64 division)
   T HuT[(MAXM + 1) * MAXM];      // Hessenberg as built (Arnoldi relation), ld MAXM+1
   T coef[MAXM + 2];              // h1 in the working precision (gather output)
   // per basis vector k: .x = h2_k, the pending second-pass coefficient of w';
@@ -394,10 +396,12 @@ __device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, lo
       sm.cs[c] = ri * inv;
       sm.sn[c] = hsub * inv;
       rho = r2 * inv;
+      sm.rinv[c] = inv;  // 1 / rho
     } else {
       rho = sqrt(r2);
       sm.cs[c] = rho == 0.0 ? 1.0 : ri / rho;
       sm.sn[c] = rho == 0.0 ? 0.0 : hsub / rho;
+      sm.rinv[c] = 1.0 / rho;
     }
     rc[c] = rho;
     rc[c + 1] = 0.0;
@@ -1490,18 +1494,35 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
     // ---- cycle end: y = R^{-1} g (upper triangular), x += V y
     if (threadIdx.x < 32) {
       for (int i = kcols - 1; i >= 0; i--) {
-        const double yi = sm.g[i] / sm.R[i + i * LD];
+        const double yi = sm.g[i] * sm.rinv[i];
         for (int l = lane; l < i; l += 32) sm.g[l] -= sm.R[l + i * LD] * yi;
         if (lane == 0) sm.y[i] = yi;
         __syncwarp();
       }
     }
     __syncthreads();
-    for (int i = lo + tid; i < hi; i += BS) {
-      double d = 0.0;
-      const long long vb = vbase(i - voff, rows);
-      for (int k = 0; k < kcols; k++) d += sm.y[k] * (double)V[vb + ((long long)k << 5)];
-      tk.x[i] += d;
+    // two points per trip and even / odd k apart: four independent FP64 chains
+    // (a dependent FP64 operation costs ~70 cycles on this GPU)
+    for (int i0 = lo + tid; i0 < hi; i0 += 2 * BS) {
+      const int i1 = i0 + BS;
+      const bool two = i1 < hi;
+      const long long vb0 = vbase(i0 - voff, rows);
+      const long long vb1 = two ? vbase(i1 - voff, rows) : vb0;
+      double d0 = 0.0, e0 = 0.0, d1 = 0.0, e1 = 0.0;
+      int k = 0;
+      for (; k + 1 < kcols; k += 2) {
+        const double ya = sm.y[k], yb = sm.y[k + 1];
+        d0 = fma(ya, (double)V[vb0 + ((long long)k << 5)], d0);
+        e0 = fma(yb, (double)V[vb0 + ((long long)(k + 1) << 5)], e0);
+        d1 = fma(ya, (double)V[vb1 + ((long long)k << 5)], d1);
+        e1 = fma(yb, (double)V[vb1 + ((long long)(k + 1) << 5)], e1);
+      }
+      if (k < kcols) {
+        d0 = fma(sm.y[k], (double)V[vb0 + ((long long)k << 5)], d0);
+        d1 = fma(sm.y[k], (double)V[vb1 + ((long long)k << 5)], d1);
+      }
+      tk.x[i0] += d0 + e0;
+      if (two) tk.x[i1] += d1 + e1;
     }
     cycles++;
     ok = group_sync(w.bar, epoch, &sm.flag);
