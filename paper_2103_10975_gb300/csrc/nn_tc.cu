@@ -10,11 +10,18 @@
 // matrices of 8 rows x 16 bytes).  The A operand is not materialised per tap:
 // the three input rows a tile needs are staged once, each as 4 column blocks
 // (8 channels each) of 132 pixel rows 16 bytes apart (so 8-row groups are 128
-// bytes apart, the stride offset, and column blocks 2112 bytes apart, the
+// bytes apart, the stride offset, and column blocks 2176 bytes apart, the
 // leading-dimension offset); a tap's operand is then the same rows shifted by
 // its x offset, i.e. a descriptor whose start address moves by 16 bytes per
 // pixel.  The weights use 128 / 512-byte offsets.
+// The rows arrive by TMA: a tensor map over the channels-last activation (4D:
+// channels, x, y, batch) and one box of 8 channels x 132 pixels per column
+// block, zero-filled outside the grid.  Each CTA runs a stream of tiles with two
+// stages of rows and two accumulators in tensor memory: while the epilogue of
+// tile k reads its accumulator, the MMAs of tile k+1 run and the rows of tile
+// k+2 are in flight.
 #include <mutex>
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -28,10 +35,16 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int kTcM = 128;                    // pixels per tile (TMEM lanes)
 constexpr int kRows = kTcM + 4;              // staged pixels per input row (dilation <= 2)
-constexpr int kLboA = kRows * 16;            // bytes between 8-channel column blocks
+constexpr int kBox = kRows * 16;             // one tensor copy: 8 channels x kRows pixels
+constexpr int kLboA = 17 * 128;              // bytes between 8-channel column blocks (a copy
+                                             // destination, 128-byte aligned, >= kBox)
 constexpr int kRowBytes = 4 * kLboA;         // one staged input row
+constexpr int kStageBytes = 3 * kRowBytes;   // the three input rows of a tile
+constexpr int kStageTx = 12 * kBox;          // bytes the 12 copies of a stage deliver
 constexpr int kWBytes = kC * kC * 2;         // one tap's B operand: 2 KB
-constexpr int kTcSmem = 3 * kRowBytes + 9 * kWBytes + 64;
+constexpr int kTcSmem = 2 * kStageBytes + 9 * kWBytes + 64;
+static_assert(kLboA >= kBox && kLboA % 128 == 0 && kStageBytes % 128 == 0,
+              "copy destinations must be 128-byte aligned and hold a box");
 
 __device__ __forceinline__ unsigned saddr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -69,9 +82,65 @@ __device__ __forceinline__ bool mbar_test_tc(unsigned bar, unsigned phase) {
 
 enum { kRelu = 0, kResid = 1, kF32 = 2 };
 
+// A tile's coordinates: batch b, grid row y, first pixel x0 of its 128.
+__device__ __forceinline__ void tile_coords(long long tIdx, int H, int tpr, int& b, int& y,
+                                            int& x0) {
+  const int tx = (int)(tIdx % tpr);
+  y = (int)((tIdx / tpr) % H);
+  b = (int)(tIdx / ((long long)tpr * H));
+  x0 = tx * kTcM;
+}
+
+// Bounded mbarrier wait (2 s); false on expiry.
+__device__ __forceinline__ bool mbar_wait_tc(unsigned bar, unsigned phase) {
+  if (mbar_test_tc(bar, phase)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_test_tc(bar, phase))
+    if (globaltimer_ns() - t0 > 2000000000ull) return false;
+  return true;
+}
+
+// The three input rows of tile (b, y, x0) into stage buffer `as`: 12 tensor
+// copies (3 rows x 4 blocks of 8 channels), each a box of 8 channels x kRows
+// pixels starting at pixel x0 - dil; pixels and rows outside the grid arrive as
+// zeros.  The stage's mbarrier expects all their bytes.
+__device__ __forceinline__ void issue_rows(const CUtensorMap* tmap, unsigned as, unsigned bar,
+                                           int b, int y, int x0, int dil, int sign) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(kStageTx)
+               : "memory");
+  for (int ty = 0; ty < 3; ty++) {
+    const int yy = y + sign * dil * (ty - 1);
+    for (int kc = 0; kc < 4; kc++)
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(as + ty * kRowBytes + kc * kLboA),
+          "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(8 * kc), "r"(x0 - dil), "r"(yy),
+          "r"(b), "r"(bar)
+          : "memory");
+  }
+}
+
+// The 18 MMAs of one tile: A from stage buffer `as`, B the staged weights,
+// D the accumulator at TMEM column offset `col`; tcgen05.commit then arrives
+// on `bar` when they (and every earlier MMA of this thread) have completed.
+__device__ __forceinline__ void issue_mmas(unsigned tmem, unsigned as, unsigned ws, int dil,
+                                           int sign, unsigned bar) {
+  for (int t = 0; t < 9; t++) {
+    // tap (ty, tx): pixel p reads staged row ty, pixel p + dil + sign*dil*(tx-1)
+    const int row0 = dil + sign * dil * (t % 3 - 1);
+    for (int h = 0; h < 2; h++)
+      tc_mma(tmem, mdesc(as + (t / 3) * kRowBytes + row0 * 16 + h * 2 * kLboA, kLboA, 128),
+             mdesc(ws + t * kWBytes + h * 256, 128, 512), (t | h) ? 1u : 0u);
+  }
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(128) conv32_tc(int B, int H, const bf16* __restrict__ in,
-                                                 const bf16* __restrict__ wop,
+__global__ void __launch_bounds__(128) conv32_tc(const __grid_constant__ CUtensorMap tmap, int B,
+                                                 int H, const bf16* __restrict__ wop,
                                                  const float* __restrict__ bias, int dil,
                                                  int sign, bf16* __restrict__ zo,
                                                  bf16* __restrict__ to,
@@ -80,10 +149,11 @@ __global__ void __launch_bounds__(128) conv32_tc(int B, int H, const bf16* __res
                                                  const float* __restrict__ addend,
                                                  int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  unsigned char* As = tc_smem;                         // 3 staged input rows
-  unsigned char* Ws = tc_smem + 3 * kRowBytes;         // 9 x 2 KB
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(Ws + 9 * kWBytes);
-  unsigned* tmem_slot = reinterpret_cast<unsigned*>(mbar + 1);
+  unsigned char* As = tc_smem;                              // 2 stages of 3 input rows
+  unsigned char* Ws = tc_smem + 2 * kStageBytes;            // 9 x 2 KB
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(Ws + 9 * kWBytes);
+  unsigned long long* mmad = full + 2;
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(mmad + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // B operand (weights) of all 9 taps: (n, k) at (n/8)*512 + (k/8)*128 + (n%8)*16 + (k%8)*2
@@ -92,12 +162,15 @@ __global__ void __launch_bounds__(128) conv32_tc(int B, int H, const bf16* __res
     const uint4 v = *reinterpret_cast<const uint4*>(wop + (t * kC + n) * kC + kc * 8);
     *reinterpret_cast<uint4*>(Ws + t * kWBytes + (n >> 3) * 512 + kc * 128 + (n & 7) * 16) = v;
   }
+  // the weights were written through the generic proxy, the MMAs read through the async one
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)) : "memory");
+    for (int i = 0; i < 4; i++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(full + i)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
                      saddr(tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -106,6 +179,7 @@ __global__ void __launch_bounds__(128) conv32_tc(int B, int H, const bf16* __res
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = *tmem_slot;
+  const unsigned as0 = saddr(As), ws = saddr(Ws);
 
   float bv[kC];
 #pragma unroll
@@ -113,54 +187,62 @@ __global__ void __launch_bounds__(128) conv32_tc(int B, int H, const bf16* __res
 
   const int tpr = (H + kTcM - 1) / kTcM;
   const long long ntiles = (long long)B * H * tpr;
-  unsigned phase = 0;
+  // this CTA's tiles: blockIdx.x + k * gridDim.x, k < K
+  const long long K = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // (thread 0) per stage / accumulator: the parity of copies or MMAs issued and
+  // not yet waited for, or -1
+  int pending[2] = {-1, -1};
+  int mpend[2] = {-1, -1};
   bool ok = true;
-  for (long long tIdx = blockIdx.x; tIdx < ntiles && ok; tIdx += gridDim.x) {
-    const int tx = (int)(tIdx % tpr);
-    const int y = (int)((tIdx / tpr) % H);
-    const int b = (int)(tIdx / ((long long)tpr * H));
-    const int x0 = tx * kTcM;
-    // input rows y + sign*dil*(ty-1), pixels x0 - dil + r (r < kRows), channels
-    // 8kc..8kc+7 at ty*kRowBytes + kc*kLboA + r*16 (zero outside the grid)
-    for (int idx = threadIdx.x; idx < 3 * kRows * 4; idx += blockDim.x) {
-      const int kc = idx & 3, r = (idx >> 2) % kRows, ty = (idx >> 2) / kRows;
-      const int yy = y + sign * dil * (ty - 1);
-      const int xx = x0 - dil + r;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (yy >= 0 && yy < H && xx >= 0 && xx < H && r < kTcM + 2 * dil)
-        v = *reinterpret_cast<const uint4*>(in + (((long long)b * H + yy) * H + xx) * kC + kc * 8);
-      *reinterpret_cast<uint4*>(As + ty * kRowBytes + kc * kLboA + r * 16) = v;
+  if (threadIdx.x == 0 && K > 0) {
+    // prologue: rows of the first two tiles, MMAs of the first
+    for (long long k = 0; k < 2 && k < K; k++) {
+      int b, y, x0;
+      tile_coords(blockIdx.x + k * gridDim.x, H, tpr, b, y, x0);
+      issue_rows(&tmap, as0 + (unsigned)k * kStageBytes, saddr(full + k), b, y, x0, dil, sign);
+      pending[k] = 0;
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    ok = mbar_wait_tc(saddr(full), 0);
+    if (ok) pending[0] = -1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (threadIdx.x == 0) {
-      for (int t = 0; t < 9; t++) {
-        // tap (ty, tx): pixel p reads staged row ty, pixel p + dil + sign*dil*(tx-1)
-        const int row0 = dil + sign * dil * (t % 3 - 1);
-        for (int h = 0; h < 2; h++)
-          tc_mma(tmem,
-                 mdesc(saddr(As + (t / 3) * kRowBytes + row0 * 16 + h * 2 * kLboA), kLboA, 128),
-                 mdesc(saddr(Ws + t * kWBytes + h * 256), 128, 512), (t | h) ? 1u : 0u);
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              saddr(mbar))
-          : "memory");
+    if (ok) {
+      issue_mmas(tmem, as0, ws, dil, sign, saddr(mmad));
+      mpend[0] = 0;
     }
-    // bounded wait for the MMAs of this tile
-    if (!mbar_test_tc(saddr(mbar), phase)) {
-      const unsigned long long t0 = globaltimer_ns();
-      while (!mbar_test_tc(saddr(mbar), phase)) {
-        if (globaltimer_ns() - t0 > 2000000000ull) {
-          atomicExch(err, 1);
-          ok = false;
-          break;
-        }
+  }
+  for (long long k = 0; k < K; k++) {
+    const int bsel = (int)(k & 1);
+    const unsigned par = (unsigned)((k >> 1) & 1);
+    if (threadIdx.x == 0 && ok && k + 1 < K) {
+      // MMAs of the next tile into the other accumulator (its last reader, the
+      // epilogue of tile k-1, finished before the CTA barrier that ended it)
+      const int nb = bsel ^ 1;
+      ok = mbar_wait_tc(saddr(full + nb), (unsigned)(((k + 1) >> 1) & 1));
+      if (ok) pending[nb] = -1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ok) {
+        issue_mmas(tmem + 32u * nb, as0 + (unsigned)nb * kStageBytes, ws, dil, sign,
+                   saddr(mmad + nb));
+        mpend[nb] = (int)(((k + 1) >> 1) & 1);
       }
     }
-    phase ^= 1u;
+    // every thread: this tile's MMAs are done (its stage and accumulator are ready)
+    if (ok && !mbar_wait_tc(saddr(mmad + bsel), par)) ok = false;
+    if (ok) mpend[bsel] = -1;
+    if (threadIdx.x == 0 && ok && k + 2 < K) {
+      // stage bsel is free again: rows of tile k + 2
+      int b, y, x0;
+      tile_coords(blockIdx.x + (k + 2) * gridDim.x, H, tpr, b, y, x0);
+      issue_rows(&tmap, as0 + (unsigned)bsel * kStageBytes, saddr(full + bsel), b, y, x0, dil,
+                 sign);
+      pending[bsel] = (int)(((k + 2) >> 1) & 1);
+    }
+    if (!ok) atomicExch(err, 1);
+    // the CTA leaves together when a wait ran out
+    if (__syncthreads_or(!ok)) break;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    int b, y, x0;
+    tile_coords(blockIdx.x + k * gridDim.x, H, tpr, b, y, x0);
     if (ok) {
       unsigned r[32];
       asm volatile(
@@ -172,7 +254,7 @@ __global__ void __launch_bounds__(128) conv32_tc(int B, int H, const bf16* __res
             "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
             "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
             "=r"(r[31])
-          : "r"(tmem + ((unsigned)(warp * 32) << 16)));
+          : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(32 * bsel)));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       const int p = warp * 32 + lane;
       const int x = x0 + p;
@@ -223,13 +305,22 @@ __global__ void __launch_bounds__(128) conv32_tc(int B, int H, const bf16* __res
         }
       }
     }
-    // every warp's TMEM reads are done before the next tile's MMAs overwrite it
+    // every warp's TMEM reads are done before a later tile's MMAs overwrite them
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
+  if (threadIdx.x == 0) {
+    // copies and MMAs still in flight (only after a wait ran out) complete
+    // before the CTA frees its tensor memory and leaves (bounded waits)
+    for (int i = 0; i < 2; i++) {
+      if (pending[i] >= 0) mbar_wait_tc(saddr(full + i), (unsigned)pending[i]);
+      if (mpend[i] >= 0) mbar_wait_tc(saddr(mmad + i), (unsigned)mpend[i]);
+    }
+  }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 int* g_tc_err = nullptr;  // set by a tile whose MMAs did not complete in time
@@ -238,6 +329,14 @@ int* g_tc_err = nullptr;  // set by a tile whose MMAs did not complete in time
 
 bool conv32_tc_applies(int dim, int H) { return dim == 2 && H >= kTcM; }
 
+// cuTensorMapEncodeTiled, looked up through the runtime (the library does not
+// link the driver library itself)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+
 cudaError_t conv32_tc_setup() {
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);
@@ -245,8 +344,15 @@ cudaError_t conv32_tc_setup() {
   cudaFuncSetAttribute(conv32_tc<kRelu>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   cudaFuncSetAttribute(conv32_tc<kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   cudaFuncSetAttribute(conv32_tc<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  g_encode = reinterpret_cast<EncodeTiledFn>(fn);
   int* flag = nullptr;
-  cudaError_t e = cudaMalloc(&flag, sizeof(int));
+  e = cudaMalloc(&flag, sizeof(int));
   if (e != cudaSuccess) return e;
   e = cudaMemset(flag, 0, sizeof(int));
   if (e != cudaSuccess) return e;
@@ -262,20 +368,35 @@ cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
     const cudaError_t e = conv32_tc_setup();
     if (e != cudaSuccess) return e;
   }
+  if (dil < 1 || dil > 2 || ((unsigned long long)in & 15ull)) return cudaErrorInvalidValue;
+  // the input activation, channels last: [B][H][H][32] BF16, as a 4D tensor
+  // (channels innermost); a copy box is 8 channels x kRows pixels of one row
+  CUtensorMap tm;
+  const cuuint64_t dims[4] = {(cuuint64_t)kC, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)kC * 2, (cuuint64_t)kC * 2 * H,
+                                 (cuuint64_t)kC * 2 * H * H};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kRows, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (g_encode(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)in, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (long long)B * H * ((H + kTcM - 1) / kTcM);
-  const int grid = (int)(ntiles < 4LL * nsm ? ntiles : 4LL * nsm);
+  // three CTAs fit an SM (shared memory); each runs a stream of tiles
+  const int grid = (int)(ntiles < 3LL * nsm ? ntiles : 3LL * nsm);
   if (mode == kRelu)
-    conv32_tc<kRelu><<<grid, 128, kTcSmem, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
-                                                addend, g_tc_err);
+    conv32_tc<kRelu><<<grid, 128, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
+                                                fo, addend, g_tc_err);
   else if (mode == kResid)
-    conv32_tc<kResid><<<grid, 128, kTcSmem, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid,
+    conv32_tc<kResid><<<grid, 128, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
                                                  fo, addend, g_tc_err);
   else
-    conv32_tc<kF32><<<grid, 128, kTcSmem, s>>>(B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
-                                               addend, g_tc_err);
+    conv32_tc<kF32><<<grid, 128, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
+                                               fo, addend, g_tc_err);
   note_launches(1);
   return cudaGetLastError();
 }
