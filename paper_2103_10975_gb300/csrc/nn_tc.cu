@@ -16,10 +16,11 @@
 // pixel.  The weights use 128 / 512-byte offsets.
 // The rows arrive by TMA: a tensor map over the channels-last activation (4D:
 // channels, x, y, batch) and one box of 8 channels x 132 pixels per column
-// block, zero-filled outside the grid.  Each CTA runs a stream of tiles with two
-// stages of rows and two accumulators in tensor memory: while the epilogue of
-// tile k reads its accumulator, the MMAs of tile k+1 run and the rows of tile
-// k+2 are in flight.
+// block, zero-filled outside the grid.  Each CTA runs a stream of tiles with
+// specialised warps that meet only at mbarriers: a producer warp keeps three
+// stages of rows in flight, an MMA warp turns each stage into one of two
+// accumulators in tensor memory, and four epilogue warps read an accumulator,
+// hand it back and store the tile while the next tiles' copies and MMAs run.
 #include <mutex>
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -42,7 +43,8 @@ constexpr int kRowBytes = 4 * kLboA;         // one staged input row
 constexpr int kStageBytes = 3 * kRowBytes;   // the three input rows of a tile
 constexpr int kStageTx = 12 * kBox;          // bytes the 12 copies of a stage deliver
 constexpr int kWBytes = kC * kC * 2;         // one tap's B operand: 2 KB
-constexpr int kTcSmem = 2 * kStageBytes + 9 * kWBytes + 64;
+constexpr int kStages = 3;                   // stages of input rows in flight per CTA
+constexpr int kTcSmem = kStages * kStageBytes + 9 * kWBytes + 128;
 static_assert(kLboA >= kBox && kLboA % 128 == 0 && kStageBytes % 128 == 0,
               "copy destinations must be 128-byte aligned and hold a box");
 
@@ -138,22 +140,31 @@ __device__ __forceinline__ void issue_mmas(unsigned tmem, unsigned as, unsigned 
       : "memory");
 }
 
+// Warp roles of conv32_tc (192 threads): warp 0 issues the TMA copies of the
+// input rows, warp 1 issues the MMAs, warps 2..5 run the epilogue (warp w reads
+// TMEM lanes 32 (w % 4) .. +31, the pixels of its quarter of the tile).
+constexpr int kTcThreads = 192;
+
 template <int MODE>
-__global__ void __launch_bounds__(128) conv32_tc(const __grid_constant__ CUtensorMap tmap, int B,
-                                                 int H, const bf16* __restrict__ wop,
-                                                 const float* __restrict__ bias, int dil,
-                                                 int sign, bf16* __restrict__ zo,
-                                                 bf16* __restrict__ to,
-                                                 const bf16* __restrict__ resid,
-                                                 float* __restrict__ fo,
-                                                 const float* __restrict__ addend,
-                                                 int* __restrict__ err) {
+__global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ CUtensorMap tmap,
+                                                        int B, int H, const bf16* __restrict__ wop,
+                                                        const float* __restrict__ bias, int dil,
+                                                        int sign, bf16* __restrict__ zo,
+                                                        bf16* __restrict__ to,
+                                                        const bf16* __restrict__ resid,
+                                                        float* __restrict__ fo,
+                                                        const float* __restrict__ addend,
+                                                        int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  unsigned char* As = tc_smem;                              // 2 stages of 3 input rows
-  unsigned char* Ws = tc_smem + 2 * kStageBytes;            // 9 x 2 KB
+  unsigned char* As = tc_smem;                                  // kStages stages of input rows
+  unsigned char* Ws = tc_smem + kStages * kStageBytes;          // 9 x 2 KB
   unsigned long long* full = reinterpret_cast<unsigned long long*>(Ws + 9 * kWBytes);
-  unsigned long long* mmad = full + 2;
-  unsigned* tmem_slot = reinterpret_cast<unsigned*>(mmad + 2);
+  unsigned long long* empty = full + kStages;   // the MMAs of a stage have completed
+  unsigned long long* tfull = empty + kStages;  // an accumulator holds a finished tile
+  unsigned long long* tempty = tfull + 2;       // the epilogue has read an accumulator
+  unsigned long long* drain = tempty + 2;       // the MMA warp's last MMAs (teardown)
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(drain + 1);
+  int* prog = reinterpret_cast<int*>(tmem_slot + 1);  // [0] copies issued, [1] stages consumed
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // B operand (weights) of all 9 taps: (n, k) at (n/8)*512 + (k/8)*128 + (n%8)*16 + (k%8)*2
@@ -165,8 +176,16 @@ __global__ void __launch_bounds__(128) conv32_tc(const __grid_constant__ CUtenso
   // the weights were written through the generic proxy, the MMAs read through the async one
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < kStages; i++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(full + i)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(empty + i)) : "memory");
+    }
+    for (int i = 0; i < 2; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(tfull + i)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(saddr(tempty + i)) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(drain)) : "memory");
+    prog[0] = prog[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -181,69 +200,69 @@ __global__ void __launch_bounds__(128) conv32_tc(const __grid_constant__ CUtenso
   const unsigned tmem = *tmem_slot;
   const unsigned as0 = saddr(As), ws = saddr(Ws);
 
-  float bv[kC];
-#pragma unroll
-  for (int o = 0; o < kC; o++) bv[o] = (MODE != kF32 && bias) ? bias[o] : 0.f;
-
   const int tpr = (H + kTcM - 1) / kTcM;
   const long long ntiles = (long long)B * H * tpr;
   // this CTA's tiles: blockIdx.x + k * gridDim.x, k < K
   const long long K = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  // (thread 0) per stage / accumulator: the parity of copies or MMAs issued and
-  // not yet waited for, or -1
-  int pending[2] = {-1, -1};
-  int mpend[2] = {-1, -1};
-  bool ok = true;
-  if (threadIdx.x == 0 && K > 0) {
-    // prologue: rows of the first two tiles, MMAs of the first
-    for (long long k = 0; k < 2 && k < K; k++) {
-      int b, y, x0;
-      tile_coords(blockIdx.x + k * gridDim.x, H, tpr, b, y, x0);
-      issue_rows(&tmap, as0 + (unsigned)k * kStageBytes, saddr(full + k), b, y, x0, dil, sign);
-      pending[k] = 0;
-    }
-    ok = mbar_wait_tc(saddr(full), 0);
-    if (ok) pending[0] = -1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-      issue_mmas(tmem, as0, ws, dil, sign, saddr(mmad));
-      mpend[0] = 0;
-    }
-  }
-  for (long long k = 0; k < K; k++) {
-    const int bsel = (int)(k & 1);
-    const unsigned par = (unsigned)((k >> 1) & 1);
-    if (threadIdx.x == 0 && ok && k + 1 < K) {
-      // MMAs of the next tile into the other accumulator (its last reader, the
-      // epilogue of tile k-1, finished before the CTA barrier that ended it)
-      const int nb = bsel ^ 1;
-      ok = mbar_wait_tc(saddr(full + nb), (unsigned)(((k + 1) >> 1) & 1));
-      if (ok) pending[nb] = -1;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (ok) {
-        issue_mmas(tmem + 32u * nb, as0 + (unsigned)nb * kStageBytes, ws, dil, sign,
-                   saddr(mmad + nb));
-        mpend[nb] = (int)(((k + 1) >> 1) & 1);
+
+  if (warp == 0) {
+    // ---- producer: rows of tile k into stage k % kStages once its MMAs are done
+    if (lane == 0) {
+      for (long long k = 0; k < K; k++) {
+        const int st = (int)(k % kStages);
+        const long long use = k / kStages;
+        if (use > 0 && !mbar_wait_tc(saddr(empty + st), (unsigned)((use - 1) & 1))) {
+          atomicExch(err, 1);
+          break;
+        }
+        int b, y, x0;
+        tile_coords(blockIdx.x + k * gridDim.x, H, tpr, b, y, x0);
+        issue_rows(&tmap, as0 + (unsigned)st * kStageBytes, saddr(full + st), b, y, x0, dil,
+                   sign);
+        prog[0] = (int)(k + 1);
       }
     }
-    // every thread: this tile's MMAs are done (its stage and accumulator are ready)
-    if (ok && !mbar_wait_tc(saddr(mmad + bsel), par)) ok = false;
-    if (ok) mpend[bsel] = -1;
-    if (threadIdx.x == 0 && ok && k + 2 < K) {
-      // stage bsel is free again: rows of tile k + 2
-      int b, y, x0;
-      tile_coords(blockIdx.x + (k + 2) * gridDim.x, H, tpr, b, y, x0);
-      issue_rows(&tmap, as0 + (unsigned)bsel * kStageBytes, saddr(full + bsel), b, y, x0, dil,
-                 sign);
-      pending[bsel] = (int)(((k + 2) >> 1) & 1);
+  } else if (warp == 1) {
+    // ---- MMA issue: tile k from stage k % kStages into accumulator k % 2
+    if (lane == 0) {
+      long long k = 0;
+      for (; k < K; k++) {
+        const int st = (int)(k % kStages), a = (int)(k & 1);
+        if (!mbar_wait_tc(saddr(full + st), (unsigned)((k / kStages) & 1))) break;
+        prog[1] = (int)(k + 1);
+        if (k >= 2 && !mbar_wait_tc(saddr(tempty + a), (unsigned)(((k >> 1) - 1) & 1))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        issue_mmas(tmem + 32u * a, as0 + (unsigned)st * kStageBytes, ws, dil, sign,
+                   saddr(empty + st));
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                saddr(tfull + a))
+            : "memory");
+      }
+      if (k < K) atomicExch(err, 1);
+      // every MMA issued has completed before the teardown frees tensor memory
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              saddr(drain))
+          : "memory");
+      mbar_wait_tc(saddr(drain), 0u);
     }
-    if (!ok) atomicExch(err, 1);
-    // the CTA leaves together when a wait ran out
-    if (__syncthreads_or(!ok)) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    int b, y, x0;
-    tile_coords(blockIdx.x + k * gridDim.x, H, tpr, b, y, x0);
-    if (ok) {
+  } else {
+    // ---- epilogue: accumulator k % 2 to the outputs of tile k
+    const int lq = warp & 3;  // TMEM lane quarter of this warp
+    float bv[kC];
+#pragma unroll
+    for (int o = 0; o < kC; o++) bv[o] = (MODE != kF32 && bias) ? bias[o] : 0.f;
+    for (long long k = 0; k < K; k++) {
+      const int ab = (int)(k & 1);
+      // a warp-uniform decision: tcgen05.ld below needs the whole warp
+      const bool okw = __all_sync(0xffffffffu, mbar_wait_tc(saddr(tfull + ab),
+                                                             (unsigned)((k >> 1) & 1)));
+      if (!okw) {
+        if (lane == 0) atomicExch(err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       unsigned r[32];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
@@ -254,9 +273,17 @@ __global__ void __launch_bounds__(128) conv32_tc(const __grid_constant__ CUtenso
             "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
             "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
             "=r"(r[31])
-          : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(32 * bsel)));
+          : "r"(tmem + ((unsigned)(lq * 32) << 16) + (unsigned)(32 * ab)));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int p = warp * 32 + lane;
+      // the accumulator may take the next tile's MMAs while this warp stores
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(tempty + ab))
+                     : "memory");
+      int b, y, x0;
+      tile_coords(blockIdx.x + k * gridDim.x, H, tpr, b, y, x0);
+      const int p = lq * 32 + lane;
       const int x = x0 + p;
       if (x < H) {
         const long long pix = ((long long)b * H + y) * H + x;
@@ -305,22 +332,20 @@ __global__ void __launch_bounds__(128) conv32_tc(const __grid_constant__ CUtenso
         }
       }
     }
-    // every warp's TMEM reads are done before a later tile's MMAs overwrite them
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    // copies and MMAs still in flight (only after a wait ran out) complete
-    // before the CTA frees its tensor memory and leaves (bounded waits)
-    for (int i = 0; i < 2; i++) {
-      if (pending[i] >= 0) mbar_wait_tc(saddr(full + i), (unsigned)pending[i]);
-      if (mpend[i] >= 0) mbar_wait_tc(saddr(mmad + i), (unsigned)mpend[i]);
-    }
+    // copies still in flight (only after a wait ran out) land before the CTA
+    // leaves (bounded waits)
+    for (int k = prog[1]; k < prog[0]; k++)
+      mbar_wait_tc(saddr(full + k % kStages), (unsigned)((k / kStages) & 1));
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
+  if (warp == 0) {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+  }
 }
 
 int* g_tc_err = nullptr;  // set by a tile whose MMAs did not complete in time
@@ -386,16 +411,16 @@ cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (long long)B * H * ((H + kTcM - 1) / kTcM);
-  // three CTAs fit an SM (shared memory); each runs a stream of tiles
-  const int grid = (int)(ntiles < 3LL * nsm ? ntiles : 3LL * nsm);
+  // two CTAs fit an SM (shared memory); each runs a stream of tiles
+  const int grid = (int)(ntiles < 2LL * nsm ? ntiles : 2LL * nsm);
   if (mode == kRelu)
-    conv32_tc<kRelu><<<grid, 128, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
+    conv32_tc<kRelu><<<grid, kTcThreads, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
                                                 fo, addend, g_tc_err);
   else if (mode == kResid)
-    conv32_tc<kResid><<<grid, 128, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
+    conv32_tc<kResid><<<grid, kTcThreads, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
                                                  fo, addend, g_tc_err);
   else
-    conv32_tc<kF32><<<grid, 128, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
+    conv32_tc<kF32><<<grid, kTcThreads, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
                                                fo, addend, g_tc_err);
   note_launches(1);
   return cudaGetLastError();
