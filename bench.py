@@ -52,12 +52,12 @@ LEARN = dict(train_iters=64, lr=2e-3, batch=8, guess_smooth=32, overlap_train=1)
 METRIC = "time-to-solution per time step (ms) and GMRES iters, learned vs plain GMRES, rel res 1e-10"
 # DRAM bytes per Arnoldi step of gmres_persistent<float, 2, 64, 256, shared V>
 # on this workload, from one ncu capture of a 300-step solve of the kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum = 1.227 MB + 0.026 MB); scaled
+# (dram__bytes_read.sum + dram__bytes_write.sum = 1.237 MB + 0.026 MB); scaled
 # to a launch by its steps.
-DRAM_BYTES_PER_STEP = 1.253e6 / 300
-# the same for the compact bulk-copy variant at 2048^2, GMRES(40): 61.30 GB over
+DRAM_BYTES_PER_STEP = 1.263e6 / 300
+# the same for the compact bulk-copy variant at 2048^2, GMRES(40): 61.31 GB over
 # an 80-step (two-cycle) capture
-DRAM_BYTES_PER_STEP_2048 = 61.30e9 / 80
+DRAM_BYTES_PER_STEP_2048 = 61.31e9 / 80
 WORKLOAD = ("2D Poisson -Lap u = f, 256x256 interior (N=65,536), zero Dirichlet, 5-point; "
             "3 moving signed Gaussians (sigma 0.1), 500-step series seed 2001; GMRES(30) "
             "rel tol 1e-10 (true FP64 residual)")

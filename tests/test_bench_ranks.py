@@ -57,3 +57,24 @@ def test_single_rank_is_identity():
     import bench
     assert bench.aggregate_ms_per_step(80.0, 4, 1, None) == 20.0
     assert bench.max_over_ranks(2.5, None) == 2.5
+
+
+def test_roofline_bytes_follow_the_accounting():
+    """The bench's byte counts against hand-worked values.  One cycle of k = 2
+    Arnoldi steps on N points, FP32 (s = 4):
+    three-sweep CGS2 (SURVEY-style): steps j = 0, 1 move s N (3(j+1) + 7) = 10 s N
+    and 13 s N; x += V y adds (k s + 16) N = 24 N; the FP64 true residual 32 N.
+    Two-pass: steps move s N (2j + 6) = 6 s N and 8 s N; x += V y s N k + 16 N;
+    the restart 16 N + s N; the final residual check 16 N + s N."""
+    import bench
+    N, s = 1000, 4
+    res = {"iters": 2, "cycles": 1}
+    assert bench.algorithmic_bytes(res, N, 30, s) == (10 + 13) * s * N + 24 * N + 32 * N
+    assert bench.algorithmic_bytes(res, N, 30, s, kappa=True) == \
+        (10 + 13) * s * N + 2 * 4 * N + 24 * N + 32 * N
+    assert bench.two_pass_bytes(res, N, 30, s) == \
+        (6 + 8) * s * N + (2 * s * N + 16 * N) + (16 * N + s * N) + (16 * N + s * N)
+    # two cycles: a full one of m = 3 steps, then 1 step
+    res = {"iters": 4, "cycles": 2}
+    per = lambda k: sum(s * N * (3 * (j + 1) + 7) for j in range(k)) + (k * s + 16) * N + 32 * N  # noqa: E731
+    assert bench.algorithmic_bytes(res, N, 3, s) == per(3) + per(1)

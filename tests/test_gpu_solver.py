@@ -373,3 +373,25 @@ def test_batch_rejects_bad_arguments():
     s0 = Solver(16, m=10)
     with pytest.raises(MLGMRESError):
         s0.solve_batch([16], [dev(np.ones(256))])
+
+
+def test_exchange_floor_probe():
+    """mlgmres_exchange_floor runs the solver's two group exchanges per step
+    alone: a positive time per step, below the full Arnoldi step at the same
+    CTA count (which adds the passes and the scalar work), and argument errors
+    rejected before any launch."""
+    import ctypes
+    from paper_2103_10975_gb300 import binding, exchange_floor
+    fl = exchange_floor(64, 30, 500)
+    assert fl > 0.0
+    b = torch.as_tensor(MovingGaussians2D(128, 2001, 500).rhs(0)).cuda()
+    s = Solver(128, m=30, rtol=1e-10, precision="fp32_refine", grid_blocks=64, max_iters=300)
+    s.solve(b)
+    _, r = s.solve(b)
+    full = 1e3 * r["tos_ms"] / r["iters"]
+    assert fl < full, (fl, full)
+    lib = binding.load_library()
+    us = ctypes.c_float(0)
+    for args in ((0, 30, 10), (64, 0, 10), (64, 65, 10), (64, 30, 0), (2000, 30, 10)):
+        assert lib.mlgmres_exchange_floor(*args, ctypes.byref(us)) == binding.MLGMRES_ERR_ARG, args
+    assert lib.mlgmres_exchange_floor(64, 30, 10, None) == binding.MLGMRES_ERR_ARG
