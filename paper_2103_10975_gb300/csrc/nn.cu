@@ -710,7 +710,7 @@ cudaError_t net_create(Net& net, int n, int bmax, unsigned long long seed, int d
   if (n < 1 || bmax < 1 ||
       (long long)bmax * (dim == 3 ? (long long)n * n * n : (long long)n * n) * kC >= (1LL << 31))
     return cudaErrorInvalidValue;
-  if (dim == 2) NN_CK(conv32_tc_setup());
+  NN_CK(conv32_tc_setup());
   NN_CK(conv32_mma_setup());
   net.extra_max = extra_max;
   net.extra_active = 0;

@@ -104,9 +104,10 @@ cudaError_t launch_conv32_mma(int dim, int mode, int B, int H, const __nv_bfloat
                               __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                               float* fo, const float* addend, cudaStream_t s);
 // The same convolution on the fifth-generation tensor cores (tcgen05.mma into
-// tensor memory), for 2D grids with at least 128 points per row.
+// tensor memory, operands by TMA), for 2D and 3D grids with at least 128 points
+// per row (the environment variable MLGMRES_TC_MIN_ROW lowers the threshold).
 bool conv32_tc_applies(int dim, int H);
-cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
+cudaError_t launch_conv32_tc(int dim, int mode, int B, int H, const __nv_bfloat16* in,
                              const __nv_bfloat16* wop, const float* bias, int dil, int sign,
                              __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                              float* fo, const float* addend, cudaStream_t s);

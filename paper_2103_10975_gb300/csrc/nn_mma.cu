@@ -351,9 +351,10 @@ cudaError_t launch_conv32_mma(int dim, int mode, int B, int H, const __nv_bfloat
                               __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                               float* fo, const float* addend, cudaStream_t s) {
   if (dil < 1 || dil > kMaxDil || (dim != 2 && dim != 3)) return cudaErrorInvalidValue;
-  // full-resolution 2D levels go to the tcgen05 kernel (tensor memory accumulators)
+  // full-resolution levels go to the tcgen05 kernel (tensor memory accumulators)
   if (conv32_tc_applies(dim, H))
-    return launch_conv32_tc(mode, B, H, in, wop, bias, dil, sign, zo, to, resid, fo, addend, s);
+    return launch_conv32_tc(dim, mode, B, H, in, wop, bias, dil, sign, zo, to, resid, fo, addend,
+                            s);
   return dim == 3 ? conv_launch<3>(mode, B, H, in, wop, bias, dil, sign, zo, to, resid, fo,
                                    addend, s)
                   : conv_launch<2>(mode, B, H, in, wop, bias, dil, sign, zo, to, resid, fo,

@@ -21,6 +21,7 @@
 // stages of rows in flight, an MMA warp turns each stage into one of two
 // accumulators in tensor memory, and four epilogue warps read an accumulator,
 // hand it back and store the tile while the next tiles' copies and MMAs run.
+#include <cstdlib>
 #include <mutex>
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -40,12 +41,21 @@ constexpr int kBox = kRows * 16;             // one tensor copy: 8 channels x kR
 constexpr int kLboA = 17 * 128;              // bytes between 8-channel column blocks (a copy
                                              // destination, 128-byte aligned, >= kBox)
 constexpr int kRowBytes = 4 * kLboA;         // one staged input row
-constexpr int kStageBytes = 3 * kRowBytes;   // the three input rows of a tile
-constexpr int kStageTx = 12 * kBox;          // bytes the 12 copies of a stage deliver
 constexpr int kWBytes = kC * kC * 2;         // one tap's B operand: 2 KB
-constexpr int kStages = 3;                   // stages of input rows in flight per CTA
-constexpr int kTcSmem = kStages * kStageBytes + 9 * kWBytes + 128;
-static_assert(kLboA >= kBox && kLboA % 128 == 0 && kStageBytes % 128 == 0,
+// per dimension: input rows per tile (3 in 2D; 3 x 3 in 3D), taps, stages in
+// flight, bytes of a stage, bytes a stage's copies deliver, shared memory
+template <int D>
+struct TcGeo {
+  static constexpr int kRowsPerTile = D == 3 ? 9 : 3;
+  static constexpr int kTaps = D == 3 ? 27 : 9;
+  static constexpr int kStages = D == 3 ? 2 : 3;
+  static constexpr int kStageBytes = kRowsPerTile * kRowBytes;
+  static constexpr int kStageTx = kRowsPerTile * 4 * kBox;
+  static constexpr int kSmem = kStages * kStageBytes + kTaps * kWBytes + 128;
+  static_assert(kStageBytes % 128 == 0, "stages must keep 128-byte alignment");
+  static_assert(kSmem <= 227 * 1024, "shared memory of one CTA");
+};
+static_assert(kLboA >= kBox && kLboA % 128 == 0,
               "copy destinations must be 128-byte aligned and hold a box");
 
 __device__ __forceinline__ unsigned saddr(const void* p) {
@@ -84,12 +94,20 @@ __device__ __forceinline__ bool mbar_test_tc(unsigned bar, unsigned phase) {
 
 enum { kRelu = 0, kResid = 1, kF32 = 2 };
 
-// A tile's coordinates: batch b, grid row y, first pixel x0 of its 128.
-__device__ __forceinline__ void tile_coords(long long tIdx, int H, int tpr, int& b, int& y,
-                                            int& x0) {
+// A tile's coordinates: batch b, plane z (3D), grid row y, first pixel x0 of its 128.
+template <int D>
+__device__ __forceinline__ void tile_coords(long long tIdx, int H, int tpr, int& b, int& z,
+                                            int& y, int& x0) {
   const int tx = (int)(tIdx % tpr);
-  y = (int)((tIdx / tpr) % H);
-  b = (int)(tIdx / ((long long)tpr * H));
+  const long long r = tIdx / tpr;
+  y = (int)(r % H);
+  if (D == 3) {
+    z = (int)((r / H) % H);
+    b = (int)(r / ((long long)H * H));
+  } else {
+    z = 0;
+    b = (int)(r / H);
+  }
   x0 = tx * kTcM;
 }
 
@@ -102,34 +120,52 @@ __device__ __forceinline__ bool mbar_wait_tc(unsigned bar, unsigned phase) {
   return true;
 }
 
-// The three input rows of tile (b, y, x0) into stage buffer `as`: 12 tensor
-// copies (3 rows x 4 blocks of 8 channels), each a box of 8 channels x kRows
-// pixels starting at pixel x0 - dil; pixels and rows outside the grid arrive as
-// zeros.  The stage's mbarrier expects all their bytes.
+// The input rows of tile (b, z, y, x0) into stage buffer `as`: per row (3 in
+// 2D: y - sd, y, y + sd; 9 in 3D: those of planes z - sd, z, z + sd, where sd
+// = sign * dil) 4 tensor copies, each a box of 8 channels x kRows pixels
+// starting at pixel x0 - dil; pixels, rows and planes outside the grid arrive
+// as zeros.  The stage's mbarrier expects all their bytes.
+template <int D>
 __device__ __forceinline__ void issue_rows(const CUtensorMap* tmap, unsigned as, unsigned bar,
-                                           int b, int y, int x0, int dil, int sign) {
+                                           int b, int z, int y, int x0, int dil, int sign) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-               "r"(kStageTx)
+               "r"(TcGeo<D>::kStageTx)
                : "memory");
-  for (int ty = 0; ty < 3; ty++) {
+  for (int r = 0; r < TcGeo<D>::kRowsPerTile; r++) {
+    const int ty = r % 3, tz = r / 3;
     const int yy = y + sign * dil * (ty - 1);
-    for (int kc = 0; kc < 4; kc++)
-      asm volatile(
-          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-          " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(as + ty * kRowBytes + kc * kLboA),
-          "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(8 * kc), "r"(x0 - dil), "r"(yy),
-          "r"(b), "r"(bar)
-          : "memory");
+    for (int kc = 0; kc < 4; kc++) {
+      const unsigned dst = as + r * kRowBytes + kc * kLboA;
+      if (D == 3) {
+        const int zz = z + sign * dil * (tz - 1);
+        asm volatile(
+            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+            "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(8 * kc), "r"(x0 - dil), "r"(yy),
+            "r"(zz), "r"(b), "r"(bar)
+            : "memory");
+      } else {
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+            "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(8 * kc), "r"(x0 - dil), "r"(yy),
+            "r"(b), "r"(bar)
+            : "memory");
+      }
+    }
   }
 }
 
-// The 18 MMAs of one tile: A from stage buffer `as`, B the staged weights,
-// D the accumulator at TMEM column offset `col`; tcgen05.commit then arrives
-// on `bar` when they (and every earlier MMA of this thread) have completed.
+// The 2 x taps MMAs of one tile (18 in 2D, 54 in 3D): A from stage buffer
+// `as`, B the staged weights, D the accumulator at TMEM column offset `col`;
+// tcgen05.commit then arrives on `bar` when they (and every earlier MMA of this
+// thread) have completed.
+template <int D>
 __device__ __forceinline__ void issue_mmas(unsigned tmem, unsigned as, unsigned ws, int dil,
                                            int sign, unsigned bar) {
-  for (int t = 0; t < 9; t++) {
-    // tap (ty, tx): pixel p reads staged row ty, pixel p + dil + sign*dil*(tx-1)
+  for (int t = 0; t < TcGeo<D>::kTaps; t++) {
+    // tap ((tz,) ty, tx): pixel p reads staged row t / 3 = (tz * 3 +) ty, pixel
+    // p + dil + sign*dil*(tx-1)
     const int row0 = dil + sign * dil * (t % 3 - 1);
     for (int h = 0; h < 2; h++)
       tc_mma(tmem, mdesc(as + (t / 3) * kRowBytes + row0 * 16 + h * 2 * kLboA, kLboA, 128),
@@ -145,7 +181,7 @@ __device__ __forceinline__ void issue_mmas(unsigned tmem, unsigned as, unsigned 
 // TMEM lanes 32 (w % 4) .. +31, the pixels of its quarter of the tile).
 constexpr int kTcThreads = 192;
 
-template <int MODE>
+template <int D, int MODE>
 __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ CUtensorMap tmap,
                                                         int B, int H, const bf16* __restrict__ wop,
                                                         const float* __restrict__ bias, int dil,
@@ -156,9 +192,12 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ 
                                                         const float* __restrict__ addend,
                                                         int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
+  using G = TcGeo<D>;
+  constexpr int kStages = G::kStages;
+  constexpr int kStageBytes = G::kStageBytes;
   unsigned char* As = tc_smem;                                  // kStages stages of input rows
-  unsigned char* Ws = tc_smem + kStages * kStageBytes;          // 9 x 2 KB
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(Ws + 9 * kWBytes);
+  unsigned char* Ws = tc_smem + kStages * kStageBytes;          // taps x 2 KB
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(Ws + G::kTaps * kWBytes);
   unsigned long long* empty = full + kStages;   // the MMAs of a stage have completed
   unsigned long long* tfull = empty + kStages;  // an accumulator holds a finished tile
   unsigned long long* tempty = tfull + 2;       // the epilogue has read an accumulator
@@ -167,8 +206,8 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ 
   int* prog = reinterpret_cast<int*>(tmem_slot + 1);  // [0] copies issued, [1] stages consumed
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // B operand (weights) of all 9 taps: (n, k) at (n/8)*512 + (k/8)*128 + (n%8)*16 + (k%8)*2
-  for (int idx = threadIdx.x; idx < 9 * kC * 4; idx += blockDim.x) {
+  // B operand (weights) of all taps: (n, k) at (n/8)*512 + (k/8)*128 + (n%8)*16 + (k%8)*2
+  for (int idx = threadIdx.x; idx < G::kTaps * kC * 4; idx += blockDim.x) {
     const int kc = idx & 3, n = (idx >> 2) & 31, t = idx >> 7;
     const uint4 v = *reinterpret_cast<const uint4*>(wop + (t * kC + n) * kC + kc * 8);
     *reinterpret_cast<uint4*>(Ws + t * kWBytes + (n >> 3) * 512 + kc * 128 + (n & 7) * 16) = v;
@@ -201,7 +240,7 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ 
   const unsigned as0 = saddr(As), ws = saddr(Ws);
 
   const int tpr = (H + kTcM - 1) / kTcM;
-  const long long ntiles = (long long)B * H * tpr;
+  const long long ntiles = (long long)B * H * tpr * (D == 3 ? H : 1);
   // this CTA's tiles: blockIdx.x + k * gridDim.x, k < K
   const long long K = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
@@ -215,10 +254,10 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ 
           atomicExch(err, 1);
           break;
         }
-        int b, y, x0;
-        tile_coords(blockIdx.x + k * gridDim.x, H, tpr, b, y, x0);
-        issue_rows(&tmap, as0 + (unsigned)st * kStageBytes, saddr(full + st), b, y, x0, dil,
-                   sign);
+        int b, z, y, x0;
+        tile_coords<D>(blockIdx.x + k * gridDim.x, H, tpr, b, z, y, x0);
+        issue_rows<D>(&tmap, as0 + (unsigned)st * kStageBytes, saddr(full + st), b, z, y, x0,
+                      dil, sign);
         prog[0] = (int)(k + 1);
       }
     }
@@ -232,8 +271,8 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ 
         prog[1] = (int)(k + 1);
         if (k >= 2 && !mbar_wait_tc(saddr(tempty + a), (unsigned)(((k >> 1) - 1) & 1))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        issue_mmas(tmem + 32u * a, as0 + (unsigned)st * kStageBytes, ws, dil, sign,
-                   saddr(empty + st));
+        issue_mmas<D>(tmem + 32u * a, as0 + (unsigned)st * kStageBytes, ws, dil, sign,
+                      saddr(empty + st));
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 saddr(tfull + a))
@@ -281,12 +320,13 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ 
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(tempty + ab))
                      : "memory");
-      int b, y, x0;
-      tile_coords(blockIdx.x + k * gridDim.x, H, tpr, b, y, x0);
+      int b, z, y, x0;
+      tile_coords<D>(blockIdx.x + k * gridDim.x, H, tpr, b, z, y, x0);
       const int p = lq * 32 + lane;
       const int x = x0 + p;
       if (x < H) {
-        const long long pix = ((long long)b * H + y) * H + x;
+        const long long pix = D == 3 ? (((long long)b * H + z) * H + y) * H + x
+                                     : ((long long)b * H + y) * H + x;
         float v[kC];
 #pragma unroll
         for (int o = 0; o < kC; o++) v[o] = __uint_as_float(r[o]) + bv[o];
@@ -350,9 +390,23 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ 
 
 int* g_tc_err = nullptr;  // set by a tile whose MMAs did not complete in time
 
+// Rows of at least this many points go to the tcgen05 kernel (128, a full
+// tile; the environment variable MLGMRES_TC_MIN_ROW lowers it, so that tests
+// run the kernel on small grids, whose rows fill part of a tile).
+int tc_min_row() {
+  const char* e = getenv("MLGMRES_TC_MIN_ROW");
+  if (e && *e) {
+    const int v = atoi(e);
+    if (v >= 1) return v;
+  }
+  return kTcM;
+}
+
 }  // namespace
 
-bool conv32_tc_applies(int dim, int H) { return dim == 2 && H >= kTcM; }
+bool conv32_tc_applies(int dim, int H) { return (dim == 2 || dim == 3) && H >= tc_min_row(); }
+
+namespace {
 
 // cuTensorMapEncodeTiled, looked up through the runtime (the library does not
 // link the driver library itself)
@@ -362,13 +416,40 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn g_encode = nullptr;
 
+template <int D>
+void set_tc_smem() {
+  cudaFuncSetAttribute(conv32_tc<D, kRelu>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       TcGeo<D>::kSmem);
+  cudaFuncSetAttribute(conv32_tc<D, kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       TcGeo<D>::kSmem);
+  cudaFuncSetAttribute(conv32_tc<D, kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       TcGeo<D>::kSmem);
+}
+
+template <int D>
+void launch_tc(int mode, int grid, cudaStream_t s, const CUtensorMap& tm, int B, int H,
+               const bf16* wop, const float* bias, int dil, int sign, bf16* zo, bf16* to,
+               const bf16* resid, float* fo, const float* addend) {
+  constexpr int sm = TcGeo<D>::kSmem;
+  if (mode == kRelu)
+    conv32_tc<D, kRelu><<<grid, kTcThreads, sm, s>>>(tm, B, H, wop, bias, dil, sign, zo, to,
+                                                     resid, fo, addend, g_tc_err);
+  else if (mode == kResid)
+    conv32_tc<D, kResid><<<grid, kTcThreads, sm, s>>>(tm, B, H, wop, bias, dil, sign, zo, to,
+                                                      resid, fo, addend, g_tc_err);
+  else
+    conv32_tc<D, kF32><<<grid, kTcThreads, sm, s>>>(tm, B, H, wop, bias, dil, sign, zo, to,
+                                                    resid, fo, addend, g_tc_err);
+}
+
+}  // namespace
+
 cudaError_t conv32_tc_setup() {
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);
   if (g_tc_err) return cudaSuccess;
-  cudaFuncSetAttribute(conv32_tc<kRelu>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  cudaFuncSetAttribute(conv32_tc<kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  cudaFuncSetAttribute(conv32_tc<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  set_tc_smem<2>();
+  set_tc_smem<3>();
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
@@ -385,7 +466,7 @@ cudaError_t conv32_tc_setup() {
   return cudaSuccess;
 }
 
-cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
+cudaError_t launch_conv32_tc(int dim, int mode, int B, int H, const __nv_bfloat16* in,
                              const __nv_bfloat16* wop, const float* bias, int dil, int sign,
                              __nv_bfloat16* zo, __nv_bfloat16* to, const __nv_bfloat16* resid,
                              float* fo, const float* addend, cudaStream_t s) {
@@ -393,35 +474,36 @@ cudaError_t launch_conv32_tc(int mode, int B, int H, const __nv_bfloat16* in,
     const cudaError_t e = conv32_tc_setup();
     if (e != cudaSuccess) return e;
   }
-  if (dil < 1 || dil > 2 || ((unsigned long long)in & 15ull)) return cudaErrorInvalidValue;
-  // the input activation, channels last: [B][H][H][32] BF16, as a 4D tensor
-  // (channels innermost); a copy box is 8 channels x kRows pixels of one row
+  if ((dim != 2 && dim != 3) || dil < 1 || dil > 2 || ((unsigned long long)in & 15ull))
+    return cudaErrorInvalidValue;
+  // the input activation, channels last: [B]([H])[H][H][32] BF16, as a tensor of
+  // rank dim + 2 (channels innermost); a copy box is 8 channels x kRows pixels of
+  // one row
   CUtensorMap tm;
-  const cuuint64_t dims[4] = {(cuuint64_t)kC, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)B};
-  const cuuint64_t strides[3] = {(cuuint64_t)kC * 2, (cuuint64_t)kC * 2 * H,
-                                 (cuuint64_t)kC * 2 * H * H};
-  const cuuint32_t box[4] = {8, (cuuint32_t)kRows, 1, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  if (g_encode(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)in, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  const cuuint64_t row = (cuuint64_t)kC * 2;  // bytes per pixel
+  const cuuint64_t h = (cuuint64_t)H;
+  const cuuint64_t dims[5] = {(cuuint64_t)kC, h, h, dim == 3 ? h : (cuuint64_t)B, (cuuint64_t)B};
+  const cuuint64_t strides[4] = {row, row * h, row * h * h, row * h * h * h};
+  const cuuint32_t box[5] = {8, (cuuint32_t)kRows, 1, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  if (g_encode(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)(dim + 2), (void*)in, dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
       CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const long long ntiles = (long long)B * H * ((H + kTcM - 1) / kTcM);
-  // two CTAs fit an SM (shared memory); each runs a stream of tiles
-  const int grid = (int)(ntiles < 2LL * nsm ? ntiles : 2LL * nsm);
-  if (mode == kRelu)
-    conv32_tc<kRelu><<<grid, kTcThreads, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
-                                                fo, addend, g_tc_err);
-  else if (mode == kResid)
-    conv32_tc<kResid><<<grid, kTcThreads, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
-                                                 fo, addend, g_tc_err);
+  long long ntiles = (long long)B * H * ((H + kTcM - 1) / kTcM);
+  if (dim == 3) ntiles *= H;
+  // CTAs that fit an SM (shared memory: two in 2D, one in 3D); each runs a
+  // stream of tiles
+  const long long per_sm = dim == 3 ? 1 : 2;
+  const int grid = (int)(ntiles < per_sm * nsm ? ntiles : per_sm * nsm);
+  if (dim == 3)
+    launch_tc<3>(mode, grid, s, tm, B, H, wop, bias, dil, sign, zo, to, resid, fo, addend);
   else
-    conv32_tc<kF32><<<grid, kTcThreads, kTcSmem, s>>>(tm, B, H, wop, bias, dil, sign, zo, to, resid,
-                                               fo, addend, g_tc_err);
+    launch_tc<2>(mode, grid, s, tm, B, H, wop, bias, dil, sign, zo, to, resid, fo, addend);
   note_launches(1);
   return cudaGetLastError();
 }

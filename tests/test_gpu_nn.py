@@ -304,3 +304,35 @@ def test_linear_model_parity():
     assert abs(loss - (d * d).mean()) <= 1e-4 * (d * d).mean()
     gr = 2.0 / (3 * N) * d.T @ u.astype(np.float64)
     assert np.abs(g.reshape(N, N) - gr).max() <= 1e-4 * np.abs(gr).max()
+
+
+# ------------------------------- tcgen05 convolution on small and ragged grids
+
+@pytest.mark.parametrize("dim,n", [(2, 16), (2, 40), (3, 8), (3, 12)])
+def test_tcgen05_convolution_on_small_grids(dim, n, monkeypatch):
+    """With MLGMRES_TC_MIN_ROW = 1 every 32 -> 32 convolution runs on the
+    TMA-fed tcgen05 kernel (rows shorter than a 128-pixel tile, ragged tiles,
+    zero-filled borders in x, y and, in 3D, z; dilation 1 and 2; the forward and
+    the data-gradient modes): forward and per-tensor gradients against the
+    oracle, as for the default kernels."""
+    monkeypatch.setenv("MLGMRES_TC_MIN_ROW", "1")
+    if dim == 2:
+        s = Solver(n, m=10, batch=2)
+        P = unpack(s.get_params(), n)
+        for k in P:
+            if k.startswith("level") and k.endswith(".w") or k == "dil.w":
+                P[k] = bf16_round(P[k])
+        u, t = sample_batch(n, 2, 11)
+    else:
+        s = Solver(n, dim=3, m=10, batch=2)
+        P = bf16_params_3d(s, n)
+        u, t = sample_batch_3d(n, 2, 11)
+    ud = torch.as_tensor(u, dtype=torch.float32).cuda()
+    y = s.nn_forward(ud).cpu().numpy()
+    for b in range(2):
+        yr = onn.forward(P, u[b], n, dim=dim)
+        assert np.linalg.norm(y[b] - yr) <= 3e-2 * np.linalg.norm(yr), b
+    loss, g = s.nn_loss_grad(ud, torch.as_tensor(t, dtype=torch.float32).cuda())
+    lr, gr = onn.loss_and_grads(P, u, t, n, dim=dim)
+    assert abs(loss - lr) <= 2e-2 * lr
+    check_grads(unpack(g, n, dim=dim), gr, "tcgen05 %dD n=%d" % (dim, n))
