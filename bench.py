@@ -81,6 +81,9 @@ def parse():
                     help="full time steps of the 2048^2 workload to time (0 = none; single GPU)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 512-instance batched workload (single GPU)")
+    ap.add_argument("--c5-steps", type=int, default=0,
+                    help="full time steps of the 192^3 variable-kappa workload to time "
+                         "(0 = none; about a minute each)")
     return ap.parse_args()
 
 
@@ -539,6 +542,7 @@ def run_ours(args):
     # and the 512-instance batched workload
     c3 = run_c3(pkg, torch, dev, args.c3_steps) if world == 1 and args.c3_steps > 0 else None
     c4 = run_c4(pkg, torch, dev) if world == 1 and not args.no_batch else None
+    c5 = run_c5(pkg, torch, dev, args.c5_steps) if world == 1 and args.c5_steps > 0 else None
 
     line = None
     if rank == 0:
@@ -595,6 +599,8 @@ def run_ours(args):
             line["c3_full_steps"] = c3
         if c4 is not None:
             line["c4_batch"] = c4
+        if c5 is not None:
+            line["c5_full_steps"] = c5
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(gen.rhs(TAU0 + W), n, TAU0 + W)
         else:
@@ -663,6 +669,29 @@ def run_c3(pkg, torch, dev, steps):
             "ms_per_step_mean": mean,
             "T12_ms": {"value": 12 * mean, "extrapolated": len(out) < 12,
                        "how": "12 x the mean of the timed steps" if len(out) < 12 else "timed"}}
+
+
+def run_c5(pkg, torch, dev, steps, n=192, m=50):
+    """Full time steps of the 192^3 variable-coefficient workload (log-normal
+    kappa, seed 5001; moving 3D Gaussians), GMRES(50) FP32 cycles + FP64
+    refinement to 1e-10: the first from x0 = 0, later ones from x_{t-1}; per
+    step the device time, iterations and the true FP64 residual (the
+    certificate: no direct solver covers variable kappa at this size)."""
+    from synthetic import MovingGaussians3D, lognormal_kappa
+    kap = lognormal_kappa(n, 5001).astype("float32")
+    gen = MovingGaussians3D(n, 5001, 200)
+    s = pkg.Solver(n, dim=3, kappa=kap, m=m, rtol=RTOL, precision="fp32_refine", guess="prev",
+                   max_iters=3 * 10 ** 6)
+    s.autotune(torch.as_tensor(gen.rhs(0)).to(dev))
+    out = []
+    for t in range(steps):
+        _, r = s.solve(torch.as_tensor(gen.rhs(t)).to(dev))
+        out.append({"t": t, "ms": r["tos_ms"], "iters": r["iters"], "relres_true": r["relres_true"],
+                    "us_per_arnoldi_step": 1e3 * r["tos_ms"] / max(1, r["iters"]),
+                    "guess": "zero" if t == 0 else "x_{t-1}"})
+    s.close()
+    return {"workload": "192^3 variable kappa (log-normal, seed 5001), 7-point, GMRES(50) FP32 "
+                        "cycles + FP64 refinement, rtol 1e-10", "steps": out}
 
 
 def run_c4(pkg, torch, dev):
