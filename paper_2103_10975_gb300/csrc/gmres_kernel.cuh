@@ -1399,12 +1399,14 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         sm.hcc[tid].x = h2;
         sm.h2h[tid] = h2;
       }
-      // hn_{j+1} from hn2T: 1/hn for the next X pass and the subdiagonal of Hu
+      // hn_{j+1} from hn2T: 1/hn for the next X pass and the subdiagonal of Hu;
+      // c_{j+1} = Hu(j+1,j) h2_j, the new vector's own coefficient
       auto set_norm = [&]() {
         const T h2v = sm.hn2T > T(0) ? sm.hn2T : T(0);
         const T hnT = sqrt(h2v);
         sm.invT = T(1) / hnT;
         sm.HuT[j + 1 + j * LD] = hnT;  // (the Givens warp reads it in FP64)
+        sm.hcc[j + 1].y = hnT * sm.coef[j];
       };
       if (tid < 32) {
         T q = T(0);
@@ -1418,6 +1420,31 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
           sm.hn2T = hn2;
           if (!fb) set_norm();
         }
+      }
+      // c_i = sum_{k >= i-1} Hu(i,k) h2_k (i <= j) for the next X pass, in the same
+      // phase as the norm: columns k < j of Hu are unchanged since the last step,
+      // column j is h1 + h2 and h2 is the gather's output (no read of what this
+      // phase writes); eight lanes per row, each a strided part of the sum,
+      // added in a fixed order
+      for (int i0 = 0; i0 <= j; i0 += BS / 8) {
+        const int i = i0 + (tid >> 3);
+        const int sub = tid & 7;
+        const int ir = min(i, j);
+        const int k0 = (ir > 0 ? ir - 1 : 0) + sub;
+        T c = T(0);
+        // all loads of a lane issued together (indices clamped into the column range)
+#pragma unroll
+        for (int t = 0; t < (MAXM + 7) / 8; t++) {
+          const int k = k0 + 8 * t;
+          const int kk = min(k, j);
+          const T hik = kk == j ? sm.h1c[ir] + sm.coef[ir] : sm.HuT[ir + kk * LD];
+          const T prod = hik * sm.coef[kk];
+          if (i <= j && k <= j) c += prod;
+        }
+        c += __shfl_xor_sync(0xffffffffu, c, 4);
+        c += __shfl_xor_sync(0xffffffffu, c, 2);
+        c += __shfl_xor_sync(0xffffffffu, c, 1);
+        if (sub == 0 && i <= j) sm.hcc[i].y = c;
       }
       __syncthreads();
       if (sm.fallback) {
@@ -1439,9 +1466,17 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         red++;
         if (tid == 0) {
           sm.hn2T = sm.coef[0];
-          set_norm();
+          const T h2v = sm.hn2T > T(0) ? sm.hn2T : T(0);
+          const T hnT = sqrt(h2v);
+          sm.invT = T(1) / hnT;
+          sm.HuT[j + 1 + j * LD] = hnT;
         }
-        if (tid <= j) sm.hcc[tid].x = T(0);
+        // w' now carries the second projection: no pending coefficients, and
+        // A w' is the next X pass's stencil itself
+        if (tid <= j + 1) {
+          sm.hcc[tid].x = T(0);
+          sm.hcc[tid].y = T(0);
+        }
         cy.pre = false;  // w' changed at this CTA's points
         __syncthreads();
       }
@@ -1453,29 +1488,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
             hist[(long long)j * (jmax + 1) + k] =
                 k <= j ? (double)sm.h1c[k] + (double)sm.h2h[k] : hnext;
         sm.stop = !(hnext * hnext > 1e-28 * (double)sm.anorm2T) ? 1 : 0;
+        // read by every thread after the next X pass's group exchange
       }
-      // c_i = sum_{k >= i-1} Hu(i,k) h2_k for the next X pass: eight lanes per
-      // row, each a strided part of the sum, added in a fixed order
-      for (int i0 = 0; i0 <= j + 1; i0 += BS / 8) {
-        const int i = i0 + (tid >> 3);
-        const int sub = tid & 7;
-        const int ir = min(i, j + 1);
-        const int k0 = (ir > 0 ? ir - 1 : 0) + sub;
-        T c = T(0);
-        // all loads of a lane issued together (indices clamped into the column range)
-#pragma unroll
-        for (int t = 0; t < (MAXM + 7) / 8; t++) {
-          const int k = k0 + 8 * t;
-          const int kk = min(k, j);
-          const T prod = sm.HuT[ir + kk * LD] * sm.hcc[kk].x;
-          if (i <= j + 1 && k <= j) c += prod;
-        }
-        c += __shfl_xor_sync(0xffffffffu, c, 4);
-        c += __shfl_xor_sync(0xffffffffu, c, 2);
-        c += __shfl_xor_sync(0xffffffffu, c, 1);
-        if (sub == 0 && i <= j + 1) sm.hcc[i].y = c;
-      }
-      __syncthreads();
       if (!arnoldi && j + 1 >= m) {
         // last column of the cycle: rotate it now (no further X pass)
         if (tid < 32)
