@@ -123,8 +123,10 @@ struct Smem {
   double redd[BS / 32][4];       // per-warp partials of the FP64 residual norms
   double tot[MAXM + 2];
   double hcol[MAXM + 2];         // the column being rotated, in FP64 (Givens warp)
-  double R[(MAXM + 1) * MAXM];   // the same columns after the Givens rotations
+  double R[(MAXM + 1) * MAXM];   // the same columns after the Givens rotations, each
+                                 // above the diagonal divided by its diagonal entry
   double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
+  float2 yf[MAXM];               // y_k as hi + lo floats (FP32 variants' V y)
   double rinv[MAXM];             // 1 / R(c,c), formed with rotation c (the back-
                                  // substitution then multiplies: no FP64 division)
   T HuT[(MAXM + 1) * MAXM];      // Hessenberg as built (Arnoldi relation), ld MAXM+1
@@ -333,6 +335,29 @@ __device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot
   __syncthreads();
 }
 
+// Double-float accumulation (error-free transformations, Dekker 1971 and
+// Knuth's TwoSum): (s, c) += (y.x + y.y) v with the head s and tail c floats.
+// The _rn intrinsics keep the compiler from contracting the steps into FMAs.
+__device__ __forceinline__ void df_fma(float& s, float& c, float2 y, float v) {
+  const float p = __fmul_rn(y.x, v);
+  float e = __fmaf_rn(y.x, v, -p);  // y.x v - p, exactly
+  e = __fmaf_rn(y.y, v, e);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));  // s + p - t
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+// The value of two (head, tail) pairs in FP64: the heads joined by TwoSum in
+// FP32, so that only two conversions and one FP64 addition remain.
+__device__ __forceinline__ double df_value(float s0, float c0, float s1, float c1) {
+  const float t = __fadd_rn(s0, s1);
+  const float z = __fsub_rn(t, s0);
+  const float err = __fadd_rn(__fsub_rn(s0, __fsub_rn(t, z)), __fsub_rn(s1, z));
+  const float c = __fadd_rn(__fadd_rn(c0, c1), err);
+  return (double)t + (double)c;
+}
+
 // Givens update of Hessenberg column c (Hu -> R): apply rotations 0..c-1, form
 // rotation c, update g, and return the stop code (0 go on, 1 end the cycle,
 // 2 non-finite).  One warp.  Applying rotation i to the running entry ri_i and
@@ -401,7 +426,9 @@ __device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, lo
       rho = sqrt(r2);
       sm.cs[c] = rho == 0.0 ? 1.0 : ri / rho;
       sm.sn[c] = rho == 0.0 ? 0.0 : hsub / rho;
-      sm.rinv[c] = 1.0 / rho;
+      // a zero column (the Krylov space is exhausted) contributes y_c = 0,
+      // the least-squares solution of smallest norm
+      sm.rinv[c] = rho == 0.0 ? 0.0 : 1.0 / rho;
     }
     rc[c] = rho;
     rc[c + 1] = 0.0;
@@ -417,6 +444,10 @@ __device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, lo
       stop = 1;
     sm.stop = stop;
   }
+  __syncwarp();
+  // R(i,c) / R(c,c) for i < c: the form the back-substitution uses
+  const double ic = sm.rinv[c];
+  for (int i = lane; i < c; i += 32) rc[i] *= ic;
   __syncwarp();
   return stop;
 }
@@ -1505,38 +1536,100 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       status = kcols;  // steps done; V_0..V_kcols written by the X passes
       break;
     }
-    // ---- cycle end: y = R^{-1} g (upper triangular), x += V y
+    // ---- cycle end: y = R^{-1} g (upper triangular), x += V y.  The Givens
+    // warp stored each column of R divided by its diagonal entry, so starting
+    // from u = g the recurrence u_l -= (R(l,i) / R(i,i)) u_i (l < i, i
+    // descending) leaves u_i = R(i,i) y_i: one FP64 FMA per column on the
+    // dependent chain, with u_i broadcast by a shuffle (the divisions by the
+    // diagonal are multiplications by 1/R(i,i), done at the end in parallel).
     if (threadIdx.x < 32) {
-      for (int i = kcols - 1; i >= 0; i--) {
-        const double yi = sm.g[i] * sm.rinv[i];
-        for (int l = lane; l < i; l += 32) sm.g[l] -= sm.R[l + i * LD] * yi;
-        if (lane == 0) sm.y[i] = yi;
-        __syncwarp();
+      constexpr int UR = (MAXM + 31) / 32;  // rows of u per lane
+      double u[UR];
+#pragma unroll
+      for (int r = 0; r < UR; r++) u[r] = lane + 32 * r < kcols ? sm.g[lane + 32 * r] : 0.0;
+#pragma unroll 4
+      for (int i = kcols - 1; i > 0; i--) {
+        double src = u[0];
+#pragma unroll
+        for (int r = 1; r < UR; r++)
+          if ((i >> 5) == r) src = u[r];
+        const double ui = __shfl_sync(0xffffffffu, src, i & 31);
+#pragma unroll
+        for (int r = 0; r < UR; r++) {
+          const int l = lane + 32 * r;
+          if (l < i) u[r] = fma(-sm.R[l + i * LD], ui, u[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < UR; r++) {
+        const int l = lane + 32 * r;
+        if (l < kcols) {
+          const double yv = u[r] * sm.rinv[l];
+          sm.y[l] = yv;
+          if constexpr (sizeof(T) == 4) {
+            // y_l as a sum of two floats (head + tail) for the double-float V y
+            const float yh = (float)yv;
+            sm.yf[l] = make_float2(yh, (float)(yv - (double)yh));
+          }
+        }
       }
     }
     __syncthreads();
-    // two points per trip and even / odd k apart: four independent FP64 chains
-    // (a dependent FP64 operation costs ~70 cycles on this GPU)
-    for (int i0 = lo + tid; i0 < hi; i0 += 2 * BS) {
-      const int i1 = i0 + BS;
-      const bool two = i1 < hi;
-      const long long vb0 = vbase(i0 - voff, rows);
-      const long long vb1 = two ? vbase(i1 - voff, rows) : vb0;
-      double d0 = 0.0, e0 = 0.0, d1 = 0.0, e1 = 0.0;
-      int k = 0;
-      for (; k + 1 < kcols; k += 2) {
-        const double ya = sm.y[k], yb = sm.y[k + 1];
-        d0 = fma(ya, (double)V[vb0 + ((long long)k << 5)], d0);
-        e0 = fma(yb, (double)V[vb0 + ((long long)(k + 1) << 5)], e0);
-        d1 = fma(ya, (double)V[vb1 + ((long long)k << 5)], d1);
-        e1 = fma(yb, (double)V[vb1 + ((long long)(k + 1) << 5)], e1);
+    if constexpr (sizeof(T) == 4) {
+      // V y in double-float arithmetic: with V in FP32 and y_k = yh_k + yl_k,
+      // each product is split exactly by an FMA (TwoProduct) and accumulated
+      // with TwoSum into a (head, tail) pair of floats, as in the Dot2
+      // algorithm of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005):
+      // about 2^-44 relative accuracy at FP32 instruction rates, where one
+      // FP64 FMA and one conversion per basis vector and point run at this
+      // GPU's FP64 rate (1/64 of FP32).  The sum is added to x in FP64.
+      // Two points per trip and even / odd k apart: four independent pairs.
+      for (int i0 = lo + tid; i0 < hi; i0 += 2 * BS) {
+        const int i1 = i0 + BS;
+        const bool two = i1 < hi;
+        const long long vb0 = vbase(i0 - voff, rows);
+        const long long vb1 = two ? vbase(i1 - voff, rows) : vb0;
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, s2_ = 0.f, c2 = 0.f, s3 = 0.f, c3 = 0.f;
+        int k = 0;
+        for (; k + 1 < kcols; k += 2) {
+          const float2 ya = sm.yf[k], yb = sm.yf[k + 1];
+          df_fma(s0, c0, ya, (float)V[vb0 + ((long long)k << 5)]);
+          df_fma(s1, c1, yb, (float)V[vb0 + ((long long)(k + 1) << 5)]);
+          df_fma(s2_, c2, ya, (float)V[vb1 + ((long long)k << 5)]);
+          df_fma(s3, c3, yb, (float)V[vb1 + ((long long)(k + 1) << 5)]);
+        }
+        if (k < kcols) {
+          const float2 ya = sm.yf[k];
+          df_fma(s0, c0, ya, (float)V[vb0 + ((long long)k << 5)]);
+          df_fma(s2_, c2, ya, (float)V[vb1 + ((long long)k << 5)]);
+        }
+        tk.x[i0] += df_value(s0, c0, s1, c1);
+        if (two) tk.x[i1] += df_value(s2_, c2, s3, c3);
       }
-      if (k < kcols) {
-        d0 = fma(sm.y[k], (double)V[vb0 + ((long long)k << 5)], d0);
-        d1 = fma(sm.y[k], (double)V[vb1 + ((long long)k << 5)], d1);
+    } else {
+      // two points per trip and even / odd k apart: four independent FP64 chains
+      // (a dependent FP64 operation costs ~70 cycles on this GPU)
+      for (int i0 = lo + tid; i0 < hi; i0 += 2 * BS) {
+        const int i1 = i0 + BS;
+        const bool two = i1 < hi;
+        const long long vb0 = vbase(i0 - voff, rows);
+        const long long vb1 = two ? vbase(i1 - voff, rows) : vb0;
+        double d0 = 0.0, e0 = 0.0, d1 = 0.0, e1 = 0.0;
+        int k = 0;
+        for (; k + 1 < kcols; k += 2) {
+          const double ya = sm.y[k], yb = sm.y[k + 1];
+          d0 = fma(ya, (double)V[vb0 + ((long long)k << 5)], d0);
+          e0 = fma(yb, (double)V[vb0 + ((long long)(k + 1) << 5)], e0);
+          d1 = fma(ya, (double)V[vb1 + ((long long)k << 5)], d1);
+          e1 = fma(yb, (double)V[vb1 + ((long long)(k + 1) << 5)], e1);
+        }
+        if (k < kcols) {
+          d0 = fma(sm.y[k], (double)V[vb0 + ((long long)k << 5)], d0);
+          d1 = fma(sm.y[k], (double)V[vb1 + ((long long)k << 5)], d1);
+        }
+        tk.x[i0] += d0 + e0;
+        if (two) tk.x[i1] += d1 + e1;
       }
-      tk.x[i0] += d0 + e0;
-      if (two) tk.x[i1] += d1 + e1;
     }
     cycles++;
     ok = group_sync(w.bar, epoch, &sm.flag);
