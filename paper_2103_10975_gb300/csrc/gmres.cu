@@ -43,8 +43,8 @@ int gmres_compact_cap(int dim, int m, int P) {
   const long long row = 32LL * 4;
   const long long share = budget / 8 / 128 * 128;
   // a stage: m rows of V and the X pass's w'/kappa windows
-  const long long stage = (long long)m * row + (dim == 2 ? Aux<float, 2>::kXBytes
-                                                          : Aux<float, 3>::kXBytes);
+  const long long stage = (long long)vrows_p(m) * row + (dim == 2 ? Aux<float, 2>::kXBytes
+                                                                   : Aux<float, 3>::kXBytes);
   const long long want = (long long)P * stage;
   const long long cap = want < share ? want : share;
   return cap >= stage ? (int)cap : 0;
@@ -111,7 +111,7 @@ int gmres_bulk_cap(bool fp32, int m, int P) {
   // a stage: m rows of V and the X pass's w'/kappa windows (the 3D size, the
   // larger of the two dimensions)
   const long long stage =
-      (long long)m * row + (fp32 ? Aux<float, 3>::kXBytes : Aux<double, 3>::kXBytes);
+      (long long)vrows_p(m) * row + (fp32 ? Aux<float, 3>::kXBytes : Aux<double, 3>::kXBytes);
   const long long want = (long long)P * stage;
   const long long cap = want < share ? want : share;
   return cap >= stage ? (int)cap : 0;

@@ -90,22 +90,8 @@ __device__ __forceinline__ T stencil(const T* __restrict__ u, int i, int n,
     return stencil3d<T>(u, i, n, kappa, uc);
 }
 
-// ------------------------------------------------------------ basis layout --
-// V is stored tile-major: for every tile of 32 consecutive grid points the
-// `rows` basis values of each point follow each other, so a warp's column of
-// V (all k for its 32 points) is one contiguous run of rows * 32 elements and
-// each per-k access is one 128-byte (FP32) or 256-byte (FP64) segment.
-__host__ __device__ __forceinline__ long long vbase(int i, int rows) {
-  return ((long long)(i >> 5) * rows << 5) + (i & 31);
-}
-__host__ __device__ __forceinline__ long long vix(int k, int i, int rows) {
-  return vbase(i, rows) + ((long long)k << 5);
-}
-
-// ----------------------------------------------------------- shared state --
-constexpr int kMaxStages = 16;  // bulk-copy stages per warp (upper bound)
-
-// Two coefficients of one basis vector side by side (one shared-memory load).
+// Two values side by side: two basis vectors at one point, or the coefficients
+// of two basis vectors (one load each).
 template <typename T>
 struct Vec2;
 template <>
@@ -116,6 +102,54 @@ template <>
 struct Vec2<double> {
   using type = double2;
 };
+
+// ------------------------------------------------------------ basis layout --
+// V is stored tile-major in pairs of basis vectors: for every tile of 32
+// consecutive grid points, the values of vectors 2q and 2q+1 at a point sit
+// side by side (one 8-byte FP32 or 16-byte FP64 word), and the pair rows
+// q = 0, 1, ... of the tile follow each other.  A warp's column block of V (all
+// k for its 32 points) is one contiguous run of vrows_p(rows) * 32 elements,
+// and one vector load gives a point two basis values, which the passes consume
+// with one paired FMA (half the load and FMA instructions of one value each).
+__host__ __device__ __forceinline__ long long vbase(int i, int rows) {
+  return ((long long)(i >> 5) * vrows_p(rows) << 5) + ((i & 31) << 1);
+}
+// offset of basis vector k from a point's vbase
+__host__ __device__ __forceinline__ int vko(int k) { return ((k >> 1) << 6) + (k & 1); }
+__host__ __device__ __forceinline__ long long vix(int k, int i, int rows) {
+  return vbase(i, rows) + vko(k);
+}
+
+// Paired FMA: (a.x b.x + c.x, a.y b.y + c.y); one instruction for FP32.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  return __ffma2_rn(a, b, c);
+}
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename T2>
+__device__ __forceinline__ T2 dup2(decltype(T2::x) v) {
+  T2 r;
+  r.x = v;
+  r.y = v;
+  return r;
+}
+
+// Stores v_j in a column: with the zero slot of v_{j+1} when j is even.
+template <typename T>
+__device__ __forceinline__ void store_vj(T* vc, int j, T vj) {
+  if (j & 1) {
+    vc[vko(j)] = vj;
+  } else {
+    typename Vec2<T>::type p;
+    p.x = vj;
+    p.y = T(0);
+    *reinterpret_cast<typename Vec2<T>::type*>(vc + vko(j)) = p;
+  }
+}
+
+// ----------------------------------------------------------- shared state --
+constexpr int kMaxStages = 16;  // bulk-copy stages per warp (upper bound)
 
 template <typename T, int MAXM, int BS>
 struct Smem {
@@ -130,10 +164,12 @@ struct Smem {
   double rinv[MAXM];             // 1 / R(c,c), formed with rotation c (the back-
                                  // substitution then multiplies: no FP64 division)
   T HuT[(MAXM + 1) * MAXM];      // Hessenberg as built (Arnoldi relation), ld MAXM+1
-  T coef[MAXM + 2];              // h1 in the working precision (gather output)
-  // per basis vector k: .x = h2_k, the pending second-pass coefficient of w';
-  // .y = c_k, the coefficient turning A w' into A v_j
-  typename Vec2<T>::type hcc[MAXM + 2];
+  alignas(16) T coef[MAXM + 2];  // gather output in the working precision
+  // per basis vector k: h2v[k] = h2_k, the pending second-pass coefficient of
+  // w', and cv[k] = c_k, the coefficient turning A w' into A v_j; the passes
+  // read them in pairs (k = 2q, 2q+1), as they read V
+  alignas(16) T h2v[MAXM + 2];
+  alignas(16) T cv[MAXM + 2];
   // the latest column's two projections, from which the Givens warp forms
   // the FP64 column (FP64 work kept off the step's critical path)
   T h1c[MAXM + 2], h2h[MAXM + 2];
@@ -532,7 +568,7 @@ __device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
   for (int k = 0; k < K; k++) acc[k] = T(0);
   T accZ = T(0);
   const T inv = sm.invT;
-  const T cj = sm.hcc[j].y;
+  const T cj = sm.cv[j];
   for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
     int ii[U];
     bool ok_[U];
@@ -551,31 +587,39 @@ __device__ __forceinline__ void x_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
     for (int k = 0; k < K; k++) {
       if (k < j) {
 #pragma unroll
-        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[vb[u] + (k << 5)] : T(0);
+        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[vb[u] + vko(k)] : T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
+    // sum_k h2_k v_k and sum_k c_k v_k with even and odd k apart, in the order
+    // of the paired passes (x_proj), so that every placement of V rounds alike
+    T sv[U][2], sz[U][2];
+#pragma unroll
+    for (int u = 0; u < U; u++) sv[u][0] = sv[u][1] = sz[u][0] = sz[u][1] = T(0);
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      if (k < j) {
+        const T h2k = sm.h2v[k], ck = sm.cv[k];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          sv[u][k & 1] = fma(h2k, col[u][k], sv[u][k & 1]);
+          sz[u][k & 1] = fma(ck, col[u][k], sz[u][k & 1]);
+        }
       }
     }
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
-      vnum[u] = wp[u];
-    }
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (k < j) {
-        const T h2k = sm.hcc[k].x, ck = sm.hcc[k].y;
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          vnum[u] -= h2k * col[u][k];
-          znum[u] -= ck * col[u][k];
-        }
-      }
+      vnum[u] = wp[u] - (sv[u][0] + sv[u][1]);
+      znum[u] -= sz[u][0] + sz[u][1];
     }
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const T vj = vnum[u] * inv;
       const T z = (znum[u] - cj * vj) * inv;
       if (ok_[u]) {
-        V[vb[u] + ((long long)j << 5)] = vj;
+        store_vj(V + vb[u], j, vj);
         Z[ii[u]] = z;
       }
       accZ += z * z;
@@ -623,17 +667,23 @@ __device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
     for (int k = 0; k < K; k++) {
       if (k <= j) {
 #pragma unroll
-        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[vb[u] + (k << 5)] : T(0);
+        for (int u = 0; u < U; u++) col[u][k] = ok_[u] ? V[vb[u] + vko(k)] : T(0);
       }
     }
+    // sum_k h1_k v_k, even and odd k apart (the order of y_proj)
+    T sq[U][2];
+#pragma unroll
+    for (int u = 0; u < U; u++) sq[u][0] = sq[u][1] = T(0);
 #pragma unroll
     for (int k = 0; k < K; k++) {
       if (k <= j) {
         const T hk = sm.coef[k];
 #pragma unroll
-        for (int u = 0; u < U; u++) q[u] -= hk * col[u][k];
+        for (int u = 0; u < U; u++) sq[u][k & 1] = fma(hk, col[u][k], sq[u][k & 1]);
       }
     }
+#pragma unroll
+    for (int u = 0; u < U; u++) q[u] -= sq[u][0] + sq[u][1];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       if (ok_[u]) WP[ii[u]] = q[u];
@@ -645,6 +695,85 @@ __device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
   }
   warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accN);
+}
+
+// ---------------------------------------- one point's column, in pairs --
+// vc points at a point's column of V (pair layout: vector k at vc[vko(k)]),
+// in shared memory (a CTA slice or a bulk-copy stage).  Even and odd k are
+// accumulated apart, two basis values per load and per paired FMA.  Every
+// pair read is whole: the X pass of an even step j stores (v_j, 0) as one
+// pair, so the slot of vector j+1 holds zero until step j+1 writes it, and a
+// pair that reaches one vector past the vectors in use adds nothing.
+
+// X pass: (sum_{k<j} h2_k v_k, sum_{k<j} c_k v_k) over the pairs that hold
+// vectors 0..j-1 (for odd j the last one also holds the zero slot of v_j).
+template <typename T, int MAXM, int BS, int K>
+__device__ __forceinline__ void x_proj(const Smem<T, MAXM, BS>& sm, const T* vc, int j, T& sv,
+                                       T& sz) {
+  using T2 = typename Vec2<T>::type;
+  const T2* h2 = reinterpret_cast<const T2*>(sm.h2v);
+  const T2* cc = reinterpret_cast<const T2*>(sm.cv);
+  const int np = (j + 1) >> 1;
+  T2 av = dup2<T2>(T(0)), az = dup2<T2>(T(0));
+#pragma unroll
+  for (int q = 0; q < K / 2; q++) {
+    if (q < np) {
+      const T2 v = *reinterpret_cast<const T2*>(vc + (q << 6));
+      av = fma2(h2[q], v, av);
+      az = fma2(cc[q], v, az);
+    }
+  }
+  sv = av.x + av.y;
+  sz = az.x + az.y;
+}
+
+// X pass dots, after v_j is stored in the column: acc_k += v_k z for k <= j
+// (for even j the last pair is (v_j, 0)).  acc holds slots 2q, 2q+1 in acc[q].
+template <typename T, int K>
+__device__ __forceinline__ void x_dots(typename Vec2<T>::type (&acc)[K / 2], const T* vc, int j,
+                                       T z) {
+  using T2 = typename Vec2<T>::type;
+  const T2 zz = dup2<T2>(z);
+  const int np = (j >> 1) + 1;
+#pragma unroll
+  for (int q = 0; q < K / 2; q++)
+    if (q < np) acc[q] = fma2(*reinterpret_cast<const T2*>(vc + (q << 6)), zz, acc[q]);
+}
+
+// Y pass: sum_{k<=j} h1_k v_k (h1 in sm.coef; for even j the last pair's
+// second value is the zero slot of v_{j+1}).
+template <typename T, int MAXM, int BS, int K>
+__device__ __forceinline__ T y_proj(const Smem<T, MAXM, BS>& sm, const T* vc, int j) {
+  using T2 = typename Vec2<T>::type;
+  const T2* h1 = reinterpret_cast<const T2*>(sm.coef);
+  const int np = (j >> 1) + 1;
+  T2 a = dup2<T2>(T(0));
+#pragma unroll
+  for (int q = 0; q < K / 2; q++)
+    if (q < np) a = fma2(h1[q], *reinterpret_cast<const T2*>(vc + (q << 6)), a);
+  return a.x + a.y;
+}
+
+// Y pass dots: acc_k += v_k w' for k <= j.
+template <typename T, int K>
+__device__ __forceinline__ void y_dots(typename Vec2<T>::type (&acc)[K / 2], const T* vc, int j,
+                                       T w) {
+  using T2 = typename Vec2<T>::type;
+  const T2 ww = dup2<T2>(w);
+  const int np = (j >> 1) + 1;
+#pragma unroll
+  for (int q = 0; q < K / 2; q++)
+    if (q < np) acc[q] = fma2(*reinterpret_cast<const T2*>(vc + (q << 6)), ww, acc[q]);
+}
+
+// warp_slots_k for accumulators held in pairs (slots 2q, 2q+1 in acc[q]).
+template <int LMAX, int K, typename T>
+__device__ __forceinline__ void warp_slots_k2(T (*red)[LMAX],
+                                              const typename Vec2<T>::type (&acc)[K / 2], int L) {
+  T a[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) a[k] = (k & 1) ? acc[k >> 1].y : acc[k >> 1].x;
+  warp_slots_k<LMAX, K, T>(red, a, L);
 }
 
 // X and Y passes with the CTA's slice of V in shared memory (2D): the same
@@ -690,13 +819,14 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
   static_assert(DIM == 2, "shared-memory slices are a 2D variant");
   constexpr int LMAX = MAXM + 2;
   constexpr int U = 2;
+  using T2 = typename Vec2<T>::type;
   const int tid = threadIdx.x;
-  T acc[K];
+  T2 acc[K / 2];
 #pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = T(0);
+  for (int q = 0; q < K / 2; q++) acc[q] = dup2<T2>(T(0));
   T accZ = T(0);
   const T inv = sm.invT;
-  const T cj = sm.hcc[j].y;
+  const T cj = sm.cv[j];
   for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
     const bool first = i0 == lo + tid;
     int ii[U];
@@ -728,32 +858,18 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
     for (int u = 0; u < U; u++) {
       if (!ok_[u]) continue;
       const T* vc = Vs + vbase(ii[u] - lo, rows);
-      T vnum = wp[u], zn = znum[u];
-#pragma unroll
-      for (int k = 0; k < K; k++) {
-        if (k < j) {
-          const T v = vc[k << 5];
-          const auto hc = sm.hcc[k];  // (h2_k, c_k) in one load
-          vnum -= hc.x * v;
-          zn -= hc.y * v;
-        }
-      }
-      const T vj = vnum * inv;
-      const T z = (zn - cj * vj) * inv;
-      Vs[vbase(ii[u] - lo, rows) + (j << 5)] = vj;
+      T sv, sz;
+      x_proj<T, MAXM, BS, K>(sm, vc, j, sv, sz);
+      const T vj = (wp[u] - sv) * inv;
+      const T z = ((znum[u] - sz) - cj * vj) * inv;
+      store_vj(Vs + vbase(ii[u] - lo, rows), j, vj);
       Z[ii[u]] = z;
       if (first) cy.z[u] = z;
       accZ += z * z;
-#pragma unroll
-      for (int k = 0; k < K; k++) {
-        if (k < j)
-          acc[k] += vc[k << 5] * z;
-        else if (k == j)
-          acc[k] += vj * z;
-      }
+      x_dots<T, K>(acc, vc, j, z);
     }
   }
-  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
+  warp_slots_k2<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accZ);
 }
 
@@ -764,10 +880,11 @@ __device__ __forceinline__ void y_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
                                           const XCarry<T>& cy) {
   constexpr int LMAX = MAXM + 2;
   constexpr int U = 2;  // the X pass's points per trip (its first trip's z is in cy)
+  using T2 = typename Vec2<T>::type;
   const int tid = threadIdx.x;
-  T acc[K];
+  T2 acc[K / 2];
 #pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = T(0);
+  for (int q = 0; q < K / 2; q++) acc[q] = dup2<T2>(T(0));
   T accN = T(0);
   for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
     const bool first = i0 == lo + tid;
@@ -784,18 +901,13 @@ __device__ __forceinline__ void y_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
     for (int u = 0; u < U; u++) {
       if (!ok_[u]) continue;
       const T* vc = Vs + vbase(ii[u] - lo, rows);
-      T qv = q[u];
-#pragma unroll
-      for (int k = 0; k < K; k++)
-        if (k <= j) qv -= sm.coef[k] * vc[k << 5];
+      const T qv = q[u] - y_proj<T, MAXM, BS, K>(sm, vc, j);
       WP[ii[u]] = qv;
       accN += qv * qv;
-#pragma unroll
-      for (int k = 0; k < K; k++)
-        if (k <= j) acc[k] += vc[k << 5] * qv;
+      y_dots<T, K>(acc, vc, j, qv);
     }
   }
-  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
+  warp_slots_k2<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accN);
 }
 
@@ -819,24 +931,29 @@ struct Aux {
   static constexpr int kYBytes = 32 * (int)sizeof(T);
 };
 
-// Per-warp ring of bulk-copy stages for one pass: `vrows` rows of V per tile
-// plus `abytes` of auxiliary values; as many stages as fit in the warp's share
-// of the staging buffer (up to pp.P), so that small j keep more tiles in flight.
+// Per-warp ring of bulk-copy stages for one pass: the pair rows holding the
+// first `vrows` rows of V per tile are copied, in a V part with room for
+// `vroom` rows, followed by `abytes` of auxiliary values; as many stages as
+// fit in the warp's share of the staging buffer (up to pp.P), so that small j
+// keep more tiles in flight.
 struct BulkRing {
   unsigned char* st;          // the warp's staging area
   unsigned long long* bars;   // the warp's stage barriers
-  unsigned vbytes;            // V part of a stage (rows * 32 * sizeof(T))
+  unsigned vcopy;             // V bytes copied per stage (whole pair rows)
+  unsigned vbytes;            // V part of a stage (vroom rows, rounded to pairs)
   unsigned bytes;             // bytes per stage (V part + auxiliary part)
   int P;                      // stages in use for this pass
 };
 
 template <typename T>
-__device__ __forceinline__ BulkRing bulk_ring(const BulkPipe& pp, int vrows, int abytes) {
+__device__ __forceinline__ BulkRing bulk_ring(const BulkPipe& pp, int vrows, int vroom,
+                                              int abytes) {
   BulkRing r;
   const int warp = threadIdx.x >> 5;
   r.st = pp.stage + (size_t)warp * pp.cap;
   r.bars = pp.bar + warp * kMaxStages;
-  r.vbytes = (unsigned)vrows * 32u * (unsigned)sizeof(T);
+  r.vcopy = (unsigned)vrows_p(vrows) * 32u * (unsigned)sizeof(T);
+  r.vbytes = (unsigned)vrows_p(vroom) * 32u * (unsigned)sizeof(T);
   r.bytes = r.vbytes + (unsigned)abytes;
   const int fit = pp.cap / (int)r.bytes;
   r.P = max(1, min(pp.P, fit));
@@ -878,7 +995,7 @@ struct AuxSrc {  // what the X pass's stages copy besides V
 };
 
 // Lane 0 issues stage q: tile lo/32 + warp + NW q.  X pass (aux != null):
-// V rows 0..r.vbytes/128-1 of the tile (layout of `rows` rows per tile) and the
+// the tile's first pair rows of V (r.vcopy bytes; `rows` rows per tile) and the
 // w'/kappa windows; Y pass: V rows and z.  Each
 // copy registers its bytes before it is issued; the single arrival comes last,
 // so the stage's phase cannot complete early.
@@ -893,9 +1010,9 @@ __device__ __forceinline__ void bulk_issue_stage(const BulkRing& r, const T* V, 
   unsigned char* st = r.st + (size_t)sidx * r.bytes;
   T* at = reinterpret_cast<T*>(st + r.vbytes);
   unsigned long long* bar = &r.bars[sidx];
-  if (r.vbytes) {
-    mbar_expect(bar, r.vbytes);
-    bulk_g2s(st, V + vbase(i0, rows), r.vbytes, bar);
+  if (r.vcopy) {
+    mbar_expect(bar, r.vcopy);
+    bulk_g2s(st, V + vbase(i0, rows), r.vcopy, bar);
   }
   if (aux) {
     const T* wp = reinterpret_cast<const T*>(aux->wp);
@@ -1000,18 +1117,20 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
                                             T s2t, const BulkPipe& pp, unsigned& phase,
                                             const AuxSrc& aux) {
   using A = Aux<T, DIM>;
+  using T2 = typename Vec2<T>::type;
   constexpr int LMAX = MAXM + 2;
   constexpr int NW = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T acc[K];
+  T2 acc[K / 2];
 #pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = T(0);
+  for (int q = 0; q < K / 2; q++) acc[q] = dup2<T2>(T(0));
   T accZ = T(0);
   const T inv = sm.invT;
-  const T cj = sm.hcc[j].y;
+  const T cj = sm.cv[j];
   const int ntile = (hi - lo + 31) >> 5;
   const int nq = ntile > warp ? (ntile - warp + NW - 1) / NW : 0;
-  const BulkRing r = bulk_ring<T>(pp, j, A::kXBytes);
+  // rows 0..j-1 copied; room for the pair holding v_j, which the pass writes
+  const BulkRing r = bulk_ring<T>(pp, j, j + 1, A::kXBytes);
   // w' (and z, V) were written through the generic proxy; the copies read
   // through the async proxy
   asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -1041,7 +1160,7 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
     }
     phase ^= 1u << sidx;
     const unsigned char* stb = r.st + (size_t)sidx * r.bytes;
-    const T* sc = reinterpret_cast<const T*>(stb) + lane;
+    const T* sc = reinterpret_cast<const T*>(stb) + 2 * lane;  // the lane's column (pair layout)
     const T* aw = reinterpret_cast<const T*>(stb + r.vbytes);
     const float* ak = (A::kK > 0 && aux.kap) ? reinterpret_cast<const float*>(aw + A::kW) : nullptr;
     const T wp = ok ? aw[4 + lane] : T(0);
@@ -1061,31 +1180,17 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
         }
       }
     }
-    T vnum = wp;
+    T sv = T(0), sz = T(0);
+    if (ok) x_proj<T, MAXM, BS, K>(sm, sc, j, sv, sz);
+    const T vj = (wp - sv) * inv;
+    const T z = ((znum - sz) - cj * vj) * inv;
     if (ok) {
-#pragma unroll
-      for (int k = 0; k < K; k++) {
-        if (k < j) {
-          const T v = sc[k << 5];
-          const auto hc = sm.hcc[k];
-          vnum -= hc.x * v;
-          znum -= hc.y * v;
-        }
-      }
-    }
-    const T vj = vnum * inv;
-    const T z = (znum - cj * vj) * inv;
-    if (ok) {
-      V[vbase(i, rows) + ((long long)j << 5)] = vj;
+      store_vj(V + vbase(i, rows), j, vj);
+      // and into the stage, whose V part has room for the pair of v_j
+      store_vj(const_cast<T*>(sc), j, vj);
       Z[i] = z;
       // points past the end of a ragged last tile hold stale values: skipped
-#pragma unroll
-      for (int k = 0; k < K; k++) {
-        if (k < j)
-          acc[k] += sc[k << 5] * z;
-        else if (k == j)
-          acc[k] += vj * z;
-      }
+      x_dots<T, K>(acc, sc, j, z);
       accZ += z * z;
     }
     __syncwarp();
@@ -1095,7 +1200,7 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
   if (!good) bulk_drain(r, pp, q, nq, phase);
   // the V_j and z stores above are read by later bulk copies (async proxy)
   asm volatile("fence.proxy.async.global;" ::: "memory");
-  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
+  warp_slots_k2<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accZ);
 }
 
@@ -1106,16 +1211,17 @@ __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
                                             const T* __restrict__ V, int rows,
                                             const BulkPipe& pp, unsigned& phase, long long ldv) {
   using A = Aux<T, DIM>;
+  using T2 = typename Vec2<T>::type;
   constexpr int LMAX = MAXM + 2;
   constexpr int NW = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T acc[K];
+  T2 acc[K / 2];
 #pragma unroll
-  for (int k = 0; k < K; k++) acc[k] = T(0);
+  for (int q = 0; q < K / 2; q++) acc[q] = dup2<T2>(T(0));
   T accN = T(0);
   const int ntile = (hi - lo + 31) >> 5;
   const int nq = ntile > warp ? (ntile - warp + NW - 1) / NW : 0;
-  const BulkRing r = bulk_ring<T>(pp, j + 1, A::kYBytes);
+  const BulkRing r = bulk_ring<T>(pp, j + 1, j + 1, A::kYBytes);
   if (lane == 0)
     for (int q = 0; q < r.P && q < nq; q++)
       bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q, nullptr, Z, ldv);
@@ -1131,24 +1237,19 @@ __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
     }
     phase ^= 1u << sidx;
     const unsigned char* stb = r.st + (size_t)sidx * r.bytes;
-    const T* sc = reinterpret_cast<const T*>(stb) + lane;
-    T qv = ok ? reinterpret_cast<const T*>(stb + r.vbytes)[lane] : T(0);
+    const T* sc = reinterpret_cast<const T*>(stb) + 2 * lane;  // the lane's column (pair layout)
     if (ok) {
-#pragma unroll
-      for (int k = 0; k < K; k++)
-        if (k <= j) qv -= sm.coef[k] * sc[k << 5];
+      const T qv = reinterpret_cast<const T*>(stb + r.vbytes)[lane] - y_proj<T, MAXM, BS, K>(sm, sc, j);
       WP[i] = qv;
       accN += qv * qv;
-#pragma unroll
-      for (int k = 0; k < K; k++)
-        if (k <= j) acc[k] += sc[k << 5] * qv;
+      y_dots<T, K>(acc, sc, j, qv);
     }
     __syncwarp();
     if (lane == 0 && q + r.P < nq)
       bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q + r.P, nullptr, Z, ldv);
   }
   if (!good) bulk_drain(r, pp, q, nq, phase);
-  warp_slots_k<LMAX, K, T>(sm.red, acc, j + 1);
+  warp_slots_k2<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accN);
 }
 
@@ -1248,13 +1349,13 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   double bnorm = 0.0;
   bool ok = true;
 
-  if (VM == kVShared && (long long)chunk * rows * (long long)sizeof(T) > kp.vsmem) {
+  if (VM == kVShared && (long long)chunk * vrows_p(rows) * (long long)sizeof(T) > kp.vsmem) {
     status = kErrConfig;  // the slice would overrun the shared-memory reservation
     goto finish;
   }
   // a warp's staging area must hold one stage of m rows and the X pass's windows
   if (VM == kVBulk &&
-      kp.bulk_cap < m * 32 * (int)sizeof(T) + Aux<T, DIM>::kXBytes) {
+      kp.bulk_cap < vrows_p(m) * 32 * (int)sizeof(T) + Aux<T, DIM>::kXBytes) {
     status = kErrConfig;
     goto finish;
   }
@@ -1324,8 +1425,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         v0 += ri * ri;
       }
       for (int k = tid; k < LMAX; k += BS) {
-        sm.hcc[k].x = T(0);
-        sm.hcc[k].y = T(0);
+        sm.h2v[k] = T(0);
+        sm.cv[k] = T(0);
       }
       warp_slot<4>(sm.redd, 0, v0);
       block_finish<4, BS, double>(1, part(), lb, sm.redd, ps);
@@ -1427,7 +1528,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       if (tid <= j) {
         const T h2 = sm.coef[tid];
         sm.HuT[tid + j * LD] = sm.h1c[tid] + h2;  // correctly rounded sum
-        sm.hcc[tid].x = h2;
+        sm.h2v[tid] = h2;
         sm.h2h[tid] = h2;
       }
       // hn_{j+1} from hn2T: 1/hn for the next X pass and the subdiagonal of Hu;
@@ -1437,7 +1538,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         const T hnT = sqrt(h2v);
         sm.invT = T(1) / hnT;
         sm.HuT[j + 1 + j * LD] = hnT;  // (the Givens warp reads it in FP64)
-        sm.hcc[j + 1].y = hnT * sm.coef[j];
+        sm.cv[j + 1] = hnT * sm.coef[j];
       };
       if (tid < 32) {
         T q = T(0);
@@ -1475,7 +1576,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         c += __shfl_xor_sync(0xffffffffu, c, 4);
         c += __shfl_xor_sync(0xffffffffu, c, 2);
         c += __shfl_xor_sync(0xffffffffu, c, 1);
-        if (sub == 0 && i <= j) sm.hcc[i].y = c;
+        if (sub == 0 && i <= j) sm.cv[i] = c;
       }
       __syncthreads();
       if (sm.fallback) {
@@ -1485,7 +1586,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
           T q = WP[i];
 #pragma unroll
           for (int k = 0; k < MAXM; k++)
-            if (k <= j) q -= sm.hcc[k].x * V[vix(k, i - voff, rows)];
+            if (k <= j) q -= sm.h2v[k] * V[vix(k, i - voff, rows)];
           WP[i] = q;
           accN += q * q;
         }
@@ -1505,8 +1606,8 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         // w' now carries the second projection: no pending coefficients, and
         // A w' is the next X pass's stencil itself
         if (tid <= j + 1) {
-          sm.hcc[tid].x = T(0);
-          sm.hcc[tid].y = T(0);
+          sm.h2v[tid] = T(0);
+          sm.cv[tid] = T(0);
         }
         cy.pre = false;  // w' changed at this CTA's points
         __syncthreads();
@@ -1591,17 +1692,19 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         const long long vb1 = two ? vbase(i1 - voff, rows) : vb0;
         float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, s2_ = 0.f, c2 = 0.f, s3 = 0.f, c3 = 0.f;
         int k = 0;
-        for (; k + 1 < kcols; k += 2) {
+        for (; k + 1 < kcols; k += 2) {  // k even: vectors k, k+1 in one load
           const float2 ya = sm.yf[k], yb = sm.yf[k + 1];
-          df_fma(s0, c0, ya, (float)V[vb0 + ((long long)k << 5)]);
-          df_fma(s1, c1, yb, (float)V[vb0 + ((long long)(k + 1) << 5)]);
-          df_fma(s2_, c2, ya, (float)V[vb1 + ((long long)k << 5)]);
-          df_fma(s3, c3, yb, (float)V[vb1 + ((long long)(k + 1) << 5)]);
+          const float2 v0 = *reinterpret_cast<const float2*>(V + vb0 + vko(k));
+          const float2 v1 = *reinterpret_cast<const float2*>(V + vb1 + vko(k));
+          df_fma(s0, c0, ya, v0.x);
+          df_fma(s1, c1, yb, v0.y);
+          df_fma(s2_, c2, ya, v1.x);
+          df_fma(s3, c3, yb, v1.y);
         }
         if (k < kcols) {
           const float2 ya = sm.yf[k];
-          df_fma(s0, c0, ya, (float)V[vb0 + ((long long)k << 5)]);
-          df_fma(s2_, c2, ya, (float)V[vb1 + ((long long)k << 5)]);
+          df_fma(s0, c0, ya, (float)V[vb0 + vko(k)]);
+          df_fma(s2_, c2, ya, (float)V[vb1 + vko(k)]);
         }
         tk.x[i0] += df_value(s0, c0, s1, c1);
         if (two) tk.x[i1] += df_value(s2_, c2, s3, c3);
@@ -1618,14 +1721,14 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         int k = 0;
         for (; k + 1 < kcols; k += 2) {
           const double ya = sm.y[k], yb = sm.y[k + 1];
-          d0 = fma(ya, (double)V[vb0 + ((long long)k << 5)], d0);
-          e0 = fma(yb, (double)V[vb0 + ((long long)(k + 1) << 5)], e0);
-          d1 = fma(ya, (double)V[vb1 + ((long long)k << 5)], d1);
-          e1 = fma(yb, (double)V[vb1 + ((long long)(k + 1) << 5)], e1);
+          d0 = fma(ya, (double)V[vb0 + vko(k)], d0);
+          e0 = fma(yb, (double)V[vb0 + vko(k + 1)], e0);
+          d1 = fma(ya, (double)V[vb1 + vko(k)], d1);
+          e1 = fma(yb, (double)V[vb1 + vko(k + 1)], e1);
         }
         if (k < kcols) {
-          d0 = fma(sm.y[k], (double)V[vb0 + ((long long)k << 5)], d0);
-          d1 = fma(sm.y[k], (double)V[vb1 + ((long long)k << 5)], d1);
+          d0 = fma(sm.y[k], (double)V[vb0 + vko(k)], d0);
+          d1 = fma(sm.y[k], (double)V[vb1 + vko(k)], d1);
         }
         tk.x[i0] += d0 + e0;
         if (two) tk.x[i1] += d1 + e1;

@@ -239,7 +239,7 @@ int use_compact(const mlgmres* h) {
 // slice does not fit).
 int single_vsmem(const mlgmres* h, int blocks, bool compact = false) {
   const long long chunk = (((long long)h->N + blocks - 1) / blocks + 31) / 32 * 32;
-  const long long need = chunk * (h->opt.m + 1) * (h->fp32 ? 4 : 8);
+  const long long need = chunk * vrows_p(h->opt.m + 1) * (h->fp32 ? 4 : 8);
   const int budget = compact ? (h->grid.dim == 2 ? gmres_compact_vsmem_budget() : 0)
                              : gmres_vsmem_budget(h->fp32);
   return need <= budget ? (int)need : 0;
@@ -603,7 +603,7 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     // V slice in shared memory when it fits (the compact variant streams V)
     h->vsmem = single_vsmem(h, h->blocks, force_compact);
     const size_t es = h->fp32 ? sizeof(float) : sizeof(double);
-    CK(cudaMalloc(&h->V, es * (size_t)(opt->m + 1) * h->ldv));
+    CK(cudaMalloc(&h->V, es * (size_t)vrows_p(opt->m + 1) * h->ldv));
     CK(cudaMalloc(&h->W0, es * (size_t)h->ldv));
     CK(cudaMalloc(&h->W1, es * (size_t)h->ldv));
     CK(cudaMalloc(&h->part, sizeof(double) * part_doubles(kPartStride)));
@@ -620,7 +620,7 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
       h->group_cap = std::max(h->group_cap, h->batch_groups);
       h->cfg_cap = kBatchCap;
       const size_t G = (size_t)h->batch_groups;
-      CK(cudaMalloc(&h->Vb, es * G * (size_t)(opt->m + 1) * h->ldv));
+      CK(cudaMalloc(&h->Vb, es * G * (size_t)vrows_p(opt->m + 1) * h->ldv));
       CK(cudaMalloc(&h->Wb, es * G * 2 * (size_t)h->ldv));
       CK(cudaMalloc(&h->partb, sizeof(double) * G * part_doubles(1)));
     }
@@ -864,7 +864,7 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
         const long long N = grid_points(dim, grids[i].n);
         const long long k = gc[go[i]];
         const long long chunk = ((N + k - 1) / k + 31) / 32 * 32;
-        need = std::max(need, chunk * (h->opt.m + 1) * (long long)es0);
+        need = std::max(need, chunk * vrows_p(h->opt.m + 1) * (long long)es0);
       }
       return need <= gmres_vsmem_budget(h->fp32) ? (int)need : 0;
     };
@@ -908,7 +908,7 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
     long long part_off = 0;
     for (int g = 0; g < G; g++) {
       GroupWork w;
-      w.V = (char*)h->Vb + es * (size_t)g * (h->opt.m + 1) * h->ldv;
+      w.V = (char*)h->Vb + es * (size_t)g * vrows_p(h->opt.m + 1) * h->ldv;
       w.ldv = h->ldv;
       w.W0 = (char*)h->Wb + es * (size_t)g * 2 * h->ldv;
       w.W1 = (char*)w.W0 + es * h->ldv;

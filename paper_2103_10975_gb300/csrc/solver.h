@@ -18,6 +18,9 @@ constexpr int kVBulk = 2;    // HBM, streamed through per-warp bulk-copy stages
 constexpr int kPartStride = 1024;  // max CTAs per group (partials row length)
 // doubles in a group's partial-sum area (two alternating sets)
 constexpr long long part_doubles(int pstride) { return 2LL * (kMaxM + 2) * pstride; }
+// Rows a tile of the basis occupies for `rows` vectors: V stores basis vectors
+// in pairs, so the count is rounded up to even (see gmres_kernel.cuh).
+__host__ __device__ constexpr int vrows_p(int rows) { return (rows + 1) & ~1; }
 
 // Per-system result written by the solver (mirrors mlgmres_result's numeric part).
 struct DevResult {

@@ -18,7 +18,7 @@ namespace mlg {
 constexpr int kStaticMaxN = 256 * 256;
 constexpr int kStaticMaxM = 32;
 constexpr long long kStaticLdv = kStaticMaxN;  // a multiple of 64
-constexpr size_t kStaticBasis = sizeof(float) * (size_t)(kStaticMaxM + 1) * kStaticLdv;
+constexpr size_t kStaticBasis = sizeof(float) * (size_t)vrows_p(kStaticMaxM + 1) * kStaticLdv;
 constexpr size_t kStaticWork = 2 * sizeof(float) * (size_t)kStaticLdv;
 constexpr size_t kStaticPart = sizeof(double) * part_doubles(kPartStride);
 constexpr size_t kStaticMisc = 4096;  // barrier counter, error flag, result, launch tables
