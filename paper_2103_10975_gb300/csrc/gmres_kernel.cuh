@@ -1010,6 +1010,46 @@ __device__ __forceinline__ void bulk_issue_stage(const BulkRing& r, const T* V, 
   unsigned char* st = r.st + (size_t)sidx * r.bytes;
   T* at = reinterpret_cast<T*>(st + r.vbytes);
   unsigned long long* bar = &r.bars[sidx];
+  // Fast path: no copy needs clipping (every window lies inside its array; the
+  // z window of the Y pass always does, since ldv is a multiple of 64 >= N).
+  // One arrive.expect_tx registers all of the stage's bytes before the copies
+  // are issued (the phase completes only when they have landed), instead of
+  // one expect_tx per copy and the clipping arithmetic of each.
+  {
+    const long long dmax = aux ? (DIM == 3 ? (long long)aux->n * aux->n : aux->n) : 0;
+    const long long lim = aux ? (aux->kap && aux->N < ldv ? aux->N : ldv) : ldv;
+    if (!aux || ((long long)i0 - dmax - 16 >= 0 && (long long)i0 + dmax + 40 <= lim)) {
+      const bool kap = aux && A::kK > 0 && aux->kap;
+      const unsigned abytes =
+          aux ? (unsigned)(A::kW * (int)sizeof(T) + (kap ? A::kW * 4 : 0)) : 32u * sizeof(T);
+      mbar_expect_tx(bar, r.vcopy + abytes);
+      if (r.vcopy) bulk_g2s(st, V + vbase(i0, rows), r.vcopy, bar);
+      if (!aux) {
+        bulk_g2s(at, Zsrc + i0, 32u * sizeof(T), bar);
+        return;
+      }
+      const T* wp = reinterpret_cast<const T*>(aux->wp);
+      const int n = aux->n, nn = n * n;
+      bulk_g2s(at, wp + (i0 - 4), A::kCen * (unsigned)sizeof(T), bar);
+#pragma unroll
+      for (int k = 0; k < A::kRows; k++) {
+        const int d = k == 0 ? -n : (k == 1 ? n : (k == 2 ? -nn : nn));
+        bulk_g2s(at + A::kCen + k * A::kRow, wp + floor_to(i0 + d, ALN),
+                 A::kRow * (unsigned)sizeof(T), bar);
+      }
+      if (kap) {
+        float* ak = reinterpret_cast<float*>(at + A::kW);
+        bulk_g2s(ak, aux->kap + (i0 - 4), A::kCen * 4u, bar);
+#pragma unroll
+        for (int k = 0; k < A::kRows; k++) {
+          const int d = k == 0 ? -n : (k == 1 ? n : (k == 2 ? -nn : nn));
+          bulk_g2s(ak + A::kCen + k * A::kRow, aux->kap + floor_to(i0 + d, 4), A::kRow * 4u, bar);
+        }
+      }
+      return;
+    }
+  }
+  // Near the ends of the arrays: each copy clipped, and registered on its own.
   if (r.vcopy) {
     mbar_expect(bar, r.vcopy);
     bulk_g2s(st, V + vbase(i0, rows), r.vcopy, bar);
