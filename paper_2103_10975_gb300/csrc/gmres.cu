@@ -28,6 +28,7 @@ int max_blocks_f2c(int* bs, int extra);
 int own_bytes_f2c();
 cudaError_t launch_gmres_f3c(const KParams& kp, int grid, cudaStream_t s);
 cudaError_t launch_gmres_f2cs(const KParams& kp, int grid, cudaStream_t s);
+cudaError_t launch_gmres_f2s32(const KParams& kp, int grid, cudaStream_t s);
 int max_blocks_f3c(int* bs, int extra);
 int own_bytes_f3c();
 
@@ -80,7 +81,8 @@ cudaError_t launch_gmres(const KParams& kp, bool fp32, int dim, int grid, cudaSt
   }
   if (fp32) {
     if (dim == 2) {
-      if (kp.vmode == kVShared) return launch_gmres_f2s(kp, grid, s);
+      if (kp.vmode == kVShared)
+        return kp.m <= kSmallM ? launch_gmres_f2s32(kp, grid, s) : launch_gmres_f2s(kp, grid, s);
       if (kp.vmode == kVBulk) return launch_gmres_f2b(kp, grid, s);
       return launch_gmres_f2d(kp, grid, s);
     }
@@ -138,6 +140,34 @@ __global__ void apply_kernel(int n, int N, const float* kappa, const double* u, 
   if (i >= N) return;
   const double h = 2.0 / (n + 1);
   out[i] = stencil<double, DIM>(u, i, n, kappa, u[i]) / (h * h);
+}
+
+__global__ void kappa_faces_kernel(int n, int N, const float* __restrict__ kappa,
+                                   float* __restrict__ faces, long long fstride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int nn = n * n;
+  const int ix = i % n, iy = (i / n) % n, iz = i / nn;
+  const double kc = kappa[i];
+  // the harmonic mean in FP64, rounded once to FP32
+  auto hm = [&](int j) {
+    const double kn = kappa[j];
+    return (float)(2.0 * kc * kn / (kc + kn));
+  };
+  faces[i] = ix < n - 1 ? hm(i + 1) : 0.f;
+  faces[fstride + i] = iy < n - 1 ? hm(i + n) : 0.f;
+  faces[2 * fstride + i] = iz < n - 1 ? hm(i + nn) : 0.f;
+  const int walls = (ix == 0) + (ix == n - 1) + (iy == 0) + (iy == n - 1) + (iz == 0) + (iz == n - 1);
+  faces[3 * fstride + i] = (float)(kc * walls);
+}
+
+cudaError_t launch_kappa_faces(int n, const float* kappa, float* faces, long long fstride,
+                               cudaStream_t s) {
+  const int N = n * n * n;
+  const int bs = 256, gr = (N + bs - 1) / bs;
+  note_launches(1);
+  kappa_faces_kernel<<<gr, bs, 0, s>>>(n, N, kappa, faces, fstride);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_apply(int dim, int n, const float* kappa, const double* u, double* out,

@@ -927,7 +927,12 @@ struct Aux {
   static constexpr int kCen = 40, kRow = 36;
   static constexpr int kW = kCen + kRows * kRow;  // elements of T (w')
   static constexpr int kK = DIM == 3 ? kW : 0;    // floats (kappa)
-  static constexpr int kXBytes = kW * (int)sizeof(T) + kK * 4;
+  // 3D with face coefficients instead of kappa (floats): fx over [i0-4, i0+36),
+  // fy, fz and fb over the tile [i0, i0+32), fy of the row -n and fz of the
+  // row -n^2 (36 values each from a 16-byte aligned start)
+  static constexpr int kFx = 0, kFy = 40, kFyM = 72, kFz = 108, kFzM = 140, kFb = 176;
+  static constexpr int kF = DIM == 3 ? 208 : 0;
+  static constexpr int kXBytes = kW * (int)sizeof(T) + (kK > kF ? kK : kF) * 4;
   static constexpr int kYBytes = 32 * (int)sizeof(T);
 };
 
@@ -990,6 +995,8 @@ __device__ __forceinline__ void stage_run(E* dst, const E* src, int want, int cn
 struct AuxSrc {  // what the X pass's stages copy besides V
   const void* wp;       // w' (elements of T)
   const float* kap;     // kappa (3D), or null when it is not staged
+  const float* fc;      // face coefficients (3D, FP32; w' padded), or null
+  long long fs;         // their array stride
   int n;
   long long N, ldv;
 };
@@ -1018,10 +1025,14 @@ __device__ __forceinline__ void bulk_issue_stage(const BulkRing& r, const T* V, 
   {
     const long long dmax = aux ? (DIM == 3 ? (long long)aux->n * aux->n : aux->n) : 0;
     const long long lim = aux ? (aux->kap && aux->N < ldv ? aux->N : ldv) : ldv;
-    if (!aux || ((long long)i0 - dmax - 16 >= 0 && (long long)i0 + dmax + 40 <= lim)) {
-      const bool kap = aux && A::kK > 0 && aux->kap;
+    // (with face coefficients, w' and the coefficients are padded: never clipped)
+    if (!aux || aux->fc ||
+        ((long long)i0 - dmax - 16 >= 0 && (long long)i0 + dmax + 40 <= lim)) {
+      const bool fcs = aux && A::kF > 0 && aux->fc;
+      const bool kap = aux && A::kK > 0 && aux->kap && !fcs;
       const unsigned abytes =
-          aux ? (unsigned)(A::kW * (int)sizeof(T) + (kap ? A::kW * 4 : 0)) : 32u * sizeof(T);
+          aux ? (unsigned)(A::kW * (int)sizeof(T) + (kap ? A::kW * 4 : 0) + (fcs ? A::kF * 4 : 0))
+              : 32u * sizeof(T);
       mbar_expect_tx(bar, r.vcopy + abytes);
       if (r.vcopy) bulk_g2s(st, V + vbase(i0, rows), r.vcopy, bar);
       if (!aux) {
@@ -1045,6 +1056,19 @@ __device__ __forceinline__ void bulk_issue_stage(const BulkRing& r, const T* V, 
           const int d = k == 0 ? -n : (k == 1 ? n : (k == 2 ? -nn : nn));
           bulk_g2s(ak + A::kCen + k * A::kRow, aux->kap + floor_to(i0 + d, 4), A::kRow * 4u, bar);
         }
+      }
+      if (fcs) {
+        float* af = reinterpret_cast<float*>(at + A::kW);
+        const float* fx = aux->fc;
+        const float* fy = fx + aux->fs;
+        const float* fz = fy + aux->fs;
+        const float* fb = fz + aux->fs;
+        bulk_g2s(af + A::kFx, fx + (i0 - 4), 160u, bar);
+        bulk_g2s(af + A::kFy, fy + i0, 128u, bar);
+        bulk_g2s(af + A::kFyM, fy + floor_to(i0 - n, 4), 144u, bar);
+        bulk_g2s(af + A::kFz, fz + i0, 128u, bar);
+        bulk_g2s(af + A::kFzM, fz + floor_to(i0 - nn, 4), 144u, bar);
+        bulk_g2s(af + A::kFb, fb + i0, 128u, bar);
       }
       return;
     }
@@ -1088,6 +1112,37 @@ __device__ __forceinline__ void bulk_drain(const BulkRing& r, const BulkPipe& pp
     if (mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns))
       phase ^= 1u << sidx;
   }
+}
+
+// The 3D operator at point i = i0 + lane from a stage's w' windows and face
+// coefficient windows: fb u_c + sum over the six faces of f (u_c - u_nb), in
+// the face order of stencil3d (-x, +x, -y, +y, -z, +z).  A wall face has
+// f = 0 here (its kappa_c u_c is in fb) and its u_nb is a zero pad or a finite
+// value of w', so no coordinate tests are needed.
+template <typename T>
+__device__ __forceinline__ T stencil_faces(const T* aw, const float* af, int i0, int lane, int n) {
+  using A = Aux<T, 3>;
+  constexpr int ALN = 16 / (int)sizeof(T);
+  const int nn = n * n;
+  const T uc = aw[4 + lane];
+  auto wrow = [&](int k, int d) {
+    return aw[A::kCen + k * A::kRow + (i0 + d - floor_to(i0 + d, ALN)) + lane];
+  };
+  const T wl = aw[3 + lane], wr = aw[5 + lane];
+  const T wd = wrow(0, -n), wt = wrow(1, n), wb = wrow(2, -nn), wf = wrow(3, nn);
+  const T fxl = (T)af[A::kFx + 3 + lane], fxr = (T)af[A::kFx + 4 + lane];
+  const T fyd = (T)af[A::kFyM + (i0 - n - floor_to(i0 - n, 4)) + lane];
+  const T fyt = (T)af[A::kFy + lane];
+  const T fzb = (T)af[A::kFzM + (i0 - nn - floor_to(i0 - nn, 4)) + lane];
+  const T fzf = (T)af[A::kFz + lane];
+  T acc = (T)af[A::kFb + lane] * uc;
+  acc += fxl * (uc - wl);
+  acc += fxr * (uc - wr);
+  acc += fyd * (uc - wd);
+  acc += fyt * (uc - wt);
+  acc += fzb * (uc - wb);
+  acc += fzf * (uc - wf);
+  return acc;
 }
 
 // The stencil of stencil<T, DIM> at point i = i0 + lane from a stage's w'
@@ -1203,14 +1258,23 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
     const T* sc = reinterpret_cast<const T*>(stb) + 2 * lane;  // the lane's column (pair layout)
     const T* aw = reinterpret_cast<const T*>(stb + r.vbytes);
     const float* ak = (A::kK > 0 && aux.kap) ? reinterpret_cast<const float*>(aw + A::kW) : nullptr;
+    const float* af = (A::kF > 0 && aux.fc) ? reinterpret_cast<const float*>(aw + A::kW) : nullptr;
     const T wp = ok ? aw[4 + lane] : T(0);
     // (2D: the division per point measured faster than the incremental form)
     if constexpr (DIM == 2) {
       px = i % n;
       py = i / n;
     }
-    T znum = ok ? s2t * stencil_staged<T, DIM>(aw, ak, kappa, i, i0, lane, n, px, py, pz) : T(0);
+    T znum = T(0);
     if constexpr (DIM == 3) {
+      if (af)
+        znum = ok ? s2t * stencil_faces<T>(aw, af, i0, lane, n) : T(0);
+      else
+        znum = ok ? s2t * stencil_staged<T, DIM>(aw, ak, kappa, i, i0, lane, n, px, py, pz) : T(0);
+    } else {
+      znum = ok ? s2t * stencil_staged<T, DIM>(aw, ak, kappa, i, i0, lane, n, px, py, pz) : T(0);
+    }
+    if (DIM == 3 && !af) {
       px += NW * 32;  // the next trip's point
       while (px >= n) {
         px -= n;
@@ -1368,6 +1432,9 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   auxs.kap = (tk.kappa && ((unsigned long long)tk.kappa & 15ull) == 0 && (N & 3) == 0)
                  ? tk.kappa
                  : nullptr;
+  // face coefficients: the FP32 3D passes only (the FP64 ones keep FP64 faces)
+  auxs.fc = (DIM == 3 && sizeof(T) == 4) ? tk.faces : nullptr;
+  auxs.fs = tk.fstride;
   auxs.n = n;
   auxs.N = N;
   auxs.ldv = w.ldv;

@@ -29,6 +29,9 @@ struct mlgmres {
   void* V = nullptr;
   void* W0 = nullptr;
   void* W1 = nullptr;
+  void* W0_alloc = nullptr;  // W0's allocation (W0 may start past a zero pad)
+  float* faces = nullptr;    // FP32 face coefficients (single 3D FP32 solves with kappa)
+  long long fstride = 0;     // their array stride
   double* part = nullptr;
   unsigned long long* bar = nullptr;  // per group: counter
   int* err = nullptr;                 // per group: error flag

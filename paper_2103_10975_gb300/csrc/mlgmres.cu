@@ -285,6 +285,9 @@ void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps
       kp.compact = 1;  // V slices in shared memory, two CTAs per SM
     }
   }
+  // face coefficients from the current kappa (one pass over the grid)
+  if (ntasks == 1 && h->htasks[0].faces)
+    CK(launch_kappa_faces(h->grid.n, h->grid.kappa_dev, h->faces, h->fstride, s));
   kp.ngroups = ngroups;
   kp.group_first = h->dcfg;
   kp.task_first = h->dcfg + (ngroups + 1);
@@ -317,6 +320,11 @@ void stage_single(mlgmres* h, const SolveTask& t, int nblocks) {
   h->hcfg[3] = 1;
   h->hcfg[4] = 0;
   h->htasks[0] = t;
+  // the handle's own 3D grid: the FP32 passes use its face coefficients
+  if (h->faces && t.kappa == h->grid.kappa_dev && t.n == h->grid.n) {
+    h->htasks[0].faces = h->faces;
+    h->htasks[0].fstride = h->fstride;
+  }
   h->hwork[0] = single_group_work(h, nblocks);
 }
 
@@ -604,7 +612,24 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     h->vsmem = single_vsmem(h, h->blocks, force_compact);
     const size_t es = h->fp32 ? sizeof(float) : sizeof(double);
     CK(cudaMalloc(&h->V, es * (size_t)vrows_p(opt->m + 1) * h->ldv));
-    CK(cudaMalloc(&h->W0, es * (size_t)h->ldv));
+    if (grid->dim == 3 && grid->kappa_dev && h->fp32) {
+      // the FP32 passes read the operator's face coefficients instead of
+      // forming harmonic means per point; w' and the coefficient arrays get
+      // zero pads of n^2 + 64 points at both ends, so that no stencil window
+      // of a bulk-copy stage is ever clipped (every stage takes the fast path)
+      const long long pad = ((long long)h->grid.n * h->grid.n + 64 + 63) / 64 * 64;
+      h->fstride = h->ldv + 2 * pad;
+      CK(cudaMalloc(&h->W0_alloc, es * (size_t)h->fstride));
+      CK(cudaMemset(h->W0_alloc, 0, es * (size_t)h->fstride));
+      h->W0 = (char*)h->W0_alloc + es * pad;
+      float* f = nullptr;
+      CK(cudaMalloc(&f, sizeof(float) * 4 * (size_t)h->fstride));
+      CK(cudaMemset(f, 0, sizeof(float) * 4 * (size_t)h->fstride));
+      h->faces = f + pad;
+    } else {
+      CK(cudaMalloc(&h->W0_alloc, es * (size_t)h->ldv));
+      h->W0 = h->W0_alloc;
+    }
     CK(cudaMalloc(&h->W1, es * (size_t)h->ldv));
     CK(cudaMalloc(&h->part, sizeof(double) * part_doubles(kPartStride)));
     h->group_cap = 1;
@@ -676,7 +701,8 @@ void mlgmres_destroy(mlgmres_t h) {
   cudaFree(h->Wb);
   cudaFree(h->partb);
   cudaFree(h->V);
-  cudaFree(h->W0);
+  cudaFree(h->W0_alloc);
+  if (h->faces) cudaFree(h->faces - (h->fstride - h->ldv) / 2);
   cudaFree(h->W1);
   cudaFree(h->part);
   cudaFree(h->bar);

@@ -11,6 +11,9 @@ constexpr int kMaxM = 64;          // largest supported restart length
 // bucket limits of the compact (2 CTAs per SM) variants: m <= 47 (2D), m <= 55 (3D)
 constexpr int kCompactM2 = 48;
 constexpr int kCompactM3 = 56;
+// restart lengths up to which the FP32 2D shared-slice variant runs its m <= 32
+// instantiation (fewer buckets of j, less code)
+constexpr int kSmallM = 32;
 // Where a launch keeps the basis V (one kernel variant each):
 constexpr int kVDirect = 0;  // HBM, loaded into registers by the passes
 constexpr int kVShared = 1;  // each CTA's slice in shared memory (2D)
@@ -44,6 +47,12 @@ struct SolveTask {
   double* x;             // guess in, solution out
   const double* x_alt;   // optional competing guess (learned), may be null
   const float* kappa;    // 3D cell coefficients, may be null
+  // FP32 face coefficients of the 3D operator (or null: formed from kappa per
+  // point): four arrays fx, fy, fz, fb at faces + a * fstride, each padded
+  // with zeros far enough past both ends that no stencil window is clipped;
+  // set only with a work vector W0 padded the same way (single 3D solves)
+  const float* faces = nullptr;
+  long long fstride = 0;
   DevResult* res;
   double* hist;          // optional |g_{j+1}|/||b|| per step (Arnoldi mode: H)
   long long hist_cap;
@@ -109,6 +118,12 @@ int gmres_compact_cap(int dim, int m, int P);
 int gmres_compact_vsmem_budget();
 
 // FP64 operator application out = A u (2D or 3D) on one grid.
+// The FP32 face coefficients of the 3D variable-coefficient operator (see
+// SolveTask::faces): fx/fy/fz(i) = harmonic mean of kappa_i and its +x/+y/+z
+// neighbour (0 on the domain's upper walls), fb(i) = kappa_i times the number
+// of the point's wall faces.
+cudaError_t launch_kappa_faces(int n, const float* kappa, float* faces, long long fstride,
+                               cudaStream_t s);
 cudaError_t launch_apply(int dim, int n, const float* kappa, const double* u, double* out,
                          cudaStream_t s);
 
