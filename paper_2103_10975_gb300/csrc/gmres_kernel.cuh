@@ -818,7 +818,6 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
                                           XCarry<T>& cy) {
   static_assert(DIM == 2, "shared-memory slices are a 2D variant");
   constexpr int LMAX = MAXM + 2;
-  constexpr int U = 2;
   using T2 = typename Vec2<T>::type;
   const int tid = threadIdx.x;
   T2 acc[K / 2];
@@ -827,47 +826,35 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
   T accZ = T(0);
   const T inv = sm.invT;
   const T cj = sm.cv[j];
-  for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
-    const bool first = i0 == lo + tid;
-    int ii[U];
-    bool ok_[U];
-    T wp[U], znum[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      ii[u] = i0 + u * BS;
-      ok_[u] = ii[u] < hi;
-    }
-    if (first && cy.pre) {
+  // one point per trip, the loop not unrolled: the body sits in the
+  // instruction stream once (the step's code is what bounds it at this size)
+  int t = 0;
+#pragma unroll 1
+  for (int i = lo + tid; i < hi; i += BS, t++) {
+    T wp, znum;
+    if (t < 2 && cy.pre) {
       // the same differences, in the same order, as stencil2d
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        const T uc = cy.c[u];
-        wp[u] = uc;
-        znum[u] = ok_[u] ? s2t * (((uc - cy.l[u]) + (uc - cy.r[u])) +
-                                  ((uc - cy.d[u]) + (uc - cy.t[u])))
-                         : T(0);
-      }
+      const bool s1 = t == 1;
+      const T uc = s1 ? cy.c[1] : cy.c[0];
+      const T l = s1 ? cy.l[1] : cy.l[0], r = s1 ? cy.r[1] : cy.r[0];
+      const T d = s1 ? cy.d[1] : cy.d[0], tp = s1 ? cy.t[1] : cy.t[0];
+      wp = uc;
+      znum = s2t * (((uc - l) + (uc - r)) + ((uc - d) + (uc - tp)));
     } else {
-#pragma unroll
-      for (int u = 0; u < U; u++) wp[u] = ok_[u] ? ldcg(WP + ii[u]) : T(0);
-#pragma unroll
-      for (int u = 0; u < U; u++)
-        znum[u] = ok_[u] ? s2t * stencil<T, DIM>(WP, ii[u], n, kappa, wp[u]) : T(0);
+      wp = ldcg(WP + i);
+      znum = s2t * stencil<T, DIM>(WP, i, n, kappa, wp);
     }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      if (!ok_[u]) continue;
-      const T* vc = Vs + vbase(ii[u] - lo, rows);
-      T sv, sz;
-      x_proj<T, MAXM, BS, K>(sm, vc, j, sv, sz);
-      const T vj = (wp[u] - sv) * inv;
-      const T z = ((znum[u] - sz) - cj * vj) * inv;
-      store_vj(Vs + vbase(ii[u] - lo, rows), j, vj);
-      Z[ii[u]] = z;
-      if (first) cy.z[u] = z;
-      accZ += z * z;
-      x_dots<T, K>(acc, vc, j, z);
-    }
+    const T* vc = Vs + vbase(i - lo, rows);
+    T sv, sz;
+    x_proj<T, MAXM, BS, K>(sm, vc, j, sv, sz);
+    const T vj = (wp - sv) * inv;
+    const T z = ((znum - sz) - cj * vj) * inv;
+    store_vj(Vs + vbase(i - lo, rows), j, vj);
+    Z[i] = z;
+    if (t == 0) cy.z[0] = z;
+    if (t == 1) cy.z[1] = z;
+    accZ += z * z;
+    x_dots<T, K>(acc, vc, j, z);
   }
   warp_slots_k2<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accZ);
@@ -879,33 +866,22 @@ __device__ __forceinline__ void y_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
                                           const T* __restrict__ Vs, int rows,
                                           const XCarry<T>& cy) {
   constexpr int LMAX = MAXM + 2;
-  constexpr int U = 2;  // the X pass's points per trip (its first trip's z is in cy)
   using T2 = typename Vec2<T>::type;
   const int tid = threadIdx.x;
   T2 acc[K / 2];
 #pragma unroll
   for (int q = 0; q < K / 2; q++) acc[q] = dup2<T2>(T(0));
   T accN = T(0);
-  for (int i0 = lo + tid; i0 < hi; i0 += U * BS) {
-    const bool first = i0 == lo + tid;
-    int ii[U];
-    bool ok_[U];
-    T q[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      ii[u] = i0 + u * BS;
-      ok_[u] = ii[u] < hi;
-      q[u] = ok_[u] ? (first ? cy.z[u] : Z[ii[u]]) : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      if (!ok_[u]) continue;
-      const T* vc = Vs + vbase(ii[u] - lo, rows);
-      const T qv = q[u] - y_proj<T, MAXM, BS, K>(sm, vc, j);
-      WP[ii[u]] = qv;
-      accN += qv * qv;
-      y_dots<T, K>(acc, vc, j, qv);
-    }
+  int t = 0;
+#pragma unroll 1
+  for (int i = lo + tid; i < hi; i += BS, t++) {
+    // z of the thread's first two points is in cy (the X pass kept it)
+    const T q = t == 0 ? cy.z[0] : (t == 1 ? cy.z[1] : Z[i]);
+    const T* vc = Vs + vbase(i - lo, rows);
+    const T qv = q - y_proj<T, MAXM, BS, K>(sm, vc, j);
+    WP[i] = qv;
+    accN += qv * qv;
+    y_dots<T, K>(acc, vc, j, qv);
   }
   warp_slots_k2<LMAX, K, T>(sm.red, acc, j + 1);
   warp_slot<LMAX>(sm.red, j + 1, accN);
