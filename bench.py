@@ -50,14 +50,17 @@ TRAIN_EVERY = 10
 # of the steps and saves 13% of the iterations.
 LEARN = dict(train_iters=64, lr=2e-3, batch=8, guess_smooth=32, overlap_train=1)
 METRIC = "time-to-solution per time step (ms) and GMRES iters, learned vs plain GMRES, rel res 1e-10"
-# DRAM bytes per Arnoldi step of gmres_persistent<float, 2, 64, 256, shared V>
+# DRAM bytes per Arnoldi step of gmres_persistent<float, 2, 32, 256, shared V>
 # on this workload, from one ncu capture of a 300-step solve of the kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum = 1.237 MB + 0.026 MB); scaled
+# (dram__bytes_read.sum + dram__bytes_write.sum = 1.192 MB + 0.022 MB); scaled
 # to a launch by its steps.
-DRAM_BYTES_PER_STEP = 1.263e6 / 300
-# the same for the compact bulk-copy variant at 2048^2, GMRES(40): 61.31 GB over
-# an 80-step (two-cycle) capture
-DRAM_BYTES_PER_STEP_2048 = 61.31e9 / 80
+DRAM_BYTES_PER_STEP = 1.214e6 / 300
+# the same for the compact bulk-copy variant at 2048^2, GMRES(40): 58.76 GB +
+# 5.30 GB over an 80-step (two-cycle) capture
+DRAM_BYTES_PER_STEP_2048 = 64.06e9 / 80
+# and for the 192^3 variable-kappa kernel, GMRES(50): 172.26 GB + 11.52 GB over a
+# 100-step (two-cycle) capture
+DRAM_BYTES_PER_STEP_3D = 183.78e9 / 100
 WORKLOAD = ("2D Poisson -Lap u = f, 256x256 interior (N=65,536), zero Dirichlet, 5-point; "
             "3 moving signed Gaussians (sigma 0.1), 500-step series seed 2001; GMRES(30) "
             "rel tol 1e-10 (true FP64 residual)")
@@ -84,6 +87,9 @@ def parse():
     ap.add_argument("--c5-steps", type=int, default=0,
                     help="full time steps of the 192^3 variable-kappa workload to time "
                          "(0 = none; about a minute each)")
+    ap.add_argument("--grid-blocks", type=int, default=0,
+                    help="CTAs of the headline solver (0 = autotuned); fixes its launch "
+                         "shape, e.g. for a profiler run whose timings would steer the autotuner")
     return ap.parse_args()
 
 
@@ -393,7 +399,8 @@ def run_ours(args):
 
     # ---- our arm: learned guess + FP32/FP64 refinement
     sol = pkg.Solver(n, m=M, rtol=RTOL, precision="fp32_refine", guess="learned",
-                     fallback="prev", warmup_steps=TAU0, seed=7 + rank, **LEARN)
+                     fallback="prev", warmup_steps=TAU0, seed=7 + rank,
+                     grid_blocks=args.grid_blocks, **LEARN)
     tuning = sol.autotune(B[0])                          # launch shape (untimed, cached)
     warm = []
     run_series(sol, 0, TAU0, True, False, warm, drain=False)   # online warm-up (collect, train)
@@ -424,7 +431,12 @@ def run_ours(args):
     traffic = DRAM_BYTES_PER_STEP * statistics.mean(r["iters"] for r in res)
     us_step = 1e3 * tos / max(1, sum(r["iters"] for r in res))
     # the step's latency floor: its two group exchanges alone at the same CTA count
-    floor_us = pkg.exchange_floor(tuning["grid_blocks"], M, 3000)
+    # (None when the probe cannot run, e.g. its co-residency check under a profiler)
+    try:
+        floor_us = pkg.exchange_floor(tuning["grid_blocks"], M, 3000)
+    except pkg.MLGMRESError as e:
+        print("exchange floor probe unavailable: %s" % e, file=sys.stderr)
+        floor_us = None
 
     # ---- end to end through the public API with host buffers
     Bh = torch.stack([torch.as_tensor(gen.rhs(t)) for t in range(TAU0 + W + K, TAU0 + W + 2 * K)])
@@ -630,8 +642,10 @@ def roofline_3d(pkg, torch, dev, hbm, peak_kind, n=192, m=50, steps=300):
     byts = algorithmic_bytes(r, N, m, 4, kappa=True)
     ach = byts / (r["tos_ms"] * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "peak_source": peak_kind, "traffic": None,
-            "frac_two_pass": (two_pass_bytes(r, N, m, 4) + 4.0 * N * r["iters"])
+            "peak_source": peak_kind, "traffic": DRAM_BYTES_PER_STEP_3D * r["iters"],
+            # the bytes the two-pass step moves, with the four FP32 face
+            # coefficient arrays in place of kappa
+            "frac_two_pass": (two_pass_bytes(r, N, m, 4) + 16.0 * N * r["iters"])
             / (r["tos_ms"] * 1e-3) / 1e9 / hbm,
             "workload": "192^3 variable kappa (log-normal, seed 5001), 7-point, GMRES(50) FP32 "
                         "cycles, one solve from x0 = 0 capped at %d Arnoldi steps" % steps,

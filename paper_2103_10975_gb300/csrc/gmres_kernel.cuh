@@ -984,11 +984,10 @@ struct AuxSrc {  // what the X pass's stages copy besides V
 // so the stage's phase cannot complete early.
 template <int NW, typename T, int DIM>
 __device__ __forceinline__ void bulk_issue_stage(const BulkRing& r, const T* V, int lo, int rows,
-                                                 int q, const AuxSrc* aux, const T* Zsrc,
+                                                 int q, int sidx, const AuxSrc* aux, const T* Zsrc,
                                                  long long ldv) {
   using A = Aux<T, DIM>;
   constexpr int ALN = 16 / (int)sizeof(T);
-  const int sidx = q % r.P;
   const int i0 = lo + (int)((threadIdx.x >> 5) + NW * q) * 32;
   unsigned char* st = r.st + (size_t)sidx * r.bytes;
   T* at = reinterpret_cast<T*>(st + r.vbytes);
@@ -1207,7 +1206,7 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
   asm volatile("fence.proxy.async.global;" ::: "memory");
   if (lane == 0)
     for (int q = 0; q < r.P && q < nq; q++)
-      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q, &aux, nullptr, aux.ldv);
+      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q, q, &aux, nullptr, aux.ldv);
   bool good = true;
   // grid coordinates of this lane's point, advanced by NW * 32 points per trip
   // (integer divisions once per pass instead of once per point)
@@ -1220,8 +1219,8 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
     pz = DIM == 3 ? t / n : 0;
   }
   int q = 0;
-  for (; q < nq; q++) {
-    const int sidx = q % r.P;
+  // stage slot of trip q (q mod P, kept as a running index: no division)
+  for (int sidx = 0; q < nq; q++, sidx = sidx + 1 == r.P ? 0 : sidx + 1) {
     const int i0 = lo + (warp + NW * q) * 32;
     const int i = i0 + lane;
     const bool ok = i < hi;
@@ -1275,7 +1274,7 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
     }
     __syncwarp();
     if (lane == 0 && q + r.P < nq)
-      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q + r.P, &aux, nullptr, aux.ldv);
+      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q + r.P, sidx, &aux, nullptr, aux.ldv);
   }
   if (!good) bulk_drain(r, pp, q, nq, phase);
   // the V_j and z stores above are read by later bulk copies (async proxy)
@@ -1304,11 +1303,11 @@ __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
   const BulkRing r = bulk_ring<T>(pp, j + 1, j + 1, A::kYBytes);
   if (lane == 0)
     for (int q = 0; q < r.P && q < nq; q++)
-      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q, nullptr, Z, ldv);
+      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q, q, nullptr, Z, ldv);
   bool good = true;
   int q = 0;
-  for (; q < nq; q++) {
-    const int sidx = q % r.P;
+  // stage slot of trip q (q mod P, kept as a running index: no division)
+  for (int sidx = 0; q < nq; q++, sidx = sidx + 1 == r.P ? 0 : sidx + 1) {
     const int i = lo + (warp + NW * q) * 32 + lane;
     const bool ok = i < hi;
     if (!mbar_wait(&r.bars[sidx], (phase >> sidx) & 1u, pp.err, pp.timeout_ns)) {
@@ -1326,7 +1325,7 @@ __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
     }
     __syncwarp();
     if (lane == 0 && q + r.P < nq)
-      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q + r.P, nullptr, Z, ldv);
+      bulk_issue_stage<NW, T, DIM>(r, V, lo, rows, q + r.P, sidx, nullptr, Z, ldv);
   }
   if (!good) bulk_drain(r, pp, q, nq, phase);
   warp_slots_k2<LMAX, K, T>(sm.red, acc, j + 1);
