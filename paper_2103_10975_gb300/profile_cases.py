@@ -4,6 +4,7 @@
     python -m paper_2103_10975_gb300.profile_cases nn --n 256 --batch 8
     python -m paper_2103_10975_gb300.profile_cases batch --count 512 --nmax 512
     python -m paper_2103_10975_gb300.profile_cases cube --n 192 --max-iters 500
+    python -m paper_2103_10975_gb300.profile_cases cube --n 192 --compact 1 --blocks 304 --stages 4
 
     python -m paper_2103_10975_gb300.profile_cases dipole --n 64 --T 200
     python -m paper_2103_10975_gb300.profile_cases floor --ctas 128 --m 30
@@ -91,7 +92,7 @@ def batch_case(count, nmin, nmax, rtol, m, stages=-1, compact=-1):
              sorted(set(r["status"] for r in res))))
 
 
-def cube_case(n, m, max_iters, stages=-1, autotune=False):
+def cube_case(n, m, max_iters, stages=-1, autotune=False, blocks=0, compact=-1):
     """192^3 variable-coefficient Poisson (log-normal kappa, seed 5001), FP32-refined
     GMRES(m) capped at max_iters steps; prints the device time per step."""
     import torch
@@ -100,7 +101,7 @@ def cube_case(n, m, max_iters, stages=-1, autotune=False):
     kap = lognormal_kappa(n, 5001).astype("float32")
     b = torch.as_tensor(MovingGaussians3D(n, 5001, 200).rhs(0)).cuda()
     s = Solver(n, dim=3, kappa=kap, m=m, rtol=1e-10, precision="fp32_refine",
-               max_iters=max_iters, v_stages=stages)
+               max_iters=max_iters, v_stages=stages, grid_blocks=blocks, compact=compact)
     if autotune:
         print("autotune:", s.autotune(b, retune=True))
     s.solve(b)
@@ -199,6 +200,8 @@ def main(argv=None):
     d.add_argument("--max-iters", type=int, default=500)
     d.add_argument("--stages", type=int, default=-1)
     d.add_argument("--autotune", action="store_true")
+    d.add_argument("--blocks", type=int, default=0)
+    d.add_argument("--compact", type=int, default=-1)
     e = sub.add_parser("dipole")
     e.add_argument("--n", type=int, default=64)
     e.add_argument("--T", type=int, default=200)
@@ -224,7 +227,8 @@ def main(argv=None):
     elif args.case == "dipole":
         dipole_case(args.n, args.T, args.tau0, args.train_iters, args.lr, args.k)
     else:
-        cube_case(args.n, args.m, args.max_iters, args.stages, args.autotune)
+        cube_case(args.n, args.m, args.max_iters, args.stages, args.autotune, args.blocks,
+                  args.compact)
 
 
 if __name__ == "__main__":
