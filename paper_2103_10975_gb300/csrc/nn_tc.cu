@@ -388,6 +388,202 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ 
   }
 }
 
+// ---------------------------------------------- weight gradient (tcgen05) --
+// part[cta][(tap*32 + k)*32 + o] = sum_p in[p + dil*off(tap)][k] g[p][o], and
+// the bias partials sum_p g[p][o] at 9*1024 + o (2D).  The pixels are the
+// reduction dimension: per x offset tx of a tap, D_tx[m][o] += A[m][q] B[q][o]
+// over the 128 pixels q of each tile, M = 128 rows m = ty*32 + k (the three
+// taps (ty, tx) times the 32 input channels, and in rows 96..127 a row of
+// ones, which makes D_tx[96][o] the sum of g), N = 32 output channels, one
+// accumulator in tensor memory per tx, kept over all of the CTA's tiles.
+// Both operands are MN-major in the no-swizzle layout (core matrices of 8 K
+// rows x 16 bytes of M or N): the staged rows are [8-channel block][pixel][8]
+// with blocks kLboA bytes apart (the stride offset, between 8-row M or N
+// groups) and 8-pixel groups 128 bytes apart (the leading offset, along K).
+// Staged rows follow each other 4 blocks apart, so the taps ty = 0, 1, 2 of
+// one tx and the row of ones are M groups 0-3, 4-7, 8-11, 12-15 of a single
+// operand, and the tap's x offset moves its start address by 16 bytes per
+// pixel.  Warp roles as in conv32_tc: a producer warp (TMA), an MMA warp, four
+// epilogue warps that read the accumulators once, at the end.
+constexpr int kWgRows = 5;  // per stage: input rows y - dil, y, y + dil, ones, g's row
+constexpr int kWgStageBytes = kWgRows * kRowBytes;
+constexpr int kWgStages = 2;
+constexpr int kWgSmem = kWgStages * kWgStageBytes + 128;
+constexpr int kWgTx = 16 * kBox;  // 3 input rows and g's row, 4 boxes each
+// D F32, A and B BF16 and MN-major, N = 32, M = 128
+constexpr unsigned kIdescWg = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                              ((32u >> 3) << 17) | ((128u >> 4) << 24);
+static_assert(kWgStageBytes % 128 == 0, "stages must keep 128-byte alignment");
+
+__device__ __forceinline__ void tc_mma_wg(unsigned tmem, unsigned long long a,
+                                          unsigned long long b, unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdescWg), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_row4d(const CUtensorMap* tmap, unsigned dst, int c, int x,
+                                          int y, int b, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(c), "r"(x), "r"(y), "r"(b), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads) wgrad_tc(const __grid_constant__ CUtensorMap tin,
+                                                       const __grid_constant__ CUtensorMap tg,
+                                                       int B, int H, int dil,
+                                                       float* __restrict__ part, int stride,
+                                                       int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char wg_smem[];
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(wg_smem + kWgStages * kWgStageBytes);
+  unsigned long long* empty = full + kWgStages;  // the MMAs of a stage have completed
+  unsigned long long* done = empty + kWgStages;  // every MMA of the CTA has completed
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(done + 1);
+  int* prog = reinterpret_cast<int*>(tmem_slot + 1);  // [0] stages issued, [1] consumed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the row of ones of each stage (BF16 1.0), written once; the copies never touch it
+  for (int st = 0; st < kWgStages; st++) {
+    unsigned* ones = reinterpret_cast<unsigned*>(wg_smem + st * kWgStageBytes + 3 * kRowBytes);
+    for (int i = threadIdx.x; i < kRowBytes / 4; i += blockDim.x) ones[i] = 0x3F803F80u;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kWgStages; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(full + i)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(empty + i)) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(done)) : "memory");
+    prog[0] = prog[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     saddr(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+  const unsigned as0 = saddr(wg_smem);
+  const int tpr = (H + kTcM - 1) / kTcM;
+  const long long ntiles = (long long)B * H * tpr;
+  const long long K = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  if (warp == 0) {
+    // ---- producer: the rows of tile k into stage k % kWgStages once its MMAs are done
+    if (lane == 0) {
+      for (long long k = 0; k < K; k++) {
+        const int st = (int)(k % kWgStages);
+        const long long use = k / kWgStages;
+        if (use > 0 && !mbar_wait_tc(saddr(empty + st), (unsigned)((use - 1) & 1))) {
+          atomicExch(err, 1);
+          break;
+        }
+        int b, z, y, x0;
+        tile_coords<2>(blockIdx.x + k * gridDim.x, H, tpr, b, z, y, x0);
+        const unsigned as = as0 + (unsigned)st * kWgStageBytes;
+        const unsigned bar = saddr(full + st);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(kWgTx)
+                     : "memory");
+        for (int ty = 0; ty < 3; ty++)
+          for (int kc = 0; kc < 4; kc++)
+            tma_row4d(&tin, as + ty * kRowBytes + kc * kLboA, 8 * kc, x0 - dil,
+                      y + dil * (ty - 1), b, bar);
+        for (int kc = 0; kc < 4; kc++)
+          tma_row4d(&tg, as + 4 * kRowBytes + kc * kLboA, 8 * kc, x0, y, b, bar);
+        prog[0] = (int)(k + 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issue: 8 K-steps of 16 pixels x 3 taps x per tile, into accumulator tx
+    if (lane == 0) {
+      long long k = 0;
+      for (; k < K; k++) {
+        const int st = (int)(k % kWgStages);
+        if (!mbar_wait_tc(saddr(full + st), (unsigned)((k / kWgStages) & 1))) break;
+        prog[1] = (int)(k + 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned as = as0 + (unsigned)st * kWgStageBytes;
+        for (int ks = 0; ks < kTcM / 16; ks++) {
+          const unsigned q = (unsigned)ks * 16u * 16u;  // the K-step's first pixel, in bytes
+          const unsigned long long bdesc = mdesc(as + 4 * kRowBytes + q, 128, kLboA);
+          for (int tx = 0; tx < 3; tx++)
+            tc_mma_wg(tmem + 32u * tx, mdesc(as + (unsigned)(dil * tx) * 16u + q, 128, kLboA),
+                      bdesc, (k | ks) ? 1u : 0u);
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                saddr(empty + st))
+            : "memory");
+      }
+      if (k < K) atomicExch(err, 1);
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              saddr(done))
+          : "memory");
+    }
+  } else {
+    // ---- epilogue: the three accumulators (and the bias sums) into the partial
+    const int lq = warp & 3;  // TMEM lane quarter: rows 32 lq .. 32 lq + 31
+    float* dst = part + (long long)blockIdx.x * stride;
+    const bool okw = __all_sync(0xffffffffu, mbar_wait_tc(saddr(done), 0u));
+    if (!okw) {
+      if (lane == 0) atomicExch(err, 1);
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int tx = 0; tx < 3; tx++) {
+        unsigned r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+              "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+              "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+              "=r"(r[31])
+            : "r"(tmem + ((unsigned)(lq * 32) << 16) + 32u * tx));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // (a CTA without tiles wrote no accumulator: its partial is zero)
+        float v[kC];
+#pragma unroll
+        for (int o = 0; o < kC; o++) v[o] = K > 0 ? __uint_as_float(r[o]) : 0.f;
+        if (lq < 3) {
+          const int tap = lq * 3 + tx, kin = lane;
+          float4* d4 = reinterpret_cast<float4*>(dst + (long long)(tap * kC + kin) * kC);
+#pragma unroll
+          for (int q4 = 0; q4 < 8; q4++)
+            d4[q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+        } else if (tx == 0 && lane == 0) {
+#pragma unroll
+          for (int o = 0; o < kC; o++) dst[9 * kC * kC + o] = v[o];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // copies still in flight (only after a wait ran out) land before the CTA
+    // leaves, and every MMA issued has completed (bounded waits)
+    for (int k = prog[1]; k < prog[0]; k++)
+      mbar_wait_tc(saddr(full + k % kWgStages), (unsigned)((k / kWgStages) & 1));
+    mbar_wait_tc(saddr(done), 0u);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+  }
+}
+
 int* g_tc_err = nullptr;  // set by a tile whose MMAs did not complete in time
 
 // Rows of at least this many points go to the tcgen05 kernel (128, a full
@@ -450,6 +646,7 @@ cudaError_t conv32_tc_setup() {
   if (g_tc_err) return cudaSuccess;
   set_tc_smem<2>();
   set_tc_smem<3>();
+  cudaFuncSetAttribute(wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
@@ -504,6 +701,40 @@ cudaError_t launch_conv32_tc(int dim, int mode, int B, int H, const __nv_bfloat1
     launch_tc<3>(mode, grid, s, tm, B, H, wop, bias, dil, sign, zo, to, resid, fo, addend);
   else
     launch_tc<2>(mode, grid, s, tm, B, H, wop, bias, dil, sign, zo, to, resid, fo, addend);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// A tensor map over a channels-last 2D activation [B][H][H][32] (BF16): boxes of
+// 8 channels x kRows pixels of one row.
+static bool encode_rows_2d(CUtensorMap* tm, const __nv_bfloat16* p, int B, int H) {
+  const cuuint64_t row = (cuuint64_t)kC * 2;
+  const cuuint64_t h = (cuuint64_t)H;
+  const cuuint64_t dims[4] = {(cuuint64_t)kC, h, h, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {row, row * h, row * h * h};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kRows, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)p, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+cudaError_t launch_wgrad_tc(int B, int H, const __nv_bfloat16* in, const __nv_bfloat16* g,
+                            int dil, float* part, int stride, int nparts, cudaStream_t s) {
+  if (!g_tc_err) {
+    const cudaError_t e = conv32_tc_setup();
+    if (e != cudaSuccess) return e;
+  }
+  if (dil < 1 || dil > 2 || nparts < 1 || stride < 9 * kC * kC + kC ||
+      ((unsigned long long)in & 15ull) || ((unsigned long long)g & 15ull) ||
+      ((unsigned long long)part & 15ull) || (stride & 3))
+    return cudaErrorInvalidValue;
+  CUtensorMap tin, tg;
+  if (!encode_rows_2d(&tin, in, B, H) || !encode_rows_2d(&tg, g, B, H))
+    return cudaErrorInvalidValue;
+  // every one of the nparts CTAs writes its partial (zeros without tiles)
+  wgrad_tc<<<nparts, kTcThreads, kWgSmem, s>>>(tin, tg, B, H, dil, part, stride, g_tc_err);
   note_launches(1);
   return cudaGetLastError();
 }
