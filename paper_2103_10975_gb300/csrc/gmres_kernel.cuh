@@ -1622,7 +1622,11 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         sm.HuT[j + 1 + j * LD] = hnT;  // (the Givens warp reads it in FP64)
         sm.cv[j + 1] = hnT * sm.coef[j];
       };
-      if (tid < 32) {
+      // the norm runs on the last warp while the c_i rows (below) leave it idle
+      // (rows 4w .. 4w+3 per warp w: the last warp's rows exceed j for small j),
+      // else on warp 0
+      const int nwarp = j < 4 * (BS / 32 - 1) ? BS / 32 - 1 : 0;
+      if ((tid >> 5) == nwarp) {
         T q = T(0);
         for (int k = lane; k <= j; k += 32) q += sm.coef[k] * sm.coef[k];
         q = warp_sum(q);
@@ -1640,7 +1644,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       // column j is h1 + h2 and h2 is the gather's output (no read of what this
       // phase writes); eight lanes per row, each a strided part of the sum,
       // added in a fixed order
-      for (int i0 = 0; i0 <= j; i0 += BS / 8) {
+      for (int i0 = 0; i0 <= j && ((tid >> 5) != nwarp || nwarp == 0); i0 += BS / 8) {
         const int i = i0 + (tid >> 3);
         const int sub = tid & 7;
         const int ir = min(i, j);
