@@ -162,16 +162,18 @@ def test_compact_variant(n, blocks):
     assert abs(r["iters"] - r0["iters"]) <= max(3, r0["iters"] // 100), (r["iters"], r0["iters"])
 
 
-def test_compact_variant_3d():
-    """The 3D compact variant (two CTAs per SM; m = 40 so that a stage of m
-    rows fits next to the 3D shared state) on variable kappa against the
+@pytest.mark.parametrize("m,stages", [(40, -1), (50, 4)])
+def test_compact_variant_3d(m, stages):
+    """The 3D compact variant (two CTAs per SM; GMRES(50) with four stages per
+    warp is the shape the autotuner picks at 192^3) on variable kappa, through
+    the face-coefficient stencil and its zero-padded windows, against the
     oracle's solution."""
     n = 24
     kap = lognormal_kappa(n, 5001, smooth_sigma=2.0).astype(np.float32)
     b = MovingGaussians3D(n, 5001, 200).rhs(7)
     xr, _, _ = native.gmres(3, n, b, m=50, rtol=1e-13, kappa=kap.astype(np.float64))
-    s = Solver(n, dim=3, kappa=kap, m=40, rtol=1e-10, precision="fp32_refine", grid_blocks=60,
-               compact=1)
+    s = Solver(n, dim=3, kappa=kap, m=m, rtol=1e-10, precision="fp32_refine", grid_blocks=60,
+               compact=1, v_stages=stages)
     x, r = s.solve(dev(b))
     assert r["status"] == 0 and r["relres_true"] <= 1e-10
     assert rel(x.cpu().numpy(), xr) <= 1e-7
