@@ -333,16 +333,21 @@ template <int BS, typename R, typename T, bool SKIP1 = false>
 __device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot, T* coef,
                                        int ps) {
   constexpr int NW = BS / 32 - (SKIP1 ? 1 : 0);
+  // slots per warp and round: 4, or 5 without warp 1, so that one round covers
+  // 32 slots either way (a second round is a second L2 round trip)
+  constexpr int Q = SKIP1 ? 5 : 4;
   const int lane = threadIdx.x & 31, warp0 = threadIdx.x >> 5;
   // (warp 1 under SKIP1 starts past every slot)
   const int warp = SKIP1 ? (warp0 == 1 ? (1 << 20) : (warp0 == 0 ? 0 : warp0 - 1)) : warp0;
-  for (int k0 = warp; k0 < L; k0 += 4 * NW) {
-    R s[4] = {R(0), R(0), R(0), R(0)};
-    // 128 partials per round, all 16 loads of a lane issued before any is used
-    for (int g0 = 0; g0 < nb; g0 += 128) {
-      R v[4][4];
+  for (int k0 = warp; k0 < L; k0 += Q * NW) {
+    R s[Q];
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < Q; q++) s[q] = R(0);
+    // 128 partials per round, all loads of a lane issued before any is used
+    for (int g0 = 0; g0 < nb; g0 += 128) {
+      R v[Q][4];
+#pragma unroll
+      for (int q = 0; q < Q; q++) {
         const int k = k0 + q * NW;
 #pragma unroll
         for (int r = 0; r < 4; r++) {
@@ -351,13 +356,13 @@ __device__ __forceinline__ void gather(const R* part, int L, int nb, double* tot
         }
       }
 #pragma unroll
-      for (int q = 0; q < 4; q++) s[q] += (v[q][0] + v[q][1]) + (v[q][2] + v[q][3]);
+      for (int q = 0; q < Q; q++) s[q] += (v[q][0] + v[q][1]) + (v[q][2] + v[q][3]);
     }
 #pragma unroll
-    for (int q = 0; q < 4; q++) s[q] = warp_sum(s[q]);
+    for (int q = 0; q < Q; q++) s[q] = warp_sum(s[q]);
     if (lane == 0) {
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
+      for (int q = 0; q < Q; q++) {
         const int k = k0 + q * NW;
         if (k < L) {
           // FP32 partials: coef only (an FP64 conversion is a long-latency
