@@ -68,7 +68,10 @@ __device__ __forceinline__ int group_arrive_wait(const GroupBarrier& gb, unsigne
   int ok = 1;
   if (ld_acquire_u64(gb.ctr) < target) {
     const unsigned long long t0 = globaltimer_ns();
+    unsigned it = 0;
     while (ld_acquire_u64(gb.ctr) < target) {
+      // the error flag and the clock every eighth poll: a poll is one load
+      if ((++it & 7u) != 0) continue;
       if (*(volatile int*)gb.err != kErrNone) { ok = 0; break; }
       if (globaltimer_ns() - t0 > gb.timeout_ns) {
         atomicCAS(gb.err, kErrNone, kErrTimeout);
