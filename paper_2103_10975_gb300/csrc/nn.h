@@ -120,14 +120,15 @@ cudaError_t conv32_mma_setup();
 // 1 if a tcgen05 convolution tile timed out waiting for its MMAs (0 otherwise).
 int conv32_tc_error();
 // Tensor-core weight gradient partials of a 32 -> 32 convolution (nparts CTAs):
-// part[cta][(tap*32 + k)*32 + o] and the bias sums at 1024 T + o.  2D grids
-// whose rows qualify for the tcgen05 convolution (conv32_tc_applies) take
+// part[cta][(tap*32 + k)*32 + o] and the bias sums at 1024 T + o.  Grids whose
+// rows qualify for the tcgen05 convolution (conv32_tc_applies) take
 // launch_wgrad_tc (tcgen05.mma with the pixels as the reduction dimension).
 cudaError_t launch_wgrad_mma(int dim, int B, int H, const __nv_bfloat16* in,
                              const __nv_bfloat16* g, int dil, float* part, int stride, int nparts,
                              cudaStream_t s);
-cudaError_t launch_wgrad_tc(int B, int H, const __nv_bfloat16* in, const __nv_bfloat16* g,
-                            int dil, float* part, int stride, int nparts, cudaStream_t s);
+cudaError_t launch_wgrad_tc(int dim, int B, int H, const __nv_bfloat16* in,
+                            const __nv_bfloat16* g, int dil, float* part, int stride, int nparts,
+                            cudaStream_t s);
 
 // infer_only: allocate what forward passes need (parameters, BF16 operand
 // copies, activations) and no gradient, Adam or minibatch buffers; such a

@@ -365,8 +365,8 @@ cudaError_t launch_wgrad_mma(int dim, int B, int H, const __nv_bfloat16* in,
                              const __nv_bfloat16* g, int dil, float* part, int stride, int nparts,
                              cudaStream_t s) {
   if (dil < 1 || dil > kMaxDil || (dim != 2 && dim != 3)) return cudaErrorInvalidValue;
-  if (dim == 2 && conv32_tc_applies(2, H))
-    return launch_wgrad_tc(B, H, in, g, dil, part, stride, nparts, s);
+  if (conv32_tc_applies(dim, H))
+    return launch_wgrad_tc(dim, B, H, in, g, dil, part, stride, nparts, s);
   if (dim == 2) {
     wgrad_mma<2><<<nparts, 128, 0, s>>>(B, H, in, g, dil, 1, part, stride);
     note_launches(1);

@@ -390,7 +390,9 @@ __global__ void __launch_bounds__(kTcThreads) conv32_tc(const __grid_constant__ 
 
 // ---------------------------------------------- weight gradient (tcgen05) --
 // part[cta][(tap*32 + k)*32 + o] = sum_p in[p + dil*off(tap)][k] g[p][o], and
-// the bias partials sum_p g[p][o] at 9*1024 + o (2D).  The pixels are the
+// the bias partials sum_p g[p][o] at T*1024 + o (T = 9 taps in 2D, 27 in 3D;
+// a 3D launch covers the nine taps of one plane offset tz, taps 9 tz + 3 ty +
+// tx, and the tz = 0 launch writes the bias partials).  The pixels are the
 // reduction dimension: per x offset tx of a tap, D_tx[m][o] += A[m][q] B[q][o]
 // over the 128 pixels q of each tile, M = 128 rows m = ty*32 + k (the three
 // taps (ty, tx) times the 32 input channels, and in rows 96..127 a row of
@@ -424,18 +426,29 @@ __device__ __forceinline__ void tc_mma_wg(unsigned tmem, unsigned long long a,
       : "memory");
 }
 
-__device__ __forceinline__ void tma_row4d(const CUtensorMap* tmap, unsigned dst, int c, int x,
-                                          int y, int b, unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-      "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(c), "r"(x), "r"(y), "r"(b), "r"(bar)
-      : "memory");
+// One box of a row: (channel c, pixel x, row y, plane z (3D), batch b).
+template <int D>
+__device__ __forceinline__ void tma_row(const CUtensorMap* tmap, unsigned dst, int c, int x,
+                                        int y, int z, int b, unsigned bar) {
+  if (D == 3)
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(c), "r"(x), "r"(y), "r"(z), "r"(b),
+        "r"(bar)
+        : "memory");
+  else
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(c), "r"(x), "r"(y), "r"(b), "r"(bar)
+        : "memory");
 }
 
+template <int D>
 __global__ void __launch_bounds__(kTcThreads) wgrad_tc(const __grid_constant__ CUtensorMap tin,
                                                        const __grid_constant__ CUtensorMap tg,
-                                                       int B, int H, int dil,
+                                                       int B, int H, int dil, int tz,
                                                        float* __restrict__ part, int stride,
                                                        int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char wg_smem[];
@@ -472,7 +485,7 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc(const __grid_constant__ C
   const unsigned tmem = *tmem_slot;
   const unsigned as0 = saddr(wg_smem);
   const int tpr = (H + kTcM - 1) / kTcM;
-  const long long ntiles = (long long)B * H * tpr;
+  const long long ntiles = (long long)B * H * tpr * (D == 3 ? H : 1);
   const long long K = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (warp == 0) {
@@ -486,18 +499,19 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc(const __grid_constant__ C
           break;
         }
         int b, z, y, x0;
-        tile_coords<2>(blockIdx.x + k * gridDim.x, H, tpr, b, z, y, x0);
+        tile_coords<D>(blockIdx.x + k * gridDim.x, H, tpr, b, z, y, x0);
         const unsigned as = as0 + (unsigned)st * kWgStageBytes;
         const unsigned bar = saddr(full + st);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                      "r"(kWgTx)
                      : "memory");
+        // (3D: the input rows of plane z + dil (tz - 1), zeros outside the grid)
         for (int ty = 0; ty < 3; ty++)
           for (int kc = 0; kc < 4; kc++)
-            tma_row4d(&tin, as + ty * kRowBytes + kc * kLboA, 8 * kc, x0 - dil,
-                      y + dil * (ty - 1), b, bar);
+            tma_row<D>(&tin, as + ty * kRowBytes + kc * kLboA, 8 * kc, x0 - dil,
+                       y + dil * (ty - 1), z + dil * (tz - 1), b, bar);
         for (int kc = 0; kc < 4; kc++)
-          tma_row4d(&tg, as + 4 * kRowBytes + kc * kLboA, 8 * kc, x0, y, b, bar);
+          tma_row<D>(&tg, as + 4 * kRowBytes + kc * kLboA, 8 * kc, x0, y, z, b, bar);
         prog[0] = (int)(k + 1);
       }
     }
@@ -532,7 +546,9 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc(const __grid_constant__ C
   } else {
     // ---- epilogue: the three accumulators (and the bias sums) into the partial
     const int lq = warp & 3;  // TMEM lane quarter: rows 32 lq .. 32 lq + 31
+    constexpr int T = D == 3 ? 27 : 9;
     float* dst = part + (long long)blockIdx.x * stride;
+    float* dw = dst + (D == 3 ? (long long)tz * 9 * kC * kC : 0);
     const bool okw = __all_sync(0xffffffffu, mbar_wait_tc(saddr(done), 0u));
     if (!okw) {
       if (lane == 0) atomicExch(err, 1);
@@ -557,13 +573,13 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc(const __grid_constant__ C
         for (int o = 0; o < kC; o++) v[o] = K > 0 ? __uint_as_float(r[o]) : 0.f;
         if (lq < 3) {
           const int tap = lq * 3 + tx, kin = lane;
-          float4* d4 = reinterpret_cast<float4*>(dst + (long long)(tap * kC + kin) * kC);
+          float4* d4 = reinterpret_cast<float4*>(dw + (long long)(tap * kC + kin) * kC);
 #pragma unroll
           for (int q4 = 0; q4 < 8; q4++)
             d4[q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
-        } else if (tx == 0 && lane == 0) {
+        } else if (tx == 0 && lane == 0 && (D == 2 || tz == 0)) {
 #pragma unroll
-          for (int o = 0; o < kC; o++) dst[9 * kC * kC + o] = v[o];
+          for (int o = 0; o < kC; o++) dst[T * kC * kC + o] = v[o];
         }
       }
     }
@@ -646,7 +662,8 @@ cudaError_t conv32_tc_setup() {
   if (g_tc_err) return cudaSuccess;
   set_tc_smem<2>();
   set_tc_smem<3>();
-  cudaFuncSetAttribute(wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+  cudaFuncSetAttribute(wgrad_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+  cudaFuncSetAttribute(wgrad_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
@@ -705,37 +722,48 @@ cudaError_t launch_conv32_tc(int dim, int mode, int B, int H, const __nv_bfloat1
   return cudaGetLastError();
 }
 
-// A tensor map over a channels-last 2D activation [B][H][H][32] (BF16): boxes of
-// 8 channels x kRows pixels of one row.
-static bool encode_rows_2d(CUtensorMap* tm, const __nv_bfloat16* p, int B, int H) {
+// A tensor map over a channels-last activation, [B][H][H][32] (2D) or
+// [B][H][H][H][32] (3D), BF16: boxes of 8 channels x kRows pixels of one row.
+static bool encode_rows(CUtensorMap* tm, const __nv_bfloat16* p, int dim, int B, int H) {
   const cuuint64_t row = (cuuint64_t)kC * 2;
   const cuuint64_t h = (cuuint64_t)H;
-  const cuuint64_t dims[4] = {(cuuint64_t)kC, h, h, (cuuint64_t)B};
-  const cuuint64_t strides[3] = {row, row * h, row * h * h};
-  const cuuint32_t box[4] = {8, (cuuint32_t)kRows, 1, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  return g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)p, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  const cuuint64_t dims[5] = {(cuuint64_t)kC, h, h, dim == 3 ? h : (cuuint64_t)B, (cuuint64_t)B};
+  const cuuint64_t strides[4] = {row, row * h, row * h * h, row * h * h * h};
+  const cuuint32_t box[5] = {8, (cuuint32_t)kRows, 1, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)(dim + 2), (void*)p, dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
 
-cudaError_t launch_wgrad_tc(int B, int H, const __nv_bfloat16* in, const __nv_bfloat16* g,
-                            int dil, float* part, int stride, int nparts, cudaStream_t s) {
+cudaError_t launch_wgrad_tc(int dim, int B, int H, const __nv_bfloat16* in,
+                            const __nv_bfloat16* g, int dil, float* part, int stride, int nparts,
+                            cudaStream_t s) {
   if (!g_tc_err) {
     const cudaError_t e = conv32_tc_setup();
     if (e != cudaSuccess) return e;
   }
-  if (dil < 1 || dil > 2 || nparts < 1 || stride < 9 * kC * kC + kC ||
-      ((unsigned long long)in & 15ull) || ((unsigned long long)g & 15ull) ||
-      ((unsigned long long)part & 15ull) || (stride & 3))
+  const int T = dim == 3 ? 27 : 9;
+  if ((dim != 2 && dim != 3) || dil < 1 || dil > 2 || nparts < 1 ||
+      stride < T * kC * kC + kC || ((unsigned long long)in & 15ull) ||
+      ((unsigned long long)g & 15ull) || ((unsigned long long)part & 15ull) || (stride & 3))
     return cudaErrorInvalidValue;
   CUtensorMap tin, tg;
-  if (!encode_rows_2d(&tin, in, B, H) || !encode_rows_2d(&tg, g, B, H))
+  if (!encode_rows(&tin, in, dim, B, H) || !encode_rows(&tg, g, dim, B, H))
     return cudaErrorInvalidValue;
-  // every one of the nparts CTAs writes its partial (zeros without tiles)
-  wgrad_tc<<<nparts, kTcThreads, kWgSmem, s>>>(tin, tg, B, H, dil, part, stride, g_tc_err);
-  note_launches(1);
+  // every one of the nparts CTAs writes its partial (zeros without tiles); in 3D
+  // one launch per plane offset tz of the taps
+  if (dim == 2) {
+    wgrad_tc<2><<<nparts, kTcThreads, kWgSmem, s>>>(tin, tg, B, H, dil, 1, part, stride,
+                                                     g_tc_err);
+    note_launches(1);
+  } else {
+    for (int tz = 0; tz < 3; tz++)
+      wgrad_tc<3><<<nparts, kTcThreads, kWgSmem, s>>>(tin, tg, B, H, dil, tz, part, stride,
+                                                       g_tc_err);
+    note_launches(3);
+  }
   return cudaGetLastError();
 }
 
