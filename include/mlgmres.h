@@ -75,7 +75,10 @@ enum {
 
 /* Problem geometry.  dim = 2 or 3; n = interior points per axis (square / cubic
  * grids); kappa_dev = n^3 cell coefficients (3D only; NULL = constant 1).  The
- * kappa array must stay valid for the handle's lifetime. */
+ * kappa array must stay valid for the handle's lifetime; it is read at the start
+ * of every solve (the FP32 cycles of a single solve use face coefficients formed
+ * from it then, the harmonic means in FP64 rounded once to FP32), so it may
+ * change between solves. */
 typedef struct {
   int dim;
   int n;
