@@ -62,7 +62,7 @@ def test_single_rank_is_identity():
 def test_roofline_bytes_follow_the_accounting():
     """The bench's byte counts against hand-worked values.  One cycle of k = 2
     Arnoldi steps on N points, FP32 (s = 4):
-    three-sweep CGS2 (SURVEY-style): steps j = 0, 1 move s N (3(j+1) + 7) = 10 s N
+    three-sweep CGS2 accounting: steps j = 0, 1 move s N (3(j+1) + 7) = 10 s N
     and 13 s N; x += V y adds (k s + 16) N = 24 N; the FP64 true residual 32 N.
     Two-pass: steps move s N (2j + 6) = 6 s N and 8 s N; x += V y s N k + 16 N;
     the restart 16 N + s N; the final residual check 16 N + s N."""

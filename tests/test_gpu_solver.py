@@ -179,6 +179,24 @@ def test_compact_variant_3d(m, stages):
     assert rel(x.cpu().numpy(), xr) <= 1e-7
 
 
+def test_kappa_changed_between_solves():
+    """kappa is read at the start of every solve: after the caller rewrites the
+    device array in place, the next FP32-refined solve (face coefficients formed
+    again) matches the oracle for the new coefficients."""
+    n = 20
+    k1 = lognormal_kappa(n, 5001, smooth_sigma=2.0).astype(np.float32)
+    k2 = lognormal_kappa(n, 5002, smooth_sigma=2.0).astype(np.float32)
+    b = MovingGaussians3D(n, 5001, 200).rhs(3)
+    s = Solver(n, dim=3, kappa=k1, m=40, rtol=1e-10, precision="fp32_refine")
+    x1, r1 = s.solve(dev(b))
+    xr1, _, _ = native.gmres(3, n, b, m=50, rtol=1e-13, kappa=k1.astype(np.float64))
+    assert r1["status"] == 0 and rel(x1.cpu().numpy(), xr1) <= 1e-7
+    s.kappa.copy_(torch.as_tensor(k2).cuda())
+    x2, r2 = s.solve(dev(b))
+    xr2, _, _ = native.gmres(3, n, b, m=50, rtol=1e-13, kappa=k2.astype(np.float64))
+    assert r2["status"] == 0 and rel(x2.cpu().numpy(), xr2) <= 1e-7
+
+
 def test_autotune_picks_the_fastest_candidate_and_caches():
     n = 512
     b = MovingGaussians2D(n, 2001, 500).rhs(2)
