@@ -33,6 +33,8 @@ struct mlgmres {
   float* faces = nullptr;    // FP32 face coefficients (single 3D FP32 solves with kappa)
   long long fstride = 0;     // their array stride
   double* part = nullptr;
+  double* Rg = nullptr;      // compact variants' triangles R (rg_blocks of them)
+  int rg_blocks = 0;
   unsigned long long* bar = nullptr;  // per group: counter
   int* err = nullptr;                 // per group: error flag
   mlg::DevResult* dres = nullptr;     // device results

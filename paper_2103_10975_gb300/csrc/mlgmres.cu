@@ -285,6 +285,7 @@ void run_solver(mlgmres* h, int ngroups, int ntasks, int grid, int arnoldi_steps
       kp.compact = 1;  // V slices in shared memory, two CTAs per SM
     }
   }
+  ARG(!kp.compact || (h->Rg && grid <= h->rg_blocks), "compact variant: grid exceeds its R workspace");
   // face coefficients from the current kappa (one pass over the grid)
   if (ntasks == 1 && h->htasks[0].faces)
     CK(launch_kappa_faces(h->grid.n, h->grid.kappa_dev, h->faces, h->fstride, s));
@@ -305,6 +306,7 @@ GroupWork single_group_work(mlgmres* h, int nblocks) {
   w.W1 = h->W1;
   w.part = h->part;
   w.pstride = kPartStride;
+  w.Rg = h->Rg;
   w.bar.ctr = h->bar;
   w.bar.err = h->err;
   // fault_inject = 1 makes the barrier wait for a CTA that is never launched
@@ -632,6 +634,12 @@ mlgmres_status mlgmres_create(const mlgmres_grid* grid, const mlgmres_options* o
     }
     CK(cudaMalloc(&h->W1, es * (size_t)h->ldv));
     CK(cudaMalloc(&h->part, sizeof(double) * part_doubles(kPartStride)));
+    if (opt->compact != 0 && gmres_compact_ok(h->fp32, grid->dim, opt->m)) {
+      // the compact variants keep each CTA's triangle R in HBM (L2-resident),
+      // which leaves room for a second bulk-copy stage per warp
+      h->rg_blocks = 2 * h->nsm;
+      CK(cudaMalloc(&h->Rg, sizeof(double) * kRgDoubles * (size_t)h->rg_blocks));
+    }
     h->group_cap = 1;
     h->cfg_cap = 1;
     if (opt->batch_slots > 0) {
@@ -705,6 +713,7 @@ void mlgmres_destroy(mlgmres_t h) {
   if (h->faces) cudaFree(h->faces - (h->fstride - h->ldv) / 2);
   cudaFree(h->W1);
   cudaFree(h->part);
+  cudaFree(h->Rg);
   cudaFree(h->bar);
   cudaFree(h->err);
   cudaFree(h->dres);
@@ -941,6 +950,7 @@ mlgmres_status mlgmres_solve_batch(mlgmres_t h, int count, const mlgmres_grid* g
       w.part = h->partb + part_off;
       part_off += part_doubles(gctas[g]);
       w.pstride = gctas[g];
+      w.Rg = h->Rg;
       w.bar.ctr = h->bar + g;
       w.bar.err = h->err + g;
       w.bar.nblocks = (unsigned)gctas[g];

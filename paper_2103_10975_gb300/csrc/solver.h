@@ -67,8 +67,13 @@ struct GroupWork {
   void* W1;
   double* part;       // 2 x (kMaxM+2) x pstride partial sums
   int pstride;        // row length of part (>= the group's CTA count)
+  double* Rg;         // compact variants: (m+1) x m FP64 triangle per CTA, indexed
+                      // by blockIdx.x (the others keep R in shared memory)
   GroupBarrier bar;
 };
+
+// Doubles of the per-CTA triangle R of the compact variants.
+constexpr long long kRgDoubles = (long long)(kCompactM3 + 1) * kCompactM3;
 
 struct KParams {
   int m;

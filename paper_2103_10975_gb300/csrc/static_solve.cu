@@ -112,6 +112,7 @@ extern "C" mlgmres_status mlgmres_solve_static(int n, int m, double rtol, long l
   w.W1 = W1;
   w.part = part;
   w.pstride = kPartStride;
+  w.Rg = nullptr;
   w.bar.ctr = bar;
   w.bar.err = err;
   w.bar.nblocks = (unsigned)blocks;
