@@ -351,7 +351,7 @@ mlgmres_status mlgmres_kernel_launches(long long* count);
  *   b_dev, x_dev:    caller-owned device arrays of n*n doubles (b input, x output).
  *   res:             may be NULL.
  * The first call on a device looks up the array's device address for that
- * device; make that first call before capturing a stream into a CUDA graph.
+ * device (and loads the module holding the array).
  * Every call uses the same array and it keeps the last call's contents (the
  * barrier state is cleared at the start of each call): calls that overlap on
  * the GPU -- from two streams or two threads -- race with each other and must
