@@ -16,6 +16,6 @@ int max_blocks_f2c(int* bs, int extra) {
   return max_blocks_t<float, 2, kCompactM2, 256, kVBulk, 2>(bs, extra);
 }
 
-int own_bytes_f2c() { return (int)smem_own_bytes<float, kCompactM2, 256, false>(); }
+int own_bytes_f2c() { return (int)smem_own_bytes<float, kCompactM2, 256>(); }
 
 }  // namespace mlg

@@ -16,6 +16,6 @@ int max_blocks_f3c(int* bs, int extra) {
   return max_blocks_t<float, 3, kCompactM3, 256, kVBulk, 2>(bs, extra);
 }
 
-int own_bytes_f3c() { return (int)smem_own_bytes<float, kCompactM3, 256, false>(); }
+int own_bytes_f3c() { return (int)smem_own_bytes<float, kCompactM3, 256>(); }
 
 }  // namespace mlg

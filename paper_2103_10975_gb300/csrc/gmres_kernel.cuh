@@ -151,15 +151,27 @@ __device__ __forceinline__ void store_vj(T* vc, int j, T vj) {
 // ----------------------------------------------------------- shared state --
 constexpr int kMaxStages = 16;  // bulk-copy stages per warp (upper bound)
 
+// Where the Givens triangle R ((MAXM + 1) x MAXM FP64) lives: in the shared
+// state, or, for the compact variants (two CTAs per SM, instantiated with the
+// bucket limits kCompactM2 / kCompactM3), in a global buffer with one region per
+// CTA of the launch, which leaves their warps room for a second bulk-copy stage
+// (R is written by the Givens warp once per step and read once per cycle).
+template <int MAXM>
+__host__ __device__ constexpr bool r_in_shared() {
+  return MAXM != kCompactM2 && MAXM != kCompactM3;
+}
+template <int MAXM>
+__host__ __device__ constexpr size_t r_doubles() { return (size_t)(MAXM + 1) * MAXM; }
+
 template <typename T, int MAXM, int BS>
 struct Smem {
   T red[BS / 32][MAXM + 2];      // per-warp partials in the working precision
   double redd[BS / 32][4];       // per-warp partials of the FP64 residual norms
   double tot[MAXM + 2];
   double hcol[MAXM + 2];         // the column being rotated, in FP64 (Givens warp)
-  // (R, the columns after the Givens rotations, each above the diagonal divided
-  // by its diagonal entry, (MAXM + 1) x MAXM FP64 with ld MAXM + 1, follows this
-  // state in shared memory, or lives in global memory per CTA: r_storage)
+  // the same columns after the Givens rotations, each above the diagonal divided
+  // by its diagonal entry; the compact variants keep them in global memory (Rg)
+  double R[r_in_shared<MAXM>() ? (MAXM + 1) * MAXM : 1];
   double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
   float2 yf[MAXM];               // y_k as hi + lo floats (FP32 variants' V y)
   double rinv[MAXM];             // 1 / R(c,c), formed with rotation c (the back-
@@ -182,24 +194,14 @@ struct Smem {
   // the staging buffers because a CTA's slice of V may occupy that space for
   // other systems of the same launch
   unsigned long long bbar[BS / 32][kMaxStages];
+  double* Rg;  // this CTA's R in global memory (the variants that keep it there)
 };
 
-// FP64 entries of R.
-template <int MAXM>
-__host__ __device__ constexpr size_t r_doubles() { return (size_t)(MAXM + 1) * MAXM; }
-// Where R lives: in shared memory after the state (RS), or in a global buffer,
-// one region per CTA of the launch.  The compact variants (two CTAs per SM) keep
-// it in global memory, which leaves their warps room for a second bulk-copy stage
-// (R is written by the Givens warp once per step and read once per cycle).
-template <int MINB>
-__host__ __device__ constexpr bool r_in_shared() { return MINB == 1; }
-
-// Shared state (with R when RS) rounded up to 128 bytes (the staging buffers
-// that follow it are bulk-copy destinations).
-template <typename T, int MAXM, int BS, bool RS = true>
+// Shared state rounded up to 128 bytes (the staging buffers that follow it are
+// bulk-copy destinations).
+template <typename T, int MAXM, int BS>
 __host__ __device__ constexpr size_t smem_own_bytes() {
-  return ((sizeof(Smem<T, MAXM, BS>) + 7) / 8 * 8 + (RS ? sizeof(double) * r_doubles<MAXM>() : 0) +
-          127) / 128 * 128;
+  return (sizeof(Smem<T, MAXM, BS>) + 127) / 128 * 128;
 }
 
 // Warp partial of slot k (lane 0 stores it); block_finish then adds the warp
@@ -421,14 +423,14 @@ __device__ __forceinline__ double df_value(float s0, float c0, float s1, float c
 // steps per round instead of one FMA per rotation (an FP64 operation has a
 // latency of about 70 cycles on this GPU).
 template <typename T, int MAXM, int BS>
-__device__ int givens_column(Smem<T, MAXM, BS>& sm, double* R, int c, double rtol_bnorm,
-                             long long it, long long max_iters, int m, double* hist,
-                             long long hist_cap, double bnorm) {
+__device__ int givens_column(Smem<T, MAXM, BS>& sm, int c, double rtol_bnorm, long long it,
+                             long long max_iters, int m, double* hist, long long hist_cap,
+                             double bnorm) {
   constexpr int LD = MAXM + 1;
   constexpr unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   double* hc = sm.hcol;
-  double* rc = R + c * LD;
+  double* rc = (r_in_shared<MAXM>() ? sm.R : sm.Rg) + c * LD;
   // column c in FP64: h1 + h2 (exact sum of two FP32 values) and hn below
   for (int i = lane; i <= c + 1; i += 32)
     hc[i] = i <= c ? (double)sm.h1c[i] + (double)sm.h2h[i] : (double)sm.HuT[c + 1 + c * LD];
@@ -1377,7 +1379,7 @@ __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
 // explicit pass applies h2 and measures the norm instead.  The Givens update
 // of column j runs on thread 0 while the CTA already starts the next X pass;
 // if it ends the cycle, that speculative pass is discarded.
-template <typename T, int DIM, int MAXM, int BS, int VM, bool RS>
+template <typename T, int DIM, int MAXM, int BS, int VM>
 __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWork& w, int lb,
                           int nb, unsigned long long& epoch, unsigned& bphase,
                           Smem<T, MAXM, BS>& sm) {
@@ -1402,19 +1404,14 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
   const bool vshared = VM == kVShared;
   T* __restrict__ Vg = (T*)w.V;
   T* __restrict__ Vs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(&sm) +
-                                            smem_own_bytes<T, MAXM, BS, RS>());
-  // R: after the shared state, or this CTA's region of the global buffer
-  double* __restrict__ Rb =
-      RS ? reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(&sm) +
-                                     (sizeof(Smem<T, MAXM, BS>) + 7) / 8 * 8)
-         : w.Rg + (size_t)blockIdx.x * r_doubles<MAXM>();
+                                            smem_own_bytes<T, MAXM, BS>());
   T* __restrict__ V = vshared ? Vs : Vg;  // cycle-end and fallback passes
   const int voff = vshared ? lo : 0;
   // bulk-copy staging of V (FP32, V in HBM): stages follow the shared state
   const bool bulk = VM == kVBulk;
   (void)bulk;
   BulkPipe pipe;
-  pipe.stage = reinterpret_cast<unsigned char*>(&sm) + smem_own_bytes<T, MAXM, BS, RS>();
+  pipe.stage = reinterpret_cast<unsigned char*>(&sm) + smem_own_bytes<T, MAXM, BS>();
   pipe.P = kp.bulk_stages;
   pipe.cap = kp.bulk_cap;
   pipe.bar = &sm.bbar[0][0];
@@ -1586,7 +1583,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
         if (arnoldi && j == jmax) { kcols = j; break; }
         auto givens_prev = [&]() {
           if (j > 0 && !arnoldi)
-            givens_column<T, MAXM, BS>(sm, Rb, j - 1, rtol_bnorm, iters, kp.max_iters, m, hist,
+            givens_column<T, MAXM, BS>(sm, j - 1, rtol_bnorm, iters, kp.max_iters, m, hist,
                                        tk.hist_cap, bnorm);
         };
         // the Givens rotation of column j-1 (warp 1) overlaps the barrier and
@@ -1733,7 +1730,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
       if (!arnoldi && j + 1 >= m) {
         // last column of the cycle: rotate it now (no further X pass)
         if (tid < 32)
-          givens_column<T, MAXM, BS>(sm, Rb, j, rtol_bnorm, iters, kp.max_iters, m, hist,
+          givens_column<T, MAXM, BS>(sm, j, rtol_bnorm, iters, kp.max_iters, m, hist,
                                      tk.hist_cap, bnorm);
         __syncthreads();
         if (sm.stop == 2) { status = kErrNonfinite; goto finish; }
@@ -1766,7 +1763,7 @@ __device__ void solve_one(const KParams& kp, const SolveTask& tk, const GroupWor
 #pragma unroll
         for (int r = 0; r < UR; r++) {
           const int l = lane + 32 * r;
-          if (l < i) u[r] = fma(-Rb[l + i * LD], ui, u[r]);
+          if (l < i) u[r] = fma(-(r_in_shared<MAXM>() ? sm.R : sm.Rg)[l + i * LD], ui, u[r]);
         }
       }
 #pragma unroll
@@ -1880,6 +1877,9 @@ __global__ void __launch_bounds__(BS, MINB) gmres_persistent(KParams kp) {
   const GroupWork w = kp.work[g];
   unsigned long long epoch = 0;
   unsigned bphase = 0;  // parity of each bulk-copy stage of this thread's warp
+  static_assert(r_in_shared<MAXM>() == (MINB == 1), "R placement follows the variant");
+  if (!r_in_shared<MAXM>() && threadIdx.x == 0)
+    sm.Rg = w.Rg + (size_t)blockIdx.x * r_doubles<MAXM>();
   if (VM == kVBulk) {
     for (int i = threadIdx.x; i < (BS / 32) * kMaxStages; i += BS)
       mbar_init(&sm.bbar[0][0] + i, 1);
@@ -1888,7 +1888,7 @@ __global__ void __launch_bounds__(BS, MINB) gmres_persistent(KParams kp) {
   }
   for (int t = kp.task_first[g]; t < kp.task_first[g + 1]; t++) {
     const SolveTask tk = kp.tasks[kp.task_order[t]];
-    solve_one<T, DIM, MAXM, BS, VM, r_in_shared<MINB>()>(kp, tk, w, lb, nb, epoch, bphase, sm);
+    solve_one<T, DIM, MAXM, BS, VM>(kp, tk, w, lb, nb, epoch, bphase, sm);
     if (*(volatile int*)w.bar.err != kErrNone) break;
     // all CTAs finish with this task's data before the next task starts
     if (!group_sync(w.bar, epoch, &sm.flag)) break;
@@ -1903,7 +1903,7 @@ template <typename T, int DIM, int MAXM, int BS, int VM, int MINB = 1>
 cudaError_t prepare_t(int extra = 0) {
   return cudaFuncSetAttribute(gmres_persistent<T, DIM, MAXM, BS, VM, MINB>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_own_bytes<T, MAXM, BS, r_in_shared<MINB>()>() + extra);
+                              (int)smem_own_bytes<T, MAXM, BS>() + extra);
 }
 
 template <typename T, int DIM, int MAXM, int BS, int VM, int MINB = 1>
@@ -1918,7 +1918,7 @@ cudaError_t launch_t(const KParams& kp, int grid, cudaStream_t s) {
   note_launches(1);
   return cudaLaunchCooperativeKernel((const void*)gmres_persistent<T, DIM, MAXM, BS, VM, MINB>,
                                      dim3(grid), dim3(BS), args,
-                                     smem_own_bytes<T, MAXM, BS, r_in_shared<MINB>()>() + extra,
+                                     smem_own_bytes<T, MAXM, BS>() + extra,
                                      s);
 }
 
@@ -1932,7 +1932,7 @@ int max_blocks_t(int* bs, int extra = 0) {
   if (prepare_t<T, DIM, MAXM, BS, VM, MINB>(extra) != cudaSuccess) return 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gmres_persistent<T, DIM, MAXM, BS, VM, MINB>,
                                                 BS,
-                                                smem_own_bytes<T, MAXM, BS, r_in_shared<MINB>()>() +
+                                                smem_own_bytes<T, MAXM, BS>() +
                                                     extra);
   *bs = BS;
   return per * nsm;
