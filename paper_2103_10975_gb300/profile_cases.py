@@ -4,7 +4,7 @@
     python -m paper_2103_10975_gb300.profile_cases nn --n 256 --batch 8
     python -m paper_2103_10975_gb300.profile_cases batch --count 512 --nmax 512
     python -m paper_2103_10975_gb300.profile_cases cube --n 192 --max-iters 500
-    python -m paper_2103_10975_gb300.profile_cases cube --n 192 --compact 1 --blocks 304 --stages 4
+    python -m paper_2103_10975_gb300.profile_cases cube --n 192 --compact 1 --blocks 304 --stages 2
 
     python -m paper_2103_10975_gb300.profile_cases dipole --n 64 --T 200
     python -m paper_2103_10975_gb300.profile_cases floor --ctas 128 --m 30
