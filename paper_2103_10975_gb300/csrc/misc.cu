@@ -47,9 +47,11 @@ __global__ void denormalise_kernel(const float* __restrict__ y, int N, const dou
 }
 
 // One damped-Jacobi sweep on the 2D operator: out = in + omega/d (b - A in),
-// d = 4/h^2 the diagonal of A.
+// d = 4/h^2 the diagonal of A.  s2 = 1/h^2 and f = omega/(4 s2) come from the
+// host (the same IEEE divisions, once per launch instead of three FP64
+// divisions per point on a GPU whose FP64 pipe is narrow).
 __global__ void jacobi_kernel(int n, const double* __restrict__ b, const double* __restrict__ xin,
-                              double* __restrict__ xout, double omega) {
+                              double* __restrict__ xout, double s2, double f) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * n) return;
   const int ix = i % n, iy = i / n;
@@ -58,18 +60,16 @@ __global__ void jacobi_kernel(int n, const double* __restrict__ b, const double*
   const double r = ix < n - 1 ? xin[i + 1] : 0.0;
   const double d = iy > 0 ? xin[i - n] : 0.0;
   const double t = iy < n - 1 ? xin[i + n] : 0.0;
-  const double h = 2.0 / (n + 1);
-  const double s2 = 1.0 / (h * h);
   const double ax = s2 * (((c - l) + (c - r)) + ((c - d) + (c - t)));
-  xout[i] = c + omega / (4.0 * s2) * (b[i] - ax);
+  xout[i] = c + f * (b[i] - ax);
 }
 
 // 3D: A u = (1/h^2) sum_faces k_f (u_c - u_nb), k_f the harmonic mean of the
 // two cells' kappa (kappa_c on a wall face, u = 0 beyond it; kappa = NULL
-// means 1); the diagonal is (1/h^2) sum_faces k_f.
+// means 1); the diagonal is (1/h^2) sum_faces k_f.  s2 = 1/h^2 from the host.
 __global__ void jacobi3d_kernel(int n, const float* __restrict__ kappa,
                                 const double* __restrict__ b, const double* __restrict__ xin,
-                                double* __restrict__ xout, double omega) {
+                                double* __restrict__ xout, double omega, double s2) {
   const long long N = (long long)n * n * n;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -90,8 +90,6 @@ __global__ void jacobi3d_kernel(int n, const float* __restrict__ kappa,
     au += kf * (c - unb);
     diag += kf;
   }
-  const double h = 2.0 / (n + 1);
-  const double s2 = 1.0 / (h * h);
   xout[i] = c + omega * (b[i] - s2 * au) / (s2 * diag);
 }
 
@@ -162,10 +160,12 @@ cudaError_t launch_normalise(const double* b, int N, const double* sumsq, float*
 }
 cudaError_t launch_jacobi(int dim, int n, const float* kappa, const double* b, const double* xin,
                           double* xout, double omega, cudaStream_t s) {
+  const double h = 2.0 / (n + 1);
+  const double s2 = 1.0 / (h * h);
   if (dim == 3)
-    jacobi3d_kernel<<<blocks_for(n * n * n), 256, 0, s>>>(n, kappa, b, xin, xout, omega);
+    jacobi3d_kernel<<<blocks_for(n * n * n), 256, 0, s>>>(n, kappa, b, xin, xout, omega, s2);
   else
-    jacobi_kernel<<<blocks_for(n * n), 256, 0, s>>>(n, b, xin, xout, omega);
+    jacobi_kernel<<<blocks_for(n * n), 256, 0, s>>>(n, b, xin, xout, s2, omega / (4.0 * s2));
   note_launches(1);
   return cudaGetLastError();
 }
