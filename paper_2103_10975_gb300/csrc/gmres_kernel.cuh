@@ -726,20 +726,43 @@ __device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
 
 // X pass: (sum_{k<j} h2_k v_k, sum_{k<j} c_k v_k) over the pairs that hold
 // vectors 0..j-1 (for odd j the last one also holds the zero slot of v_j).
-template <typename T, int MAXM, int BS, int K>
+// W4: FP32 coefficients by 16-byte loads (faster in the shared-slice and 3D
+// passes; the 2D bulk-copy pass runs 0.5% faster with 8-byte loads).
+template <typename T, int MAXM, int BS, int K, bool W4 = true>
 __device__ __forceinline__ void x_proj(const Smem<T, MAXM, BS>& sm, const T* vc, int j, T& sv,
                                        T& sz) {
   using T2 = typename Vec2<T>::type;
-  const T2* h2 = reinterpret_cast<const T2*>(sm.h2v);
-  const T2* cc = reinterpret_cast<const T2*>(sm.cv);
   const int np = (j + 1) >> 1;
   T2 av = dup2<T2>(T(0)), az = dup2<T2>(T(0));
+  if constexpr (sizeof(T) == 4 && W4) {
+    // FP32: the coefficients of pairs 2p and 2p+1 in one 16-byte load each,
+    // issued for the whole bucket (h2v and cv are initialised to their end);
+    // only the V loads and the FMAs depend on j, in the same order as below
+    float4 h[K / 4], c[K / 4];
 #pragma unroll
-  for (int q = 0; q < K / 2; q++) {
-    if (q < np) {
-      const T2 v = *reinterpret_cast<const T2*>(vc + (q << 6));
-      av = fma2(h2[q], v, av);
-      az = fma2(cc[q], v, az);
+    for (int p = 0; p < K / 4; p++) {
+      h[p] = reinterpret_cast<const float4*>(sm.h2v)[p];
+      c[p] = reinterpret_cast<const float4*>(sm.cv)[p];
+    }
+#pragma unroll
+    for (int q = 0; q < K / 2; q++) {
+      if (q < np) {
+        const T2 v = *reinterpret_cast<const T2*>(vc + (q << 6));
+        const float4 hq = h[q >> 1], cq = c[q >> 1];
+        av = fma2((q & 1) ? make_float2(hq.z, hq.w) : make_float2(hq.x, hq.y), v, av);
+        az = fma2((q & 1) ? make_float2(cq.z, cq.w) : make_float2(cq.x, cq.y), v, az);
+      }
+    }
+  } else {
+    const T2* h2 = reinterpret_cast<const T2*>(sm.h2v);
+    const T2* cc = reinterpret_cast<const T2*>(sm.cv);
+#pragma unroll
+    for (int q = 0; q < K / 2; q++) {
+      if (q < np) {
+        const T2 v = *reinterpret_cast<const T2*>(vc + (q << 6));
+        av = fma2(h2[q], v, av);
+        az = fma2(cc[q], v, az);
+      }
     }
   }
   sv = av.x + av.y;
@@ -761,15 +784,30 @@ __device__ __forceinline__ void x_dots(typename Vec2<T>::type (&acc)[K / 2], con
 
 // Y pass: sum_{k<=j} h1_k v_k (h1 in sm.coef; for even j the last pair's
 // second value is the zero slot of v_{j+1}).
-template <typename T, int MAXM, int BS, int K>
+template <typename T, int MAXM, int BS, int K, bool W4 = true>
 __device__ __forceinline__ T y_proj(const Smem<T, MAXM, BS>& sm, const T* vc, int j) {
   using T2 = typename Vec2<T>::type;
-  const T2* h1 = reinterpret_cast<const T2*>(sm.coef);
   const int np = (j >> 1) + 1;
   T2 a = dup2<T2>(T(0));
+  if constexpr (sizeof(T) == 4 && W4) {
+    // FP32: h1 of pairs 2p and 2p+1 in one 16-byte load (as in x_proj)
+    float4 h[K / 4];
 #pragma unroll
-  for (int q = 0; q < K / 2; q++)
-    if (q < np) a = fma2(h1[q], *reinterpret_cast<const T2*>(vc + (q << 6)), a);
+    for (int p = 0; p < K / 4; p++) h[p] = reinterpret_cast<const float4*>(sm.coef)[p];
+#pragma unroll
+    for (int q = 0; q < K / 2; q++) {
+      if (q < np) {
+        const float4 hq = h[q >> 1];
+        a = fma2((q & 1) ? make_float2(hq.z, hq.w) : make_float2(hq.x, hq.y),
+                 *reinterpret_cast<const T2*>(vc + (q << 6)), a);
+      }
+    }
+  } else {
+    const T2* h1 = reinterpret_cast<const T2*>(sm.coef);
+#pragma unroll
+    for (int q = 0; q < K / 2; q++)
+      if (q < np) a = fma2(h1[q], *reinterpret_cast<const T2*>(vc + (q << 6)), a);
+  }
   return a.x + a.y;
 }
 
@@ -1279,7 +1317,7 @@ __device__ __forceinline__ void x_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
       }
     }
     T sv = T(0), sz = T(0);
-    if (ok) x_proj<T, MAXM, BS, K>(sm, sc, j, sv, sz);
+    if (ok) x_proj<T, MAXM, BS, K, DIM == 3>(sm, sc, j, sv, sz);
     const T vj = (wp - sv) * inv;
     const T z = ((znum - sz) - cj * vj) * inv;
     if (ok) {
@@ -1337,7 +1375,8 @@ __device__ __forceinline__ void y_pass_bulk(Smem<T, MAXM, BS>& sm, int lo, int h
     const unsigned char* stb = r.st + (size_t)sidx * r.bytes;
     const T* sc = reinterpret_cast<const T*>(stb) + 2 * lane;  // the lane's column (pair layout)
     if (ok) {
-      const T qv = reinterpret_cast<const T*>(stb + r.vbytes)[lane] - y_proj<T, MAXM, BS, K>(sm, sc, j);
+      const T qv = reinterpret_cast<const T*>(stb + r.vbytes)[lane] -
+                   y_proj<T, MAXM, BS, K, DIM == 3>(sm, sc, j);
       WP[i] = qv;
       accN += qv * qv;
       y_dots<T, K>(acc, sc, j, qv);
