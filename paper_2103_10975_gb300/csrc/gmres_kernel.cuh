@@ -157,9 +157,11 @@ constexpr int kMaxStages = 16;  // bulk-copy stages per warp (upper bound)
 // CTA of the launch, which leaves their warps room for a second bulk-copy stage
 // (R is written by the Givens warp once per step and read once per cycle).
 template <int MAXM>
-__host__ __device__ constexpr bool r_in_shared() {
-  return MAXM != kCompactM2 && MAXM != kCompactM3;
+__host__ __device__ constexpr bool compact_bucket() {
+  return MAXM == kCompactM2 || MAXM == kCompactM3;
 }
+template <int MAXM>
+__host__ __device__ constexpr bool r_in_shared() { return !compact_bucket<MAXM>(); }
 template <int MAXM>
 __host__ __device__ constexpr size_t r_doubles() { return (size_t)(MAXM + 1) * MAXM; }
 
@@ -726,8 +728,9 @@ __device__ __forceinline__ void y_pass(Smem<T, MAXM, BS>& sm, int lo, int hi, in
 
 // X pass: (sum_{k<j} h2_k v_k, sum_{k<j} c_k v_k) over the pairs that hold
 // vectors 0..j-1 (for odd j the last one also holds the zero slot of v_j).
-// W4: FP32 coefficients by 16-byte loads (faster in the shared-slice and 3D
-// passes; the 2D bulk-copy pass runs 0.5% faster with 8-byte loads).
+// W4: FP32 coefficients by 16-byte loads (faster in the one-CTA-per-SM
+// shared-slice passes and the 3D passes; the 2D bulk-copy pass runs 0.5% faster
+// with 8-byte loads, and the compact shared-slice variant spills with them).
 template <typename T, int MAXM, int BS, int K, bool W4 = true>
 __device__ __forceinline__ void x_proj(const Smem<T, MAXM, BS>& sm, const T* vc, int j, T& sv,
                                        T& sz) {
@@ -903,7 +906,7 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
     }
     const T* vc = Vs + vbase(i - lo, rows);
     T sv, sz;
-    x_proj<T, MAXM, BS, K>(sm, vc, j, sv, sz);
+    x_proj<T, MAXM, BS, K, !compact_bucket<MAXM>()>(sm, vc, j, sv, sz);
     const T vj = (wp - sv) * inv;
     const T z = ((znum - sz) - cj * vj) * inv;
     store_vj(Vs + vbase(i - lo, rows), j, vj);
@@ -935,7 +938,7 @@ __device__ __forceinline__ void y_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
     // z of the thread's first two points is in cy (the X pass kept it)
     const T q = t == 0 ? cy.z[0] : (t == 1 ? cy.z[1] : Z[i]);
     const T* vc = Vs + vbase(i - lo, rows);
-    const T qv = q - y_proj<T, MAXM, BS, K>(sm, vc, j);
+    const T qv = q - y_proj<T, MAXM, BS, K, !compact_bucket<MAXM>()>(sm, vc, j);
     WP[i] = qv;
     accN += qv * qv;
     y_dots<T, K>(acc, vc, j, qv);
