@@ -52,16 +52,16 @@ LEARN = dict(train_iters=64, lr=2e-3, batch=8, guess_smooth=32, overlap_train=1)
 METRIC = "time-to-solution per time step (ms) and GMRES iters, learned vs plain GMRES, rel res 1e-10"
 # DRAM bytes per Arnoldi step of gmres_persistent<float, 2, 32, 256, shared V>
 # on this workload, from one ncu capture of a 300-step solve of the kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum = 1.193 MB + 0.024 MB); scaled
+# (dram__bytes_read.sum + dram__bytes_write.sum = 1.190 MB + 0.022 MB); scaled
 # to a launch by its steps.
-DRAM_BYTES_PER_STEP = 1.217e6 / 300
+DRAM_BYTES_PER_STEP = 1.212e6 / 300
 # the same for the compact bulk-copy variant at 2048^2, GMRES(40) (304 CTAs, two
 # stages): 58.91 GB + 5.31 GB over an 80-step (two-cycle) capture
 DRAM_BYTES_PER_STEP_2048 = 64.22e9 / 80
 # and for the 192^3 variable-kappa kernel, GMRES(50), in the shape the autotuner
-# picks (the compact variant, 304 CTAs, two stages): 172.99 GB + 11.54 GB over a
+# picks (the compact variant, 304 CTAs, two stages): 172.99 GB + 11.53 GB over a
 # 100-step (two-cycle) capture
-DRAM_BYTES_PER_STEP_3D = 184.53e9 / 100
+DRAM_BYTES_PER_STEP_3D = 184.52e9 / 100
 WORKLOAD = ("2D Poisson -Lap u = f, 256x256 interior (N=65,536), zero Dirichlet, 5-point; "
             "3 moving signed Gaussians (sigma 0.1), 500-step series seed 2001; GMRES(30) "
             "rel tol 1e-10 (true FP64 residual)")
