@@ -19,8 +19,11 @@ steps (data collection and the first training, Sec. 2.3) untimed.
 The same line carries, as sub-objects, the other workloads on one GPU: a
 capped 2048^2 solve for the HBM roofline (`roofline_hbm`), full time steps of
 the 2048^2 refinement workload with the error against the DST-I solution
-(`c3_full_steps`, --c3-steps, 1 by default) and the 512-instance batched
-workload in one persistent launch (`c4_batch`, --no-batch to skip).
+(`c3_full_steps`, --c3-steps, 1 by default), the 512-instance batched
+workload in one persistent launch (`c4_batch`, --no-batch to skip), a capped
+192^3 variable-kappa solve (`roofline_3d`) and full time steps of that
+workload certified by the true FP64 residual (`c5_full_steps`, --c5-steps, 1
+by default).
 """
 
 import argparse
@@ -85,9 +88,9 @@ def parse():
                     help="full time steps of the 2048^2 workload to time (0 = none; single GPU)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 512-instance batched workload (single GPU)")
-    ap.add_argument("--c5-steps", type=int, default=0,
+    ap.add_argument("--c5-steps", type=int, default=1,
                     help="full time steps of the 192^3 variable-kappa workload to time "
-                         "(0 = none; about a minute each)")
+                         "(0 = none; 35-45 s each; single GPU)")
     ap.add_argument("--grid-blocks", type=int, default=0,
                     help="CTAs of the headline solver (0 = autotuned); fixes its launch "
                          "shape, e.g. for a profiler run whose timings would steer the autotuner")
