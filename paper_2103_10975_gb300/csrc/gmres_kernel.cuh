@@ -932,13 +932,36 @@ __device__ __forceinline__ void y_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
 #pragma unroll
   for (int q = 0; q < K / 2; q++) acc[q] = dup2<T2>(T(0));
   T accN = T(0);
+  // FP32, one CTA per SM: h1 in registers for all of the thread's points (one
+  // set of 16-byte loads per pass instead of one per point)
+  constexpr bool hreg = sizeof(T) == 4 && !compact_bucket<MAXM>();
+  float4 h1r[hreg ? K / 4 : 1];
+  if constexpr (hreg) {
+#pragma unroll
+    for (int p = 0; p < K / 4; p++) h1r[p] = reinterpret_cast<const float4*>(sm.coef)[p];
+  }
   int t = 0;
 #pragma unroll 1
   for (int i = lo + tid; i < hi; i += BS, t++) {
     // z of the thread's first two points is in cy (the X pass kept it)
     const T q = t == 0 ? cy.z[0] : (t == 1 ? cy.z[1] : Z[i]);
     const T* vc = Vs + vbase(i - lo, rows);
-    const T qv = q - y_proj<T, MAXM, BS, K, !compact_bucket<MAXM>()>(sm, vc, j);
+    T qv;
+    if constexpr (hreg) {
+      const int np = (j >> 1) + 1;
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int qq = 0; qq < K / 2; qq++) {
+        if (qq < np) {
+          const float4 hq = h1r[qq >> 1];
+          a = fma2((qq & 1) ? make_float2(hq.z, hq.w) : make_float2(hq.x, hq.y),
+                   *reinterpret_cast<const float2*>(vc + (qq << 6)), a);
+        }
+      }
+      qv = q - (a.x + a.y);
+    } else {
+      qv = q - y_proj<T, MAXM, BS, K, !compact_bucket<MAXM>()>(sm, vc, j);
+    }
     WP[i] = qv;
     accN += qv * qv;
     y_dots<T, K>(acc, vc, j, qv);
