@@ -886,6 +886,17 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
   T accZ = T(0);
   const T inv = sm.invT;
   const T cj = sm.cv[j];
+  // FP32, m <= 32: h2 and c in registers for all of the thread's points (at
+  // larger bucket limits they spill)
+  constexpr bool creg = sizeof(T) == 4 && MAXM <= kSmallM;
+  float4 h2r[creg ? K / 4 : 1], ccr[creg ? K / 4 : 1];
+  if constexpr (creg) {
+#pragma unroll
+    for (int p = 0; p < K / 4; p++) {
+      h2r[p] = reinterpret_cast<const float4*>(sm.h2v)[p];
+      ccr[p] = reinterpret_cast<const float4*>(sm.cv)[p];
+    }
+  }
   // one point per trip, the loop not unrolled: the body sits in the
   // instruction stream once (the step's code is what bounds it at this size)
   int t = 0;
@@ -906,7 +917,23 @@ __device__ __forceinline__ void x_pass_sm(Smem<T, MAXM, BS>& sm, int lo, int hi,
     }
     const T* vc = Vs + vbase(i - lo, rows);
     T sv, sz;
-    x_proj<T, MAXM, BS, K, !compact_bucket<MAXM>()>(sm, vc, j, sv, sz);
+    if constexpr (creg) {
+      const int np = (j + 1) >> 1;
+      float2 av = make_float2(0.f, 0.f), az = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < K / 2; q++) {
+        if (q < np) {
+          const float2 v = *reinterpret_cast<const float2*>(vc + (q << 6));
+          const float4 hq = h2r[q >> 1], cq = ccr[q >> 1];
+          av = fma2((q & 1) ? make_float2(hq.z, hq.w) : make_float2(hq.x, hq.y), v, av);
+          az = fma2((q & 1) ? make_float2(cq.z, cq.w) : make_float2(cq.x, cq.y), v, az);
+        }
+      }
+      sv = av.x + av.y;
+      sz = az.x + az.y;
+    } else {
+      x_proj<T, MAXM, BS, K, !compact_bucket<MAXM>()>(sm, vc, j, sv, sz);
+    }
     const T vj = (wp - sv) * inv;
     const T z = ((znum - sz) - cj * vj) * inv;
     store_vj(Vs + vbase(i - lo, rows), j, vj);
