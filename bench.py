@@ -55,9 +55,9 @@ LEARN = dict(train_iters=64, lr=2e-3, batch=8, guess_smooth=32, overlap_train=1)
 METRIC = "time-to-solution per time step (ms) and GMRES iters, learned vs plain GMRES, rel res 1e-10"
 # DRAM bytes per Arnoldi step of gmres_persistent<float, 2, 32, 256, shared V>
 # on this workload, from one ncu capture of a 300-step solve of the kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum = 1.190 MB + 0.022 MB); scaled
+# (dram__bytes_read.sum + dram__bytes_write.sum = 1.191 MB + 0.022 MB); scaled
 # to a launch by its steps.
-DRAM_BYTES_PER_STEP = 1.212e6 / 300
+DRAM_BYTES_PER_STEP = 1.213e6 / 300
 # the same for the compact bulk-copy variant at 2048^2, GMRES(40) (304 CTAs, two
 # stages): 58.91 GB + 5.31 GB over an 80-step (two-cycle) capture
 DRAM_BYTES_PER_STEP_2048 = 64.22e9 / 80
