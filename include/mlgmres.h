@@ -147,7 +147,7 @@ typedef struct {
                                 (1 - grow_tol) times its value at the previous phase */
   int compact;               /* the two-CTAs-per-SM variants (at most 128 registers, smaller
                                 shared state) for FP32 grids: 2D with m <= 47 (V slices in
-                                shared memory when they fit, else streamed), 3D with m <= 44
+                                shared memory when they fit, else streamed), 3D with m <= 55
                                 (streamed): -1 = if the autotuner chose it, 0 = never, 1 =
                                 always (where it applies) */
   int model;                 /* MLGMRES_MODEL_CONV: the multi-scale network of Sec. 2.1;

@@ -52,7 +52,7 @@ int gmres_compact_cap(int dim, int m, int P) {
 }
 
 bool gmres_compact_ok(bool fp32, int dim, int m) {
-  // and one stage of m rows must fit in a warp's share (3D: m <= 44 on GB300)
+  // and one stage of m rows must fit in a warp's share (m <= 55 in 3D on GB300)
   return fp32 && (dim == 2 ? m < kCompactM2 : m < kCompactM3) && gmres_compact_cap(dim, m, 1) > 0;
 }
 

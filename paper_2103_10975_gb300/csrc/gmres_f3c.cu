@@ -1,9 +1,9 @@
 // The compact variant for the 3D variable-coefficient operator: FP32 inner
 // precision, V streamed through bulk-copy stages, two co-resident CTAs per
 // SM (at most 128 registers per thread); restart lengths up to the bucket
-// limit 55 whose stage of m rows fits next to the larger 3D shared state
-// (m <= 44 on GB300).  Compiled
-// on its own so the variants build in parallel.
+// limit 55 whose stage of m rows fits next to the 3D shared state (all of
+// them on GB300, the triangle R being in global memory).  Compiled on its own
+// so the variants build in parallel.
 #include "gmres_kernel.cuh"
 
 namespace mlg {

@@ -162,12 +162,12 @@ def test_compact_variant(n, blocks):
     assert abs(r["iters"] - r0["iters"]) <= max(3, r0["iters"] // 100), (r["iters"], r0["iters"])
 
 
-@pytest.mark.parametrize("m,stages", [(40, -1), (50, 4)])
+@pytest.mark.parametrize("m,stages", [(40, -1), (50, 4), (50, 2), (55, -1)])
 def test_compact_variant_3d(m, stages):
-    """The 3D compact variant (two CTAs per SM; GMRES(50) with four stages per
-    warp is the shape the autotuner picks at 192^3) on variable kappa, through
-    the face-coefficient stencil and its zero-padded windows, against the
-    oracle's solution."""
+    """The 3D compact variant (two CTAs per SM; GMRES(50) with two stages per
+    warp is the shape the autotuner picks at 192^3; m = 55 is its bucket limit)
+    on variable kappa, through the face-coefficient stencil and its zero-padded
+    windows, against the oracle's solution."""
     n = 24
     kap = lognormal_kappa(n, 5001, smooth_sigma=2.0).astype(np.float32)
     b = MovingGaussians3D(n, 5001, 200).rhs(7)
